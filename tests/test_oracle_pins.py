@@ -1,0 +1,656 @@
+"""Pins for the CPU oracle: each test checks it against something other than itself --
+values the paper prints, closed forms, textbook facts of discrete Morse theory, brute
+force on tiny inputs, or hand-built fields whose expected edit follows from the paper's
+case descriptions (Sec. 4.3 / 4.4)."""
+import itertools
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2409_17346_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------------------
+# helpers written from the definitions, independent of the oracle's C code
+# --------------------------------------------------------------------------------------
+
+def _coords(v, nx, ny):
+    return v % nx, (v // nx) % ny, v // (nx * ny)
+
+
+def _adj(u, v, nx, ny):
+    a = np.array(_coords(u, nx, ny))
+    b = np.array(_coords(v, nx, ny))
+    d = b - a
+    return u != v and (np.all((d >= 0) & (d <= 1)) or np.all((d <= 0) & (d >= -1)))
+
+
+def _rows_to_sets(rows):
+    return {tuple(int(x) for x in r if x >= 0) for r in rows}
+
+
+def _pairs_dict(field):
+    """cell (tuple of ids) -> partner (tuple), from the oracle's pair list"""
+    d = {}
+    for r in oracle.gradient_pairs(field):
+        L = tuple(int(x) for x in r[:4] if x >= 0)
+        U = tuple(int(x) for x in r[4:] if x >= 0)
+        d[L] = U
+        d[U] = L
+    return d
+
+
+def _crit_counts(field, dim):
+    _, d = oracle.critical_cells(field)
+    return np.bincount(d, minlength=dim + 1)
+
+
+# --------------------------------------------------------------------------------------
+# worked example (Sec. 3.1, Fig. 3)
+# --------------------------------------------------------------------------------------
+
+def _read_golden(name):
+    vals, pairs, crit = {}, [], []
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.split("#")[0].strip()
+            if not line:
+                continue
+            tok = line.split()
+            if tok[0] == "pair_f":
+                pairs.append((tok[1], tok[2]))
+            elif tok[0] == "critical_fhat":
+                crit.append(tok[1])
+            else:
+                vals[tok[0]] = (float(tok[1]), float(tok[2]))
+    return vals, pairs, crit
+
+
+def test_worked_example_sec3_1():
+    vals, pairs, crit = _read_golden("worked_example_sec3_1.txt")
+    # embed triangle ijk as triangle {0,1,3} of a 2x2 grid; vertex 2 is far above
+    ids = {"k": 0, "j": 1, "i": 3}
+    f = np.full(4, 10.0, np.float32)
+    fh = np.full(4, 10.0, np.float32)
+    for name, v in ids.items():
+        f[v], fh[v] = vals[name]
+    f = f.reshape(2, 2)
+    fh = fh.reshape(2, 2)
+    P = _pairs_dict(f)
+    for vname, ename in pairs:
+        edge = tuple(sorted(ids[c] for c in ename))
+        assert P[(ids[vname],)] == edge
+    cells, dims = oracle.critical_cells(fh)
+    crit_vertices = {int(c[0]) for c, d in zip(cells, dims) if d == 0}
+    for name in crit:
+        assert ids[name] in crit_vertices
+    # the FPmin j of the example is fixed by lowering the extra vertex of j's f-partner (k)
+    cases, _ = oracle.targets(f, fh, pass_=0)
+    rows = {tuple(int(x) for x in r[1:] if x >= 0): int(r[0]) for r in cases}
+    assert rows[(ids["j"],)] == ids["k"]
+
+
+# --------------------------------------------------------------------------------------
+# the complex (Sec. 4.8.1: N1 ~ 7 N0, N2 ~ 12 N0, N3 ~ 6 N0 in 3D)
+# --------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dims", [(2, 2, 1), (3, 2, 1), (5, 4, 1), (2, 2, 2), (3, 4, 2), (4, 3, 5)])
+def test_cell_counts_closed_form(dims):
+    nx, ny, nz = dims
+    rows = oracle.cells(nx, ny, nz)
+    nv = (rows >= 0).sum(axis=1)
+    counts = np.bincount(nv - 1, minlength=4)
+    if nz == 1:
+        e = (nx - 1) * ny + nx * (ny - 1) + (nx - 1) * (ny - 1)
+        t = 2 * (nx - 1) * (ny - 1)
+        assert list(counts[:3]) == [nx * ny, e, t] and counts[3] == 0
+    else:
+        a, b, c = nx - 1, ny - 1, nz - 1
+        e = a * ny * nz + nx * b * nz + nx * ny * c + a * b * nz + a * ny * c + nx * b * c + a * b * c
+        tets = 6 * a * b * c
+        tris = 1 - nx * ny * nz + e + tets      # Euler characteristic of a box is 1
+        assert list(counts) == [nx * ny * nz, e, tris, tets]
+
+
+@pytest.mark.parametrize("dims", [(3, 3, 1), (2, 3, 2), (3, 3, 3)])
+def test_cells_are_exactly_the_cliques(dims):
+    """The Kuhn cells are the cliques of the neighbour graph (the complex is a flag complex)."""
+    nx, ny, nz = dims
+    n = nx * ny * nz
+    adj = {v: {w for w in range(n) if _adj(v, w, nx, ny)} for v in range(n)}
+    cliques = set()
+    for v in range(n):
+        cliques.add((v,))
+        for k in (2, 3, 4):
+            for comb in itertools.combinations(sorted(adj[v] | {v}), k):
+                if v != comb[0]:
+                    continue
+                if all(b in adj[a] for a, b in itertools.combinations(comb, 2)):
+                    cliques.add(comb)
+    assert _rows_to_sets(oracle.cells(nx, ny, nz)) == cliques
+
+
+# --------------------------------------------------------------------------------------
+# pairing: closed-form rules (Sec. 4.2) == brute-force Eq. 1 + lowest cofacet (Sec. 3.1)
+# --------------------------------------------------------------------------------------
+
+_SHAPES = [(2, 2), (3, 3), (4, 3), (3, 5), (5, 5), (2, 2, 2), (3, 3, 2), (2, 3, 4), (3, 3, 3), (4, 4, 3)]
+
+
+@pytest.mark.parametrize("shape", _SHAPES)
+@pytest.mark.parametrize("kind", ["normal", "equal", "binary", "signed_zero", "few_levels"])
+def test_rules_equal_brute_force(shape, kind):
+    rng = np.random.default_rng(hash((shape, kind)) % 2**32)
+    shp = shape[::-1]
+    for rep in range(3):
+        if kind == "normal":
+            a = rng.standard_normal(shp)
+        elif kind == "equal":
+            a = np.zeros(shp)
+        elif kind == "binary":
+            a = rng.integers(0, 2, shp).astype(float)
+        elif kind == "signed_zero":
+            a = np.where(rng.random(shp) < 0.5, -0.0, 0.0) + (rng.random(shp) < 0.2)
+        else:
+            a = rng.integers(0, 4, shp).astype(float) * 0.25
+        a = a.astype(np.float32)
+        assert np.array_equal(oracle.gradient_pairs(a), oracle.gradient_pairs(a, brute=True))
+
+
+def test_pairs_are_a_matching_of_facet_pairs():
+    rng = np.random.default_rng(7)
+    for shp in [(6, 7), (4, 5, 3)]:
+        a = rng.standard_normal(shp).astype(np.float32)
+        seen = set()
+        for r in oracle.gradient_pairs(a):
+            L = tuple(x for x in r[:4] if x >= 0)
+            U = tuple(x for x in r[4:] if x >= 0)
+            assert len(U) == len(L) + 1 and set(L) < set(U)
+            assert L not in seen and U not in seen
+            seen.add(L)
+            seen.add(U)
+
+
+def test_gradient_is_acyclic():
+    """V-paths never close: the Hasse diagram with gradient pairs reversed is a DAG."""
+    rng = np.random.default_rng(11)
+    for shp in [(5, 6), (3, 4, 4)]:
+        a = rng.integers(0, 3, shp).astype(np.float32)
+        P = _pairs_dict(a)
+        cells = _rows_to_sets(oracle.cells(*shp[::-1], *([1] if len(shp) == 2 else [])))
+        edges = {c: [] for c in cells}
+        for U in cells:
+            for i in range(len(U)):
+                L = U[:i] + U[i + 1:]
+                if not L:
+                    continue
+                if P.get(L) == U:
+                    edges[L].append(U)        # paired: point upward
+                else:
+                    edges[U].append(L)        # unpaired facet: point downward
+        state = {}
+
+        def dfs(c):
+            state[c] = 1
+            for d in edges[c]:
+                if state.get(d) == 1:
+                    return False
+                if d not in state and not dfs(d):
+                    return False
+            state[c] = 2
+            return True
+
+        import sys
+        sys.setrecursionlimit(100000)
+        assert all(dfs(c) for c in cells if c not in state)
+
+
+# --------------------------------------------------------------------------------------
+# critical cells: Euler characteristic, SoS special cases, fields with known counts
+# --------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape", [(8, 9), (13, 4), (4, 5, 6), (7, 3, 3)])
+def test_euler_characteristic(shape):
+    rng = np.random.default_rng(5)
+    for kind in range(3):
+        a = [rng.standard_normal(shape), rng.integers(0, 2, shape) * 1.0, np.zeros(shape)][kind]
+        c = _crit_counts(a.astype(np.float32), len(shape))
+        assert sum((-1) ** d * c[d] for d in range(len(c))) == 1
+
+
+@pytest.mark.parametrize("shape", [(4, 6), (5, 3, 4)])
+def test_constant_field_is_the_index_ramp(shape):
+    """With all values equal SoS orders vertices by index: one minimum at vertex 0, no
+    other critical cell, and exactly the pairs of the field f_v = v."""
+    const = np.zeros(shape, np.float32)
+    ramp = np.arange(const.size, dtype=np.float32).reshape(shape)
+    cells, dims = oracle.critical_cells(const)
+    assert len(cells) == 1 and dims[0] == 0 and cells[0][0] == 0
+    assert np.array_equal(oracle.gradient_pairs(const), oracle.gradient_pairs(ramp))
+
+
+def test_pairing_depends_on_order_only():
+    rng = np.random.default_rng(3)
+    a = rng.standard_normal((6, 5, 4)).astype(np.float32)
+    ranks = np.argsort(np.argsort(a.reshape(-1), kind="stable"), kind="stable").reshape(a.shape)
+    assert np.array_equal(oracle.gradient_pairs(a), oracle.gradient_pairs(ranks.astype(np.float32)))
+    assert np.array_equal(oracle.gradient_pairs(a), oracle.gradient_pairs((a * 3 + 1).astype(np.float32)))
+
+
+def test_single_peak_and_bowl_counts():
+    """Fields whose critical cells follow from the geometry.  Q(d) = dx^2 + dy^2 - dx dy is
+    the quadratic form under which all six neighbours of a vertex of the 2D triangulation
+    are at distance 1, so a Q-radial peak has a lower link on which the field is linear:
+    one interior maximum, the four box corners as minima, and by the Euler characteristic
+    four saddles.  A bowl (2D or 3D) flows to one interior minimum and out through the
+    boundary: one minimum and nothing else."""
+    for n in (9, 12):
+        y, x = np.mgrid[0:n, 0:n].astype(float)
+        dx, dy = x - n / 2 + 0.137, y - n / 2 + 0.291
+        Q = dx * dx + dy * dy - dx * dy
+        assert list(_crit_counts((-Q).astype(np.float32), 2)) == [4, 4, 1]
+        assert list(_crit_counts(Q.astype(np.float32), 2)) == [1, 0, 0]
+    for n in (6, 7):
+        z, y, x = np.mgrid[0:n, 0:n, 0:n].astype(float)
+        r2 = (x - n / 2 + 0.137) ** 2 + (y - n / 2 + 0.291) ** 2 + (z - n / 2 + 0.173) ** 2
+        assert list(_crit_counts(r2.astype(np.float32), 3)) == [1, 0, 0, 0]
+
+
+# --------------------------------------------------------------------------------------
+# separatrices: brute-force V-path enumeration from the pair list
+# --------------------------------------------------------------------------------------
+
+def _brute_paths(field, nx, ny, nz):
+    P = _pairs_dict(field)
+    cells = _rows_to_sets(oracle.cells(nx, ny, nz))
+    dim = 3 if nz > 1 else 2
+    crit = {c for c in cells if c not in P}
+    cof = {c: [] for c in cells}
+    for U in cells:
+        for i in range(len(U)):
+            L = U[:i] + U[i + 1:]
+            if L:
+                cof[L].append(U)
+    desc, asc = [], []
+    for s in sorted(crit):
+        if len(s) == 2:
+            for start in s:
+                seq, u = [], (start,)
+                while u not in crit:           # alternate vertex -> paired edge -> vertex
+                    e = P[u]
+                    seq.append((u, e))
+                    u = tuple(x for x in e if x not in u)
+                desc.append((s, (start,), len(seq), u))
+        if len(s) == dim:
+            for beta in sorted(cof[s]):
+                seq, b = [], beta
+                while True:                    # alternate top cell -> paired facet -> cofacet
+                    if b in crit:
+                        term = b
+                        break
+                    a = P[b]
+                    seq.append((a, b))
+                    nxt = [c for c in cof[a] if c != b]
+                    if not nxt:
+                        term = a
+                        break
+                    b = nxt[0]
+                asc.append((s, beta, len(seq), term))
+    return desc, asc
+
+
+@pytest.mark.parametrize("shape", [(7, 8), (6, 5, 4)])
+def test_separatrices_match_brute_force(shape):
+    rng = np.random.default_rng(17)
+    a = rng.standard_normal(shape).astype(np.float32)
+    dims = shape[::-1] + ((1,) if len(shape) == 2 else ())
+    desc, asc = _brute_paths(a, *dims)
+
+    def rows(kind):
+        out = set()
+        for r in oracle.separatrices(a, kind):
+            t = lambda q: tuple(int(x) for x in q if x >= 0)
+            out.add((t(r[0:4]), t(r[4:8]), int(r[8]), t(r[9:13])))
+        return out
+
+    assert rows(0) == set(desc)
+    assert rows(1) == set(asc)
+    assert len(desc) > 0 and len(asc) > 0
+
+
+# --------------------------------------------------------------------------------------
+# edit arithmetic (Eq. 2, Sec. 4.7)
+# --------------------------------------------------------------------------------------
+
+def test_edit_values_exact_case():
+    """f = 1, f_hat = 1.125, xi = 0.25, q_max = 2: step 1/16; every value exact."""
+    lb, ub, fc, qv = oracle.edit_values(np.float32([1.0]), np.float32([1.125]), 0.25, 2)
+    assert lb[0] == 0.75 and ub[0] == 1.25 and fc[0] == 1.125
+    assert list(qv[0]) == [1.125, 1.0625, 1.0]
+
+
+def test_edit_values_clamp_and_signed_zero():
+    f = np.float32([0.5, 0.5, -0.25, 0.25])
+    fh = np.float32([2.0, -2.0, 0.0, 0.0])
+    lb, ub, fc, _ = oracle.edit_values(f, fh, 0.25, 3)
+    assert fc[0] == ub[0] == 0.75 and fc[1] == lb[1] == 0.25
+    # exact zero bounds: f - xi rounds toward +inf (+0), f + xi toward -inf (-0)
+    assert ub[2] == 0.0 and np.signbit(ub[2])
+    assert lb[3] == 0.0 and not np.signbit(lb[3])
+
+
+def test_edit_bounds_are_tight_and_safe():
+    """lb is the smallest float >= f - xi and ub the largest float <= f + xi, exactly."""
+    rng = np.random.default_rng(23)
+    f = np.concatenate([rng.standard_normal(2000), rng.uniform(-1e-38, 1e-38, 200),
+                        [1.0, -1.0, 2.0 ** -126, -(2.0 ** -149), 0.0, -0.0, 3.0e-39]]).astype(np.float32)
+    for xi in (1e-3, 2.0 ** -20, 3.3e-7, 1e-39):
+        xi = float(np.float32(xi))
+        lb, ub, _, _ = oracle.edit_values(f, f, xi, 6)
+        for i in range(len(f)):
+            lo = Fraction(float(f[i])) - Fraction(xi)
+            hi = Fraction(float(f[i])) + Fraction(xi)
+            assert Fraction(float(lb[i])) >= lo
+            assert Fraction(float(np.nextafter(lb[i], np.float32(-np.inf)))) < lo
+            assert Fraction(float(ub[i])) <= hi
+            assert Fraction(float(np.nextafter(ub[i], np.float32(np.inf)))) > hi
+
+
+def test_quantised_values_are_rounded_steps():
+    """value_q is the float nearest to fc - fl(q * step), monotone in q, within one rounding."""
+    rng = np.random.default_rng(29)
+    f = rng.uniform(-3, 3, 500).astype(np.float32)
+    fh = (f + rng.uniform(-1e-3, 1e-3, 500)).astype(np.float32)
+    xi = float(np.float32(1e-3))
+    _, _, fc, qv = oracle.edit_values(f, fh, xi, 6)
+    step = Fraction(xi) / 64
+    for i in range(len(f)):
+        assert all(qv[i, q + 1] <= qv[i, q] for q in range(6))
+        for q in range(7):
+            exact = Fraction(float(fc[i])) - q * step
+            ulp = Fraction(float(np.spacing(np.float32(abs(float(exact)) + 1e-30))))
+            assert abs(Fraction(float(qv[i, q])) - exact) <= ulp
+
+
+# --------------------------------------------------------------------------------------
+# false-case rules on hand-built fields (Sec. 4.3)
+# --------------------------------------------------------------------------------------
+
+def _case_target(f, g, cell, pass_=0, tier=4):
+    cases, _ = oracle.targets(np.float32(f), np.float32(g), pass_=pass_, tier=tier)
+    found = [int(r[0]) for r in cases if tuple(int(x) for x in r[1:] if x >= 0) == cell]
+    assert len(found) == 1, (cell, cases)
+    return found[0]
+
+
+RAMP = np.arange(9, dtype=np.float32).reshape(3, 3)     # 3x3 grid, vertex id = x + 3 y
+
+
+def test_fp_min_lowers_partner():
+    """FPmin: vertex 4 pairs with edge {0,4} in f; in g it is a minimum -> lower 0."""
+    g = RAMP.copy(); g[1, 1] = -1
+    assert _case_target(RAMP, g, (4,)) == 0
+
+
+def test_fn_min_lowers_itself():
+    """FNmin: vertex 0 is a minimum in f but paired in g -> lower vertex 0."""
+    g = RAMP.copy(); g[0, 0] = 4.5
+    assert _case_target(RAMP, g, (0,)) == 0
+
+
+def test_fp_1saddle_vertex_type():
+    """Edge {0,4} is paired with vertex 4 in f; in g vertex 4 pairs with {4,8} and no
+    triangle takes the edge, so it is critical -> lower 0 (the vertex of the edge that is
+    not the f-partner vertex)."""
+    g = RAMP.copy(); g[2, 2] = -0.5
+    assert _case_target(RAMP, g, (0, 4)) == 0
+
+
+def test_fp_1saddle_triangle_type():
+    """Edge {1,4} is paired with triangle {0,1,4} in f; in g it is critical -> lower 0,
+    the extra vertex of the f-partner triangle."""
+    g = np.float32([1.5, 1, 2, 0.5, 4, 5, 6, 7, 8]).reshape(3, 3)
+    assert _case_target(RAMP, g, (1, 4)) == 0
+
+
+F_SADDLE = np.float32([0, 5, 1, 6, 7, 8]).reshape(2, 3)    # minima 0 and 2, saddle {1,2}
+
+
+def test_fn_1saddle_vertex_type_paper_choice():
+    """Saddle {1,2} (f: 2 below 1) is paired in g with vertex 2, now above 1 ->
+    lower vertex 2 so that g_2 < g_1 again (the paper's FN1saddle fix)."""
+    g = np.float32([0, 0.5, 1, 6, 7, 8]).reshape(2, 3)
+    assert _case_target(F_SADDLE, g, (1, 2)) == 2
+
+
+def test_fn_1saddle_vertex_type_repairs_facet():
+    """Saddle {1,2} is paired in g with its higher vertex 1 while the order of 1 and 2 is
+    still f's: lowering 1 cannot help within the bound, so the f-pairing of vertex 1
+    (edge {0,1}) is repaired by lowering 0."""
+    g = np.float32([1.5, 5, 1, 6, 7, 8]).reshape(2, 3)
+    assert _case_target(F_SADDLE, g, (1, 2)) == 0
+
+
+def test_fn_1saddle_triangle_type():
+    """Saddle {1,2} is paired in g with triangle {1,2,5} -> lower the edge's f-lowest
+    vertex (2)."""
+    g = np.float32([0, 5, 1, 6, 7, -1]).reshape(2, 3)
+    assert _case_target(F_SADDLE, g, (1, 2)) == 2
+
+
+F_MAX = np.float32([0, 1, 2, 3, 8, 4, 5, 6, 7]).reshape(3, 3)  # max triangle {4,7,8}
+
+
+def test_fp_max_2d():
+    """Triangle {0,1,4} is paired with edge {1,4} in the ramp; in g it is a maximum ->
+    lower 0, its extra vertex."""
+    g = np.float32([10, 11, 2, 3, 12, 5, 6, 7, 8]).reshape(3, 3)
+    assert _case_target(RAMP, g, (0, 1, 4)) == 0
+
+
+def test_fn_max_2d_paper_choice():
+    """Max {4,7,8} is paired in g with edge {4,7}; its f-lowest vertex 7 is lowered (one
+    of the paper's choices i or k)."""
+    g = np.float32([0, 1, 2, 6.5, 8, 4, 5, 6, 5.5]).reshape(3, 3)
+    assert oracle.critical_cells(F_MAX)[1].tolist().count(2) == 1
+    assert _case_target(F_MAX, g, (4, 7, 8)) == 7
+
+
+def test_fn_max_2d_repairs_facet():
+    """Max {4,7,8} is paired in g with its f-highest edge {4,8}; the edge's f-partner
+    {4,5,8} is restored by lowering 5."""
+    g = np.float32([0, 1, 2, 3, 8, 7.5, 5, 6, 7]).reshape(3, 3)
+    assert _case_target(F_MAX, g, (4, 7, 8)) == 5
+
+
+@pytest.mark.parametrize("shape", [(6, 7), (4, 4, 4), (3, 5, 4)])
+def test_case_rules_on_random_fields(shape):
+    """For every false case of every dimension: an FP case lowers the extra vertex of the
+    cell's f-partner; an FN case lowers one of the vertices of the g-pair's lower cell,
+    the lowest in f (or, when the order of the cell is unchanged, repairs a facet)."""
+    rng = np.random.default_rng(31)
+    f = rng.standard_normal(shape).astype(np.float32)
+    g = (f + rng.uniform(-0.4, 0.4, shape)).astype(np.float32)
+    Pf, Pg = _pairs_dict(f), _pairs_dict(g)
+    cases, _ = oracle.targets(f, g, pass_=0)
+    assert len(cases) > 5
+    fl = f.reshape(-1)
+    gl = g.reshape(-1)
+    key_f = lambda v: (fl[v], v)
+    key_g = lambda v: (gl[v], v)
+    for r in cases:
+        t = int(r[0])
+        cell = tuple(int(x) for x in r[1:] if x >= 0)
+        if cell in Pf and cell not in Pg:
+            U, L = (Pf[cell], cell) if len(Pf[cell]) > len(cell) else (cell, Pf[cell])
+            assert t == (set(U) - set(L)).pop()
+        else:
+            assert cell not in Pf and cell in Pg
+            P = Pg[cell]
+            L = cell if len(P) > len(cell) else P
+            if len(P) > len(cell) or min(cell, key=key_g) != min(cell, key=key_f):
+                assert t == min(cell, key=key_f) and t in L
+            else:
+                Q = Pf.get(L)
+                if Q is None:
+                    assert t == min(L, key=key_f)
+                else:
+                    big, small = (Q, L) if len(Q) > len(L) else (L, Q)
+                    assert t == (set(big) - set(small)).pop()
+
+
+# --------------------------------------------------------------------------------------
+# S-pass troublemakers (Sec. 4.4)
+# --------------------------------------------------------------------------------------
+
+def test_zero_dim_troublemaker():
+    """Hand-built 0-dim troublemaker (Sec. 4.4).  In f (ids x + 4 y) vertex 6 (value 6)
+    pairs with edge {6,7} (7 is its lowest lower neighbour, value 2) and lies on the
+    descending separatrix of saddle {5,6}.  Swapping the values of vertices 2 and 7 leaves
+    every critical cell in place but makes vertex 6 pair with {2,6}: the S-pass must lower
+    j = 7 so that 6 pairs with {6,7} again, and it is the only troublemaker."""
+    f = np.float32([[9, 10, 4, 1], [7, 8, 6, 2], [0, 3, 11, 5]])
+    g = np.float32([[9, 10, 2, 1], [7, 8, 6, 4], [0, 3, 11, 5]])
+    assert len(oracle.targets(f, g, pass_=0)[0]) == 0
+    cases, _ = oracle.targets(f, g, pass_=1, tier=4)
+    assert [int(c[0]) for c in cases] == [7]
+    assert _case_target(f, g, (6, 7), pass_=1) == 7
+
+
+def test_troublemakers_random_descending():
+    """Perturb one vertex on a descending separatrix of a random field so that it pairs
+    with a different lower neighbour while the critical cells stay the same; the S-pass
+    must then lower the original partner of the first disagreeing vertex."""
+    rng = np.random.default_rng(41)
+    hits = 0
+    for trial in range(200):
+        f = rng.standard_normal((7, 7)).astype(np.float32)
+        Pf = _pairs_dict(f)
+        rows = oracle.separatrices(f, 0)
+        rows = [r for r in rows if r[8] >= 2]
+        if not rows:
+            continue
+        r = rows[int(rng.integers(0, len(rows)))]
+        # walk the f-path: u0 -> ... ; pick the first vertex of the path
+        u = int(r[4])
+        w = (set(Pf[(u,)]) - {u}).pop()
+        fl = f.reshape(-1)
+        lower = [v for v in range(f.size) if _adj(u, v, 7, 7) and (fl[v], v) < (fl[u], u) and v != w]
+        if not lower:
+            continue
+        v2 = lower[0]
+        g = f.copy().reshape(-1)
+        g[v2] = np.nextafter(fl[w], np.float32(-np.inf))
+        g = g.reshape(f.shape)
+        if len(oracle.targets(f, g, pass_=0)[0]):
+            continue
+        Pg = _pairs_dict(g)
+        if Pg.get((u,)) == Pf[(u,)]:
+            continue
+        cases, _ = oracle.targets(f, g, pass_=1, tier=4)
+        assert w in {int(c[0]) for c in cases}
+        hits += 1
+    assert hits >= 3
+
+
+# --------------------------------------------------------------------------------------
+# the whole loop: invariants and final MSC equality (Sec. 4.1, 4.5)
+# --------------------------------------------------------------------------------------
+
+def _exact_bound_ok(f, g, xi):
+    fl, gl = f.reshape(-1).astype(np.float64), g.reshape(-1).astype(np.float64)
+    # differences of floats within a few binades are exact in double
+    d = np.abs(gl - fl)
+    return bool(np.all(d <= xi))
+
+
+def _cases():
+    yield synth.config_case("gauss2d")
+    yield synth.config_case("gauss2d", seed=9, size=(23, 41), rel=1e-2)
+    yield synth.config_case("multiscale2d", size=(40, 56), rel=1e-2)
+    yield synth.config_case("grf3d", size=9, rel=1e-2)
+    yield synth.config_case("kolmogorov3d", size=10, rel=3e-3)
+
+
+@pytest.mark.parametrize("idx", range(5))
+@pytest.mark.parametrize("tier", [1, 2, 3, 4])
+def test_loop_converges_and_preserves_msc(idx, tier):
+    f, fh, xi, _ = list(_cases())[idx]
+    r = oracle.fix(f, fh, xi, tier=tier)
+    assert r["status"] == 0
+    g = r["g"]
+    assert _exact_bound_ok(f, g, xi)
+    rep = oracle.verify(f, g)
+    dim = f.ndim
+    ext = [rep["fp0"], rep["fn0"], rep["fp%d" % dim], rep["fn%d" % dim]]
+    assert sum(ext) == 0
+    if tier >= 2:
+        assert all(rep[k] == 0 for k in ("fp0", "fp1", "fp2", "fp3", "fn0", "fn1", "fn2", "fn3"))
+    if tier == 3:
+        assert rep["term_desc"] == 0 and rep["term_asc"] == 0
+    if tier == 4:
+        assert rep["sep_desc"] == 0 and rep["sep_asc"] == 0 and rep["sep_saddle"] == 0
+    c = _crit_counts(g, dim)
+    assert sum((-1) ** d * c[d] for d in range(len(c))) == 1
+    # the critical cells of g are exactly those of f
+    if tier >= 2:
+        cf, df = oracle.critical_cells(f)
+        cg, dg = oracle.critical_cells(g)
+        assert np.array_equal(cf, cg) and np.array_equal(df, dg)
+    # stored edits rebuild g bit-exactly on the decompression side
+    qm, li, lv = oracle.edits_from_state(f, fh, xi, r["state"], g)
+    g2 = oracle.apply_edits(fh, xi, 6, qm, li, lv)
+    assert np.array_equal(g2.view(np.uint32), g.view(np.uint32))
+
+
+def test_edits_are_monotone_per_iteration():
+    """g^(k+1) <= g^(k) at every vertex (Sec. 3.2) except exact-fallback restores, and
+    g >= f - xi throughout, checked on every prefix of the loop."""
+    f, fh, xi, tier = synth.config_case("gauss2d", seed=3, size=(20, 24), rel=2e-2)
+    full = oracle.fix(f, fh, xi, tier=4)
+    n = full["n_c"] + full["n_s"]
+    assert n > 3
+    prev = None
+    for k in range(1, n + 1):
+        r = oracle.fix(f, fh, xi, tier=4, max_iters=k)
+        assert r["status"] in (0, 4)
+        g = r["g"]
+        assert _exact_bound_ok(f, g, xi)
+        if prev is not None:
+            ok = (g <= prev[0]) | (r["state"] == oracle.ST_EXACT)
+            assert ok.all()
+        prev = (g, r["state"])
+    assert np.array_equal(prev[0], full["g"])
+
+
+def test_stall_fallback_on_floor_ties():
+    """f - xi can round two different f values to the same float; SoS then orders the
+    floors by index, against f.  Vertex 1 (below vertex 0 in f) and vertex 0 tie at the
+    floor: the loop must restore them to f exactly (exact fallback) or report a stall."""
+    a = np.float32(-1.0 + 2.0 ** -24)        # f of vertex 1 (lower)
+    b = np.float32(-1.0 + 2.0 ** -23)        # f of vertex 0 (higher)
+    xi = float(np.float32(2.0 ** -23))
+    lb, _, _, _ = oracle.edit_values(np.float32([a, b]), np.float32([a, b]), xi, 6)
+    assert lb[0] == lb[1] == -1.0
+    f = np.float32([[b, a], [10, 11]])
+    fh = np.float32([[b - 0.0, a + 2 ** -24], [10, 11]])
+    fh[0, 0] = lb[1]                          # vertex 0 already at its floor
+    fh = fh.astype(np.float32)
+    r = oracle.fix(f, fh, xi, tier=4)
+    assert r["status"] == 0 and r["n_exact_iters"] >= 1
+    assert oracle.verify(f, r["g"])["fp0"] == 0
+    r2 = oracle.fix(f, fh, xi, tier=4, exact_fallback=0)
+    assert r2["status"] == 6
+
+
+def test_invalid_inputs_rejected():
+    f = np.zeros((4, 4), np.float32)
+    bad = f.copy(); bad[1, 1] = np.nan
+    assert oracle.fix(f, bad, 0.1)["status"] == 1
+    assert oracle.fix(f, f, 0.0)["status"] == 1
+    assert oracle.fix(f, f, 0.1, q_max=8)["status"] == 1
