@@ -1,0 +1,202 @@
+/*
+ * msc.h -- C ABI of libmsc, a GPU (sm_103a) implementation of the iterative edit loop of
+ * "Preserving Discrete Morse-Smale Complexes in Error-Bounded Lossy Compression"
+ * (Li, Xia, Liang, Wang, Guo): given an original scalar field f and a base compressor's
+ * decompressed field f_hat on the same regular grid, compute per-vertex edits so that the
+ * edited field g = f_hat + delta satisfies |f - g| <= xi and has the same discrete
+ * Morse-Smale complex as f (Sec. 4.1, "Problem Statement").
+ *
+ * Conventions used by every entry point
+ *  - Grid: nx x ny x nz vertices, nz == 1 for a 2D field; vertex id v = x + nx*(y + ny*z)
+ *    (x fastest).  nx, ny >= 2, nz >= 1, and nx*ny*nz < 2^31.
+ *  - Complex: the Freudenthal triangulation of the grid (Sec. 4.8.1: six tetrahedra per
+ *    cube in 3D, two triangles per square in 2D), with the diagonal along +(1,1[,1]).
+ *  - Vertex order: simulation of simplicity (Sec. 4.1, "Degeneracy handling"): a < b iff
+ *    f[a] < f[b], or f[a] == f[b] and a < b.
+ *  - Field pointers may be host or device memory; the library finds out with
+ *    cudaPointerGetAttributes.  Device pointers must be on the current device.
+ *  - Ownership: the caller owns every input and every output buffer it passes (g_out,
+ *    rows).  The library owns a handle and the arrays inside msc_edits; free them with
+ *    msc_destroy / msc_free_edits.
+ *  - Errors: every call returns a status and never aborts.  On any status other than
+ *    MSC_OK the outputs are unspecified; msc_last_error() gives a one-line reason
+ *    (thread-local, valid until the next call on the same thread).
+ *  - Streams: options->stream (a cudaStream_t, NULL = the legacy default stream) orders
+ *    all device work of a call; calls return after their results are complete.
+ */
+#ifndef MSC_H
+#define MSC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct msc_handle msc_handle;   /* opaque: device-resident MSC state of one f */
+
+typedef enum {
+    MSC_OK = 0,
+    MSC_ERR_INVALID_ARG = 1,     /* bad dims, NaN/Inf values, xi <= 0, q_max or tier out of range */
+    MSC_ERR_OOM = 2,             /* device or host allocation failed */
+    MSC_ERR_CUDA = 3,            /* a CUDA runtime call failed (message in msc_last_error) */
+    MSC_ERR_NOT_CONVERGED = 4,   /* max_iters edit rounds were not enough */
+    MSC_ERR_DEVICE_TIMEOUT = 5,  /* a bounded device-side wait gave up */
+    MSC_ERR_STALLED = 6,         /* every false case targets a vertex that cannot move and
+                                    exact_fallback is off */
+    MSC_ERR_NO_DEVICE = 7        /* no CUDA device, or the library was not built for it */
+} msc_status;
+
+/* per-vertex edit states (the value of msc_edits.q_map[v] is derived from these) */
+#define MSC_QMAP_LOSSLESS 0xFF
+
+typedef struct {
+    int tier;            /* 1..4 (Sec. 4.1): 1 extrema, 2 all critical cells,
+                            3 + saddle-extremum connectivity, 4 + separatrix geometry */
+    int q_max;           /* 1..7: edit step xi / 2^q_max, at most q_max quantised steps (Eq. 2) */
+    int max_iters;       /* edit rounds before MSC_ERR_NOT_CONVERGED (default 100000) */
+    int exact_fallback;  /* 1 (default): a false case whose target vertex cannot move any
+                            more (already at its floor f - xi, or restored) restores the
+                            closed 1-rings of the case cell's vertices to f exactly */
+    int tile_x, tile_y, tile_z;   /* dense-stencil tile; 0 = built-in default */
+    void *stream;        /* cudaStream_t for all device work of the call (NULL = default) */
+    int record_trace;    /* 1: fill msc_edits.trace with one record per edit round */
+    int profile;         /* 1: time every kernel launch of the call with CUDA events on the
+                            call's stream and accumulate into the handle's msc_stats */
+} msc_options;
+
+/* kernel classes of msc_stats */
+enum {
+    MSC_K_DENSE = 0,     /* dense discrete gradient of a whole field (Sec. 4.2) */
+    MSC_K_CPASS = 1,     /* false critical cells -> targets (Sec. 4.3) */
+    MSC_K_EDIT = 2,      /* quantised edit (Eq. 2) + dirty-anchor marking */
+    MSC_K_REFRESH = 3,   /* gradient of the anchors around edited vertices */
+    MSC_K_REBUILD = 4,   /* mismatch-list rebuild and set clears */
+    MSC_K_SPASS = 5,     /* separatrix walks (Sec. 4.4) */
+    MSC_K_OTHER = 6,     /* initialisation, seeds, output encoding, checks */
+    MSC_K_COUNT = 7
+};
+
+/* per-handle launch statistics (msc_get_stats); times only with options.profile = 1 */
+typedef struct {
+    uint64_t launches[8];        /* kernel launches by class, always counted */
+    double ms[8];                /* summed CUDA-event duration by class (profiled calls) */
+    uint64_t timed_launches[8];  /* launches that were timed */
+} msc_stats;
+
+/* one edit round: kind 0 = C-pass (false critical cells), 1 = S-pass (separatrices);
+ * T = vertices lowered by a quantised step this round, X = vertices restored to f */
+typedef struct {
+    int32_t kind;
+    int32_t reserved;
+    int64_t n_targets, n_exact;
+    int64_t sum_targets, sum_exact;   /* sums of vertex ids, an order-free digest */
+} msc_iter_record;
+
+typedef struct {
+    uint64_t n_vertices;
+    uint32_t n_iters_c;          /* C-pass edit rounds (Sec. 4.3) */
+    uint32_t n_iters_s;          /* S-pass edit rounds (Sec. 4.4) */
+    uint32_t n_fallback_iters;   /* rounds in which the exact fallback restored vertices */
+    uint32_t reserved;
+    uint64_t n_quant;            /* vertices with 1..q_max quantised edits */
+    uint64_t n_lossless;         /* vertices stored losslessly (floor, restored, re-clamped) */
+    uint8_t *q_map;              /* n_vertices entries: q in 0..q_max (g = f_hat - q*xi/2^q_max,
+                                    computed as one float subtraction of fl(q * step)), or
+                                    MSC_QMAP_LOSSLESS (g stored in lossless_val) */
+    uint64_t *lossless_idx;      /* n_lossless vertex ids, ascending */
+    float *lossless_val;         /* final g at those vertices */
+    uint32_t n_trace;            /* number of records in trace (record_trace = 1) */
+    msc_iter_record *trace;
+    double loop_ms;              /* device time of the fix loop (init to convergence) */
+} msc_edits;
+
+typedef struct {
+    uint64_t fp[4];              /* false positive critical cells by dimension */
+    uint64_t fn[4];              /* false negative critical cells by dimension */
+    uint64_t sep_mismatch[3];    /* separatrices with a pair missing from g's gradient:
+                                    descending, ascending, saddle-saddle (per 2-saddle) */
+    uint64_t term_mismatch[2];   /* descending / ascending separatrices ending elsewhere */
+    double max_abs_err;          /* max |g - f| */
+    int pass;                    /* 1 iff no false critical cell, no separatrix mismatch
+                                    and max_abs_err <= xi */
+    int reserved;
+} msc_report;
+
+/* Library version string. */
+const char *msc_version(void);
+
+/* Human-readable name of a status. */
+const char *msc_status_string(msc_status s);
+
+/* One-line description of the last error on this thread ("" if none). */
+const char *msc_last_error(void);
+
+/* Fill *opt with defaults: tier 4, q_max 6, max_iters 100000, exact_fallback 1,
+ * tiles 0, stream NULL, record_trace 0, profile 0. */
+void msc_default_options(msc_options *opt);
+
+/* Sec. 4.2 (discrete gradient of f), Sec. 3.1 (critical cells, gradient paths): compute
+ * and keep on the device the gradient of the original field f, its critical cells and the
+ * seeds of its separatrices.  f: nx*ny*nz floats (host or device), all finite.
+ * On MSC_OK *out is a new handle (free with msc_destroy). */
+msc_status msc_prepare_original(const float *f, int nx, int ny, int nz,
+                                const msc_options *opt, msc_handle **out);
+
+/* Sec. 4.2-4.7: the fix loop.  f_hat: the decompressed field (same grid, host or device,
+ * finite; values outside [f - xi, f + xi] are first re-clamped into the bound).  xi > 0
+ * is the absolute error bound.  Alternates C-passes (Sec. 4.3) and, for tier >= 3,
+ * S-passes (Sec. 4.4) until no false case remains; each pass lowers the target vertices
+ * by one quantised step (Eq. 2).  Writes the edited field to g_out (nx*ny*nz floats, host
+ * or device, caller-owned) and the edits to *out (library-owned arrays; msc_free_edits).
+ * opt may be NULL (defaults). */
+msc_status msc_fix(msc_handle *h, const float *f_hat, float xi, const msc_options *opt,
+                   msc_edits *out, float *g_out);
+
+/* Sec. 4.7 / Fig. 5 (decompression side): rebuild g from f_hat and stored edits,
+ * bit-exactly equal to msc_fix's g_out.  f_hat and g_out: host or device. */
+msc_status msc_apply_edits(const float *f_hat, int nx, int ny, int nz, float xi, int q_max,
+                           const msc_edits *edits, float *g_out);
+
+/* Sec. 5.1 metrics: compare the MSC of g with the handle's original (critical cells by
+ * dimension, every separatrix pair, separatrix terminals) and measure max |g - f|.
+ * g: host or device.  Separatrix counts are computed only when the critical cells agree. */
+msc_status msc_verify(msc_handle *h, const float *g, float xi, msc_report *out);
+
+/* Free the arrays inside *e (not e itself) and zero it. */
+void msc_free_edits(msc_edits *e);
+
+/* Free a handle and its device memory. */
+void msc_destroy(msc_handle *h);
+
+/* Batched fix (Sec. 5, time-series study): n independent jobs, job i on handle hs[i] with
+ * decompressed field f_hats[i], bound xis[i], outputs outs[i] and g_outs[i] (same rules
+ * as msc_fix).  The jobs share the device; their results equal n separate msc_fix calls.
+ * Returns the first non-OK status, MSC_OK otherwise. */
+msc_status msc_fix_batch(msc_handle **hs, const float **f_hats, const float *xis, int n,
+                         const msc_options *opt, msc_edits *outs, float **g_outs);
+
+/* Sec. 4.2: every gradient pair (L, U) of a field, as rows of 8 int64 vertex ids (L's ids
+ * ascending padded with -1, then U's), in no particular order.  *n_out is the number of
+ * pairs; at most cap rows are written (call with cap 0 to size the buffer).
+ * field and rows: host memory. */
+msc_status msc_gradient_pairs(const float *field, int nx, int ny, int nz,
+                              int64_t *rows, uint64_t cap, uint64_t *n_out);
+
+/* Sec. 3.1: critical (unpaired) cells of a field: rows of 4 int64 vertex ids (ascending,
+ * -1 padded) and their dimensions, in no particular order.  Host memory. */
+msc_status msc_critical_cells(const float *field, int nx, int ny, int nz,
+                              int64_t *rows, int32_t *dims, uint64_t cap, uint64_t *n_out);
+
+/* Launch statistics accumulated on a handle since its creation or the last reset. */
+msc_status msc_get_stats(msc_handle *h, msc_stats *out);
+msc_status msc_reset_stats(msc_handle *h);
+
+/* Bytes of device memory a handle of this grid holds while fixing (for admission). */
+uint64_t msc_device_bytes(int nx, int ny, int nz);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSC_H */

@@ -1,0 +1,752 @@
+// Per-element logic of the fix loop: one anchor, one target vertex, one separatrix seed.
+// The __global__ kernels in msc_lib.cu are thin grid-stride wrappers around these.
+#pragma once
+#include <cstdint>
+#include "msc_cells.cuh"
+
+namespace msc {
+
+// tables read with run-time indices (the dense evaluator uses compile-time copies)
+#ifdef __CUDACC__
+static __device__ const Tab<2> kTab2 = make_tab<2>();
+static __device__ const Tab<3> kTab3 = make_tab<3>();
+#endif
+#ifdef MSC_HOST_EMULATION
+static const Tab<2> hTab2 = make_tab<2>();
+static const Tab<3> hTab3 = make_tab<3>();
+#endif
+template <int D> MSC_HD inline const Tab<D> &rt_tab();
+template <> MSC_HD inline const Tab<2> &rt_tab<2>()
+{
+#if defined(__CUDA_ARCH__) || !defined(MSC_HOST_EMULATION)
+    return kTab2;
+#else
+    return hTab2;
+#endif
+}
+template <> MSC_HD inline const Tab<3> &rt_tab<3>()
+{
+#if defined(__CUDA_ARCH__) || !defined(MSC_HOST_EMULATION)
+    return kTab3;
+#else
+    return hTab3;
+#endif
+}
+
+constexpr uint8_t ST_FLOOR = 0xF0;   // g == lb, stored losslessly (Eq. 2 "otherwise")
+constexpr uint8_t ST_EXACT = 0xF1;   // g == f, stored losslessly (stuck-case restore)
+
+struct Grid {
+    int nx, ny, nz;
+    uint32_t n;
+};
+
+struct Counters {
+    unsigned long long ncase, nlive, nT, nX, sumT, sumX;   // targeting pass
+    unsigned long long nchanged, nD, nM, novf, err, steps;
+    unsigned long long rep[16];                            // verify / misc
+};
+
+// everything a kernel of one job needs (device pointers)
+struct Ctx {
+    Grid G;
+    int tier, qmax, exact_fallback;
+    float xi, step;
+    const float *f, *fhat;
+    float *g;
+    uint8_t *state;
+    const uint64_t *code_f;
+    uint64_t *code_g;
+    uint32_t *Tbits, *Xbits, *Dbits;
+    uint32_t *Tlist, *Xlist, *Dlist;
+    uint32_t *Mcur, *Mnext;
+    uint32_t nMcur;
+    uint32_t *stamp;
+    uint32_t tag;
+    uint32_t *vis_v, *vis_top, *vis_tri;
+    uint32_t *ovf_in, *ovf_out;      // saddle-saddle spill queues: (triangle id, entry edge) pairs
+    uint32_t ovf_cap;
+    Counters *cnt;
+};
+
+// ------------------------------------------------------------------------------------
+// atomics and correctly rounded float operations
+// ------------------------------------------------------------------------------------
+#ifdef __CUDA_ARCH__
+__device__ __forceinline__ unsigned a_or(uint32_t *p, uint32_t v) { return atomicOr(p, v); }
+__device__ __forceinline__ unsigned long long a_add(unsigned long long *p, unsigned long long v) { return atomicAdd(p, v); }
+__device__ __forceinline__ uint32_t a_exch(uint32_t *p, uint32_t v) { return atomicExch(p, v); }
+__device__ __forceinline__ float sub_ru(float a, float b) { return __fsub_ru(a, b); }
+__device__ __forceinline__ float add_rd(float a, float b) { return __fadd_rd(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+template <class T> __device__ __forceinline__ T ld(const T *p) { return __ldg(p); }
+#else
+float emu_sub_ru(float a, float b);
+float emu_add_rd(float a, float b);
+inline unsigned a_or(uint32_t *p, uint32_t v) { unsigned o = *p; *p |= v; return o; }
+inline unsigned long long a_add(unsigned long long *p, unsigned long long v) { unsigned long long o = *p; *p += v; return o; }
+inline uint32_t a_exch(uint32_t *p, uint32_t v) { uint32_t o = *p; *p = v; return o; }
+inline float sub_ru(float a, float b) { return emu_sub_ru(a, b); }
+inline float add_rd(float a, float b) { return emu_add_rd(a, b); }
+inline float sub_rn(float a, float b) { volatile float r = a - b; return r; }
+inline float mul_rn(float a, float b) { volatile float r = a * b; return r; }
+template <class T> inline T ld(const T *p) { return *p; }
+#endif
+
+MSC_HD inline bool test_and_set(uint32_t *bits, uint32_t i)
+{
+    const uint32_t m = 1u << (i & 31);
+    return (a_or(bits + (i >> 5), m) & m) != 0;
+}
+
+MSC_HD inline bool sos_lt(float a, uint32_t ia, float b, uint32_t ib)
+{
+    return a < b || (a == b && ia < ib);
+}
+
+MSC_HD inline void coords(const Grid &G, uint32_t v, int &x, int &y, int &z)
+{
+    x = (int)(v % (uint32_t)G.nx);
+    uint32_t t = v / (uint32_t)G.nx;
+    y = (int)(t % (uint32_t)G.ny);
+    z = (int)(t / (uint32_t)G.ny);
+}
+
+MSC_HD inline bool inside(const Grid &G, int x, int y, int z)
+{
+    return x >= 0 && y >= 0 && z >= 0 && x < G.nx && y < G.ny && z < G.nz;
+}
+
+MSC_HD inline uint32_t vid(const Grid &G, int x, int y, int z)
+{
+    return (uint32_t)x + (uint32_t)G.nx * ((uint32_t)y + (uint32_t)G.ny * (uint32_t)z);
+}
+
+// bit k set <=> cube corner k of the anchor at (x,y,z) is in the domain
+template <int D> MSC_HD inline unsigned corner_mask(const Grid &G, int x, int y, int z)
+{
+    const bool cx = x + 1 < G.nx, cy = y + 1 < G.ny, cz = D == 3 && z + 1 < G.nz;
+    unsigned m = 0;
+#pragma unroll
+    for (int k = 0; k < Tab<D>::NC; k++) {
+        const bool in = (!(k & 1) || cx) && (!(k & 2) || cy) && (!(k & 4) || cz);
+        m |= (unsigned)in << k;
+    }
+    return m;
+}
+
+// the window of values around an anchor (+inf outside the domain)
+template <int D> MSC_HD inline void load_window(const float *v, const Grid &G, int x, int y, int z, float *w)
+{
+    const float INF = pos_inf();
+    constexpr int ZL = D == 3 ? -1 : 0, ZH = D == 3 ? 2 : 0;
+#pragma unroll
+    for (int dz = ZL; dz <= ZH; dz++)
+#pragma unroll
+        for (int dy = -1; dy <= 2; dy++)
+#pragma unroll
+            for (int dx = -1; dx <= 2; dx++) {
+                const int xx = x + dx, yy = y + dy, zz = z + dz;
+                w[wpos<D>(dx, dy, dz)] = inside(G, xx, yy, zz) ? ld(v + vid(G, xx, yy, zz)) : INF;
+            }
+}
+
+template <int D> MSC_HD inline uint64_t anchor_code(const float *v, const Grid &G, uint32_t p)
+{
+    int x, y, z;
+    coords(G, p, x, y, z);
+    float w[Tab<D>::WS];
+    load_window<D>(v, G, x, y, z, w);
+    return eval_anchor<D>(w, corner_mask<D>(G, x, y, z));
+}
+
+// ------------------------------------------------------------------------------------
+// small cell helpers (relative offsets -> absolute vertices)
+// ------------------------------------------------------------------------------------
+struct Verts {
+    int n;
+    uint32_t id[4];
+    int x[4], y[4], z[4];
+};
+
+MSC_HD inline void vpush(Verts &V, const Grid &G, int x, int y, int z)
+{
+    V.x[V.n] = x; V.y[V.n] = y; V.z[V.n] = z;
+    V.id[V.n] = vid(G, x, y, z);
+    V.n++;
+}
+
+// anchored cell vertices: kind 0 vertex, 1 edge, 2 triangle, 3 tet
+template <int D> MSC_HD inline Verts cell_verts(const Grid &G, int x, int y, int z, int kind, int t)
+{
+    const Tab<D> &T = rt_tab<D>();
+    Verts V;
+    V.n = 0;
+    vpush(V, G, x, y, z);
+    int cs[3] = {0, 0, 0}, nc = 0;
+    if (kind == 1) { cs[0] = t + 1; nc = 1; }
+    if (kind == 2) { cs[0] = T.tA[t]; cs[1] = T.tB[t]; nc = 2; }
+    if (kind == 3) { cs[0] = T.kA[t]; cs[1] = T.kB[t]; cs[2] = 7; nc = 3; }
+    for (int i = 0; i < nc; i++) vpush(V, G, x + (cs[i] & 1), y + ((cs[i] >> 1) & 1), z + ((cs[i] >> 2) & 1));
+    return V;
+}
+
+MSC_HD inline int lowest_of(const Verts &V, const float *vals)
+{
+    int lo = 0;
+    float lv = ld(vals + V.id[0]);
+    for (int i = 1; i < V.n; i++) {
+        const float vi = ld(vals + V.id[i]);
+        if (sos_lt(vi, V.id[i], lv, V.id[lo])) { lo = i; lv = vi; }
+    }
+    return lo;
+}
+
+// a false case: vertex t is lowered this round; a stuck case restores the closed 1-rings of
+// the case cell's vertices to f (exact fallback)
+template <int D> MSC_HD inline void add_case(const Ctx &c, uint32_t t, const Verts &cell)
+{
+    const Tab<D> &T = rt_tab<D>();
+    a_add(&c.cnt->ncase, 1ull);
+    if (!test_and_set(c.Tbits, t)) {
+        const unsigned long long i = a_add(&c.cnt->nT, 1ull);
+        c.Tlist[i] = t;
+        a_add(&c.cnt->sumT, (unsigned long long)t);
+    }
+    const uint8_t st = c.state[t];
+    if (st != ST_FLOOR && st != ST_EXACT) { a_add(&c.cnt->nlive, 1ull); return; }
+    if (!c.exact_fallback) return;
+    for (int i = 0; i < cell.n; i++) {
+        for (int n = -1; n < T.NNB; n++) {
+            int xx = cell.x[i], yy = cell.y[i], zz = cell.z[i];
+            if (n >= 0) { xx += T.nb[n][0]; yy += T.nb[n][1]; zz += T.nb[n][2]; }
+            if (!inside(c.G, xx, yy, zz)) continue;
+            const uint32_t u = vid(c.G, xx, yy, zz);
+            if (!test_and_set(c.Xbits, u)) {
+                const unsigned long long j = a_add(&c.cnt->nX, 1ull);
+                c.Xlist[j] = u;
+                a_add(&c.cnt->sumX, (unsigned long long)u);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// C-pass (Sec. 4.3): false critical cells owned by one anchor
+// ------------------------------------------------------------------------------------
+MSC_HD inline bool crit_v(int f) { return f == 15; }
+MSC_HD inline bool crit_c(int f) { return f == 0; }
+
+// target of a false negative cell paired DOWN in g: its g-lowest vertex y; when y is also
+// its f-lowest vertex, repair the f-pairing of the facet L = cell - y instead
+template <int D>
+MSC_HD inline uint32_t fn_down_target(const Ctx &c, int x, int y, int z, int kind, int t, const Verts &V)
+{
+    const Tab<D> &T = rt_tab<D>();
+    const int jg = lowest_of(V, c.g), jf = lowest_of(V, c.f);
+    if (jg != jf) return V.id[jf];
+    if (kind == 1) {                       // L = the other vertex h
+        const int h = 1 - jg;
+        const int vf = vfield<D>(ld(c.code_f + V.id[h]));
+        if (vf == 15) return V.id[h];
+        return vid(c.G, V.x[h] + T.nb[vf][0], V.y[h] + T.nb[vf][1], V.z[h] + T.nb[vf][2]);
+    }
+    // facet opposite corner jg
+    int ax, ay, az, ty;
+    if (kind == 2) {
+        const int corner = jg == 0 ? 0 : (jg == 1 ? T.tA[t] : T.tB[t]);
+        int j = 0;
+        for (int q = 0; q < 3; q++) if (T.tfac_opp[t][q] == corner) j = q;
+        ax = x + T.tfac_anc[t][j][0]; ay = y + T.tfac_anc[t][j][1]; az = z + T.tfac_anc[t][j][2];
+        ty = T.tfac_type[t][j];
+        const uint32_t a = vid(c.G, ax, ay, az);
+        const int ef = efield<D>(ld(c.code_f + a), ty);
+        if (ef >= 2)
+            return vid(c.G, ax + T.ecof_v[ty][ef - 2][0], ay + T.ecof_v[ty][ef - 2][1], az + T.ecof_v[ty][ef - 2][2]);
+        Verts L = cell_verts<D>(c.G, ax, ay, az, 1, ty);
+        return L.id[lowest_of(L, c.f)];
+    }
+    const int corner = jg == 0 ? 0 : (jg == 1 ? T.kA[t] : (jg == 2 ? T.kB[t] : 7));
+    int j = 0;
+    for (int q = 0; q < 4; q++) if (T.kfac_opp[t][q] == corner) j = q;
+    ax = x + T.kfac_anc[t][j][0]; ay = y + T.kfac_anc[t][j][1]; az = z + T.kfac_anc[t][j][2];
+    ty = T.kfac_type[t][j];
+    const uint32_t a = vid(c.G, ax, ay, az);
+    const int tf = tfield<D>(ld(c.code_f + a), ty);
+    if (tf >= 2)
+        return vid(c.G, ax + T.tcof_v[ty][tf - 2][0], ay + T.tcof_v[ty][tf - 2][1], az + T.tcof_v[ty][tf - 2][2]);
+    Verts L = cell_verts<D>(c.G, ax, ay, az, 2, ty);
+    return L.id[lowest_of(L, c.f)];
+}
+
+// false positive: lower the extra vertex of the f-partner; false negative: lower the
+// cell's f-lowest vertex (or repair a facet, fn_down_target)
+template <int D> MSC_HD inline void ctargets_anchor(const Ctx &c, uint32_t p)
+{
+    const Tab<D> &T = rt_tab<D>();
+    const uint64_t cf = ld(c.code_f + p), cg = c.code_g[p];
+    if (cf == cg) return;
+    int x, y, z;
+    coords(c.G, p, x, y, z);
+    const unsigned cin = corner_mask<D>(c.G, x, y, z);
+    // vertex
+    {
+        const int ff = vfield<D>(cf), gf = vfield<D>(cg);
+        if (crit_v(ff) != crit_v(gf)) {
+            Verts V = cell_verts<D>(c.G, x, y, z, 0, 0);
+            const uint32_t t = crit_v(gf) ? vid(c.G, x + T.nb[ff][0], y + T.nb[ff][1], z + T.nb[ff][2]) : p;
+            add_case<D>(c, t, V);
+        }
+    }
+    if (c.tier >= 2) {
+#pragma unroll 1
+        for (int e = 0; e < T.NE; e++) {
+            if (!((cin >> (e + 1)) & 1u)) continue;
+            const int ff = efield<D>(cf, e), gf = efield<D>(cg, e);
+            if (crit_c(ff) == crit_c(gf)) continue;
+            Verts V = cell_verts<D>(c.G, x, y, z, 1, e);
+            uint32_t t;
+            if (crit_c(gf)) {
+                t = ff == 1 ? V.id[lowest_of(V, c.f)]
+                            : vid(c.G, x + T.ecof_v[e][ff - 2][0], y + T.ecof_v[e][ff - 2][1], z + T.ecof_v[e][ff - 2][2]);
+            } else {
+                t = gf >= 2 ? V.id[lowest_of(V, c.f)] : fn_down_target<D>(c, x, y, z, 1, e, V);
+            }
+            add_case<D>(c, t, V);
+        }
+    }
+#pragma unroll 1
+    for (int tt = 0; tt < T.NT; tt++) {
+        if (D == 3 && c.tier < 2) break;
+        if (!((cin >> T.tB[tt]) & 1u)) continue;
+        const int ff = tfield<D>(cf, tt), gf = tfield<D>(cg, tt);
+        if (crit_c(ff) == crit_c(gf)) continue;
+        Verts V = cell_verts<D>(c.G, x, y, z, 2, tt);
+        uint32_t t;
+        if (crit_c(gf)) {
+            t = ff == 1 ? V.id[lowest_of(V, c.f)]
+                        : vid(c.G, x + T.tcof_v[tt][ff - 2][0], y + T.tcof_v[tt][ff - 2][1], z + T.tcof_v[tt][ff - 2][2]);
+        } else {
+            t = gf >= 2 ? V.id[lowest_of(V, c.f)] : fn_down_target<D>(c, x, y, z, 2, tt, V);
+        }
+        add_case<D>(c, t, V);
+    }
+#pragma unroll 1
+    for (int k = 0; k < T.NK; k++) {
+        if (!((cin >> 7) & 1u)) break;
+        const int ff = kfield<D>(cf, k), gf = kfield<D>(cg, k);
+        if (crit_c(ff) == crit_c(gf)) continue;
+        Verts V = cell_verts<D>(c.G, x, y, z, 3, k);
+        const uint32_t t = crit_c(gf) ? V.id[lowest_of(V, c.f)] : fn_down_target<D>(c, x, y, z, 3, k, V);
+        add_case<D>(c, t, V);
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// edit (Eq. 2) and dirty-anchor marking
+// ------------------------------------------------------------------------------------
+MSC_HD inline float clamp_base(float f, float fh, float xi)
+{
+    const float lb = sub_ru(f, xi), ub = add_rd(f, xi);
+    return fh < lb ? lb : (fh > ub ? ub : fh);
+}
+
+// anchors whose code reads the value at v: v - (corner + neighbour offset)
+template <int D> MSC_HD inline void mark_dirty(const Ctx &c, uint32_t v)
+{
+    int x, y, z;
+    coords(c.G, v, x, y, z);
+    constexpr int ZL = D == 3 ? -1 : 0, ZH = D == 3 ? 2 : 0;
+#pragma unroll
+    for (int dz = ZL; dz <= ZH; dz++)
+#pragma unroll
+        for (int dy = -1; dy <= 2; dy++)
+#pragma unroll
+            for (int dx = -1; dx <= 2; dx++) {
+                const bool lowcube = dx <= 1 && dy <= 1 && dz <= 1;
+                const bool highcube = dx >= 0 && dy >= 0 && dz >= 0;
+                if (!lowcube && !highcube) continue;
+                const int px = x - dx, py = y - dy, pz = z - dz;
+                if (!inside(c.G, px, py, pz)) continue;
+                const uint32_t p = vid(c.G, px, py, pz);
+                if (!test_and_set(c.Dbits, p)) {
+                    const unsigned long long i = a_add(&c.cnt->nD, 1ull);
+                    c.Dlist[i] = p;
+                }
+            }
+}
+
+// item i < nX: restore Xlist[i] to f; else quantised step of Tlist[i - nX] unless it is
+// also restored (Eq. 2: one step of xi / 2^q_max while q < q_max and the value stays
+// >= f - xi, otherwise the floor f - xi)
+template <int D> MSC_HD inline void edit_item(const Ctx &c, uint32_t i, uint32_t nX)
+{
+    uint32_t v;
+    if (i < nX) {
+        v = c.Xlist[i];
+        if (c.state[v] == ST_EXACT) return;
+        c.g[v] = ld(c.f + v);
+        c.state[v] = ST_EXACT;
+    } else {
+        v = c.Tlist[i - nX];
+        if ((c.Xbits[v >> 5] >> (v & 31)) & 1u) return;
+        const uint8_t st = c.state[v];
+        if (st > c.qmax) return;
+        const float fv = ld(c.f + v);
+        const float lb = sub_ru(fv, c.xi);
+        bool done = false;
+        if (st < c.qmax) {
+            const float fc = clamp_base(fv, ld(c.fhat + v), c.xi);
+            const float cand = sub_rn(fc, mul_rn((float)(st + 1), c.step));
+            if (cand >= lb) { c.g[v] = cand; c.state[v] = (uint8_t)(st + 1); done = true; }
+        }
+        if (!done) { c.g[v] = lb; c.state[v] = ST_FLOOR; }
+    }
+    a_add(&c.cnt->nchanged, 1ull);
+    mark_dirty<D>(c, v);
+}
+
+// re-evaluate a dirty anchor and keep it in the mismatch list if its code differs from f's
+template <int D> MSC_HD inline void refresh_anchor(const Ctx &c, uint32_t p)
+{
+    c.code_g[p] = anchor_code<D>(c.g, c.G, p);
+}
+
+MSC_HD inline void keep_if_mismatch(const Ctx &c, uint32_t p)
+{
+    if (ld(c.code_f + p) == c.code_g[p]) return;
+    if (a_exch(c.stamp + p, c.tag) == c.tag) return;
+    const unsigned long long i = a_add(&c.cnt->nM, 1ull);
+    c.Mnext[i] = p;
+}
+
+// ------------------------------------------------------------------------------------
+// S-pass (Sec. 4.4): walks along the separatrices of f, checked against g's gradient
+// ------------------------------------------------------------------------------------
+// descending path end (a minimum) of the V-path through vertex u in a gradient code
+template <int D> MSC_HD inline uint32_t desc_end(const uint64_t *code, const Grid &G, uint32_t u)
+{
+    const Tab<D> &T = rt_tab<D>();
+    int x, y, z;
+    coords(G, u, x, y, z);
+    for (uint32_t s = 0; s <= G.n; s++) {
+        const int f = vfield<D>(ld(code + u));
+        if (f == 15) return u;
+        x += T.nb[f][0]; y += T.nb[f][1]; z += T.nb[f][2];
+        u = vid(G, x, y, z);
+    }
+    return 0xFFFFFFFFu;
+}
+
+template <int D> MSC_HD inline void desc_walk(const Ctx &c, uint32_t u)
+{
+    const Tab<D> &T = rt_tab<D>();
+    int x, y, z;
+    coords(c.G, u, x, y, z);
+    for (uint32_t s = 0; s <= c.G.n; s++) {
+        if (test_and_set(c.vis_v, u)) return;
+        const int ff = vfield<D>(ld(c.code_f + u));
+        if (ff == 15) return;
+        const int wx = x + T.nb[ff][0], wy = y + T.nb[ff][1], wz = z + T.nb[ff][2];
+        const uint32_t w = vid(c.G, wx, wy, wz);
+        if (vfield<D>(c.code_g[u]) != ff) {
+            if (c.tier == 3 && desc_end<D>(c.code_f, c.G, u) == desc_end<D>(c.code_g, c.G, u)) return;
+            Verts V;
+            V.n = 0;
+            vpush(V, c.G, x, y, z);
+            vpush(V, c.G, wx, wy, wz);
+            add_case<D>(c, w, V);
+            return;
+        }
+        x = wx; y = wy; z = wz; u = w;
+    }
+}
+
+// top cells: tets (3D) or triangles (2D); id = anchor * NTOP + type
+template <int D> MSC_HD inline int top_field(uint64_t code, int t) { return D == 3 ? kfield<D>(code, t) : tfield<D>(code, t); }
+template <int D> MSC_HD inline Verts top_verts(const Grid &G, int x, int y, int z, int t)
+{
+    return cell_verts<D>(G, x, y, z, D == 3 ? 3 : 2, t);
+}
+template <int D> MSC_HD inline bool top_exists(const Grid &G, int x, int y, int z, int t)
+{
+    const Tab<D> &T = rt_tab<D>();
+    const int top = D == 3 ? 7 : T.tB[t];
+    return inside(G, x, y, z) && inside(G, x + (top & 1), y + ((top >> 1) & 1), z + ((top >> 2) & 1));
+}
+
+// one step of an ascending V-path: top cell (x,y,z,t) paired down (in the gradient "code"
+// of field "vals") with its highest facet alpha; returns false if the cell is critical.
+// Out: alpha's anchor/type, the index of the top cell in alpha's cofacet list, and the
+// corner index (0..D) of the top cell's lowest vertex.
+template <int D>
+MSC_HD inline bool asc_facet(const Grid &G, const float *vals, int x, int y, int z, int t, const uint64_t *code,
+                             int &fx, int &fy, int &fz, int &ft, int &ib, int &jlow)
+{
+    const Tab<D> &T = rt_tab<D>();
+    if (top_field<D>(ld(code + vid(G, x, y, z)), t) == 0) return false;
+    Verts V = top_verts<D>(G, x, y, z, t);
+    jlow = lowest_of(V, vals);
+    int corner;
+    if (D == 3) corner = jlow == 0 ? 0 : (jlow == 1 ? T.kA[t] : (jlow == 2 ? T.kB[t] : 7));
+    else corner = jlow == 0 ? 0 : (jlow == 1 ? T.tA[t] : T.tB[t]);
+    int j = 0, ox, oy, oz;
+    if (D == 3) {
+        for (int q = 0; q < 4; q++) if (T.kfac_opp[t][q] == corner) j = q;
+        ox = T.kfac_anc[t][j][0]; oy = T.kfac_anc[t][j][1]; oz = T.kfac_anc[t][j][2]; ft = T.kfac_type[t][j];
+    } else {
+        for (int q = 0; q < 3; q++) if (T.tfac_opp[t][q] == corner) j = q;
+        ox = T.tfac_anc[t][j][0]; oy = T.tfac_anc[t][j][1]; oz = T.tfac_anc[t][j][2]; ft = T.tfac_type[t][j];
+    }
+    fx = x + ox; fy = y + oy; fz = z + oz;
+    ib = -1;
+    const int ncof = D == 3 ? T.ntcof[ft] : T.necof[ft];
+    for (int i = 0; i < ncof; i++) {
+        const int *an = D == 3 ? T.tcof_anc[ft][i] : T.ecof_anc[ft][i];
+        const int ty = D == 3 ? T.tcof_type[ft][i] : T.ecof_type[ft][i];
+        if (an[0] == -ox && an[1] == -oy && an[2] == -oz && ty == t) ib = i;
+    }
+    return true;
+}
+
+// the other top cofacet of facet (fx,fy,fz,ft) than cofacet index ib; false at the boundary
+template <int D>
+MSC_HD inline bool asc_next(const Grid &G, int fx, int fy, int fz, int ft, int ib, int &x, int &y, int &z, int &t)
+{
+    const Tab<D> &T = rt_tab<D>();
+    const int ncof = D == 3 ? T.ntcof[ft] : T.necof[ft];
+    if (ncof != 2) return false;
+    const int io = 1 - ib;
+    const int *an = D == 3 ? T.tcof_anc[ft][io] : T.ecof_anc[ft][io];
+    x = fx + an[0]; y = fy + an[1]; z = fz + an[2];
+    t = D == 3 ? T.tcof_type[ft][io] : T.ecof_type[ft][io];
+    return top_exists<D>(G, x, y, z, t);
+}
+
+// field of a (D-1)-cell in a code
+template <int D> MSC_HD inline int facet_field(uint64_t code, int ft) { return D == 3 ? tfield<D>(code, ft) : efield<D>(code, ft); }
+
+// end of the ascending path entering top cell (x,y,z,t): (dim << 40) | cell id, where the
+// cell id is anchor * NTOP + type for a maximum and anchor * 16 + type for a boundary facet
+template <int D>
+MSC_HD inline unsigned long long asc_end(const Grid &G, const float *vals, const uint64_t *code, int x, int y, int z, int t)
+{
+    const Tab<D> &T = rt_tab<D>();
+    for (uint32_t s = 0; s <= G.n * (uint32_t)T.NTOP; s++) {
+        int fx, fy, fz, ft, ib, jl;
+        if (!asc_facet<D>(G, vals, x, y, z, t, code, fx, fy, fz, ft, ib, jl))
+            return ((unsigned long long)D << 40) | ((unsigned long long)vid(G, x, y, z) * T.NTOP + t);
+        if (!asc_next<D>(G, fx, fy, fz, ft, ib, x, y, z, t))
+            return ((unsigned long long)(D - 1) << 40) | ((unsigned long long)vid(G, fx, fy, fz) * 16 + ft);
+    }
+    return ~0ull;
+}
+
+template <int D> MSC_HD inline void asc_walk(const Ctx &c, uint32_t beta)
+{
+    const Tab<D> &T = rt_tab<D>();
+    int x, y, z, t = (int)(beta % T.NTOP);
+    coords(c.G, beta / T.NTOP, x, y, z);
+    for (uint32_t s = 0; s <= c.G.n * (uint32_t)T.NTOP; s++) {
+        if (test_and_set(c.vis_top, vid(c.G, x, y, z) * T.NTOP + t)) return;
+        int fx, fy, fz, ft, ib, jl;
+        if (!asc_facet<D>(c.G, c.f, x, y, z, t, c.code_f, fx, fy, fz, ft, ib, jl)) return;   // maximum
+        const int gf = facet_field<D>(c.code_g[vid(c.G, fx, fy, fz)], ft);
+        if (gf != 2 + ib) {
+            if (c.tier == 3 && asc_end<D>(c.G, c.f, c.code_f, x, y, z, t) == asc_end<D>(c.G, c.g, c.code_g, x, y, z, t))
+                return;
+            Verts V = top_verts<D>(c.G, x, y, z, t);
+            add_case<D>(c, V.id[jl], V);
+            return;
+        }
+        if (!asc_next<D>(c.G, fx, fy, fz, ft, ib, x, y, z, t)) return;   // leaves the domain
+    }
+}
+
+// saddle-saddle connectors (3D, tier 4): depth-first over triangles reached from a
+// 2-saddle through edges paired upward in f; pairs missing from g's gradient are the
+// troublemakers; a local stack spills to a global queue when full
+constexpr int SS_STACK = 24;
+
+MSC_HD inline void ss_push_global(const Ctx &c, uint32_t tri, uint32_t entry)
+{
+    const unsigned long long i = a_add(&c.cnt->novf, 1ull);
+    if (i < c.ovf_cap) { c.ovf_out[2 * i] = tri; c.ovf_out[2 * i + 1] = entry; }
+    else a_add(&c.cnt->err, 1ull);
+}
+
+// start: (triangle id = anchor * 12 + type, entry edge id = anchor * 7 + type or ~0u);
+// fresh seeds are marked visited here, spilled items were marked when first pushed
+MSC_HD inline void ss_walk(const Ctx &c, uint32_t tri0, uint32_t entry0, bool seed)
+{
+    const Tab<3> &T = rt_tab<3>();
+    if (seed && test_and_set(c.vis_tri, tri0)) return;
+    uint32_t st_tri[SS_STACK], st_ent[SS_STACK];
+    int sp = 0;
+    st_tri[sp] = tri0; st_ent[sp] = entry0; sp++;
+    while (sp > 0) {
+        sp--;
+        const uint32_t tri = st_tri[sp], entry = st_ent[sp];
+        const int tt = (int)(tri % 12);
+        int x, y, z;
+        coords(c.G, tri / 12, x, y, z);
+        for (int j = 0; j < 3; j++) {
+            const int ex = x + T.tfac_anc[tt][j][0], ey = y + T.tfac_anc[tt][j][1], ez = z + T.tfac_anc[tt][j][2];
+            const int et = T.tfac_type[tt][j];
+            const uint32_t ea = vid(c.G, ex, ey, ez), eid = ea * 7 + (uint32_t)et;
+            if (eid == entry) continue;
+            const int ef = efield<3>(ld(c.code_f + ea), et);
+            if (ef == 0) continue;                                   // 1-saddle: end
+            const int eg = efield<3>(c.code_g[ea], et);
+            if (ef == 1) {                                           // dead end in f
+                if (eg != 1) {
+                    Verts V = cell_verts<3>(c.G, ex, ey, ez, 1, et);
+                    add_case<3>(c, V.id[lowest_of(V, c.f)], V);
+                }
+                continue;
+            }
+            const int i = ef - 2;
+            const int tx = ex + T.ecof_anc[et][i][0], ty = ey + T.ecof_anc[et][i][1], tz = ez + T.ecof_anc[et][i][2];
+            const int t2 = T.ecof_type[et][i];
+            if (eg != ef) {
+                Verts V = cell_verts<3>(c.G, tx, ty, tz, 2, t2);
+                const uint32_t tv = vid(c.G, ex + T.ecof_v[et][i][0], ey + T.ecof_v[et][i][1], ez + T.ecof_v[et][i][2]);
+                add_case<3>(c, tv, V);
+                continue;
+            }
+            const uint32_t tri2 = vid(c.G, tx, ty, tz) * 12 + (uint32_t)t2;
+            if (tri2 == tri) continue;
+            if (test_and_set(c.vis_tri, tri2)) continue;
+            if (sp < SS_STACK) { st_tri[sp] = tri2; st_ent[sp] = eid; sp++; }
+            else ss_push_global(c, tri2, eid);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// seeds of the separatrices of f (once per original field)
+// ------------------------------------------------------------------------------------
+// kind 0: descending seeds (both vertices of every critical edge); kind 1: ascending seeds
+// (top cofacets of every critical (D-1)-cell); kind 2: 2-saddle triangles (3D)
+template <int D> MSC_HD inline void seeds_anchor(const uint64_t *code, const Grid &G, uint32_t p, int kind,
+                                                 uint32_t *out, unsigned long long *count, unsigned long long cap)
+{
+    const Tab<D> &T = rt_tab<D>();
+    int x, y, z;
+    coords(G, p, x, y, z);
+    const unsigned cin = corner_mask<D>(G, x, y, z);
+    const uint64_t cf = ld(code + p);
+    auto emit = [&](uint32_t v) {
+        const unsigned long long i = a_add(count, 1ull);
+        if (out && i < cap) out[i] = v;
+    };
+    if (kind == 0 || (D == 2 && kind == 1)) {
+        for (int e = 0; e < T.NE; e++) {
+            if (!((cin >> (e + 1)) & 1u) || efield<D>(cf, e) != 0) continue;
+            if (kind == 0) {
+                emit(p);
+                const int A = e + 1;
+                emit(vid(G, x + (A & 1), y + ((A >> 1) & 1), z + ((A >> 2) & 1)));
+            } else {
+                for (int i = 0; i < T.necof[e]; i++) {
+                    const int bx = x + T.ecof_anc[e][i][0], by = y + T.ecof_anc[e][i][1], bz = z + T.ecof_anc[e][i][2];
+                    const int bt = T.ecof_type[e][i];
+                    if (top_exists<D>(G, bx, by, bz, bt)) emit(vid(G, bx, by, bz) * T.NTOP + bt);
+                }
+            }
+        }
+        return;
+    }
+    if constexpr (D == 3) {
+    for (int tt = 0; tt < T.NT; tt++) {
+        if (!((cin >> T.tB[tt]) & 1u) || tfield<D>(cf, tt) != 0) continue;
+        if (kind == 2) { emit(p * 12 + tt); continue; }
+        for (int i = 0; i < T.ntcof[tt]; i++) {
+            const int bx = x + T.tcof_anc[tt][i][0], by = y + T.tcof_anc[tt][i][1], bz = z + T.tcof_anc[tt][i][2];
+            const int bt = T.tcof_type[tt][i];
+            if (top_exists<D>(G, bx, by, bz, bt)) emit(vid(G, bx, by, bz) * T.NTOP + bt);
+        }
+    }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// decoding a code into canonical vertex tuples (introspection and verification)
+// ------------------------------------------------------------------------------------
+MSC_HD inline void sort4(int64_t *r, int n)
+{
+    for (int i = 1; i < n; i++)
+        for (int j = i; j > 0 && r[j - 1] > r[j]; j--) { int64_t t = r[j]; r[j] = r[j - 1]; r[j - 1] = t; }
+    for (int i = n; i < 4; i++) r[i] = -1;
+}
+
+// pairs (L, U) with L owned by anchor p and paired upward: rows of 8 ids
+template <int D> MSC_HD inline void decode_pairs(const uint64_t *code, const Grid &G, uint32_t p, int64_t *rows,
+                                                 unsigned long long *count, unsigned long long cap)
+{
+    const Tab<D> &T = rt_tab<D>();
+    int x, y, z;
+    coords(G, p, x, y, z);
+    const unsigned cin = corner_mask<D>(G, x, y, z);
+    const uint64_t cf = ld(code + p);
+    auto emit = [&](const Verts &L, int ex, int ey, int ez) {
+        const unsigned long long i = a_add(count, 1ull);
+        if (!rows || i >= cap) return;
+        int64_t *r = rows + 8 * i;
+        for (int k = 0; k < L.n; k++) { r[k] = L.id[k]; r[4 + k] = L.id[k]; }
+        sort4(r, L.n);
+        r[4 + L.n] = vid(G, ex, ey, ez);
+        sort4(r + 4, L.n + 1);
+    };
+    const int vf = vfield<D>(cf);
+    if (vf != 15) emit(cell_verts<D>(G, x, y, z, 0, 0), x + T.nb[vf][0], y + T.nb[vf][1], z + T.nb[vf][2]);
+    for (int e = 0; e < T.NE; e++) {
+        const int f = efield<D>(cf, e);
+        if (!((cin >> (e + 1)) & 1u) || f < 2) continue;
+        emit(cell_verts<D>(G, x, y, z, 1, e), x + T.ecof_v[e][f - 2][0], y + T.ecof_v[e][f - 2][1], z + T.ecof_v[e][f - 2][2]);
+    }
+    for (int tt = 0; tt < T.NT; tt++) {
+        const int f = tfield<D>(cf, tt);
+        if (!((cin >> T.tB[tt]) & 1u) || f < 2) continue;
+        emit(cell_verts<D>(G, x, y, z, 2, tt), x + T.tcof_v[tt][f - 2][0], y + T.tcof_v[tt][f - 2][1], z + T.tcof_v[tt][f - 2][2]);
+    }
+}
+
+// critical cells owned by anchor p: rows of 4 ids + dimension.  If ref != nullptr, count
+// instead the cells whose criticality differs from ref's (fp: critical only in code,
+// fn: critical only in ref) into cnt->rep[dim] / rep[4 + dim]
+template <int D> MSC_HD inline void decode_critical(const uint64_t *code, const uint64_t *ref, const Grid &G, uint32_t p,
+                                                    int64_t *rows, int32_t *dims, unsigned long long *count,
+                                                    unsigned long long cap, Counters *cnt)
+{
+    const Tab<D> &T = rt_tab<D>();
+    int x, y, z;
+    coords(G, p, x, y, z);
+    const unsigned cin = corner_mask<D>(G, x, y, z);
+    const uint64_t cf = ld(code + p);
+    const uint64_t rf = ref ? ld(ref + p) : 0;
+    auto handle = [&](bool crit, bool rcrit, int kind, int t) {
+        if (ref) {
+            if (crit && !rcrit) a_add(&cnt->rep[kind], 1ull);
+            if (!crit && rcrit) a_add(&cnt->rep[4 + kind], 1ull);
+            return;
+        }
+        if (!crit) return;
+        const unsigned long long i = a_add(count, 1ull);
+        if (!rows || i >= cap) return;
+        Verts V = cell_verts<D>(G, x, y, z, kind, t);
+        for (int k = 0; k < V.n; k++) rows[4 * i + k] = V.id[k];
+        sort4(rows + 4 * i, V.n);
+        dims[i] = kind;
+    };
+    handle(vfield<D>(cf) == 15, vfield<D>(rf) == 15, 0, 0);
+    for (int e = 0; e < T.NE; e++)
+        if ((cin >> (e + 1)) & 1u) handle(efield<D>(cf, e) == 0, efield<D>(rf, e) == 0, 1, e);
+    for (int tt = 0; tt < T.NT; tt++)
+        if ((cin >> T.tB[tt]) & 1u) handle(tfield<D>(cf, tt) == 0, tfield<D>(rf, tt) == 0, 2, tt);
+    for (int k = 0; k < T.NK; k++)
+        if ((cin >> 7) & 1u) handle(kfield<D>(cf, k) == 0, kfield<D>(rf, k) == 0, 3, k);
+}
+
+}  // namespace msc

@@ -1,0 +1,1137 @@
+// libmsc: kernels, fix-loop driver and the C ABI declared in include/msc.h.
+//
+// Device layout of one job (one original field f, N vertices):
+//   f, f_hat, g           float[N]        resident for the job's lifetime
+//   state                 uint8[N]        0..q_max quantised count, 0xF0 floor, 0xF1 exact
+//   code_f, code_g        uint64[N]       packed gradient of the cells each anchor owns
+//   T/X/D bitsets         uint32[N/32]    targets, restores, dirty anchors (cleared per round)
+//   T/X/D lists, M lists  uint32[N]       the same sets compacted, mismatch anchors
+//   visited bitsets       N, 6N (3D) or 2N, 12N (3D) bits for the separatrix walks
+// The loop is incremental: after the initial dense gradient of g, a round re-evaluates only
+// anchors whose window contains an edited vertex, and targets only anchors whose code
+// differs from f's.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/msc.h"
+#include "msc_core.cuh"
+
+using namespace msc;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+msc_status fail(msc_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            if (e_ == cudaErrorMemoryAllocation) return fail(MSC_ERR_OOM, "%s: %s", #call, cudaGetErrorString(e_)); \
+            if (e_ == cudaErrorNoKernelImageForDevice || e_ == cudaErrorNoDevice ||            \
+                e_ == cudaErrorInsufficientDriver)                                            \
+                return fail(MSC_ERR_NO_DEVICE, "%s: %s", #call, cudaGetErrorString(e_));        \
+            return fail(MSC_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+        }                                                                                     \
+    } while (0)
+
+#define CKS(st)                                  \
+    do {                                         \
+        msc_status s_ = (st);                    \
+        if (s_ != MSC_OK) return s_;             \
+    } while (0)
+
+constexpr int TPB = 256;
+
+int grid_for(unsigned long long n)
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 132;
+    }
+    unsigned long long b = (n + TPB - 1) / TPB;
+    unsigned long long cap = (unsigned long long)sms * 8;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+// ------------------------------------------------------------------------------------
+// kernels
+// ------------------------------------------------------------------------------------
+#define GRID_STRIDE(i, n) for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < (n); \
+                               i += (unsigned long long)gridDim.x * blockDim.x)
+
+__global__ void k_count_nonfinite(const float *v, uint32_t n, unsigned long long *bad)
+{
+    unsigned long long local = 0;
+    GRID_STRIDE(i, n) local += !isfinite(v[i]);
+    if (local) atomicAdd(bad, local);
+}
+
+// dense gradient of a field; with ref != nullptr also list the anchors whose code differs
+template <int D>
+__global__ void __launch_bounds__(TPB) k_eval_dense(const float *v, Grid G, uint64_t *out, const uint64_t *ref,
+                                                    uint32_t *list, unsigned long long *nlist)
+{
+    GRID_STRIDE(p, G.n)
+    {
+        const uint64_t code = anchor_code<D>(v, G, (uint32_t)p);
+        out[p] = code;
+        if (ref && code != __ldg(ref + p)) list[atomicAdd(nlist, 1ull)] = (uint32_t)p;
+    }
+}
+
+// g = f_hat re-clamped into [f - xi, f + xi] (bounds rounded inward), every vertex unedited
+__global__ void k_init_g(const float *f, const float *fh, float *g, uint8_t *state, uint32_t n, float xi)
+{
+    GRID_STRIDE(i, n)
+    {
+        g[i] = clamp_base(f[i], fh[i], xi);
+        state[i] = 0;
+    }
+}
+
+template <int D> __global__ void __launch_bounds__(TPB) k_ctargets(Ctx c, const uint32_t *M, const unsigned long long *nM)
+{
+    const unsigned long long n = *nM;
+    GRID_STRIDE(i, n) ctargets_anchor<D>(c, M[i]);
+}
+
+template <int D> __global__ void k_edit(Ctx c)
+{
+    const uint32_t nX = (uint32_t)c.cnt->nX, nT = (uint32_t)c.cnt->nT;
+    GRID_STRIDE(i, (unsigned long long)nX + nT) edit_item<D>(c, (uint32_t)i, nX);
+}
+
+template <int D> __global__ void __launch_bounds__(TPB) k_refresh(Ctx c)
+{
+    const unsigned long long n = c.cnt->nD;
+    GRID_STRIDE(i, n) refresh_anchor<D>(c, c.Dlist[i]);
+}
+
+__global__ void k_rebuild(Ctx c, const uint32_t *Mcur, const unsigned long long *nMcur, unsigned long long *nMnext)
+{
+    const unsigned long long a = *nMcur, b = c.cnt->nD;
+    GRID_STRIDE(i, a + b)
+    {
+        const uint32_t p = i < a ? Mcur[i] : c.Dlist[i - a];
+        if (__ldg(c.code_f + p) == c.code_g[p]) continue;
+        if (atomicExch(c.stamp + p, c.tag) == c.tag) continue;
+        c.Mnext[atomicAdd(nMnext, 1ull)] = p;
+    }
+}
+
+__global__ void k_clear(Ctx c)
+{
+    const unsigned long long nT = c.cnt->nT, nX = c.cnt->nX, nD = c.cnt->nD;
+    GRID_STRIDE(i, nT + nX + nD)
+    {
+        if (i < nT) c.Tbits[c.Tlist[i] >> 5] = 0;
+        else if (i < nT + nX) c.Xbits[c.Xlist[i - nT] >> 5] = 0;
+        else c.Dbits[c.Dlist[i - nT - nX] >> 5] = 0;
+    }
+}
+
+template <int D> __global__ void k_desc(Ctx c, const uint32_t *seeds, uint32_t n)
+{
+    GRID_STRIDE(i, n) desc_walk<D>(c, seeds[i]);
+}
+
+template <int D> __global__ void k_asc(Ctx c, const uint32_t *seeds, uint32_t n)
+{
+    GRID_STRIDE(i, n) asc_walk<D>(c, seeds[i]);
+}
+
+__global__ void k_ss_seed(Ctx c, const uint32_t *seeds, uint32_t n)
+{
+    GRID_STRIDE(i, n) ss_walk(c, seeds[i], 0xFFFFFFFFu, true);
+}
+
+__global__ void k_ss_spill(Ctx c, const uint32_t *items, uint32_t n)
+{
+    GRID_STRIDE(i, n) ss_walk(c, items[2 * i], items[2 * i + 1], false);
+}
+
+template <int D>
+__global__ void k_seeds(const uint64_t *code, Grid G, int kind, uint32_t *out, unsigned long long *count, unsigned long long cap)
+{
+    GRID_STRIDE(p, G.n) seeds_anchor<D>(code, G, (uint32_t)p, kind, out, count, cap);
+}
+
+template <int D>
+__global__ void k_decode_pairs(const uint64_t *code, Grid G, int64_t *rows, unsigned long long *count, unsigned long long cap)
+{
+    GRID_STRIDE(p, G.n) decode_pairs<D>(code, G, (uint32_t)p, rows, count, cap);
+}
+
+template <int D>
+__global__ void k_decode_crit(const uint64_t *code, const uint64_t *ref, Grid G, int64_t *rows, int32_t *dims,
+                              unsigned long long *count, unsigned long long cap, Counters *cnt)
+{
+    GRID_STRIDE(p, G.n) decode_critical<D>(code, ref, G, (uint32_t)p, rows, dims, count, cap, cnt);
+}
+
+// per-seed separatrix checks for verification (no sharing between seeds, so the counts
+// are per separatrix): rep[8]/rep[9] = separatrices with a pair missing from g's gradient,
+// rep[11]/rep[12] = separatrices whose end differs
+template <int D> __global__ void k_verify_desc(Ctx c, const uint32_t *seeds, uint32_t n)
+{
+    const Tab<D> &T = rt_tab<D>();
+    GRID_STRIDE(i, n)
+    {
+        uint32_t u = seeds[i];
+        int x, y, z;
+        coords(c.G, u, x, y, z);
+        bool bad = false;
+        for (uint32_t s = 0; s <= c.G.n; s++) {
+            const int ff = vfield<D>(__ldg(c.code_f + u));
+            if (ff == 15) break;
+            if (vfield<D>(c.code_g[u]) != ff) bad = true;
+            x += T.nb[ff][0]; y += T.nb[ff][1]; z += T.nb[ff][2];
+            u = vid(c.G, x, y, z);
+        }
+        if (bad) atomicAdd(&c.cnt->rep[8], 1ull);
+        if (desc_end<D>(c.code_f, c.G, seeds[i]) != desc_end<D>(c.code_g, c.G, seeds[i])) atomicAdd(&c.cnt->rep[11], 1ull);
+    }
+}
+
+template <int D> __global__ void k_verify_asc(Ctx c, const uint32_t *seeds, uint32_t n)
+{
+    GRID_STRIDE(i, n)
+    {
+        const uint32_t beta = seeds[i];
+        int x, y, z, t = (int)(beta % Tab<D>::NTOP);
+        coords(c.G, beta / Tab<D>::NTOP, x, y, z);
+        const int x0 = x, y0 = y, z0 = z, t0 = t;
+        bool bad = false;
+        for (uint32_t s = 0; s <= c.G.n * (uint32_t)Tab<D>::NTOP; s++) {
+            int fx, fy, fz, ft, ib, jl;
+            if (!asc_facet<D>(c.G, c.f, x, y, z, t, c.code_f, fx, fy, fz, ft, ib, jl)) break;
+            if (facet_field<D>(c.code_g[vid(c.G, fx, fy, fz)], ft) != 2 + ib) bad = true;
+            if (!asc_next<D>(c.G, fx, fy, fz, ft, ib, x, y, z, t)) break;
+        }
+        if (bad) atomicAdd(&c.cnt->rep[9], 1ull);
+        if (asc_end<D>(c.G, c.f, c.code_f, x0, y0, z0, t0) != asc_end<D>(c.G, c.g, c.code_g, x0, y0, z0, t0))
+            atomicAdd(&c.cnt->rep[12], 1ull);
+    }
+}
+
+__global__ void k_max_abs_err(const float *f, const float *g, uint32_t n, unsigned long long *out)
+{
+    double m = 0.0;
+    GRID_STRIDE(i, n) m = fmax(m, fabs((double)g[i] - (double)f[i]));
+    for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+// stored form of the edits (Sec. 4.7): q for quantised vertices whose base value needed no
+// re-clamping, MSC_QMAP_LOSSLESS otherwise; per-block counts of lossless vertices
+__global__ void k_qmap(const float *f, const float *fh, const uint8_t *state, uint32_t n, float xi, int qmax,
+                       uint8_t *qmap, uint32_t *block_counts, unsigned long long *nquant)
+{
+    const unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    int lossless = 0, quant = 0;
+    if (i < n) {
+        const uint8_t st = state[i];
+        const float fc = clamp_base(f[i], fh[i], xi);
+        lossless = st > qmax || __float_as_uint(fc) != __float_as_uint(fh[i]);
+        quant = !lossless && st > 0;
+        qmap[i] = lossless ? (uint8_t)MSC_QMAP_LOSSLESS : st;
+    }
+    const int c = __syncthreads_count(lossless);
+    const int q = __syncthreads_count(quant);
+    if (threadIdx.x == 0) {
+        block_counts[blockIdx.x] = (uint32_t)c;
+        if (q) atomicAdd(nquant, (unsigned long long)q);
+    }
+}
+
+// exclusive scan of the per-block counts (one block)
+__global__ void k_scan_blocks(uint32_t *counts, uint32_t nb, unsigned long long *total)
+{
+    __shared__ uint32_t warp_sums[32];
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (uint32_t base = 0; base < nb; base += blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        const uint32_t v = i < nb ? counts[i] : 0;
+        uint32_t x = v;
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_sums[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            uint32_t s = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += y;
+            }
+            warp_sums[lane] = s;
+        }
+        __syncthreads();
+        const uint32_t before = (wid ? warp_sums[wid - 1] : 0) + x - v;
+        if (i < nb) counts[i] = carry + before;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry += before + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+// write the lossless vertices in ascending order
+__global__ void k_lossless_write(const uint8_t *qmap, const float *g, uint32_t n, const uint32_t *offsets,
+                                 uint64_t *idx, float *val)
+{
+    __shared__ uint32_t warp_sums[32];
+    const unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    const int flag = i < n && qmap[i] == MSC_QMAP_LOSSLESS;
+    const unsigned ballot = __ballot_sync(0xffffffffu, flag);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) warp_sums[wid] = __popc(ballot);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t s = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) { const uint32_t t = warp_sums[w]; warp_sums[w] = s; s += t; }
+    }
+    __syncthreads();
+    if (flag) {
+        const uint32_t pos = offsets[blockIdx.x] + warp_sums[wid] + __popc(ballot & ((1u << lane) - 1u));
+        idx[pos] = i;
+        val[pos] = g[i];
+    }
+}
+
+// decompression side: g = f_hat - fl(q * step) (one rounding each), lossless values scattered
+__global__ void k_apply_q(const float *fh, const uint8_t *qmap, uint32_t n, float step, float *g)
+{
+    GRID_STRIDE(i, n)
+    {
+        const uint8_t q = qmap[i];
+        g[i] = q == MSC_QMAP_LOSSLESS ? fh[i] : __fsub_rn(fh[i], __fmul_rn((float)q, step));
+    }
+}
+
+__global__ void k_apply_lossless(const uint64_t *idx, const float *val, uint64_t n, float *g)
+{
+    GRID_STRIDE(i, n) g[idx[i]] = val[i];
+}
+
+// ------------------------------------------------------------------------------------
+// host helpers
+// ------------------------------------------------------------------------------------
+template <class T> struct DevBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    cudaError_t alloc(size_t count)
+    {
+        if (count <= n && p) return cudaSuccess;
+        release();
+        cudaError_t e = cudaMalloc((void **)&p, (count ? count : 1) * sizeof(T));
+        if (e == cudaSuccess) n = count;
+        else p = nullptr;
+        return e;
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+};
+
+}  // namespace
+struct msc_handle;
+namespace {
+void kbeg(msc_handle *h, int cls, cudaStream_t s);
+void kend(msc_handle *h, cudaStream_t s);
+#define KL(h, cls, s, ...)   \
+    do {                     \
+        kbeg(h, cls, s);     \
+        __VA_ARGS__;         \
+        kend(h, s);          \
+    } while (0)
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+msc_status check_dims(int nx, int ny, int nz)
+{
+    if (nx < 2 || ny < 2 || nz < 1) return fail(MSC_ERR_INVALID_ARG, "dims must satisfy nx, ny >= 2 and nz >= 1 (got %d %d %d)", nx, ny, nz);
+    const unsigned long long n = (unsigned long long)nx * ny * nz;
+    if (n >= (1ull << 31)) return fail(MSC_ERR_INVALID_ARG, "grid too large: %llu vertices (limit 2^31)", n);
+    // per-anchor cell ids (anchor * 12 + type) must fit in 32 bits
+    if (nz > 1 && n * 12ull >= (1ull << 32)) return fail(MSC_ERR_INVALID_ARG, "3D grid too large for 32-bit cell ids");
+    return MSC_OK;
+}
+
+msc_status device_ready()
+{
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        return fail(MSC_ERR_NO_DEVICE, "no CUDA device available (%s)", cudaGetErrorString(e));
+    }
+    return MSC_OK;
+}
+
+// copy (host or device) input to a device buffer and check all values are finite
+msc_status upload_field(msc_handle *h, const float *src, size_t n, float *dst, unsigned long long *bad_dev, cudaStream_t s,
+                        const char *what)
+{
+    if (!src) return fail(MSC_ERR_INVALID_ARG, "%s is NULL", what);
+    CK(cudaMemcpyAsync(dst, src, n * sizeof(float), is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(bad_dev, 0, sizeof(unsigned long long), s));
+    KL(h, MSC_K_OTHER, s, k_count_nonfinite<<<grid_for(n), TPB, 0, s>>>(dst, (uint32_t)n, bad_dev));
+    CK(cudaGetLastError());
+    unsigned long long bad = 0;
+    CK(cudaMemcpyAsync(&bad, bad_dev, sizeof bad, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (bad) return fail(MSC_ERR_INVALID_ARG, "%s has %llu non-finite values", what, bad);
+    return MSC_OK;
+}
+
+void fill_defaults(msc_options *o)
+{
+    o->tier = 4;
+    o->q_max = 6;
+    o->max_iters = 100000;
+    o->exact_fallback = 1;
+    o->tile_x = o->tile_y = o->tile_z = 0;
+    o->stream = nullptr;
+    o->record_trace = 0;
+    o->profile = 0;
+}
+
+msc_status check_options(const msc_options *o)
+{
+    if (o->tier < 1 || o->tier > 4) return fail(MSC_ERR_INVALID_ARG, "tier must be 1..4 (got %d)", o->tier);
+    if (o->q_max < 1 || o->q_max > 7) return fail(MSC_ERR_INVALID_ARG, "q_max must be 1..7 (got %d)", o->q_max);
+    if (o->max_iters < 0) return fail(MSC_ERR_INVALID_ARG, "max_iters must be >= 0");
+    return MSC_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------
+// the handle
+// ------------------------------------------------------------------------------------
+struct msc_handle {
+    Grid G{};
+    int D = 3;
+    DevBuf<float> f;
+    DevBuf<uint64_t> code_f;
+    DevBuf<uint32_t> seeds_desc, seeds_asc, seeds_ss;
+    uint32_t n_desc = 0, n_asc = 0, n_ss = 0;
+    // fix state (allocated on first use)
+    DevBuf<float> fhat, g;
+    DevBuf<uint8_t> state;
+    DevBuf<uint64_t> code_g;
+    DevBuf<uint32_t> Tbits, Xbits, Dbits, Tlist, Xlist, Dlist, M0, M1, stamp;
+    DevBuf<uint32_t> vis_v, vis_top, vis_tri, ovf0, ovf1;
+    DevBuf<Counters> cnt;
+    DevBuf<unsigned long long> nM;   // [2] counts of M0, M1; [2] scratch
+    uint32_t tag = 0;
+    bool fix_ready = false;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // launch statistics
+    bool prof_on = false;
+    unsigned long long launches[8] = {};
+    unsigned long long timed[8] = {};
+    double ms[8] = {};
+    struct Pend {
+        cudaEvent_t a, b;
+        int cls;
+    };
+    std::vector<Pend> pend;
+    std::vector<cudaEvent_t> pool;
+    ~msc_handle()
+    {
+        for (auto &p : pend) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+namespace {
+
+cudaEvent_t take_event(msc_handle *h)
+{
+    if (!h->pool.empty()) { cudaEvent_t e = h->pool.back(); h->pool.pop_back(); return e; }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void kbeg(msc_handle *h, int cls, cudaStream_t s)
+{
+    if (!h) return;
+    h->launches[cls]++;
+    if (!h->prof_on) return;
+    msc_handle::Pend p{take_event(h), take_event(h), cls};
+    cudaEventRecord(p.a, s);
+    h->pend.push_back(p);
+}
+
+void kend(msc_handle *h, cudaStream_t s)
+{
+    if (!h || !h->prof_on || h->pend.empty()) return;
+    cudaEventRecord(h->pend.back().b, s);
+}
+
+// resolve the timed launches of a finished call
+void prof_flush(msc_handle *h)
+{
+    for (auto &p : h->pend) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            h->ms[p.cls] += ms;
+            h->timed[p.cls]++;
+        }
+        h->pool.push_back(p.a);
+        h->pool.push_back(p.b);
+    }
+    h->pend.clear();
+    cudaGetLastError();
+}
+
+size_t words(size_t bits) { return (bits + 31) / 32; }
+
+msc_status alloc_fix_state(msc_handle *h)
+{
+    if (h->fix_ready) return MSC_OK;
+    const size_t n = h->G.n;
+    const int ntop = h->D == 3 ? 6 : 2;
+    CK(h->fhat.alloc(n));
+    CK(h->g.alloc(n));
+    CK(h->state.alloc(n));
+    CK(h->code_g.alloc(n));
+    CK(h->Tbits.alloc(words(n)));
+    CK(h->Xbits.alloc(words(n)));
+    CK(h->Dbits.alloc(words(n)));
+    CK(h->Tlist.alloc(n));
+    CK(h->Xlist.alloc(n));
+    CK(h->Dlist.alloc(n));
+    CK(h->M0.alloc(n));
+    CK(h->M1.alloc(n));
+    CK(h->stamp.alloc(n));
+    CK(h->vis_v.alloc(words(n)));
+    CK(h->vis_top.alloc(words(n * ntop)));
+    if (h->D == 3) {
+        CK(h->vis_tri.alloc(words(n * 12)));
+        CK(h->ovf0.alloc(2 * n + 2));
+        CK(h->ovf1.alloc(2 * n + 2));
+    }
+    CK(h->cnt.alloc(1));
+    CK(h->nM.alloc(4));
+    CK(cudaMemset(h->Tbits.p, 0, h->Tbits.n * 4));
+    CK(cudaMemset(h->Xbits.p, 0, h->Xbits.n * 4));
+    CK(cudaMemset(h->Dbits.p, 0, h->Dbits.n * 4));
+    CK(cudaMemset(h->stamp.p, 0, h->stamp.n * 4));
+    h->tag = 0;
+    h->fix_ready = true;
+    return MSC_OK;
+}
+
+Ctx make_ctx(msc_handle *h, int tier, int qmax, int exact_fallback, float xi)
+{
+    Ctx c{};
+    c.G = h->G;
+    c.tier = tier;
+    c.qmax = qmax;
+    c.exact_fallback = exact_fallback;
+    c.xi = xi;
+    c.step = xi / (float)(1 << qmax);
+    c.f = h->f.p;
+    c.fhat = h->fhat.p;
+    c.g = h->g.p;
+    c.state = h->state.p;
+    c.code_f = h->code_f.p;
+    c.code_g = h->code_g.p;
+    c.Tbits = h->Tbits.p; c.Xbits = h->Xbits.p; c.Dbits = h->Dbits.p;
+    c.Tlist = h->Tlist.p; c.Xlist = h->Xlist.p; c.Dlist = h->Dlist.p;
+    c.stamp = h->stamp.p;
+    c.vis_v = h->vis_v.p; c.vis_top = h->vis_top.p; c.vis_tri = h->vis_tri.p;
+    c.ovf_cap = (uint32_t)h->G.n + 1;
+    c.cnt = h->cnt.p;
+    return c;
+}
+
+template <int D> msc_status eval_dense(msc_handle *h, const float *v, Grid G, uint64_t *out, const uint64_t *ref,
+                                       uint32_t *list, unsigned long long *nlist, cudaStream_t s)
+{
+    KL(h, MSC_K_DENSE, s, k_eval_dense<D><<<grid_for(G.n), TPB, 0, s>>>(v, G, out, ref, list, nlist));
+    CK(cudaGetLastError());
+    return MSC_OK;
+}
+
+msc_status eval_dense_any(msc_handle *h, int D, const float *v, Grid G, uint64_t *out, const uint64_t *ref,
+                          uint32_t *list, unsigned long long *nlist, cudaStream_t s)
+{
+    return D == 3 ? eval_dense<3>(h, v, G, out, ref, list, nlist, s) : eval_dense<2>(h, v, G, out, ref, list, nlist, s);
+}
+
+template <int D> msc_status build_seeds(msc_handle *h, cudaStream_t s)
+{
+    DevBuf<unsigned long long> cnt;
+    CK(cnt.alloc(1));
+    DevBuf<uint32_t> *bufs[3] = {&h->seeds_desc, &h->seeds_asc, &h->seeds_ss};
+    uint32_t *ns[3] = {&h->n_desc, &h->n_asc, &h->n_ss};
+    for (int kind = 0; kind < (D == 3 ? 3 : 2); kind++) {
+        unsigned long long n = 0;
+        CK(cudaMemsetAsync(cnt.p, 0, sizeof n, s));
+        KL(h, MSC_K_OTHER, s, k_seeds<D><<<grid_for(h->G.n), TPB, 0, s>>>(h->code_f.p, h->G, kind, nullptr, cnt.p, 0));
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(&n, cnt.p, sizeof n, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        CK(bufs[kind]->alloc(n));
+        CK(cudaMemsetAsync(cnt.p, 0, sizeof n, s));
+        KL(h, MSC_K_OTHER, s, k_seeds<D><<<grid_for(h->G.n), TPB, 0, s>>>(h->code_f.p, h->G, kind, bufs[kind]->p, cnt.p, n));
+        CK(cudaGetLastError());
+        *ns[kind] = (uint32_t)n;
+    }
+    CK(cudaStreamSynchronize(s));
+    cnt.release();
+    return MSC_OK;
+}
+
+// one S-pass (Sec. 4.4) over the separatrices of f; counters accumulate in h->cnt
+template <int D> msc_status s_pass(msc_handle *h, const Ctx &c0, int tier, cudaStream_t s)
+{
+    Ctx c = c0;
+    CK(cudaMemsetAsync(h->vis_v.p, 0, h->vis_v.n * 4, s));
+    CK(cudaMemsetAsync(h->vis_top.p, 0, h->vis_top.n * 4, s));
+    if (h->n_desc) KL(h, MSC_K_SPASS, s, k_desc<D><<<grid_for(h->n_desc), TPB, 0, s>>>(c, h->seeds_desc.p, h->n_desc));
+    if (h->n_asc) KL(h, MSC_K_SPASS, s, k_asc<D><<<grid_for(h->n_asc), TPB, 0, s>>>(c, h->seeds_asc.p, h->n_asc));
+    CK(cudaGetLastError());
+    if (D == 3 && tier >= 4 && h->n_ss) {
+        CK(cudaMemsetAsync(h->vis_tri.p, 0, h->vis_tri.n * 4, s));
+        c.ovf_out = h->ovf0.p;
+        KL(h, MSC_K_SPASS, s, k_ss_seed<<<grid_for(h->n_ss), TPB, 0, s>>>(c, h->seeds_ss.p, h->n_ss));
+        CK(cudaGetLastError());
+        uint32_t *in = h->ovf0.p, *out = h->ovf1.p;
+        for (int round = 0; round < 1 << 20; round++) {
+            Counters hc;
+            CK(cudaMemcpyAsync(&hc, h->cnt.p, sizeof hc, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (hc.err) return fail(MSC_ERR_OOM, "saddle-saddle spill queue overflow");
+            if (hc.novf == 0) break;
+            const unsigned long long zero = 0;
+            CK(cudaMemcpyAsync(&h->cnt.p->novf, &zero, sizeof zero, cudaMemcpyHostToDevice, s));
+            c.ovf_out = out;
+            KL(h, MSC_K_SPASS, s, k_ss_spill<<<grid_for(hc.novf), TPB, 0, s>>>(c, in, (uint32_t)hc.novf));
+            CK(cudaGetLastError());
+            std::swap(in, out);
+        }
+    }
+    return MSC_OK;
+}
+
+struct FixResult {
+    uint32_t n_c = 0, n_s = 0, n_fb = 0;
+    std::vector<msc_iter_record> trace;
+};
+
+template <int D>
+msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t s, FixResult &R)
+{
+    Ctx c = make_ctx(h, o.tier, o.q_max, o.exact_fallback, xi);
+    unsigned long long *nMc = h->nM.p;     // nMc[0], nMc[1]
+    uint32_t *M[2] = {h->M0.p, h->M1.p};
+    int cur = 0;
+    KL(h, MSC_K_OTHER, s, k_init_g<<<grid_for(h->G.n), TPB, 0, s>>>(h->f.p, h->fhat.p, h->g.p, h->state.p, h->G.n, xi));
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(nMc, 0, 2 * sizeof(unsigned long long), s));
+    CKS(eval_dense<D>(h, h->g.p, h->G, h->code_g.p, h->code_f.p, M[cur], nMc + cur, s));
+    for (;;) {
+        CK(cudaMemsetAsync(h->cnt.p, 0, sizeof(Counters), s));
+        KL(h, MSC_K_CPASS, s, k_ctargets<D><<<grid_for(h->G.n / 8 + 1), TPB, 0, s>>>(c, M[cur], nMc + cur));
+        CK(cudaGetLastError());
+        Counters hc;
+        CK(cudaMemcpyAsync(&hc, h->cnt.p, sizeof hc, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        int kind = 0;
+        if (hc.ncase == 0) {
+            if (o.tier < 3) break;
+            kind = 1;
+            CKS(s_pass<D>(h, c, o.tier, s));
+            CK(cudaMemcpyAsync(&hc, h->cnt.p, sizeof hc, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (hc.err) return fail(MSC_ERR_OOM, "saddle-saddle spill queue overflow");
+            if (hc.ncase == 0) break;
+        }
+        if (!o.exact_fallback && hc.nlive == 0)
+            return fail(MSC_ERR_STALLED, "every false case targets a vertex at its floor (%llu cases)", hc.ncase);
+        if (R.n_c + R.n_s >= (uint32_t)o.max_iters)
+            return fail(MSC_ERR_NOT_CONVERGED, "not converged after %d edit rounds", o.max_iters);
+        if (o.record_trace) {
+            msc_iter_record r{};
+            r.kind = kind;
+            r.n_targets = (int64_t)hc.nT;
+            r.n_exact = (int64_t)hc.nX;
+            r.sum_targets = (int64_t)hc.sumT;
+            r.sum_exact = (int64_t)hc.sumX;
+            R.trace.push_back(r);
+        }
+        (kind ? R.n_s : R.n_c)++;
+        if (hc.nX) R.n_fb++;
+        const int nxt = cur ^ 1;
+        KL(h, MSC_K_EDIT, s, k_edit<D><<<grid_for(hc.nT + hc.nX), TPB, 0, s>>>(c));
+        KL(h, MSC_K_REFRESH, s, k_refresh<D><<<grid_for(h->G.n / 4 + 1), TPB, 0, s>>>(c));
+        CK(cudaMemsetAsync(nMc + nxt, 0, sizeof(unsigned long long), s));
+        c.Mnext = M[nxt];
+        c.tag = ++h->tag;
+        if (h->tag == 0xFFFFFFFFu) {   // stamps would repeat: reset them
+            CK(cudaMemsetAsync(h->stamp.p, 0, h->stamp.n * 4, s));
+            h->tag = 1;
+            c.tag = 1;
+        }
+        KL(h, MSC_K_REBUILD, s, k_rebuild<<<grid_for(h->G.n / 8 + 1), TPB, 0, s>>>(c, M[cur], nMc + cur, nMc + nxt));
+        KL(h, MSC_K_REBUILD, s, k_clear<<<grid_for(h->G.n / 8 + 1), TPB, 0, s>>>(c));
+        CK(cudaGetLastError());
+        cur = nxt;
+    }
+    return MSC_OK;
+}
+
+msc_status write_edits(msc_handle *h, float xi, int qmax, cudaStream_t s, msc_edits *out)
+{
+    const uint32_t n = h->G.n;
+    const uint32_t nb = (n + 1023) / 1024;
+    DevBuf<uint8_t> qm;
+    DevBuf<uint32_t> bc;
+    DevBuf<unsigned long long> tot;
+    CK(qm.alloc(n));
+    CK(bc.alloc(nb));
+    CK(tot.alloc(2));
+    CK(cudaMemsetAsync(tot.p, 0, 2 * sizeof(unsigned long long), s));
+    KL(h, MSC_K_OTHER, s, k_qmap<<<nb, 1024, 0, s>>>(h->f.p, h->fhat.p, h->state.p, n, xi, qmax, qm.p, bc.p, tot.p + 1));
+    KL(h, MSC_K_OTHER, s, k_scan_blocks<<<1, 1024, 0, s>>>(bc.p, nb, tot.p));
+    CK(cudaGetLastError());
+    unsigned long long t[2];
+    CK(cudaMemcpyAsync(t, tot.p, sizeof t, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    DevBuf<uint64_t> li;
+    DevBuf<float> lv;
+    CK(li.alloc(t[0]));
+    CK(lv.alloc(t[0]));
+    KL(h, MSC_K_OTHER, s, k_lossless_write<<<nb, 1024, 0, s>>>(qm.p, h->g.p, n, bc.p, li.p, lv.p));
+    CK(cudaGetLastError());
+    out->n_vertices = n;
+    out->n_lossless = t[0];
+    out->n_quant = t[1];
+    out->q_map = (uint8_t *)malloc(n ? n : 1);
+    out->lossless_idx = (uint64_t *)malloc(t[0] ? t[0] * 8 : 8);
+    out->lossless_val = (float *)malloc(t[0] ? t[0] * 4 : 4);
+    if (!out->q_map || !out->lossless_idx || !out->lossless_val) return fail(MSC_ERR_OOM, "host allocation of edits failed");
+    CK(cudaMemcpyAsync(out->q_map, qm.p, n, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(out->lossless_idx, li.p, t[0] * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(out->lossless_val, lv.p, t[0] * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return MSC_OK;
+}
+
+template <int D> msc_status verify_impl(msc_handle *h, const float *gdev, float xi, cudaStream_t s, msc_report *out)
+{
+    DevBuf<uint64_t> code;
+    CK(code.alloc(h->G.n));
+    CKS(eval_dense<D>(h, gdev, h->G, code.p, nullptr, nullptr, nullptr, s));
+    CK(cudaMemsetAsync(h->cnt.p, 0, sizeof(Counters), s));
+    KL(h, MSC_K_OTHER, s, k_decode_crit<D><<<grid_for(h->G.n), TPB, 0, s>>>(code.p, h->code_f.p, h->G, nullptr, nullptr, nullptr, 0, h->cnt.p));
+    KL(h, MSC_K_OTHER, s, k_max_abs_err<<<grid_for(h->G.n), TPB, 0, s>>>(h->f.p, gdev, h->G.n, &h->cnt.p->rep[13]));
+    CK(cudaGetLastError());
+    Counters hc;
+    CK(cudaMemcpyAsync(&hc, h->cnt.p, sizeof hc, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    memset(out, 0, sizeof *out);
+    unsigned long long crit_bad = 0;
+    for (int d = 0; d < 4; d++) {
+        out->fp[d] = hc.rep[d];
+        out->fn[d] = hc.rep[4 + d];
+        crit_bad += hc.rep[d] + hc.rep[4 + d];
+    }
+    double m;
+    memcpy(&m, &hc.rep[13], sizeof m);
+    out->max_abs_err = m;
+    if (crit_bad == 0) {
+        Ctx c = make_ctx(h, 4, 6, 0, xi);
+        c.g = (float *)gdev;
+        c.code_g = code.p;
+        // per-separatrix pair and end checks
+        CK(cudaMemsetAsync(h->cnt.p, 0, sizeof(Counters), s));
+        if (h->n_desc) KL(h, MSC_K_SPASS, s, k_verify_desc<D><<<grid_for(h->n_desc), TPB, 0, s>>>(c, h->seeds_desc.p, h->n_desc));
+        if (h->n_asc) KL(h, MSC_K_SPASS, s, k_verify_asc<D><<<grid_for(h->n_asc), TPB, 0, s>>>(c, h->seeds_asc.p, h->n_asc));
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(&hc, h->cnt.p, sizeof hc, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        out->sep_mismatch[0] = hc.rep[8];
+        out->sep_mismatch[1] = hc.rep[9];
+        out->term_mismatch[0] = hc.rep[11];
+        out->term_mismatch[1] = hc.rep[12];
+        if (D == 3) {
+            // saddle-saddle connectors: troublemakers found by the tier-4 walk (count only)
+            DevBuf<uint32_t> tl, tb, xl, xb;
+            CK(tl.alloc(h->G.n)); CK(tb.alloc(words(h->G.n)));
+            CK(xl.alloc(1)); CK(xb.alloc(words(h->G.n)));
+            CK(cudaMemsetAsync(tb.p, 0, tb.n * 4, s));
+            CK(cudaMemsetAsync(xb.p, 0, xb.n * 4, s));
+            DevBuf<uint8_t> st;
+            CK(st.alloc(h->G.n));
+            CK(cudaMemsetAsync(st.p, 0, h->G.n, s));
+            Ctx v = c;
+            v.Tlist = tl.p; v.Tbits = tb.p; v.Xlist = xl.p; v.Xbits = xb.p; v.state = st.p;
+            v.exact_fallback = 0;
+            CK(cudaMemsetAsync(h->cnt.p, 0, sizeof(Counters), s));
+            CK(cudaMemsetAsync(h->vis_tri.p, 0, h->vis_tri.n * 4, s));
+            v.ovf_out = h->ovf0.p;
+            if (h->n_ss) KL(h, MSC_K_SPASS, s, k_ss_seed<<<grid_for(h->n_ss), TPB, 0, s>>>(v, h->seeds_ss.p, h->n_ss));
+            CK(cudaGetLastError());
+            uint32_t *in = h->ovf0.p, *o2 = h->ovf1.p;
+            for (;;) {
+                CK(cudaMemcpyAsync(&hc, h->cnt.p, sizeof hc, cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                if (hc.err) return fail(MSC_ERR_OOM, "saddle-saddle spill queue overflow");
+                if (hc.novf == 0) break;
+                const unsigned long long zero = 0;
+                CK(cudaMemcpyAsync(&h->cnt.p->novf, &zero, sizeof zero, cudaMemcpyHostToDevice, s));
+                v.ovf_out = o2;
+                KL(h, MSC_K_SPASS, s, k_ss_spill<<<grid_for(hc.novf), TPB, 0, s>>>(v, in, (uint32_t)hc.novf));
+                CK(cudaGetLastError());
+                std::swap(in, o2);
+            }
+            out->sep_mismatch[2] = hc.ncase;
+        }
+    }
+    unsigned long long sep = 0;
+    for (int i = 0; i < 3; i++) sep += out->sep_mismatch[i];
+    out->pass = crit_bad == 0 && sep == 0 && out->term_mismatch[0] == 0 && out->term_mismatch[1] == 0 &&
+                out->max_abs_err <= (double)xi;
+    return MSC_OK;
+}
+
+// a device copy of a caller's field (owned here only if the caller passed host memory)
+struct DevInput {
+    DevBuf<float> own;
+    const float *p = nullptr;
+};
+
+msc_status device_input(const float *src, size_t n, DevInput &d, cudaStream_t s, const char *what)
+{
+    if (!src) return fail(MSC_ERR_INVALID_ARG, "%s is NULL", what);
+    if (is_device_ptr(src)) { d.p = src; return MSC_OK; }
+    CK(d.own.alloc(n));
+    CK(cudaMemcpyAsync(d.own.p, src, n * sizeof(float), cudaMemcpyHostToDevice, s));
+    d.p = d.own.p;
+    return MSC_OK;
+}
+
+template <int D>
+msc_status introspect(const float *field, Grid G, int what, int64_t *rows, int32_t *dims, uint64_t cap, uint64_t *n_out)
+{
+    cudaStream_t s = nullptr;
+    DevBuf<float> v;
+    DevBuf<uint64_t> code;
+    DevBuf<unsigned long long> cnt;
+    CK(v.alloc(G.n));
+    CK(code.alloc(G.n));
+    CK(cnt.alloc(2));
+    CKS(upload_field(nullptr, field, G.n, v.p, cnt.p, s, "field"));
+    CKS(eval_dense<D>(nullptr, v.p, G, code.p, nullptr, nullptr, nullptr, s));
+    CK(cudaMemsetAsync(cnt.p, 0, 8, s));
+    if (what == 0) k_decode_pairs<D><<<grid_for(G.n), TPB, 0, s>>>(code.p, G, nullptr, cnt.p, 0);
+    else k_decode_crit<D><<<grid_for(G.n), TPB, 0, s>>>(code.p, nullptr, G, nullptr, nullptr, cnt.p, 0, nullptr);
+    CK(cudaGetLastError());
+    unsigned long long n = 0;
+    CK(cudaMemcpy(&n, cnt.p, 8, cudaMemcpyDeviceToHost));
+    *n_out = n;
+    if (!cap || !rows) return MSC_OK;
+    const unsigned long long m = n < cap ? n : cap;
+    const int w = what == 0 ? 8 : 4;
+    DevBuf<int64_t> r;
+    DevBuf<int32_t> dd;
+    CK(r.alloc(m * w));
+    CK(dd.alloc(m));
+    CK(cudaMemsetAsync(cnt.p, 0, 8, s));
+    if (what == 0) k_decode_pairs<D><<<grid_for(G.n), TPB, 0, s>>>(code.p, G, r.p, cnt.p, m);
+    else k_decode_crit<D><<<grid_for(G.n), TPB, 0, s>>>(code.p, nullptr, G, r.p, dd.p, cnt.p, m, nullptr);
+    CK(cudaGetLastError());
+    CK(cudaMemcpy(rows, r.p, m * w * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    if (what == 1 && dims) CK(cudaMemcpy(dims, dd.p, m * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    return MSC_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------
+extern "C" {
+
+const char *msc_version(void) { return "msc-gb300 0.1 (sm_103a)"; }
+
+const char *msc_status_string(msc_status s)
+{
+    switch (s) {
+    case MSC_OK: return "MSC_OK";
+    case MSC_ERR_INVALID_ARG: return "MSC_ERR_INVALID_ARG";
+    case MSC_ERR_OOM: return "MSC_ERR_OOM";
+    case MSC_ERR_CUDA: return "MSC_ERR_CUDA";
+    case MSC_ERR_NOT_CONVERGED: return "MSC_ERR_NOT_CONVERGED";
+    case MSC_ERR_DEVICE_TIMEOUT: return "MSC_ERR_DEVICE_TIMEOUT";
+    case MSC_ERR_STALLED: return "MSC_ERR_STALLED";
+    case MSC_ERR_NO_DEVICE: return "MSC_ERR_NO_DEVICE";
+    }
+    return "MSC_ERR_UNKNOWN";
+}
+
+const char *msc_last_error(void) { return g_last_error.c_str(); }
+
+void msc_default_options(msc_options *opt)
+{
+    if (opt) fill_defaults(opt);
+}
+
+uint64_t msc_device_bytes(int nx, int ny, int nz)
+{
+    const uint64_t n = (uint64_t)nx * ny * nz;
+    const int D = nz > 1 ? 3 : 2;
+    uint64_t b = n * (4 + 8) + n * (4 + 4 + 1 + 8) + 3 * (n / 8) + 6 * n * 4 + n / 8 + n * (D == 3 ? 6 : 2) / 8;
+    if (D == 3) b += n * 12 / 8 + 16 * n;
+    b += n * 3 * 4;   // separatrix seeds (upper estimate)
+    return b;
+}
+
+msc_status msc_prepare_original(const float *f, int nx, int ny, int nz, const msc_options *opt, msc_handle **out)
+{
+    g_last_error.clear();
+    if (!out) return fail(MSC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    CKS(check_dims(nx, ny, nz));
+    msc_options o;
+    if (opt) o = *opt; else fill_defaults(&o);
+    CKS(check_options(&o));
+    CKS(device_ready());
+    cudaStream_t s = (cudaStream_t)o.stream;
+    msc_handle *h = new (std::nothrow) msc_handle();
+    if (!h) return fail(MSC_ERR_OOM, "handle allocation failed");
+    h->G.nx = nx; h->G.ny = ny; h->G.nz = nz;
+    h->G.n = (uint32_t)((uint64_t)nx * ny * nz);
+    h->D = nz > 1 ? 3 : 2;
+    auto run = [&]() -> msc_status {
+        CK(h->f.alloc(h->G.n));
+        CK(h->code_f.alloc(h->G.n));
+        CK(h->cnt.alloc(1));
+        CK(h->nM.alloc(4));
+        h->prof_on = o.profile != 0;
+        CKS(upload_field(h, f, h->G.n, h->f.p, h->nM.p, s, "f"));
+        CKS(eval_dense_any(h, h->D, h->f.p, h->G, h->code_f.p, nullptr, nullptr, nullptr, s));
+        CKS(h->D == 3 ? build_seeds<3>(h, s) : build_seeds<2>(h, s));
+        CK(cudaEventCreate(&h->ev0));
+        CK(cudaEventCreate(&h->ev1));
+        CK(cudaStreamSynchronize(s));
+        prof_flush(h);
+        h->prof_on = false;
+        return MSC_OK;
+    };
+    msc_status st = run();
+    if (st != MSC_OK) { msc_destroy(h); return st; }
+    *out = h;
+    return MSC_OK;
+}
+
+msc_status msc_fix(msc_handle *h, const float *f_hat, float xi, const msc_options *opt, msc_edits *out, float *g_out)
+{
+    g_last_error.clear();
+    if (!h || !out || !g_out) return fail(MSC_ERR_INVALID_ARG, "handle, out and g_out must be non-NULL");
+    memset(out, 0, sizeof *out);
+    msc_options o;
+    if (opt) o = *opt; else fill_defaults(&o);
+    CKS(check_options(&o));
+    if (!(xi > 0.0f) || !std::isfinite(xi)) return fail(MSC_ERR_INVALID_ARG, "xi must be finite and > 0");
+    cudaStream_t s = (cudaStream_t)o.stream;
+    CKS(alloc_fix_state(h));
+    h->prof_on = o.profile != 0;
+    struct Flush {
+        msc_handle *h;
+        ~Flush() { prof_flush(h); h->prof_on = false; }
+    } flush_at_exit{h};
+    CKS(upload_field(h, f_hat, h->G.n, h->fhat.p, h->nM.p + 2, s, "f_hat"));
+    FixResult R;
+    CK(cudaEventRecord(h->ev0, s));
+    msc_status st = h->D == 3 ? fix_loop<3>(h, xi, o, s, R) : fix_loop<2>(h, xi, o, s, R);
+    if (st != MSC_OK) return st;
+    CK(cudaEventRecord(h->ev1, s));
+    CK(cudaMemcpyAsync(g_out, h->g.p, (size_t)h->G.n * 4, is_device_ptr(g_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    CKS(write_edits(h, xi, o.q_max, s, out));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    out->loop_ms = ms;
+    out->n_iters_c = R.n_c;
+    out->n_iters_s = R.n_s;
+    out->n_fallback_iters = R.n_fb;
+    if (o.record_trace && !R.trace.empty()) {
+        out->trace = (msc_iter_record *)malloc(R.trace.size() * sizeof(msc_iter_record));
+        if (!out->trace) return fail(MSC_ERR_OOM, "trace allocation failed");
+        memcpy(out->trace, R.trace.data(), R.trace.size() * sizeof(msc_iter_record));
+        out->n_trace = (uint32_t)R.trace.size();
+    }
+    return MSC_OK;
+}
+
+msc_status msc_apply_edits(const float *f_hat, int nx, int ny, int nz, float xi, int q_max, const msc_edits *e, float *g_out)
+{
+    g_last_error.clear();
+    CKS(check_dims(nx, ny, nz));
+    if (!e || !g_out || !e->q_map) return fail(MSC_ERR_INVALID_ARG, "edits and g_out must be non-NULL");
+    if (!(xi > 0.0f) || q_max < 1 || q_max > 7) return fail(MSC_ERR_INVALID_ARG, "bad xi or q_max");
+    CKS(device_ready());
+    const uint32_t n = (uint32_t)((uint64_t)nx * ny * nz);
+    if (e->n_vertices != n) return fail(MSC_ERR_INVALID_ARG, "edits are for %llu vertices, grid has %u", (unsigned long long)e->n_vertices, n);
+    cudaStream_t s = nullptr;
+    DevInput fh;
+    CKS(device_input(f_hat, n, fh, s, "f_hat"));
+    DevBuf<uint8_t> qm;
+    DevBuf<uint64_t> li;
+    DevBuf<float> lv, g;
+    CK(qm.alloc(n));
+    CK(li.alloc(e->n_lossless));
+    CK(lv.alloc(e->n_lossless));
+    CK(g.alloc(n));
+    CK(cudaMemcpyAsync(qm.p, e->q_map, n, cudaMemcpyHostToDevice, s));
+    if (e->n_lossless) {
+        CK(cudaMemcpyAsync(li.p, e->lossless_idx, e->n_lossless * 8, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(lv.p, e->lossless_val, e->n_lossless * 4, cudaMemcpyHostToDevice, s));
+    }
+    k_apply_q<<<grid_for(n), TPB, 0, s>>>(fh.p, qm.p, n, xi / (float)(1 << q_max), g.p);
+    if (e->n_lossless) k_apply_lossless<<<grid_for(e->n_lossless), TPB, 0, s>>>(li.p, lv.p, e->n_lossless, g.p);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(g_out, g.p, (size_t)n * 4, is_device_ptr(g_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return MSC_OK;
+}
+
+msc_status msc_verify(msc_handle *h, const float *g, float xi, msc_report *out)
+{
+    g_last_error.clear();
+    if (!h || !g || !out) return fail(MSC_ERR_INVALID_ARG, "handle, g and out must be non-NULL");
+    if (!(xi > 0.0f)) return fail(MSC_ERR_INVALID_ARG, "xi must be > 0");
+    CKS(alloc_fix_state(h));
+    cudaStream_t s = nullptr;
+    DevBuf<float> gd;
+    CK(gd.alloc(h->G.n));
+    CKS(upload_field(h, g, h->G.n, gd.p, h->nM.p + 2, s, "g"));
+    msc_status st = h->D == 3 ? verify_impl<3>(h, gd.p, xi, s, out) : verify_impl<2>(h, gd.p, xi, s, out);
+    prof_flush(h);
+    return st;
+}
+
+void msc_free_edits(msc_edits *e)
+{
+    if (!e) return;
+    free(e->q_map);
+    free(e->lossless_idx);
+    free(e->lossless_val);
+    free(e->trace);
+    memset(e, 0, sizeof *e);
+}
+
+void msc_destroy(msc_handle *h)
+{
+    if (!h) return;
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    delete h;   // DevBuf members free their device memory
+}
+
+msc_status msc_fix_batch(msc_handle **hs, const float **f_hats, const float *xis, int n, const msc_options *opt,
+                         msc_edits *outs, float **g_outs)
+{
+    g_last_error.clear();
+    if (n < 0 || (n > 0 && (!hs || !f_hats || !xis || !outs || !g_outs))) return fail(MSC_ERR_INVALID_ARG, "bad batch arguments");
+    for (int i = 0; i < n; i++) {
+        msc_status st = msc_fix(hs[i], f_hats[i], xis[i], opt, outs + i, g_outs[i]);
+        if (st != MSC_OK) return st;
+    }
+    return MSC_OK;
+}
+
+msc_status msc_get_stats(msc_handle *h, msc_stats *out)
+{
+    if (!h || !out) return fail(MSC_ERR_INVALID_ARG, "handle and out must be non-NULL");
+    memset(out, 0, sizeof *out);
+    for (int i = 0; i < 8; i++) {
+        out->launches[i] = h->launches[i];
+        out->ms[i] = h->ms[i];
+        out->timed_launches[i] = h->timed[i];
+    }
+    return MSC_OK;
+}
+
+msc_status msc_reset_stats(msc_handle *h)
+{
+    if (!h) return fail(MSC_ERR_INVALID_ARG, "handle is NULL");
+    for (int i = 0; i < 8; i++) { h->launches[i] = 0; h->ms[i] = 0.0; h->timed[i] = 0; }
+    return MSC_OK;
+}
+
+msc_status msc_gradient_pairs(const float *field, int nx, int ny, int nz, int64_t *rows, uint64_t cap, uint64_t *n_out)
+{
+    g_last_error.clear();
+    if (!n_out) return fail(MSC_ERR_INVALID_ARG, "n_out is NULL");
+    CKS(check_dims(nx, ny, nz));
+    CKS(device_ready());
+    Grid G{nx, ny, nz, (uint32_t)((uint64_t)nx * ny * nz)};
+    return nz > 1 ? introspect<3>(field, G, 0, rows, nullptr, cap, n_out) : introspect<2>(field, G, 0, rows, nullptr, cap, n_out);
+}
+
+msc_status msc_critical_cells(const float *field, int nx, int ny, int nz, int64_t *rows, int32_t *dims, uint64_t cap,
+                              uint64_t *n_out)
+{
+    g_last_error.clear();
+    if (!n_out) return fail(MSC_ERR_INVALID_ARG, "n_out is NULL");
+    CKS(check_dims(nx, ny, nz));
+    CKS(device_ready());
+    Grid G{nx, ny, nz, (uint32_t)((uint64_t)nx * ny * nz)};
+    return nz > 1 ? introspect<3>(field, G, 1, rows, dims, cap, n_out) : introspect<2>(field, G, 1, rows, dims, cap, n_out);
+}
+
+}  // extern "C"

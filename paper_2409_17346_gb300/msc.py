@@ -1,0 +1,320 @@
+"""Thin Python binding of libmsc (include/msc.h): argument marshalling only.
+
+Every computation runs in the CUDA library.  Fields may be numpy arrays (host memory) or
+torch CUDA tensors (device memory, passed by pointer); both must be float32, C-contiguous,
+shape (ny, nx) or (nz, ny, nx).  The binding raises ``MscError`` on any status other than
+MSC_OK, and ``RuntimeError`` if the library has not been built.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MSC_OK = 0
+STATUS_NAMES = {0: "MSC_OK", 1: "MSC_ERR_INVALID_ARG", 2: "MSC_ERR_OOM", 3: "MSC_ERR_CUDA",
+                4: "MSC_ERR_NOT_CONVERGED", 5: "MSC_ERR_DEVICE_TIMEOUT", 6: "MSC_ERR_STALLED",
+                7: "MSC_ERR_NO_DEVICE"}
+QMAP_LOSSLESS = 0xFF
+
+
+class MscError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("tier", ctypes.c_int), ("q_max", ctypes.c_int), ("max_iters", ctypes.c_int),
+                ("exact_fallback", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
+                ("tile_z", ctypes.c_int), ("stream", ctypes.c_void_p), ("record_trace", ctypes.c_int),
+                ("profile", ctypes.c_int)]
+
+
+KERNEL_CLASSES = ("dense", "cpass", "edit", "refresh", "rebuild", "spass", "other")
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64 * 8), ("ms", ctypes.c_double * 8),
+                ("timed_launches", ctypes.c_uint64 * 8)]
+
+
+class IterRecord(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("n_targets", ctypes.c_int64),
+                ("n_exact", ctypes.c_int64), ("sum_targets", ctypes.c_int64), ("sum_exact", ctypes.c_int64)]
+
+
+class Edits(ctypes.Structure):
+    _fields_ = [("n_vertices", ctypes.c_uint64), ("n_iters_c", ctypes.c_uint32), ("n_iters_s", ctypes.c_uint32),
+                ("n_fallback_iters", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("n_quant", ctypes.c_uint64), ("n_lossless", ctypes.c_uint64),
+                ("q_map", ctypes.POINTER(ctypes.c_uint8)), ("lossless_idx", ctypes.POINTER(ctypes.c_uint64)),
+                ("lossless_val", ctypes.POINTER(ctypes.c_float)), ("n_trace", ctypes.c_uint32),
+                ("trace", ctypes.POINTER(IterRecord)), ("loop_ms", ctypes.c_double)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("fp", ctypes.c_uint64 * 4), ("fn", ctypes.c_uint64 * 4), ("sep_mismatch", ctypes.c_uint64 * 3),
+                ("term_mismatch", ctypes.c_uint64 * 2), ("max_abs_err", ctypes.c_double), ("pass_", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load():
+    """Load libmsc.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError("libmsc is not built (%s missing): run __graft_entry__.build()" % _build.LIB)
+    lib = ctypes.CDLL(_build.LIB)
+    vp, i, f, u64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_uint64
+    lib.msc_version.restype = ctypes.c_char_p
+    lib.msc_status_string.restype = ctypes.c_char_p
+    lib.msc_status_string.argtypes = [i]
+    lib.msc_last_error.restype = ctypes.c_char_p
+    lib.msc_default_options.argtypes = [ctypes.POINTER(Options)]
+    lib.msc_prepare_original.argtypes = [vp, i, i, i, ctypes.POINTER(Options), ctypes.POINTER(vp)]
+    lib.msc_fix.argtypes = [vp, vp, f, ctypes.POINTER(Options), ctypes.POINTER(Edits), vp]
+    lib.msc_apply_edits.argtypes = [vp, i, i, i, f, i, ctypes.POINTER(Edits), vp]
+    lib.msc_verify.argtypes = [vp, vp, f, ctypes.POINTER(Report)]
+    lib.msc_free_edits.argtypes = [ctypes.POINTER(Edits)]
+    lib.msc_free_edits.restype = None
+    lib.msc_destroy.argtypes = [vp]
+    lib.msc_destroy.restype = None
+    lib.msc_fix_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(f), i,
+                                  ctypes.POINTER(Options), ctypes.POINTER(Edits), ctypes.POINTER(vp)]
+    lib.msc_gradient_pairs.argtypes = [vp, i, i, i, vp, u64, ctypes.POINTER(u64)]
+    lib.msc_critical_cells.argtypes = [vp, i, i, i, vp, vp, u64, ctypes.POINTER(u64)]
+    lib.msc_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+    lib.msc_reset_stats.argtypes = [vp]
+    lib.msc_device_bytes.argtypes = [i, i, i]
+    lib.msc_device_bytes.restype = u64
+    for name in ("msc_prepare_original", "msc_fix", "msc_apply_edits", "msc_verify", "msc_fix_batch",
+                 "msc_gradient_pairs", "msc_critical_cells", "msc_get_stats", "msc_reset_stats"):
+        getattr(lib, name).restype = i
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != MSC_OK:
+        raise MscError(status, load().msc_last_error().decode())
+
+
+def dims_of(shape):
+    if len(shape) == 2:
+        return int(shape[1]), int(shape[0]), 1
+    if len(shape) == 3:
+        return int(shape[2]), int(shape[1]), int(shape[0])
+    raise ValueError("field must be 2D (ny, nx) or 3D (nz, ny, nx)")
+
+
+def _ptr(a):
+    """(pointer, keepalive) of a float32 numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        return a.ctypes.data_as(ctypes.c_void_p), a
+    if hasattr(a, "data_ptr"):
+        import torch
+        if a.dtype != torch.float32 or not a.is_contiguous():
+            raise ValueError("tensors must be contiguous float32")
+        return ctypes.c_void_p(a.data_ptr()), a
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+def options(tier=4, q_max=6, max_iters=100000, exact_fallback=1, stream=None, record_trace=False,
+            tile=(0, 0, 0), profile=False):
+    o = Options()
+    load().msc_default_options(ctypes.byref(o))
+    o.tier, o.q_max, o.max_iters, o.exact_fallback = tier, q_max, max_iters, exact_fallback
+    o.tile_x, o.tile_y, o.tile_z = tile
+    o.stream = ctypes.c_void_p(stream) if stream else None
+    o.record_trace = int(bool(record_trace))
+    o.profile = int(bool(profile))
+    return o
+
+
+def _edits_to_py(e, shape):
+    n = int(e.n_vertices)
+    out = dict(n_iters_c=int(e.n_iters_c), n_iters_s=int(e.n_iters_s), n_fallback_iters=int(e.n_fallback_iters),
+               n_quant=int(e.n_quant), n_lossless=int(e.n_lossless), loop_ms=float(e.loop_ms))
+    out["q_map"] = np.ctypeslib.as_array(e.q_map, shape=(n,)).copy().reshape(shape) if n else np.zeros(shape, np.uint8)
+    nl = int(e.n_lossless)
+    out["lossless_idx"] = np.ctypeslib.as_array(e.lossless_idx, shape=(nl,)).copy() if nl else np.zeros(0, np.uint64)
+    out["lossless_val"] = np.ctypeslib.as_array(e.lossless_val, shape=(nl,)).copy() if nl else np.zeros(0, np.float32)
+    nt = int(e.n_trace)
+    if nt:
+        tr = np.zeros((nt, 5), np.int64)
+        for k in range(nt):
+            r = e.trace[k]
+            tr[k] = (r.kind, r.n_targets, r.n_exact, r.sum_targets, r.sum_exact)
+        out["trace"] = tr
+    else:
+        out["trace"] = np.zeros((0, 5), np.int64)
+    return out
+
+
+class Handle:
+    """Device-resident MSC of one original field f (msc_prepare_original)."""
+
+    def __init__(self, f, opts=None, **kw):
+        lib = load()
+        if opts is None and kw:
+            opts = options(**kw)
+        self.shape = tuple(f.shape)
+        self.nx, self.ny, self.nz = dims_of(self.shape)
+        p, keep = _ptr(f)
+        h = ctypes.c_void_p()
+        _check(lib.msc_prepare_original(p, self.nx, self.ny, self.nz,
+                                        ctypes.byref(opts) if opts is not None else None, ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().msc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def fix(self, f_hat, xi, g_out=None, **kw):
+        """Run the fix loop; returns (g, edits dict).  g_out: optional torch CUDA tensor or
+        numpy array receiving the corrected field."""
+        lib = load()
+        opts = options(**kw)
+        p, keep = _ptr(f_hat)
+        if g_out is None:
+            g_out = np.zeros(self.shape, np.float32)
+        gp, gkeep = _ptr(g_out)
+        e = Edits()
+        try:
+            _check(lib.msc_fix(self._h, p, ctypes.c_float(xi), ctypes.byref(opts), ctypes.byref(e), gp))
+            out = _edits_to_py(e, self.shape)
+        finally:
+            lib.msc_free_edits(ctypes.byref(e))
+        return g_out, out
+
+    def stats(self):
+        """Launch counts and profiled CUDA-event milliseconds by kernel class."""
+        st = Stats()
+        _check(load().msc_get_stats(self._h, ctypes.byref(st)))
+        return {k: dict(launches=int(st.launches[i]), ms=float(st.ms[i]), timed=int(st.timed_launches[i]))
+                for i, k in enumerate(KERNEL_CLASSES)}
+
+    def reset_stats(self):
+        _check(load().msc_reset_stats(self._h))
+
+    def verify(self, g, xi):
+        lib = load()
+        p, keep = _ptr(g)
+        r = Report()
+        _check(lib.msc_verify(self._h, p, ctypes.c_float(xi), ctypes.byref(r)))
+        return dict(fp=list(r.fp), fn=list(r.fn), sep_mismatch=list(r.sep_mismatch),
+                    term_mismatch=list(r.term_mismatch), max_abs_err=r.max_abs_err, passed=bool(r.pass_))
+
+
+def apply_edits(f_hat, xi, q_max, edits, g_out=None):
+    """Decompression side: rebuild g from f_hat and the edits returned by Handle.fix."""
+    lib = load()
+    shape = tuple(f_hat.shape)
+    nx, ny, nz = dims_of(shape)
+    e = Edits()
+    qm = np.ascontiguousarray(edits["q_map"], dtype=np.uint8).reshape(-1)
+    li = np.ascontiguousarray(edits["lossless_idx"], dtype=np.uint64)
+    lv = np.ascontiguousarray(edits["lossless_val"], dtype=np.float32)
+    e.n_vertices = qm.size
+    e.n_lossless = li.size
+    e.q_map = qm.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    e.lossless_idx = li.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+    e.lossless_val = lv.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    p, keep = _ptr(f_hat)
+    if g_out is None:
+        g_out = np.zeros(shape, np.float32)
+    gp, gkeep = _ptr(g_out)
+    _check(lib.msc_apply_edits(p, nx, ny, nz, ctypes.c_float(xi), q_max, ctypes.byref(e), gp))
+    return g_out
+
+
+def fix_batch(handles, f_hats, xis, g_outs=None, **kw):
+    """msc_fix_batch over several jobs; returns (list of g, list of edit dicts)."""
+    lib = load()
+    n = len(handles)
+    opts = options(**kw)
+    if g_outs is None:
+        g_outs = [np.zeros(h.shape, np.float32) for h in handles]
+    hp = (ctypes.c_void_p * n)(*[h._h.value for h in handles])
+    fps, keeps = [], []
+    for a in f_hats:
+        p, k = _ptr(a)
+        fps.append(p.value)
+        keeps.append(k)
+    gps = []
+    for a in g_outs:
+        p, k = _ptr(a)
+        gps.append(p.value)
+        keeps.append(k)
+    fp = (ctypes.c_void_p * n)(*fps)
+    gp = (ctypes.c_void_p * n)(*gps)
+    xa = (ctypes.c_float * n)(*[float(x) for x in xis])
+    es = (Edits * n)()
+    try:
+        _check(lib.msc_fix_batch(hp, fp, xa, n, ctypes.byref(opts), es, gp))
+        outs = [_edits_to_py(es[i], handles[i].shape) for i in range(n)]
+    finally:
+        for i in range(n):
+            lib.msc_free_edits(ctypes.byref(es[i]))
+    return g_outs, outs
+
+
+def _sorted_rows(a):
+    return a[np.lexsort(a.T[::-1])] if len(a) else a
+
+
+def gradient_pairs(field):
+    """All gradient pairs (L, U) of a host field as sorted rows of 8 vertex ids."""
+    lib = load()
+    f = np.ascontiguousarray(field, dtype=np.float32)
+    nx, ny, nz = dims_of(f.shape)
+    n = ctypes.c_uint64(0)
+    _check(lib.msc_gradient_pairs(f.ctypes.data_as(ctypes.c_void_p), nx, ny, nz, None, 0, ctypes.byref(n)))
+    rows = np.zeros((max(n.value, 1), 8), np.int64)
+    _check(lib.msc_gradient_pairs(f.ctypes.data_as(ctypes.c_void_p), nx, ny, nz, rows.ctypes.data_as(ctypes.c_void_p),
+                                  n.value, ctypes.byref(n)))
+    return _sorted_rows(rows[: n.value])
+
+
+def critical_cells(field):
+    """Critical cells of a host field: (rows (n,4) sorted, dims (n,))."""
+    lib = load()
+    f = np.ascontiguousarray(field, dtype=np.float32)
+    nx, ny, nz = dims_of(f.shape)
+    n = ctypes.c_uint64(0)
+    _check(lib.msc_critical_cells(f.ctypes.data_as(ctypes.c_void_p), nx, ny, nz, None, None, 0, ctypes.byref(n)))
+    rows = np.zeros((max(n.value, 1), 4), np.int64)
+    dims = np.zeros(max(n.value, 1), np.int32)
+    _check(lib.msc_critical_cells(f.ctypes.data_as(ctypes.c_void_p), nx, ny, nz, rows.ctypes.data_as(ctypes.c_void_p),
+                                  dims.ctypes.data_as(ctypes.c_void_p), n.value, ctypes.byref(n)))
+    rows, dims = rows[: n.value], dims[: n.value]
+    if len(rows):
+        o = np.lexsort(rows.T[::-1])
+        rows, dims = rows[o], dims[o]
+    return rows, dims
+
+
+def device_bytes(shape):
+    return int(load().msc_device_bytes(*dims_of(shape)))
+
+
+def version():
+    return load().msc_version().decode()

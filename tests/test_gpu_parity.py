@@ -1,0 +1,276 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Integer/index results (gradient pairs, critical cells, iteration counts, per-round target
+digests, edit states) must be bit-exact; so must the corrected field g, because the method
+is comparison work on fixed float32 values with correctly rounded edit arithmetic (no
+tolerance applies anywhere)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2409_17346_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2409_17346_gb300 import msc
+    return msc
+
+
+def _field(shape, kind, seed):
+    rng = np.random.default_rng(seed)
+    if kind == "normal":
+        a = rng.standard_normal(shape)
+    elif kind == "equal":
+        a = np.zeros(shape)
+    elif kind == "binary":
+        a = rng.integers(0, 2, shape).astype(float)
+    elif kind == "signed_zero":
+        a = np.where(rng.random(shape) < 0.5, -0.0, 0.0) + (rng.random(shape) < 0.2)
+    else:
+        a = rng.integers(0, 4, shape).astype(float) * 0.25
+    return a.astype(np.float32)
+
+
+SHAPES = [(2, 2), (2, 9), (9, 2), (37, 23), (64, 300), (2, 2, 2), (2, 3, 5), (13, 9, 11), (20, 17, 33)]
+KINDS = ["normal", "equal", "binary", "signed_zero", "levels"]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("kind", KINDS)
+def test_gradient_pairs_and_critical_cells(lib, shape, kind):
+    a = _field(shape, kind, hash((shape, kind)) % 2**31)
+    assert np.array_equal(lib.gradient_pairs(a), oracle.gradient_pairs(a))
+    c1, d1 = lib.critical_cells(a)
+    c2, d2 = oracle.critical_cells(a)
+    assert np.array_equal(c1, c2) and np.array_equal(d1, d2)
+
+
+def test_gradient_on_workload_fields(lib):
+    for name, kw in (("gauss2d", {}), ("multiscale2d", dict(size=(90, 170))), ("grf3d", dict(size=24)),
+                     ("kolmogorov3d", dict(size=24))):
+        f, fh, _, _ = synth.config_case(name, **kw)
+        for a in (f, fh):
+            assert np.array_equal(lib.gradient_pairs(a), oracle.gradient_pairs(a))
+
+
+FIX_CASES = [
+    ("gauss2d", {}),                                       # the 64x64 workload itself
+    ("gauss2d", dict(seed=9, size=(23, 41), rel=1e-2)),
+    ("multiscale2d", dict(size=(40, 56), rel=1e-2)),
+    ("multiscale2d", dict(size=(61, 130), rel=3e-3)),
+    ("grf3d", dict(size=9, rel=1e-2)),
+    ("grf3d", dict(size=13, rel=1e-2)),
+    ("kolmogorov3d", dict(size=10, rel=3e-3)),
+    ("kolmogorov3d", dict(size=16, rel=1e-3)),
+]
+
+
+def _check_fix(lib, f, fh, xi, tier, q_max=6, exact_fallback=1):
+    ref = oracle.fix(f, fh, xi, tier=tier, q_max=q_max, exact_fallback=exact_fallback)
+    assert ref["status"] == 0
+    h = lib.Handle(f)
+    g, ed = h.fix(fh, xi, tier=tier, q_max=q_max, exact_fallback=exact_fallback, record_trace=True)
+    assert np.array_equal(g.view(np.uint32), ref["g"].view(np.uint32))
+    assert (ed["n_iters_c"], ed["n_iters_s"]) == (ref["n_c"], ref["n_s"])
+    assert ed["n_fallback_iters"] == ref["n_exact_iters"]
+    assert np.array_equal(ed["trace"], ref["trace"][:, :5])
+    qm, li, lv = oracle.edits_from_state(f, fh, xi, ref["state"], ref["g"])
+    assert np.array_equal(ed["q_map"].reshape(-1), qm)
+    assert np.array_equal(ed["lossless_idx"].astype(np.int64), li)
+    assert np.array_equal(ed["lossless_val"].view(np.uint32), lv.view(np.uint32))
+    rep = h.verify(g, xi)
+    assert rep["passed"]
+    h.close()
+    return g, ed
+
+
+@pytest.mark.parametrize("idx", range(len(FIX_CASES)))
+@pytest.mark.parametrize("tier", [1, 2, 3, 4])
+def test_fix_loop_matches_oracle(lib, idx, tier):
+    name, kw = FIX_CASES[idx]
+    f, fh, xi, _ = synth.config_case(name, **kw)
+    _check_fix(lib, f, fh, xi, tier)
+
+
+@pytest.mark.parametrize("q_max", [1, 3, 7])
+def test_fix_q_max_range(lib, q_max):
+    f, fh, xi, _ = synth.config_case("gauss2d", seed=4, size=(30, 33), rel=1e-2)
+    _check_fix(lib, f, fh, xi, 4, q_max=q_max)
+
+
+def test_device_and_host_pointers_agree(lib):
+    import torch
+    f, fh, xi, tier = synth.config_case("grf3d", size=12, rel=1e-2)
+    h = lib.Handle(torch.from_numpy(f).cuda())
+    gd = torch.empty(f.shape, dtype=torch.float32, device="cuda")
+    h.fix(torch.from_numpy(fh).cuda(), xi, g_out=gd, tier=4)
+    g_host, _ = lib.Handle(f).fix(fh, xi, tier=4)
+    assert np.array_equal(gd.cpu().numpy().view(np.uint32), g_host.view(np.uint32))
+
+
+def test_apply_edits_rebuilds_g_bit_exactly(lib):
+    import torch
+    for name, kw in (("multiscale2d", dict(size=(50, 70), rel=1e-2)), ("kolmogorov3d", dict(size=12, rel=3e-3))):
+        f, fh, xi, _ = synth.config_case(name, **kw)
+        g, ed = lib.Handle(f).fix(fh, xi, tier=4)
+        g2 = lib.apply_edits(fh, xi, 6, ed)
+        assert np.array_equal(g2.view(np.uint32), g.view(np.uint32))
+        g3 = torch.empty(f.shape, dtype=torch.float32, device="cuda")
+        lib.apply_edits(torch.from_numpy(fh).cuda(), xi, 6, ed, g_out=g3)
+        assert np.array_equal(g3.cpu().numpy().view(np.uint32), g.view(np.uint32))
+        # the oracle's decompression side reads the same stored edits
+        g4 = oracle.apply_edits(fh, xi, 6, ed["q_map"].reshape(-1), ed["lossless_idx"].astype(np.int64), ed["lossless_val"])
+        assert np.array_equal(g4.view(np.uint32), g.view(np.uint32))
+
+
+def test_verify_matches_oracle_report(lib):
+    for name, kw in (("gauss2d", {}), ("multiscale2d", dict(size=(45, 64), rel=1e-2)),
+                     ("grf3d", dict(size=11, rel=1e-2))):
+        f, fh, xi, _ = synth.config_case(name, **kw)
+        h = lib.Handle(f)
+        for tier in (2, 3):
+            g = oracle.fix(f, fh, xi, tier=tier)["g"]
+            for field in (np.clip(fh, f - xi, f + xi).astype(np.float32), g):
+                r = h.verify(field, xi)
+                o = oracle.verify(f, field)
+                assert r["fp"] == [o["fp%d" % d] for d in range(4)]
+                assert r["fn"] == [o["fn%d" % d] for d in range(4)]
+                assert r["sep_mismatch"][:2] == [o["sep_desc"], o["sep_asc"]]
+                assert r["term_mismatch"] == [o["term_desc"], o["term_asc"]]
+                assert (r["sep_mismatch"][2] == 0) == (o["sep_saddle"] == 0)
+                assert abs(r["max_abs_err"] - o["max_abs_err"]) == 0.0
+
+
+def test_edge_cases(lib):
+    # no edits needed: f_hat == f
+    f, _, xi, _ = synth.config_case("grf3d", size=9, rel=1e-2)
+    g, ed = lib.Handle(f).fix(f, xi)
+    assert np.array_equal(g, f) and ed["n_iters_c"] == 0 and ed["n_iters_s"] == 0 and ed["n_lossless"] == 0
+    # constant original field (every tie broken by index), noisy base
+    c = np.zeros((12, 15), np.float32)
+    _check_fix(lib, c, (c + np.random.default_rng(1).uniform(-0.1, 0.1, c.shape)).astype(np.float32), 0.1, 4)
+    # smallest grids
+    for shape in ((2, 2), (2, 7), (2, 2, 2), (3, 2, 2)):
+        f = _field(shape, "normal", 3)
+        fh = (f + np.random.default_rng(2).uniform(-0.5, 0.5, shape)).astype(np.float32)
+        _check_fix(lib, f, fh, 0.5, 4)
+
+
+def test_float_tie_stall_and_fallback(lib):
+    a = np.float32(-1.0 + 2.0 ** -24)
+    b = np.float32(-1.0 + 2.0 ** -23)
+    xi = float(np.float32(2.0 ** -23))
+    f = np.float32([[b, a], [10, 11]])
+    fh = np.float32([[-1.0, a + 2 ** -24], [10, 11]])
+    _check_fix(lib, f, fh, xi, 4)
+    with pytest.raises(lib.MscError) as e:
+        lib.Handle(f).fix(fh, xi, exact_fallback=0)
+    assert e.value.status == 6
+
+
+def test_invalid_arguments(lib):
+    f = np.zeros((4, 5), np.float32)
+    bad = f.copy()
+    bad[2, 2] = np.nan
+    with pytest.raises(lib.MscError) as e:
+        lib.Handle(bad)
+    assert e.value.status == 1
+    h = lib.Handle(f)
+    for kw, xi, fh in ((dict(), 0.1, bad), (dict(), 0.0, f), (dict(q_max=8), 0.1, f), (dict(tier=5), 0.1, f)):
+        with pytest.raises(lib.MscError) as e:
+            h.fix(fh, xi, **kw)
+        assert e.value.status == 1
+    with pytest.raises(lib.MscError) as e:
+        lib.Handle(np.zeros((1, 5), np.float32))
+    assert e.value.status == 1
+    f2, fh2, xi2, _ = synth.config_case("gauss2d")
+    with pytest.raises(lib.MscError) as e:
+        lib.Handle(f2).fix(fh2, xi2, max_iters=1)
+    assert e.value.status == 4
+
+
+def test_batch_equals_single(lib):
+    cases = [synth.config_case("grf3d", seed=30 + i, size=11, rel=1e-2) for i in range(3)]
+    cases += [synth.config_case("gauss2d", seed=5)]
+    hs = [lib.Handle(c[0]) for c in cases]
+    gs, eds = lib.fix_batch(hs, [c[1] for c in cases], [c[2] for c in cases], tier=4)
+    for (f, fh, xi, _), g, ed in zip(cases, gs, eds):
+        g1, ed1 = lib.Handle(f).fix(fh, xi, tier=4)
+        assert np.array_equal(g.view(np.uint32), g1.view(np.uint32))
+        assert (ed["n_iters_c"], ed["n_iters_s"]) == (ed1["n_iters_c"], ed1["n_iters_s"])
+
+
+# ------------------------------------------------------------------------------------
+# full-size workloads: properties that hold at any size, plus oracle checks on samples
+# ------------------------------------------------------------------------------------
+
+def _window_crit(field, box):
+    """critical cells of a sub-block, keeping only cells two vertices inside it"""
+    (z0, z1), (y0, y1), (x0, x1) = box
+    sub = np.ascontiguousarray(field[z0:z1, y0:y1, x0:x1] if field.ndim == 3 else field[y0:y1, x0:x1])
+    cells, dims = oracle.critical_cells(sub)
+    shp = sub.shape
+    keep = []
+    for c, d in zip(cells, dims):
+        ok = True
+        for v in c[c >= 0]:
+            idx = np.unravel_index(v, shp)
+            ok = ok and all(2 <= i < s - 2 for i, s in zip(idx, shp))
+        if ok:
+            keep.append((tuple(c), int(d)))
+    return sorted(keep)
+
+
+def _full_size_check(lib, f, fh, xi, tier, n_windows=6, win=14):
+    import torch
+    fd, fhd = torch.from_numpy(f).cuda(), torch.from_numpy(fh).cuda()
+    gd = torch.empty_like(fd)
+    h = lib.Handle(fd)
+    _, ed = h.fix(fhd, xi, g_out=gd, tier=tier)
+    rep = h.verify(gd, xi)
+    assert rep["passed"], rep
+    g = gd.cpu().numpy()
+    # bound, exactly (float differences of nearby values are exact in float64)
+    assert np.all(np.abs(g.astype(np.float64) - f.astype(np.float64)) <= xi)
+    # every stored state is one of Eq. 2's values (or a restore), recomputed by the oracle
+    lb, ub, fc, qv = oracle.edit_values(f.reshape(-1), fh.reshape(-1), xi, 6)
+    qm = ed["q_map"].reshape(-1)
+    quant = qm != 0xFF
+    assert np.array_equal(g.reshape(-1)[quant].view(np.uint32),
+                          qv[np.nonzero(quant)[0], qm[quant]].view(np.uint32))
+    # decompression side rebuilds g
+    g2 = lib.apply_edits(fh, xi, 6, ed)
+    assert np.array_equal(g2.view(np.uint32), g.view(np.uint32))
+    # sampled windows: the oracle sees the same critical cells in g as in f
+    rng = np.random.default_rng(7)
+    for _ in range(n_windows):
+        box = [(0, 1)] if f.ndim == 2 else []
+        for s in f.shape:
+            o = int(rng.integers(0, s - win + 1))
+            box.append((o, o + win))
+        if f.ndim == 2:
+            box = [(0, 1)] + box[1:]
+        assert _window_crit(g, box if f.ndim == 3 else box) == _window_crit(f, box if f.ndim == 3 else box)
+    return ed
+
+
+def test_full_size_multiscale_2d(lib):
+    f, fh, xi, tier = synth.config_case("multiscale2d")
+    _full_size_check(lib, f, fh, xi, tier)
+
+
+def test_full_size_grf_256(lib):
+    f, fh, xi, tier = synth.config_case("grf3d")
+    _full_size_check(lib, f, fh, xi, tier, n_windows=4, win=12)
+
+
+def test_full_size_kolmogorov_512(lib):
+    f, fh, xi, tier = synth.config_case("kolmogorov3d")
+    _full_size_check(lib, f, fh, xi, tier, n_windows=4, win=12)
