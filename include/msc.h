@@ -118,8 +118,11 @@ typedef struct {
                                     descending, ascending, saddle-saddle (per 2-saddle) */
     uint64_t term_mismatch[2];   /* descending / ascending separatrices ending elsewhere */
     double max_abs_err;          /* max |g - f| */
-    int pass;                    /* 1 iff no false critical cell, no separatrix mismatch
-                                    and max_abs_err <= xi */
+    int pass;                    /* pass_tier[3]: the full MSC (tier 4) is preserved */
+    int pass_tier[4];            /* pass_tier[t-1] = 1 iff max_abs_err <= xi and tier t holds:
+                                    1 no false extremum, 2 no false critical cell,
+                                    3 + no separatrix ending elsewhere,
+                                    4 + no separatrix pair missing from g's gradient */
     int reserved;
 } msc_report;
 

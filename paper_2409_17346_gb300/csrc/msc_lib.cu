@@ -843,8 +843,14 @@ template <int D> msc_status verify_impl(msc_handle *h, const float *gdev, float 
     }
     unsigned long long sep = 0;
     for (int i = 0; i < 3; i++) sep += out->sep_mismatch[i];
-    out->pass = crit_bad == 0 && sep == 0 && out->term_mismatch[0] == 0 && out->term_mismatch[1] == 0 &&
-                out->max_abs_err <= (double)xi;
+    const bool bound = out->max_abs_err <= (double)xi;
+    const bool ext = out->fp[0] + out->fn[0] + out->fp[D] + out->fn[D] == 0;
+    const bool term = out->term_mismatch[0] + out->term_mismatch[1] == 0;
+    out->pass_tier[0] = bound && ext;
+    out->pass_tier[1] = bound && crit_bad == 0;
+    out->pass_tier[2] = out->pass_tier[1] && term;
+    out->pass_tier[3] = out->pass_tier[2] && sep == 0;
+    out->pass = out->pass_tier[3];
     return MSC_OK;
 }
 

@@ -57,7 +57,7 @@ class Edits(ctypes.Structure):
 class Report(ctypes.Structure):
     _fields_ = [("fp", ctypes.c_uint64 * 4), ("fn", ctypes.c_uint64 * 4), ("sep_mismatch", ctypes.c_uint64 * 3),
                 ("term_mismatch", ctypes.c_uint64 * 2), ("max_abs_err", ctypes.c_double), ("pass_", ctypes.c_int),
-                ("reserved", ctypes.c_int)]
+                ("pass_tier", ctypes.c_int * 4), ("reserved", ctypes.c_int)]
 
 
 _lib = None
@@ -221,7 +221,8 @@ class Handle:
         r = Report()
         _check(lib.msc_verify(self._h, p, ctypes.c_float(xi), ctypes.byref(r)))
         return dict(fp=list(r.fp), fn=list(r.fn), sep_mismatch=list(r.sep_mismatch),
-                    term_mismatch=list(r.term_mismatch), max_abs_err=r.max_abs_err, passed=bool(r.pass_))
+                    term_mismatch=list(r.term_mismatch), max_abs_err=r.max_abs_err, passed=bool(r.pass_),
+                    passed_tier=[bool(x) for x in r.pass_tier])
 
 
 def apply_edits(f_hat, xi, q_max, edits, g_out=None):

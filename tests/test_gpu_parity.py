@@ -86,7 +86,8 @@ def _check_fix(lib, f, fh, xi, tier, q_max=6, exact_fallback=1):
     assert np.array_equal(ed["lossless_idx"].astype(np.int64), li)
     assert np.array_equal(ed["lossless_val"].view(np.uint32), lv.view(np.uint32))
     rep = h.verify(g, xi)
-    assert rep["passed"]
+    assert rep["passed_tier"][tier - 1]
+    assert all(rep["passed_tier"][:tier])
     h.close()
     return g, ed
 
@@ -235,7 +236,7 @@ def _full_size_check(lib, f, fh, xi, tier, n_windows=6, win=14):
     h = lib.Handle(fd)
     _, ed = h.fix(fhd, xi, g_out=gd, tier=tier)
     rep = h.verify(gd, xi)
-    assert rep["passed"], rep
+    assert rep["passed_tier"][tier - 1], rep
     g = gd.cpu().numpy()
     # bound, exactly (float differences of nearby values are exact in float64)
     assert np.all(np.abs(g.astype(np.float64) - f.astype(np.float64)) <= xi)
