@@ -232,6 +232,7 @@ def main():
     # per-class device time over the timed steps; the dominant class sets the roofline
     cls_ms = {k: sum(s[k]["ms"] for s, _ in stats) for k in msc.KERNEL_CLASSES}
     cls_launch = {k: sum(s[k]["timed"] for s, _ in stats) for k in msc.KERNEL_CLASSES}
+    cls_items = {k: sum(s[k]["items"] for s, _ in stats) for k in msc.KERNEL_CLASSES}
     launches = sum(s[k]["launches"] for s, _ in stats for k in msc.KERNEL_CLASSES)
     dom = max(cls_ms, key=cls_ms.get)
     peak, peak_kind = peaks()
@@ -286,6 +287,8 @@ def main():
                        "l2": "inputs (%d MB each) exceed L2; no flush" % (4 * n >> 20),
                        "verify_passed": rep["passed"],
                        "kernel_ms_per_step": {k: v / args.steps for k, v in cls_ms.items()},
+                       "kernel_launches_per_step": {k: v / args.steps for k, v in cls_launch.items()},
+                       "kernel_items_per_step": {k: v / args.steps for k, v in cls_items.items()},
                        "launches_per_step": launches / args.steps},
             "roofline": roof, "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
         }

@@ -72,16 +72,21 @@ enum {
     MSC_K_EDIT = 2,      /* quantised edit (Eq. 2) + dirty-anchor marking */
     MSC_K_REFRESH = 3,   /* gradient of the anchors around edited vertices */
     MSC_K_REBUILD = 4,   /* mismatch-list rebuild and set clears */
-    MSC_K_SPASS = 5,     /* separatrix walks (Sec. 4.4) */
-    MSC_K_OTHER = 6,     /* initialisation, seeds, output encoding, checks */
-    MSC_K_COUNT = 7
+    MSC_K_SEP_INIT = 5,  /* separatrix state: first build of an S-pass (Sec. 4.4) */
+    MSC_K_SEP_UPDATE = 6,/* separatrix state: updates around edits; full walks (tier 3) */
+    MSC_K_SEP_TARGETS = 7,/* troublemakers from the separatrix state */
+    MSC_K_OTHER = 8,     /* initialisation, seeds, output encoding, checks */
+    MSC_K_COUNT = 9
 };
 
 /* per-handle launch statistics (msc_get_stats); times only with options.profile = 1 */
 typedef struct {
-    uint64_t launches[8];        /* kernel launches by class, always counted */
-    double ms[8];                /* summed CUDA-event duration by class (profiled calls) */
-    uint64_t timed_launches[8];  /* launches that were timed */
+    uint64_t launches[12];       /* kernel launches by class, always counted */
+    double ms[12];               /* summed CUDA-event duration by class (profiled calls) */
+    uint64_t timed_launches[12]; /* launches that were timed */
+    uint64_t items[12];          /* work items processed by class: anchors (dense, separatrix
+                                    init), edited vertices (edit), separatrix node updates
+                                    (separatrix update), mismatch anchors (separatrix targets) */
 } msc_stats;
 
 /* one edit round: kind 0 = C-pass (false critical cells), 1 = S-pass (separatrices);

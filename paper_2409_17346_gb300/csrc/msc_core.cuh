@@ -43,7 +43,8 @@ struct Grid {
 
 struct Counters {
     unsigned long long ncase, nlive, nT, nX, sumT, sumX;   // targeting pass
-    unsigned long long nchanged, nD, nM, novf, err, steps;
+    unsigned long long nchanged, nD, nM, novf, err, nSD;
+    unsigned long long steps[4];                           // cells stepped: desc, asc, saddle
     unsigned long long rep[16];                            // verify / misc
 };
 
@@ -67,6 +68,10 @@ struct Ctx {
     uint32_t *ovf_in, *ovf_out;      // saddle-saddle spill queues: (triangle id, entry edge) pairs
     uint32_t ovf_cap;
     Counters *cnt;
+    // persistent separatrix state (tier 4): one byte per node, see "separatrix state" below
+    uint8_t *ns_v, *ns_top, *ns_tri, *ns_dead;
+    uint32_t *sDbits, *sDlist;       // anchors dirtied since the last S-pass
+    int track_dirty;
 };
 
 // ------------------------------------------------------------------------------------
@@ -92,6 +97,19 @@ inline float add_rd(float a, float b) { return emu_add_rd(a, b); }
 inline float sub_rn(float a, float b) { volatile float r = a - b; return r; }
 inline float mul_rn(float a, float b) { volatile float r = a * b; return r; }
 template <class T> inline T ld(const T *p) { return *p; }
+#endif
+
+// add v to a hot counter: one atomic per group of converged threads
+#ifdef __CUDA_ARCH__
+__device__ __forceinline__ void count_add(unsigned long long *p, unsigned long long v)
+{
+    const unsigned mask = __activemask();
+    const unsigned lo = __reduce_add_sync(mask, (unsigned)(v & 0xffffffffu));
+    const unsigned hi = __reduce_add_sync(mask, (unsigned)(v >> 32));
+    if ((threadIdx.x & 31) == (unsigned)(__ffs(mask) - 1)) atomicAdd(p, ((unsigned long long)hi << 32) + lo);
+}
+#else
+inline void count_add(unsigned long long *p, unsigned long long v) { *p += v; }
 #endif
 
 MSC_HD inline bool test_and_set(uint32_t *bits, uint32_t i)
@@ -439,12 +457,12 @@ template <int D> MSC_HD inline uint32_t desc_end(const uint64_t *code, const Gri
     return 0xFFFFFFFFu;
 }
 
-template <int D> MSC_HD inline void desc_walk(const Ctx &c, uint32_t u)
+template <int D> MSC_HD inline void desc_walk_impl(const Ctx &c, uint32_t u, uint32_t &s)
 {
     const Tab<D> &T = rt_tab<D>();
     int x, y, z;
     coords(c.G, u, x, y, z);
-    for (uint32_t s = 0; s <= c.G.n; s++) {
+    for (s = 0; s <= c.G.n; s++) {
         if (test_and_set(c.vis_v, u)) return;
         const int ff = vfield<D>(ld(c.code_f + u));
         if (ff == 15) return;
@@ -461,6 +479,13 @@ template <int D> MSC_HD inline void desc_walk(const Ctx &c, uint32_t u)
         }
         x = wx; y = wy; z = wz; u = w;
     }
+}
+
+template <int D> MSC_HD inline void desc_walk(const Ctx &c, uint32_t u)
+{
+    uint32_t s = 0;
+    desc_walk_impl<D>(c, u, s);
+    count_add(&c.cnt->steps[0], (unsigned long long)s + 1);
 }
 
 // top cells: tets (3D) or triangles (2D); id = anchor * NTOP + type
@@ -543,12 +568,12 @@ MSC_HD inline unsigned long long asc_end(const Grid &G, const float *vals, const
     return ~0ull;
 }
 
-template <int D> MSC_HD inline void asc_walk(const Ctx &c, uint32_t beta)
+template <int D> MSC_HD inline void asc_walk_impl(const Ctx &c, uint32_t beta, uint32_t &s)
 {
     const Tab<D> &T = rt_tab<D>();
     int x, y, z, t = (int)(beta % T.NTOP);
     coords(c.G, beta / T.NTOP, x, y, z);
-    for (uint32_t s = 0; s <= c.G.n * (uint32_t)T.NTOP; s++) {
+    for (s = 0; s <= c.G.n * (uint32_t)T.NTOP; s++) {
         if (test_and_set(c.vis_top, vid(c.G, x, y, z) * T.NTOP + t)) return;
         int fx, fy, fz, ft, ib, jl;
         if (!asc_facet<D>(c.G, c.f, x, y, z, t, c.code_f, fx, fy, fz, ft, ib, jl)) return;   // maximum
@@ -562,6 +587,13 @@ template <int D> MSC_HD inline void asc_walk(const Ctx &c, uint32_t beta)
         }
         if (!asc_next<D>(c.G, fx, fy, fz, ft, ib, x, y, z, t)) return;   // leaves the domain
     }
+}
+
+template <int D> MSC_HD inline void asc_walk(const Ctx &c, uint32_t beta)
+{
+    uint32_t s = 0;
+    asc_walk_impl<D>(c, beta, s);
+    count_add(&c.cnt->steps[1], (unsigned long long)s + 1);
 }
 
 // saddle-saddle connectors (3D, tier 4): depth-first over triangles reached from a
@@ -584,9 +616,11 @@ MSC_HD inline void ss_walk(const Ctx &c, uint32_t tri0, uint32_t entry0, bool se
     if (seed && test_and_set(c.vis_tri, tri0)) return;
     uint32_t st_tri[SS_STACK], st_ent[SS_STACK];
     int sp = 0;
+    unsigned long long nvis = 0;
     st_tri[sp] = tri0; st_ent[sp] = entry0; sp++;
     while (sp > 0) {
         sp--;
+        nvis++;
         const uint32_t tri = st_tri[sp], entry = st_ent[sp];
         const int tt = (int)(tri % 12);
         int x, y, z;
@@ -620,6 +654,318 @@ MSC_HD inline void ss_walk(const Ctx &c, uint32_t tri0, uint32_t entry0, bool se
             if (test_and_set(c.vis_tri, tri2)) continue;
             if (sp < SS_STACK) { st_tri[sp] = tri2; st_ent[sp] = eid; sp++; }
             else ss_push_global(c, tri2, eid);
+        }
+    }
+    count_add(&c.cnt->steps[2], nvis);
+}
+
+// ------------------------------------------------------------------------------------
+// separatrix state (tier 4): the S-pass walks kept incrementally across S-passes
+// ------------------------------------------------------------------------------------
+// The S-pass of Sec. 4.4 walks every separatrix of f from its saddle and stops at the first
+// pair missing from g's gradient.  The set of cells such a walk reaches depends on g only
+// through the pairs it checks, and between two S-passes g changes only around edited
+// vertices.  So the walks are kept as a state: one byte per node
+//   descending: a vertex u (its pair (u, u next_f(u)));     ascending: a top cell beta (its
+//   pair with its f-facet); saddle-saddle: a triangle t' = V_f(e) (pair (e, t')) and every
+//   edge paired down in f (a dead end of the triangle walk);
+// holding bit 7 = the node's f-pair is missing from g ("mismatch"), bit 6 = the node is a
+// seed, bits 0..5 = the number of reached predecessors passing into it.  A path node is
+// reached iff it is a seed or has such a predecessor, and passes on iff reached and not
+// mismatched; a triangle node is reached (passes on) iff it is a seed, or has a reached
+// parent and no mismatch.  Troublemakers are the mismatched nodes with a reached
+// predecessor - exactly the first disagreeing pairs the walks stop at.  Counts change by
+// atomic byte updates whose before/after values decide what to pass on, so concurrent
+// updates always settle on the same state.
+constexpr uint8_t NS_MIS = 0x80, NS_SEED = 0x40, NS_CNT = 0x3F;
+
+MSC_HD inline uint8_t byte_add(uint8_t *base, uint32_t i, int delta)
+{
+#ifdef __CUDA_ARCH__
+    const int sh = 8 * (int)(i & 3u);
+    const uint32_t old = atomicAdd((uint32_t *)(base + (i & ~3u)), (uint32_t)delta << sh);
+    return (uint8_t)(old >> sh);
+#else
+    const uint8_t o = base[i];
+    base[i] = (uint8_t)(o + delta);
+    return o;
+#endif
+}
+
+MSC_HD inline uint8_t byte_xor(uint8_t *base, uint32_t i, uint8_t m)
+{
+#ifdef __CUDA_ARCH__
+    const int sh = 8 * (int)(i & 3u);
+    const uint32_t old = atomicXor((uint32_t *)(base + (i & ~3u)), (uint32_t)m << sh);
+    return (uint8_t)(old >> sh);
+#else
+    const uint8_t o = base[i];
+    base[i] = (uint8_t)(o ^ m);
+    return o;
+#endif
+}
+
+MSC_HD inline uint8_t byte_or(uint8_t *base, uint32_t i, uint8_t m)
+{
+#ifdef __CUDA_ARCH__
+    const int sh = 8 * (int)(i & 3u);
+    const uint32_t old = atomicOr((uint32_t *)(base + (i & ~3u)), (uint32_t)m << sh);
+    return (uint8_t)(old >> sh);
+#else
+    const uint8_t o = base[i];
+    base[i] = (uint8_t)(o | m);
+    return o;
+#endif
+}
+
+MSC_HD inline uint8_t byte_load(const uint8_t *base, uint32_t i) { return ((const volatile uint8_t *)base)[i]; }
+
+MSC_HD inline bool path_reached(uint8_t b) { return (b & NS_SEED) || (b & NS_CNT); }
+MSC_HD inline int path_passes(uint8_t b) { return path_reached(b) && !(b & NS_MIS); }
+MSC_HD inline int tri_passes(uint8_t b) { return (b & NS_SEED) || ((b & NS_CNT) && !(b & NS_MIS)); }
+
+// successor of vertex u on its descending V-path in f
+template <int D> MSC_HD inline bool desc_succ(const Ctx &c, uint32_t u, uint32_t &w)
+{
+    const Tab<D> &T = rt_tab<D>();
+    const int ff = vfield<D>(ld(c.code_f + u));
+    if (ff == 15) return false;
+    int x, y, z;
+    coords(c.G, u, x, y, z);
+    w = vid(c.G, x + T.nb[ff][0], y + T.nb[ff][1], z + T.nb[ff][2]);
+    return true;
+}
+
+// successor of top cell beta on its ascending V-path in f
+template <int D> MSC_HD inline bool asc_succ(const Ctx &c, uint32_t beta, uint32_t &nb)
+{
+    int x, y, z, t = (int)(beta % Tab<D>::NTOP);
+    coords(c.G, beta / Tab<D>::NTOP, x, y, z);
+    int fx, fy, fz, ft, ib, jl;
+    if (!asc_facet<D>(c.G, c.f, x, y, z, t, c.code_f, fx, fy, fz, ft, ib, jl)) return false;
+    if (!asc_next<D>(c.G, fx, fy, fz, ft, ib, x, y, z, t)) return false;
+    nb = vid(c.G, x, y, z) * Tab<D>::NTOP + (uint32_t)t;
+    return true;
+}
+
+// add delta to the reached-predecessor count of a path node and follow the change along
+// the path (kind 0: descending vertices, 1: ascending top cells)
+template <int D> MSC_HD inline void path_push(const Ctx &c, int kind, uint32_t w, int delta)
+{
+    uint8_t *ns = kind == 0 ? c.ns_v : c.ns_top;
+    unsigned long long n = 0;
+    for (uint32_t s = 0; s <= c.G.n * (uint32_t)Tab<D>::NTOP; s++) {
+        n++;
+        const uint8_t o = byte_add(ns, w, delta), nw = (uint8_t)(o + delta);
+        const int d = path_passes(nw) - path_passes(o);
+        if (!d) break;
+        uint32_t nx;
+        if (!(kind == 0 ? desc_succ<D>(c, w, nx) : asc_succ<D>(c, w, nx))) break;
+        w = nx;
+        delta = d;
+    }
+    count_add(&c.cnt->steps[kind], n);
+}
+
+// a path node becomes a seed / changes its mismatch bit
+template <int D> MSC_HD inline void path_change(const Ctx &c, int kind, uint32_t u, uint8_t o, uint8_t nw)
+{
+    const int d = path_passes(nw) - path_passes(o);
+    uint32_t w;
+    if (d && (kind == 0 ? desc_succ<D>(c, u, w) : asc_succ<D>(c, u, w))) path_push<D>(c, kind, w, d);
+}
+
+// children of a reached triangle node: its facet edges other than the one it is paired with
+// in f; an edge paired up in f leads to its partner triangle, an edge paired down is a dead
+// end, a critical edge (1-saddle) ends the walk
+MSC_HD inline int tri_children(const Ctx &c, uint32_t tri, uint32_t *out, bool *dead)
+{
+    const Tab<3> &T = rt_tab<3>();
+    const int tt = (int)(tri % 12);
+    int x, y, z;
+    coords(c.G, tri / 12, x, y, z);
+    int entry = -1;
+    if (tfield<3>(ld(c.code_f + tri / 12), tt) == 1) {
+        Verts V = cell_verts<3>(c.G, x, y, z, 2, tt);
+        const int jl = lowest_of(V, c.f);
+        const int corner = jl == 0 ? 0 : (jl == 1 ? T.tA[tt] : T.tB[tt]);
+        for (int j = 0; j < 3; j++) if (T.tfac_opp[tt][j] == corner) entry = j;
+    }
+    int n = 0;
+    for (int j = 0; j < 3; j++) {
+        if (j == entry) continue;
+        const int ex = x + T.tfac_anc[tt][j][0], ey = y + T.tfac_anc[tt][j][1], ez = z + T.tfac_anc[tt][j][2];
+        const int et = T.tfac_type[tt][j];
+        const uint32_t ea = vid(c.G, ex, ey, ez);
+        const int ef = efield<3>(ld(c.code_f + ea), et);
+        if (ef == 0) continue;
+        if (ef == 1) { out[n] = ea * 7 + (uint32_t)et; dead[n] = true; n++; continue; }
+        const int i = ef - 2;
+        out[n] = vid(c.G, ex + T.ecof_anc[et][i][0], ey + T.ecof_anc[et][i][1], ez + T.ecof_anc[et][i][2]) * 12 +
+                 (uint32_t)T.ecof_type[et][i];
+        dead[n] = false;
+        n++;
+    }
+    return n;
+}
+
+MSC_HD inline void ss_spill(const Ctx &c, uint32_t tri, int delta)
+{
+    const unsigned long long i = a_add(&c.cnt->novf, 1ull);
+    if (i < c.ovf_cap) { c.ovf_out[2 * i] = tri; c.ovf_out[2 * i + 1] = (uint32_t)delta; }
+    else a_add(&c.cnt->err, 1ull);
+}
+
+// a triangle node's passing state changed by dv: pass dv to all its children, and keep
+// following changes depth-first (local stack, spilled to a global queue when full)
+MSC_HD inline void tri_propagate(const Ctx &c, uint32_t tri0, int dv0, bool apply_first, int delta0)
+{
+    uint32_t st[SS_STACK];
+    int sd[SS_STACK];
+    int sp = 0;
+    unsigned long long n = 0;
+    if (apply_first) { st[sp] = tri0; sd[sp] = delta0; sp++; }
+    auto expand = [&](uint32_t t, int dv) {
+        uint32_t ch[3];
+        bool dead[3];
+        const int k = tri_children(c, t, ch, dead);
+        for (int i = 0; i < k; i++) {
+            if (dead[i]) { byte_add(c.ns_dead, ch[i], dv); continue; }
+            if (sp < SS_STACK) { st[sp] = ch[i]; sd[sp] = dv; sp++; }
+            else ss_spill(c, ch[i], dv);
+        }
+    };
+    if (!apply_first) expand(tri0, dv0);
+    while (sp > 0) {
+        sp--;
+        const uint32_t t = st[sp];
+        const int d = sd[sp];
+        n++;
+        const uint8_t o = byte_add(c.ns_tri, t, d), nw = (uint8_t)(o + d);
+        const int dv = tri_passes(nw) - tri_passes(o);
+        if (dv) expand(t, dv);
+    }
+    count_add(&c.cnt->steps[2], n);
+}
+
+// node states of the pairs anchored at p, from the codes of f and g.  init: only set the
+// mismatch bits (all counts are zero); otherwise flip changed bits and propagate.
+template <int D> MSC_HD inline void node_bits(const Ctx &c, uint32_t p, bool init)
+{
+    const Tab<D> &T = rt_tab<D>();
+    const uint64_t cf = ld(c.code_f + p), cg = c.code_g[p];
+    int x, y, z;
+    coords(c.G, p, x, y, z);
+    auto set_path = [&](int kind, uint32_t u, bool m) {
+        uint8_t *ns = kind == 0 ? c.ns_v : c.ns_top;
+        if (init) { if (m) byte_or(ns, u, NS_MIS); return; }
+        if (((byte_load(ns, u) & NS_MIS) != 0) == m) return;
+        const uint8_t o = byte_xor(ns, u, NS_MIS);
+        path_change<D>(c, kind, u, o, (uint8_t)(o ^ NS_MIS));
+    };
+    const int vf = vfield<D>(cf);
+    if (vf != 15) set_path(0, p, vfield<D>(cg) != vf);
+    const int nfac = D == 3 ? T.NT : T.NE;
+    for (int ft = 0; ft < nfac; ft++) {
+        const int ff = facet_field<D>(cf, ft);
+        if (ff < 2) continue;
+        const int i = ff - 2;
+        const int *an = D == 3 ? T.tcof_anc[ft][i] : T.ecof_anc[ft][i];
+        const int bt = D == 3 ? T.tcof_type[ft][i] : T.ecof_type[ft][i];
+        set_path(1, vid(c.G, x + an[0], y + an[1], z + an[2]) * T.NTOP + (uint32_t)bt, facet_field<D>(cg, ft) != ff);
+    }
+    if constexpr (D == 3) {
+        for (int et = 0; et < T.NE; et++) {
+            const int ef = efield<D>(cf, et);
+            if (ef == 0) continue;
+            const bool m = efield<D>(cg, et) != ef;
+            if (ef == 1) {
+                const uint32_t e = p * 7 + (uint32_t)et;
+                if (init) { if (m) byte_or(c.ns_dead, e, NS_MIS); continue; }
+                if (((byte_load(c.ns_dead, e) & NS_MIS) != 0) != m) byte_xor(c.ns_dead, e, NS_MIS);
+                continue;
+            }
+            const int i = ef - 2;
+            const uint32_t t2 = vid(c.G, x + T.ecof_anc[et][i][0], y + T.ecof_anc[et][i][1], z + T.ecof_anc[et][i][2]) * 12 +
+                                (uint32_t)T.ecof_type[et][i];
+            if (init) { if (m) byte_or(c.ns_tri, t2, NS_MIS); continue; }
+            if (((byte_load(c.ns_tri, t2) & NS_MIS) != 0) == m) continue;
+            const uint8_t o = byte_xor(c.ns_tri, t2, NS_MIS);
+            const int dv = tri_passes((uint8_t)(o ^ NS_MIS)) - tri_passes(o);
+            if (dv) tri_propagate(c, t2, dv, false, 0);
+        }
+    }
+}
+
+// seeds: kind 0 descending vertex, 1 ascending top cell, 2 2-saddle triangle
+template <int D> MSC_HD inline void node_seed(const Ctx &c, int kind, uint32_t u)
+{
+    if (kind == 2) {
+        const uint8_t o = byte_or(c.ns_tri, u, NS_SEED);
+        if (o & NS_SEED) return;
+        const int dv = tri_passes((uint8_t)(o | NS_SEED)) - tri_passes(o);
+        if (dv) tri_propagate(c, u, dv, false, 0);
+        return;
+    }
+    uint8_t *ns = kind == 0 ? c.ns_v : c.ns_top;
+    const uint8_t o = byte_or(ns, u, NS_SEED);
+    if (o & NS_SEED) return;
+    path_change<D>(c, kind, u, o, (uint8_t)(o | NS_SEED));
+}
+
+// troublemakers among the pairs anchored at p (p has a code mismatch)
+template <int D> MSC_HD inline void node_targets(const Ctx &c, uint32_t p)
+{
+    const Tab<D> &T = rt_tab<D>();
+    const uint64_t cf = ld(c.code_f + p), cg = c.code_g[p];
+    if (cf == cg) return;
+    int x, y, z;
+    coords(c.G, p, x, y, z);
+    const int vf = vfield<D>(cf);
+    if (vf != 15) {
+        const uint8_t b = byte_load(c.ns_v, p);
+        if ((b & NS_MIS) && path_reached(b)) {
+            Verts V;
+            V.n = 0;
+            vpush(V, c.G, x, y, z);
+            vpush(V, c.G, x + T.nb[vf][0], y + T.nb[vf][1], z + T.nb[vf][2]);
+            add_case<D>(c, V.id[1], V);
+        }
+    }
+    const int nfac = D == 3 ? T.NT : T.NE;
+    for (int ft = 0; ft < nfac; ft++) {
+        const int ff = facet_field<D>(cf, ft);
+        if (ff < 2) continue;
+        const int i = ff - 2;
+        const int *an = D == 3 ? T.tcof_anc[ft][i] : T.ecof_anc[ft][i];
+        const int bt = D == 3 ? T.tcof_type[ft][i] : T.ecof_type[ft][i];
+        const int bx = x + an[0], by = y + an[1], bz = z + an[2];
+        const uint8_t b = byte_load(c.ns_top, vid(c.G, bx, by, bz) * T.NTOP + (uint32_t)bt);
+        if ((b & NS_MIS) && path_reached(b)) {
+            Verts V = top_verts<D>(c.G, bx, by, bz, bt);
+            add_case<D>(c, V.id[lowest_of(V, c.f)], V);
+        }
+    }
+    if constexpr (D == 3) {
+        for (int et = 0; et < T.NE; et++) {
+            const int ef = efield<D>(cf, et);
+            if (ef == 0) continue;
+            if (ef == 1) {
+                const uint8_t b = byte_load(c.ns_dead, p * 7 + (uint32_t)et);
+                if ((b & NS_MIS) && (b & NS_CNT)) {
+                    Verts V = cell_verts<3>(c.G, x, y, z, 1, et);
+                    add_case<3>(c, V.id[lowest_of(V, c.f)], V);
+                }
+                continue;
+            }
+            const int i = ef - 2;
+            const int tx = x + T.ecof_anc[et][i][0], ty = y + T.ecof_anc[et][i][1], tz = z + T.ecof_anc[et][i][2];
+            const int t2 = T.ecof_type[et][i];
+            const uint8_t b = byte_load(c.ns_tri, vid(c.G, tx, ty, tz) * 12 + (uint32_t)t2);
+            if ((b & NS_MIS) && (b & NS_CNT) && !(b & NS_SEED)) {
+                Verts V = cell_verts<3>(c.G, tx, ty, tz, 2, t2);
+                add_case<3>(c, vid(c.G, x + T.ecof_v[et][i][0], y + T.ecof_v[et][i][1], z + T.ecof_v[et][i][2]), V);
+            }
         }
     }
 }

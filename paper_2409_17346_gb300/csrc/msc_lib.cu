@@ -134,12 +134,14 @@ template <int D> __global__ void __launch_bounds__(TPB) k_refresh(Ctx c)
     GRID_STRIDE(i, n) refresh_anchor<D>(c, c.Dlist[i]);
 }
 
-__global__ void k_rebuild(Ctx c, const uint32_t *Mcur, const unsigned long long *nMcur, unsigned long long *nMnext)
+__global__ void k_rebuild(Ctx c, const uint32_t *Mcur, const unsigned long long *nMcur, unsigned long long *nMnext,
+                          unsigned long long *nSD)
 {
     const unsigned long long a = *nMcur, b = c.cnt->nD;
     GRID_STRIDE(i, a + b)
     {
         const uint32_t p = i < a ? Mcur[i] : c.Dlist[i - a];
+        if (i >= a && c.track_dirty && !test_and_set(c.sDbits, p)) c.sDlist[atomicAdd(nSD, 1ull)] = p;
         if (__ldg(c.code_f + p) == c.code_g[p]) continue;
         if (atomicExch(c.stamp + p, c.tag) == c.tag) continue;
         c.Mnext[atomicAdd(nMnext, 1ull)] = p;
@@ -175,6 +177,39 @@ __global__ void k_ss_seed(Ctx c, const uint32_t *seeds, uint32_t n)
 __global__ void k_ss_spill(Ctx c, const uint32_t *items, uint32_t n)
 {
     GRID_STRIDE(i, n) ss_walk(c, items[2 * i], items[2 * i + 1], false);
+}
+
+template <int D> __global__ void __launch_bounds__(TPB) k_node_init(Ctx c)
+{
+    GRID_STRIDE(p, c.G.n) node_bits<D>(c, (uint32_t)p, true);
+}
+
+template <int D> __global__ void k_node_seed(Ctx c, int kind, const uint32_t *seeds, uint32_t n)
+{
+    GRID_STRIDE(i, n) node_seed<D>(c, kind, seeds[i]);
+}
+
+template <int D> __global__ void k_node_update(Ctx c, const unsigned long long *nSD)
+{
+    const unsigned long long n = *nSD;
+    GRID_STRIDE(i, n) node_bits<D>(c, c.sDlist[i], false);
+}
+
+__global__ void k_tri_spill(Ctx c, const uint32_t *items, uint32_t n)
+{
+    GRID_STRIDE(i, n) tri_propagate(c, items[2 * i], 0, true, (int)items[2 * i + 1]);
+}
+
+template <int D> __global__ void k_node_targets(Ctx c, const uint32_t *M, const unsigned long long *nM)
+{
+    const unsigned long long n = *nM;
+    GRID_STRIDE(i, n) node_targets<D>(c, M[i]);
+}
+
+__global__ void k_sd_clear(Ctx c, unsigned long long *nSD)
+{
+    const unsigned long long n = *nSD;
+    GRID_STRIDE(i, n) c.sDbits[c.sDlist[i] >> 5] = 0;
 }
 
 template <int D>
@@ -469,6 +504,8 @@ struct msc_handle {
     DevBuf<uint64_t> code_g;
     DevBuf<uint32_t> Tbits, Xbits, Dbits, Tlist, Xlist, Dlist, M0, M1, stamp;
     DevBuf<uint32_t> vis_v, vis_top, vis_tri, ovf0, ovf1;
+    DevBuf<uint8_t> ns_v, ns_top, ns_tri, ns_dead;
+    DevBuf<uint32_t> sDbits, sDlist;
     DevBuf<Counters> cnt;
     DevBuf<unsigned long long> nM;   // [2] counts of M0, M1; [2] scratch
     uint32_t tag = 0;
@@ -476,9 +513,10 @@ struct msc_handle {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // launch statistics
     bool prof_on = false;
-    unsigned long long launches[8] = {};
-    unsigned long long timed[8] = {};
-    double ms[8] = {};
+    unsigned long long launches[12] = {};
+    unsigned long long timed[12] = {};
+    unsigned long long items[12] = {};
+    double ms[12] = {};
     struct Pend {
         cudaEvent_t a, b;
         int cls;
@@ -561,6 +599,15 @@ msc_status alloc_fix_state(msc_handle *h)
         CK(h->ovf0.alloc(2 * n + 2));
         CK(h->ovf1.alloc(2 * n + 2));
     }
+    CK(h->ns_v.alloc(n + 4));
+    CK(h->ns_top.alloc(n * ntop + 4));
+    if (h->D == 3) {
+        CK(h->ns_tri.alloc(n * 12 + 4));
+        CK(h->ns_dead.alloc(n * 7 + 4));
+    }
+    CK(h->sDbits.alloc(words(n)));
+    CK(h->sDlist.alloc(n));
+    CK(cudaMemset(h->sDbits.p, 0, h->sDbits.n * 4));
     CK(h->cnt.alloc(1));
     CK(h->nM.alloc(4));
     CK(cudaMemset(h->Tbits.p, 0, h->Tbits.n * 4));
@@ -593,6 +640,9 @@ Ctx make_ctx(msc_handle *h, int tier, int qmax, int exact_fallback, float xi)
     c.vis_v = h->vis_v.p; c.vis_top = h->vis_top.p; c.vis_tri = h->vis_tri.p;
     c.ovf_cap = (uint32_t)h->G.n + 1;
     c.cnt = h->cnt.p;
+    c.ns_v = h->ns_v.p; c.ns_top = h->ns_top.p; c.ns_tri = h->ns_tri.p; c.ns_dead = h->ns_dead.p;
+    c.sDbits = h->sDbits.p; c.sDlist = h->sDlist.p;
+    c.track_dirty = 0;
     return c;
 }
 
@@ -640,13 +690,13 @@ template <int D> msc_status s_pass(msc_handle *h, const Ctx &c0, int tier, cudaS
     Ctx c = c0;
     CK(cudaMemsetAsync(h->vis_v.p, 0, h->vis_v.n * 4, s));
     CK(cudaMemsetAsync(h->vis_top.p, 0, h->vis_top.n * 4, s));
-    if (h->n_desc) KL(h, MSC_K_SPASS, s, k_desc<D><<<grid_for(h->n_desc), TPB, 0, s>>>(c, h->seeds_desc.p, h->n_desc));
-    if (h->n_asc) KL(h, MSC_K_SPASS, s, k_asc<D><<<grid_for(h->n_asc), TPB, 0, s>>>(c, h->seeds_asc.p, h->n_asc));
+    if (h->n_desc) KL(h, MSC_K_SEP_UPDATE, s, k_desc<D><<<grid_for(h->n_desc), TPB, 0, s>>>(c, h->seeds_desc.p, h->n_desc));
+    if (h->n_asc) KL(h, MSC_K_SEP_UPDATE, s, k_asc<D><<<grid_for(h->n_asc), TPB, 0, s>>>(c, h->seeds_asc.p, h->n_asc));
     CK(cudaGetLastError());
     if (D == 3 && tier >= 4 && h->n_ss) {
         CK(cudaMemsetAsync(h->vis_tri.p, 0, h->vis_tri.n * 4, s));
         c.ovf_out = h->ovf0.p;
-        KL(h, MSC_K_SPASS, s, k_ss_seed<<<grid_for(h->n_ss), TPB, 0, s>>>(c, h->seeds_ss.p, h->n_ss));
+        KL(h, MSC_K_SEP_UPDATE, s, k_ss_seed<<<grid_for(h->n_ss), TPB, 0, s>>>(c, h->seeds_ss.p, h->n_ss));
         CK(cudaGetLastError());
         uint32_t *in = h->ovf0.p, *out = h->ovf1.p;
         for (int round = 0; round < 1 << 20; round++) {
@@ -658,11 +708,59 @@ template <int D> msc_status s_pass(msc_handle *h, const Ctx &c0, int tier, cudaS
             const unsigned long long zero = 0;
             CK(cudaMemcpyAsync(&h->cnt.p->novf, &zero, sizeof zero, cudaMemcpyHostToDevice, s));
             c.ovf_out = out;
-            KL(h, MSC_K_SPASS, s, k_ss_spill<<<grid_for(hc.novf), TPB, 0, s>>>(c, in, (uint32_t)hc.novf));
+            KL(h, MSC_K_SEP_UPDATE, s, k_ss_spill<<<grid_for(hc.novf), TPB, 0, s>>>(c, in, (uint32_t)hc.novf));
             CK(cudaGetLastError());
             std::swap(in, out);
         }
     }
+    return MSC_OK;
+}
+
+// tier-4 S-pass from the persistent separatrix state: built once per fix, then updated at
+// the anchors dirtied since the previous S-pass; troublemakers read at the mismatch anchors
+template <int D> msc_status s_pass_state(msc_handle *h, Ctx &c, bool &built, const uint32_t *M,
+                                         unsigned long long *nM, unsigned long long *nSD, cudaStream_t s)
+{
+    c.ovf_out = D == 3 ? h->ovf0.p : nullptr;
+    if (!built) {
+        CK(cudaMemsetAsync(h->ns_v.p, 0, h->ns_v.n, s));
+        CK(cudaMemsetAsync(h->ns_top.p, 0, h->ns_top.n, s));
+        if (D == 3) {
+            CK(cudaMemsetAsync(h->ns_tri.p, 0, h->ns_tri.n, s));
+            CK(cudaMemsetAsync(h->ns_dead.p, 0, h->ns_dead.n, s));
+        }
+        KL(h, MSC_K_SEP_INIT, s, k_node_init<D><<<grid_for(h->G.n), TPB, 0, s>>>(c));
+        if (h->n_desc) KL(h, MSC_K_SEP_INIT, s, k_node_seed<D><<<grid_for(h->n_desc), TPB, 0, s>>>(c, 0, h->seeds_desc.p, h->n_desc));
+        if (h->n_asc) KL(h, MSC_K_SEP_INIT, s, k_node_seed<D><<<grid_for(h->n_asc), TPB, 0, s>>>(c, 1, h->seeds_asc.p, h->n_asc));
+        if (D == 3 && h->n_ss) KL(h, MSC_K_SEP_INIT, s, k_node_seed<D><<<grid_for(h->n_ss), TPB, 0, s>>>(c, 2, h->seeds_ss.p, h->n_ss));
+        CK(cudaGetLastError());
+        h->items[MSC_K_SEP_INIT] += h->G.n;
+        built = true;
+        c.track_dirty = 1;
+    } else {
+        KL(h, MSC_K_SEP_UPDATE, s, k_node_update<D><<<grid_for(h->G.n / 16 + 1), TPB, 0, s>>>(c, nSD));
+        CK(cudaGetLastError());
+    }
+    if (D == 3) {
+        uint32_t *in = h->ovf0.p, *out = h->ovf1.p;
+        for (int round = 0; round < 1 << 20; round++) {
+            Counters hc;
+            CK(cudaMemcpyAsync(&hc, h->cnt.p, sizeof hc, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (hc.err) return fail(MSC_ERR_OOM, "separatrix spill queue overflow");
+            if (hc.novf == 0) break;
+            const unsigned long long zero = 0;
+            CK(cudaMemcpyAsync(&h->cnt.p->novf, &zero, sizeof zero, cudaMemcpyHostToDevice, s));
+            c.ovf_out = out;
+            KL(h, MSC_K_SEP_UPDATE, s, k_tri_spill<<<grid_for(hc.novf), TPB, 0, s>>>(c, in, (uint32_t)hc.novf));
+            CK(cudaGetLastError());
+            std::swap(in, out);
+        }
+    }
+    KL(h, MSC_K_SEP_UPDATE, s, k_sd_clear<<<grid_for(h->G.n / 16 + 1), TPB, 0, s>>>(c, nSD));
+    CK(cudaMemsetAsync(nSD, 0, sizeof(unsigned long long), s));
+    KL(h, MSC_K_SEP_TARGETS, s, k_node_targets<D><<<grid_for(h->G.n / 16 + 1), TPB, 0, s>>>(c, M, nM));
+    CK(cudaGetLastError());
     return MSC_OK;
 }
 
@@ -680,8 +778,15 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
     int cur = 0;
     KL(h, MSC_K_OTHER, s, k_init_g<<<grid_for(h->G.n), TPB, 0, s>>>(h->f.p, h->fhat.p, h->g.p, h->state.p, h->G.n, xi));
     CK(cudaGetLastError());
-    CK(cudaMemsetAsync(nMc, 0, 2 * sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(nMc, 0, 4 * sizeof(unsigned long long), s));
+    // sets left over by an earlier call that stopped with an error
+    CK(cudaMemsetAsync(h->Tbits.p, 0, h->Tbits.n * 4, s));
+    CK(cudaMemsetAsync(h->Xbits.p, 0, h->Xbits.n * 4, s));
+    CK(cudaMemsetAsync(h->Dbits.p, 0, h->Dbits.n * 4, s));
+    CK(cudaMemsetAsync(h->sDbits.p, 0, h->sDbits.n * 4, s));
     CKS(eval_dense<D>(h, h->g.p, h->G, h->code_g.p, h->code_f.p, M[cur], nMc + cur, s));
+    bool sep_built = false;
+    h->items[MSC_K_DENSE] += h->G.n;
     for (;;) {
         CK(cudaMemsetAsync(h->cnt.p, 0, sizeof(Counters), s));
         KL(h, MSC_K_CPASS, s, k_ctargets<D><<<grid_for(h->G.n / 8 + 1), TPB, 0, s>>>(c, M[cur], nMc + cur));
@@ -693,9 +798,11 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
         if (hc.ncase == 0) {
             if (o.tier < 3) break;
             kind = 1;
-            CKS(s_pass<D>(h, c, o.tier, s));
+            if (o.tier >= 4) CKS(s_pass_state<D>(h, c, sep_built, M[cur], nMc + cur, nMc + 3, s));
+            else CKS(s_pass<D>(h, c, o.tier, s));
             CK(cudaMemcpyAsync(&hc, h->cnt.p, sizeof hc, cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
+            h->items[MSC_K_SEP_UPDATE] += hc.steps[0] + hc.steps[1] + hc.steps[2];
             if (hc.err) return fail(MSC_ERR_OOM, "saddle-saddle spill queue overflow");
             if (hc.ncase == 0) break;
         }
@@ -713,6 +820,7 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
             R.trace.push_back(r);
         }
         (kind ? R.n_s : R.n_c)++;
+        h->items[MSC_K_EDIT] += hc.nT + hc.nX;
         if (hc.nX) R.n_fb++;
         const int nxt = cur ^ 1;
         KL(h, MSC_K_EDIT, s, k_edit<D><<<grid_for(hc.nT + hc.nX), TPB, 0, s>>>(c));
@@ -725,7 +833,7 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
             h->tag = 1;
             c.tag = 1;
         }
-        KL(h, MSC_K_REBUILD, s, k_rebuild<<<grid_for(h->G.n / 8 + 1), TPB, 0, s>>>(c, M[cur], nMc + cur, nMc + nxt));
+        KL(h, MSC_K_REBUILD, s, k_rebuild<<<grid_for(h->G.n / 8 + 1), TPB, 0, s>>>(c, M[cur], nMc + cur, nMc + nxt, nMc + 3));
         KL(h, MSC_K_REBUILD, s, k_clear<<<grid_for(h->G.n / 8 + 1), TPB, 0, s>>>(c));
         CK(cudaGetLastError());
         cur = nxt;
@@ -798,8 +906,8 @@ template <int D> msc_status verify_impl(msc_handle *h, const float *gdev, float 
         c.code_g = code.p;
         // per-separatrix pair and end checks
         CK(cudaMemsetAsync(h->cnt.p, 0, sizeof(Counters), s));
-        if (h->n_desc) KL(h, MSC_K_SPASS, s, k_verify_desc<D><<<grid_for(h->n_desc), TPB, 0, s>>>(c, h->seeds_desc.p, h->n_desc));
-        if (h->n_asc) KL(h, MSC_K_SPASS, s, k_verify_asc<D><<<grid_for(h->n_asc), TPB, 0, s>>>(c, h->seeds_asc.p, h->n_asc));
+        if (h->n_desc) KL(h, MSC_K_OTHER, s, k_verify_desc<D><<<grid_for(h->n_desc), TPB, 0, s>>>(c, h->seeds_desc.p, h->n_desc));
+        if (h->n_asc) KL(h, MSC_K_OTHER, s, k_verify_asc<D><<<grid_for(h->n_asc), TPB, 0, s>>>(c, h->seeds_asc.p, h->n_asc));
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(&hc, h->cnt.p, sizeof hc, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -823,7 +931,7 @@ template <int D> msc_status verify_impl(msc_handle *h, const float *gdev, float 
             CK(cudaMemsetAsync(h->cnt.p, 0, sizeof(Counters), s));
             CK(cudaMemsetAsync(h->vis_tri.p, 0, h->vis_tri.n * 4, s));
             v.ovf_out = h->ovf0.p;
-            if (h->n_ss) KL(h, MSC_K_SPASS, s, k_ss_seed<<<grid_for(h->n_ss), TPB, 0, s>>>(v, h->seeds_ss.p, h->n_ss));
+            if (h->n_ss) KL(h, MSC_K_SEP_UPDATE, s, k_ss_seed<<<grid_for(h->n_ss), TPB, 0, s>>>(v, h->seeds_ss.p, h->n_ss));
             CK(cudaGetLastError());
             uint32_t *in = h->ovf0.p, *o2 = h->ovf1.p;
             for (;;) {
@@ -834,7 +942,7 @@ template <int D> msc_status verify_impl(msc_handle *h, const float *gdev, float 
                 const unsigned long long zero = 0;
                 CK(cudaMemcpyAsync(&h->cnt.p->novf, &zero, sizeof zero, cudaMemcpyHostToDevice, s));
                 v.ovf_out = o2;
-                KL(h, MSC_K_SPASS, s, k_ss_spill<<<grid_for(hc.novf), TPB, 0, s>>>(v, in, (uint32_t)hc.novf));
+                KL(h, MSC_K_SEP_UPDATE, s, k_ss_spill<<<grid_for(hc.novf), TPB, 0, s>>>(v, in, (uint32_t)hc.novf));
                 CK(cudaGetLastError());
                 std::swap(in, o2);
             }
@@ -970,6 +1078,7 @@ msc_status msc_prepare_original(const float *f, int nx, int ny, int nz, const ms
         h->prof_on = o.profile != 0;
         CKS(upload_field(h, f, h->G.n, h->f.p, h->nM.p, s, "f"));
         CKS(eval_dense_any(h, h->D, h->f.p, h->G, h->code_f.p, nullptr, nullptr, nullptr, s));
+        h->items[MSC_K_DENSE] += h->G.n;
         CKS(h->D == 3 ? build_seeds<3>(h, s) : build_seeds<2>(h, s));
         CK(cudaEventCreate(&h->ev0));
         CK(cudaEventCreate(&h->ev1));
@@ -1104,10 +1213,11 @@ msc_status msc_get_stats(msc_handle *h, msc_stats *out)
 {
     if (!h || !out) return fail(MSC_ERR_INVALID_ARG, "handle and out must be non-NULL");
     memset(out, 0, sizeof *out);
-    for (int i = 0; i < 8; i++) {
+    for (int i = 0; i < 12; i++) {
         out->launches[i] = h->launches[i];
         out->ms[i] = h->ms[i];
         out->timed_launches[i] = h->timed[i];
+        out->items[i] = h->items[i];
     }
     return MSC_OK;
 }
@@ -1115,7 +1225,7 @@ msc_status msc_get_stats(msc_handle *h, msc_stats *out)
 msc_status msc_reset_stats(msc_handle *h)
 {
     if (!h) return fail(MSC_ERR_INVALID_ARG, "handle is NULL");
-    for (int i = 0; i < 8; i++) { h->launches[i] = 0; h->ms[i] = 0.0; h->timed[i] = 0; }
+    for (int i = 0; i < 12; i++) { h->launches[i] = 0; h->ms[i] = 0.0; h->timed[i] = 0; h->items[i] = 0; }
     return MSC_OK;
 }
 

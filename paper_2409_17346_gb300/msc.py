@@ -32,12 +32,12 @@ class Options(ctypes.Structure):
                 ("profile", ctypes.c_int)]
 
 
-KERNEL_CLASSES = ("dense", "cpass", "edit", "refresh", "rebuild", "spass", "other")
+KERNEL_CLASSES = ("dense", "cpass", "edit", "refresh", "rebuild", "sep_init", "sep_update", "sep_targets", "other")
 
 
 class Stats(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_uint64 * 8), ("ms", ctypes.c_double * 8),
-                ("timed_launches", ctypes.c_uint64 * 8)]
+    _fields_ = [("launches", ctypes.c_uint64 * 12), ("ms", ctypes.c_double * 12),
+                ("timed_launches", ctypes.c_uint64 * 12), ("items", ctypes.c_uint64 * 12)]
 
 
 class IterRecord(ctypes.Structure):
@@ -209,7 +209,8 @@ class Handle:
         """Launch counts and profiled CUDA-event milliseconds by kernel class."""
         st = Stats()
         _check(load().msc_get_stats(self._h, ctypes.byref(st)))
-        return {k: dict(launches=int(st.launches[i]), ms=float(st.ms[i]), timed=int(st.timed_launches[i]))
+        return {k: dict(launches=int(st.launches[i]), ms=float(st.ms[i]), timed=int(st.timed_launches[i]),
+                        items=int(st.items[i]))
                 for i, k in enumerate(KERNEL_CLASSES)}
 
     def reset_stats(self):

@@ -197,6 +197,23 @@ def test_invalid_arguments(lib):
     assert e.value.status == 4
 
 
+def test_handle_reuse_after_error_and_repeat(lib):
+    """A handle stays correct after a call that stopped early and across repeated fixes."""
+    f, fh, xi, _ = synth.config_case("kolmogorov3d", size=14, rel=1e-3)
+    h = lib.Handle(f)
+    with pytest.raises(lib.MscError):
+        h.fix(fh, xi, tier=4, max_iters=3)
+    ref = oracle.fix(f, fh, xi, tier=4)
+    for _ in range(2):
+        g, ed = h.fix(fh, xi, tier=4)
+        assert np.array_equal(g.view(np.uint32), ref["g"].view(np.uint32))
+        assert (ed["n_iters_c"], ed["n_iters_s"]) == (ref["n_c"], ref["n_s"])
+    f2, fh2, xi2, _ = synth.config_case("kolmogorov3d", seed=11, size=14, rel=1e-3)
+    ref2 = oracle.fix(f, fh2, xi2, tier=4)
+    g2, _ = h.fix(fh2, xi2, tier=4)
+    assert np.array_equal(g2.view(np.uint32), ref2["g"].view(np.uint32))
+
+
 def test_batch_equals_single(lib):
     cases = [synth.config_case("grf3d", seed=30 + i, size=11, rel=1e-2) for i in range(3)]
     cases += [synth.config_case("gauss2d", seed=5)]
