@@ -60,16 +60,12 @@ struct Ctx {
     uint64_t *code_g;
     uint32_t *Tbits, *Xbits, *Dbits;
     uint32_t *Tlist, *Xlist, *Dlist;
-    uint32_t *Mcur, *Mnext;
-    uint32_t nMcur;
-    uint32_t *stamp;
-    uint32_t tag;
     uint32_t *vis_v, *vis_top, *vis_tri;
     uint32_t *ovf_in, *ovf_out;      // saddle-saddle spill queues: (triangle id, entry edge) pairs
     uint32_t ovf_cap;
     Counters *cnt;
     // persistent separatrix state (tier 4): one byte per node, see "separatrix state" below
-    uint8_t *ns_v, *ns_top, *ns_tri, *ns_dead;
+    int32_t *ns_v, *ns_top, *ns_tri, *ns_dead;
     uint32_t *sDbits, *sDlist;       // anchors dirtied since the last S-pass
     int track_dirty;
 };
@@ -110,6 +106,21 @@ __device__ __forceinline__ void count_add(unsigned long long *p, unsigned long l
 }
 #else
 inline void count_add(unsigned long long *p, unsigned long long v) { *p += v; }
+#endif
+
+// slot in a list whose length lives in *n: one atomic per group of converged threads
+#ifdef __CUDA_ARCH__
+__device__ __forceinline__ unsigned long long list_slot(unsigned long long *n)
+{
+    const unsigned mask = __activemask();
+    const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(n, (unsigned long long)__popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    return base + __popc(mask & ((1u << lane) - 1u));
+}
+#else
+inline unsigned long long list_slot(unsigned long long *n) { return (*n)++; }
 #endif
 
 MSC_HD inline bool test_and_set(uint32_t *bits, uint32_t i)
@@ -226,14 +237,13 @@ MSC_HD inline int lowest_of(const Verts &V, const float *vals)
 template <int D> MSC_HD inline void add_case(const Ctx &c, uint32_t t, const Verts &cell)
 {
     const Tab<D> &T = rt_tab<D>();
-    a_add(&c.cnt->ncase, 1ull);
+    count_add(&c.cnt->ncase, 1ull);
     if (!test_and_set(c.Tbits, t)) {
-        const unsigned long long i = a_add(&c.cnt->nT, 1ull);
-        c.Tlist[i] = t;
-        a_add(&c.cnt->sumT, (unsigned long long)t);
+        c.Tlist[list_slot(&c.cnt->nT)] = t;
+        count_add(&c.cnt->sumT, (unsigned long long)t);
     }
     const uint8_t st = c.state[t];
-    if (st != ST_FLOOR && st != ST_EXACT) { a_add(&c.cnt->nlive, 1ull); return; }
+    if (st != ST_FLOOR && st != ST_EXACT) { count_add(&c.cnt->nlive, 1ull); return; }
     if (!c.exact_fallback) return;
     for (int i = 0; i < cell.n; i++) {
         for (int n = -1; n < T.NNB; n++) {
@@ -242,9 +252,8 @@ template <int D> MSC_HD inline void add_case(const Ctx &c, uint32_t t, const Ver
             if (!inside(c.G, xx, yy, zz)) continue;
             const uint32_t u = vid(c.G, xx, yy, zz);
             if (!test_and_set(c.Xbits, u)) {
-                const unsigned long long j = a_add(&c.cnt->nX, 1ull);
-                c.Xlist[j] = u;
-                a_add(&c.cnt->sumX, (unsigned long long)u);
+                c.Xlist[list_slot(&c.cnt->nX)] = u;
+                count_add(&c.cnt->sumX, (unsigned long long)u);
             }
         }
     }
@@ -370,8 +379,9 @@ MSC_HD inline float clamp_base(float f, float fh, float xi)
     return fh < lb ? lb : (fh > ub ? ub : fh);
 }
 
-// anchors whose code reads the value at v: v - (corner + neighbour offset)
-template <int D> MSC_HD inline void mark_dirty(const Ctx &c, uint32_t v)
+// anchors whose code reads the value at v: v - (corner + neighbour offset); each newly
+// dirty anchor is handed to app (which appends it to the dirty list)
+template <int D, class App> MSC_HD inline void mark_dirty(const Ctx &c, uint32_t v, App &&app)
 {
     int x, y, z;
     coords(c.G, v, x, y, z);
@@ -388,17 +398,14 @@ template <int D> MSC_HD inline void mark_dirty(const Ctx &c, uint32_t v)
                 const int px = x - dx, py = y - dy, pz = z - dz;
                 if (!inside(c.G, px, py, pz)) continue;
                 const uint32_t p = vid(c.G, px, py, pz);
-                if (!test_and_set(c.Dbits, p)) {
-                    const unsigned long long i = a_add(&c.cnt->nD, 1ull);
-                    c.Dlist[i] = p;
-                }
+                if (!test_and_set(c.Dbits, p)) app(p);
             }
 }
 
 // item i < nX: restore Xlist[i] to f; else quantised step of Tlist[i - nX] unless it is
 // also restored (Eq. 2: one step of xi / 2^q_max while q < q_max and the value stays
 // >= f - xi, otherwise the floor f - xi)
-template <int D> MSC_HD inline void edit_item(const Ctx &c, uint32_t i, uint32_t nX)
+template <int D, class App> MSC_HD inline void edit_item(const Ctx &c, uint32_t i, uint32_t nX, App &&app)
 {
     uint32_t v;
     if (i < nX) {
@@ -421,8 +428,30 @@ template <int D> MSC_HD inline void edit_item(const Ctx &c, uint32_t i, uint32_t
         }
         if (!done) { c.g[v] = lb; c.state[v] = ST_FLOOR; }
     }
-    a_add(&c.cnt->nchanged, 1ull);
-    mark_dirty<D>(c, v);
+    mark_dirty<D>(c, v, app);
+}
+
+// one bit per cell the anchor owns: set if the cell is critical (tier 1: extrema only)
+template <int D> MSC_HD inline uint64_t crit_sig(uint64_t code, int tier)
+{
+    constexpr int NE = Tab<D>::NE, NT = Tab<D>::NT, NK = Tab<D>::NK;
+    uint64_t sig = (code & 15u) == 15u;
+    if (tier >= 2 || D == 2) {
+        // a 3-bit edge field is critical iff all its bits are 0 (likewise 2-bit triangle fields)
+        if (tier >= 2) {
+            const uint64_t e = code >> 4;
+            uint64_t nz = 0;
+            for (int i = 0; i < NE; i++) nz |= (uint64_t)(((e >> (3 * i)) & 7u) != 0) << i;
+            sig |= (~nz & ((1ull << NE) - 1)) << 1;
+        }
+        const uint64_t t = code >> Tab<D>::TRI_BIT0;
+        uint64_t nzt = 0;
+        for (int i = 0; i < NT; i++) nzt |= (uint64_t)(((t >> (2 * i)) & 3u) != 0) << i;
+        sig |= (~nzt & ((1ull << NT) - 1)) << (1 + NE);
+    }
+    const uint64_t k = code >> Tab<D>::TET_BIT0;
+    sig |= (~k & ((1ull << NK) - 1)) << (1 + NE + NT);
+    return sig;
 }
 
 // re-evaluate a dirty anchor and keep it in the mismatch list if its code differs from f's
@@ -431,13 +460,6 @@ template <int D> MSC_HD inline void refresh_anchor(const Ctx &c, uint32_t p)
     c.code_g[p] = anchor_code<D>(c.g, c.G, p);
 }
 
-MSC_HD inline void keep_if_mismatch(const Ctx &c, uint32_t p)
-{
-    if (ld(c.code_f + p) == c.code_g[p]) return;
-    if (a_exch(c.stamp + p, c.tag) == c.tag) return;
-    const unsigned long long i = a_add(&c.cnt->nM, 1ull);
-    c.Mnext[i] = p;
-}
 
 // ------------------------------------------------------------------------------------
 // S-pass (Sec. 4.4): walks along the separatrices of f, checked against g's gradient
@@ -603,7 +625,7 @@ constexpr int SS_STACK = 24;
 
 MSC_HD inline void ss_push_global(const Ctx &c, uint32_t tri, uint32_t entry)
 {
-    const unsigned long long i = a_add(&c.cnt->novf, 1ull);
+    const unsigned long long i = list_slot(&c.cnt->novf);
     if (i < c.ovf_cap) { c.ovf_out[2 * i] = tri; c.ovf_out[2 * i + 1] = entry; }
     else a_add(&c.cnt->err, 1ull);
 }
@@ -665,64 +687,60 @@ MSC_HD inline void ss_walk(const Ctx &c, uint32_t tri0, uint32_t entry0, bool se
 // The S-pass of Sec. 4.4 walks every separatrix of f from its saddle and stops at the first
 // pair missing from g's gradient.  The set of cells such a walk reaches depends on g only
 // through the pairs it checks, and between two S-passes g changes only around edited
-// vertices.  So the walks are kept as a state: one byte per node
+// vertices.  So the walks are kept as a state: one 32-bit word per node
 //   descending: a vertex u (its pair (u, u next_f(u)));     ascending: a top cell beta (its
 //   pair with its f-facet); saddle-saddle: a triangle t' = V_f(e) (pair (e, t')) and every
 //   edge paired down in f (a dead end of the triangle walk);
-// holding bit 7 = the node's f-pair is missing from g ("mismatch"), bit 6 = the node is a
-// seed, bits 0..5 = the number of reached predecessors passing into it.  A path node is
-// reached iff it is a seed or has such a predecessor, and passes on iff reached and not
-// mismatched; a triangle node is reached (passes on) iff it is a seed, or has a reached
-// parent and no mismatch.  Troublemakers are the mismatched nodes with a reached
-// predecessor - exactly the first disagreeing pairs the walks stop at.  Counts change by
-// atomic byte updates whose before/after values decide what to pass on, so concurrent
-// updates always settle on the same state.
-constexpr uint8_t NS_MIS = 0x80, NS_SEED = 0x40, NS_CNT = 0x3F;
+// holding bit 0 = the node's f-pair is missing from g ("mismatch"), bit 1 = the node is a
+// seed, bits 2.. = the signed number of reached predecessors passing into it.  A path node
+// is reached iff it is a seed or has such a predecessor, and passes on iff reached and not
+// mismatched; a triangle node passes on iff it is a seed, or has a reached parent and no
+// mismatch.  Troublemakers are the mismatched nodes with a reached predecessor - exactly
+// the first disagreeing pairs the walks stop at.  Every change is one atomic on the node's
+// word and its before/after values decide the +-1 passed on, so concurrent updates settle
+// on the same state in any order (a count may dip below zero while a +1 is in flight; the
+// signed field holds that without touching any other node).
+constexpr int32_t NS_MIS = 1, NS_SEED = 2, NS_ONE = 4;
 
-MSC_HD inline uint8_t byte_add(uint8_t *base, uint32_t i, int delta)
+MSC_HD inline int32_t node_add(int32_t *ns, uint32_t i, int delta)
 {
 #ifdef __CUDA_ARCH__
-    const int sh = 8 * (int)(i & 3u);
-    const uint32_t old = atomicAdd((uint32_t *)(base + (i & ~3u)), (uint32_t)delta << sh);
-    return (uint8_t)(old >> sh);
+    return atomicAdd(ns + i, delta * NS_ONE);
 #else
-    const uint8_t o = base[i];
-    base[i] = (uint8_t)(o + delta);
+    const int32_t o = ns[i];
+    ns[i] = o + delta * NS_ONE;
     return o;
 #endif
 }
 
-MSC_HD inline uint8_t byte_xor(uint8_t *base, uint32_t i, uint8_t m)
+MSC_HD inline int32_t node_xor(int32_t *ns, uint32_t i, int32_t m)
 {
 #ifdef __CUDA_ARCH__
-    const int sh = 8 * (int)(i & 3u);
-    const uint32_t old = atomicXor((uint32_t *)(base + (i & ~3u)), (uint32_t)m << sh);
-    return (uint8_t)(old >> sh);
+    return atomicXor(ns + i, m);
 #else
-    const uint8_t o = base[i];
-    base[i] = (uint8_t)(o ^ m);
+    const int32_t o = ns[i];
+    ns[i] = o ^ m;
     return o;
 #endif
 }
 
-MSC_HD inline uint8_t byte_or(uint8_t *base, uint32_t i, uint8_t m)
+MSC_HD inline int32_t node_or(int32_t *ns, uint32_t i, int32_t m)
 {
 #ifdef __CUDA_ARCH__
-    const int sh = 8 * (int)(i & 3u);
-    const uint32_t old = atomicOr((uint32_t *)(base + (i & ~3u)), (uint32_t)m << sh);
-    return (uint8_t)(old >> sh);
+    return atomicOr(ns + i, m);
 #else
-    const uint8_t o = base[i];
-    base[i] = (uint8_t)(o | m);
+    const int32_t o = ns[i];
+    ns[i] = o | m;
     return o;
 #endif
 }
 
-MSC_HD inline uint8_t byte_load(const uint8_t *base, uint32_t i) { return ((const volatile uint8_t *)base)[i]; }
+MSC_HD inline int32_t node_load(const int32_t *ns, uint32_t i) { return ((const volatile int32_t *)ns)[i]; }
 
-MSC_HD inline bool path_reached(uint8_t b) { return (b & NS_SEED) || (b & NS_CNT); }
-MSC_HD inline int path_passes(uint8_t b) { return path_reached(b) && !(b & NS_MIS); }
-MSC_HD inline int tri_passes(uint8_t b) { return (b & NS_SEED) || ((b & NS_CNT) && !(b & NS_MIS)); }
+MSC_HD inline int32_t node_count(int32_t b) { return b >> 2; }
+MSC_HD inline bool path_reached(int32_t b) { return (b & NS_SEED) || node_count(b) > 0; }
+MSC_HD inline int path_passes(int32_t b) { return path_reached(b) && !(b & NS_MIS); }
+MSC_HD inline int tri_passes(int32_t b) { return (b & NS_SEED) || (node_count(b) > 0 && !(b & NS_MIS)); }
 
 // successor of vertex u on its descending V-path in f
 template <int D> MSC_HD inline bool desc_succ(const Ctx &c, uint32_t u, uint32_t &w)
@@ -752,11 +770,11 @@ template <int D> MSC_HD inline bool asc_succ(const Ctx &c, uint32_t beta, uint32
 // the path (kind 0: descending vertices, 1: ascending top cells)
 template <int D> MSC_HD inline void path_push(const Ctx &c, int kind, uint32_t w, int delta)
 {
-    uint8_t *ns = kind == 0 ? c.ns_v : c.ns_top;
+    int32_t *ns = kind == 0 ? c.ns_v : c.ns_top;
     unsigned long long n = 0;
     for (uint32_t s = 0; s <= c.G.n * (uint32_t)Tab<D>::NTOP; s++) {
         n++;
-        const uint8_t o = byte_add(ns, w, delta), nw = (uint8_t)(o + delta);
+        const int32_t o = node_add(ns, w, delta), nw = o + delta * NS_ONE;
         const int d = path_passes(nw) - path_passes(o);
         if (!d) break;
         uint32_t nx;
@@ -768,7 +786,7 @@ template <int D> MSC_HD inline void path_push(const Ctx &c, int kind, uint32_t w
 }
 
 // a path node becomes a seed / changes its mismatch bit
-template <int D> MSC_HD inline void path_change(const Ctx &c, int kind, uint32_t u, uint8_t o, uint8_t nw)
+template <int D> MSC_HD inline void path_change(const Ctx &c, int kind, uint32_t u, int32_t o, int32_t nw)
 {
     const int d = path_passes(nw) - path_passes(o);
     uint32_t w;
@@ -811,7 +829,7 @@ MSC_HD inline int tri_children(const Ctx &c, uint32_t tri, uint32_t *out, bool *
 
 MSC_HD inline void ss_spill(const Ctx &c, uint32_t tri, int delta)
 {
-    const unsigned long long i = a_add(&c.cnt->novf, 1ull);
+    const unsigned long long i = list_slot(&c.cnt->novf);
     if (i < c.ovf_cap) { c.ovf_out[2 * i] = tri; c.ovf_out[2 * i + 1] = (uint32_t)delta; }
     else a_add(&c.cnt->err, 1ull);
 }
@@ -830,7 +848,7 @@ MSC_HD inline void tri_propagate(const Ctx &c, uint32_t tri0, int dv0, bool appl
         bool dead[3];
         const int k = tri_children(c, t, ch, dead);
         for (int i = 0; i < k; i++) {
-            if (dead[i]) { byte_add(c.ns_dead, ch[i], dv); continue; }
+            if (dead[i]) { node_add(c.ns_dead, ch[i], dv); continue; }
             if (sp < SS_STACK) { st[sp] = ch[i]; sd[sp] = dv; sp++; }
             else ss_spill(c, ch[i], dv);
         }
@@ -841,7 +859,7 @@ MSC_HD inline void tri_propagate(const Ctx &c, uint32_t tri0, int dv0, bool appl
         const uint32_t t = st[sp];
         const int d = sd[sp];
         n++;
-        const uint8_t o = byte_add(c.ns_tri, t, d), nw = (uint8_t)(o + d);
+        const int32_t o = node_add(c.ns_tri, t, d), nw = o + d * NS_ONE;
         const int dv = tri_passes(nw) - tri_passes(o);
         if (dv) expand(t, dv);
     }
@@ -857,11 +875,11 @@ template <int D> MSC_HD inline void node_bits(const Ctx &c, uint32_t p, bool ini
     int x, y, z;
     coords(c.G, p, x, y, z);
     auto set_path = [&](int kind, uint32_t u, bool m) {
-        uint8_t *ns = kind == 0 ? c.ns_v : c.ns_top;
-        if (init) { if (m) byte_or(ns, u, NS_MIS); return; }
-        if (((byte_load(ns, u) & NS_MIS) != 0) == m) return;
-        const uint8_t o = byte_xor(ns, u, NS_MIS);
-        path_change<D>(c, kind, u, o, (uint8_t)(o ^ NS_MIS));
+        int32_t *ns = kind == 0 ? c.ns_v : c.ns_top;
+        if (init) { if (m) node_or(ns, u, NS_MIS); return; }
+        if (((node_load(ns, u) & NS_MIS) != 0) == m) return;
+        const int32_t o = node_xor(ns, u, NS_MIS);
+        path_change<D>(c, kind, u, o, o ^ NS_MIS);
     };
     const int vf = vfield<D>(cf);
     if (vf != 15) set_path(0, p, vfield<D>(cg) != vf);
@@ -881,17 +899,17 @@ template <int D> MSC_HD inline void node_bits(const Ctx &c, uint32_t p, bool ini
             const bool m = efield<D>(cg, et) != ef;
             if (ef == 1) {
                 const uint32_t e = p * 7 + (uint32_t)et;
-                if (init) { if (m) byte_or(c.ns_dead, e, NS_MIS); continue; }
-                if (((byte_load(c.ns_dead, e) & NS_MIS) != 0) != m) byte_xor(c.ns_dead, e, NS_MIS);
+                if (init) { if (m) node_or(c.ns_dead, e, NS_MIS); continue; }
+                if (((node_load(c.ns_dead, e) & NS_MIS) != 0) != m) node_xor(c.ns_dead, e, NS_MIS);
                 continue;
             }
             const int i = ef - 2;
             const uint32_t t2 = vid(c.G, x + T.ecof_anc[et][i][0], y + T.ecof_anc[et][i][1], z + T.ecof_anc[et][i][2]) * 12 +
                                 (uint32_t)T.ecof_type[et][i];
-            if (init) { if (m) byte_or(c.ns_tri, t2, NS_MIS); continue; }
-            if (((byte_load(c.ns_tri, t2) & NS_MIS) != 0) == m) continue;
-            const uint8_t o = byte_xor(c.ns_tri, t2, NS_MIS);
-            const int dv = tri_passes((uint8_t)(o ^ NS_MIS)) - tri_passes(o);
+            if (init) { if (m) node_or(c.ns_tri, t2, NS_MIS); continue; }
+            if (((node_load(c.ns_tri, t2) & NS_MIS) != 0) == m) continue;
+            const int32_t o = node_xor(c.ns_tri, t2, NS_MIS);
+            const int dv = tri_passes(o ^ NS_MIS) - tri_passes(o);
             if (dv) tri_propagate(c, t2, dv, false, 0);
         }
     }
@@ -901,16 +919,16 @@ template <int D> MSC_HD inline void node_bits(const Ctx &c, uint32_t p, bool ini
 template <int D> MSC_HD inline void node_seed(const Ctx &c, int kind, uint32_t u)
 {
     if (kind == 2) {
-        const uint8_t o = byte_or(c.ns_tri, u, NS_SEED);
+        const int32_t o = node_or(c.ns_tri, u, NS_SEED);
         if (o & NS_SEED) return;
-        const int dv = tri_passes((uint8_t)(o | NS_SEED)) - tri_passes(o);
+        const int dv = tri_passes(o | NS_SEED) - tri_passes(o);
         if (dv) tri_propagate(c, u, dv, false, 0);
         return;
     }
-    uint8_t *ns = kind == 0 ? c.ns_v : c.ns_top;
-    const uint8_t o = byte_or(ns, u, NS_SEED);
+    int32_t *ns = kind == 0 ? c.ns_v : c.ns_top;
+    const int32_t o = node_or(ns, u, NS_SEED);
     if (o & NS_SEED) return;
-    path_change<D>(c, kind, u, o, (uint8_t)(o | NS_SEED));
+    path_change<D>(c, kind, u, o, o | NS_SEED);
 }
 
 // troublemakers among the pairs anchored at p (p has a code mismatch)
@@ -923,7 +941,7 @@ template <int D> MSC_HD inline void node_targets(const Ctx &c, uint32_t p)
     coords(c.G, p, x, y, z);
     const int vf = vfield<D>(cf);
     if (vf != 15) {
-        const uint8_t b = byte_load(c.ns_v, p);
+        const int32_t b = node_load(c.ns_v, p);
         if ((b & NS_MIS) && path_reached(b)) {
             Verts V;
             V.n = 0;
@@ -940,7 +958,7 @@ template <int D> MSC_HD inline void node_targets(const Ctx &c, uint32_t p)
         const int *an = D == 3 ? T.tcof_anc[ft][i] : T.ecof_anc[ft][i];
         const int bt = D == 3 ? T.tcof_type[ft][i] : T.ecof_type[ft][i];
         const int bx = x + an[0], by = y + an[1], bz = z + an[2];
-        const uint8_t b = byte_load(c.ns_top, vid(c.G, bx, by, bz) * T.NTOP + (uint32_t)bt);
+        const int32_t b = node_load(c.ns_top, vid(c.G, bx, by, bz) * T.NTOP + (uint32_t)bt);
         if ((b & NS_MIS) && path_reached(b)) {
             Verts V = top_verts<D>(c.G, bx, by, bz, bt);
             add_case<D>(c, V.id[lowest_of(V, c.f)], V);
@@ -951,8 +969,8 @@ template <int D> MSC_HD inline void node_targets(const Ctx &c, uint32_t p)
             const int ef = efield<D>(cf, et);
             if (ef == 0) continue;
             if (ef == 1) {
-                const uint8_t b = byte_load(c.ns_dead, p * 7 + (uint32_t)et);
-                if ((b & NS_MIS) && (b & NS_CNT)) {
+                const int32_t b = node_load(c.ns_dead, p * 7 + (uint32_t)et);
+                if ((b & NS_MIS) && node_count(b) > 0) {
                     Verts V = cell_verts<3>(c.G, x, y, z, 1, et);
                     add_case<3>(c, V.id[lowest_of(V, c.f)], V);
                 }
@@ -961,8 +979,8 @@ template <int D> MSC_HD inline void node_targets(const Ctx &c, uint32_t p)
             const int i = ef - 2;
             const int tx = x + T.ecof_anc[et][i][0], ty = y + T.ecof_anc[et][i][1], tz = z + T.ecof_anc[et][i][2];
             const int t2 = T.ecof_type[et][i];
-            const uint8_t b = byte_load(c.ns_tri, vid(c.G, tx, ty, tz) * 12 + (uint32_t)t2);
-            if ((b & NS_MIS) && (b & NS_CNT) && !(b & NS_SEED)) {
+            const int32_t b = node_load(c.ns_tri, vid(c.G, tx, ty, tz) * 12 + (uint32_t)t2);
+            if ((b & NS_MIS) && node_count(b) > 0 && !(b & NS_SEED)) {
                 Verts V = cell_verts<3>(c.G, tx, ty, tz, 2, t2);
                 add_case<3>(c, vid(c.G, x + T.ecof_v[et][i][0], y + T.ecof_v[et][i][1], z + T.ecof_v[et][i][2]), V);
             }
@@ -975,18 +993,14 @@ template <int D> MSC_HD inline void node_targets(const Ctx &c, uint32_t p)
 // ------------------------------------------------------------------------------------
 // kind 0: descending seeds (both vertices of every critical edge); kind 1: ascending seeds
 // (top cofacets of every critical (D-1)-cell); kind 2: 2-saddle triangles (3D)
-template <int D> MSC_HD inline void seeds_anchor(const uint64_t *code, const Grid &G, uint32_t p, int kind,
-                                                 uint32_t *out, unsigned long long *count, unsigned long long cap)
+template <int D, class Emit> MSC_HD inline void seeds_anchor(const uint64_t *code, const Grid &G, uint32_t p, int kind,
+                                                             Emit &&emit)
 {
     const Tab<D> &T = rt_tab<D>();
     int x, y, z;
     coords(G, p, x, y, z);
     const unsigned cin = corner_mask<D>(G, x, y, z);
     const uint64_t cf = ld(code + p);
-    auto emit = [&](uint32_t v) {
-        const unsigned long long i = a_add(count, 1ull);
-        if (out && i < cap) out[i] = v;
-    };
     if (kind == 0 || (D == 2 && kind == 1)) {
         for (int e = 0; e < T.NE; e++) {
             if (!((cin >> (e + 1)) & 1u) || efield<D>(cf, e) != 0) continue;
@@ -1037,7 +1051,7 @@ template <int D> MSC_HD inline void decode_pairs(const uint64_t *code, const Gri
     const unsigned cin = corner_mask<D>(G, x, y, z);
     const uint64_t cf = ld(code + p);
     auto emit = [&](const Verts &L, int ex, int ey, int ez) {
-        const unsigned long long i = a_add(count, 1ull);
+        const unsigned long long i = list_slot(count);
         if (!rows || i >= cap) return;
         int64_t *r = rows + 8 * i;
         for (int k = 0; k < L.n; k++) { r[k] = L.id[k]; r[4 + k] = L.id[k]; }
@@ -1079,7 +1093,7 @@ template <int D> MSC_HD inline void decode_critical(const uint64_t *code, const 
             return;
         }
         if (!crit) return;
-        const unsigned long long i = a_add(count, 1ull);
+        const unsigned long long i = list_slot(count);
         if (!rows || i >= cap) return;
         Verts V = cell_verts<D>(G, x, y, z, kind, t);
         for (int k = 0; k < V.n; k++) rows[4 * i + k] = V.id[k];

@@ -86,6 +86,45 @@ int grid_for(unsigned long long n)
 #define GRID_STRIDE(i, n) for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < (n); \
                                i += (unsigned long long)gridDim.x * blockDim.x)
 
+// Appends to a global list staged in shared memory: threads reserve slots with shared
+// atomics and a block publishes its items with one global atomic per round (spilling
+// straight to the list only if the stage is full), instead of one same-address global
+// atomic per item.  Kernels using a stage run whole-block rounds of blockDim.x items.
+template <int CAP> struct Stage {
+    uint32_t buf[CAP];
+    unsigned n;
+    unsigned long long base;
+};
+
+template <int CAP> __device__ __forceinline__ void st_init(Stage<CAP> &s)
+{
+    if (threadIdx.x == 0) s.n = 0;
+    __syncthreads();
+}
+
+template <int CAP> __device__ __forceinline__ void st_push(Stage<CAP> &s, uint32_t v, uint32_t *gl, unsigned long long *gn)
+{
+    const unsigned k = atomicAdd(&s.n, 1u);
+    if (k < CAP) s.buf[k] = v;
+    else gl[atomicAdd(gn, 1ull)] = v;
+}
+
+template <int CAP> __device__ __forceinline__ void st_flush(Stage<CAP> &s, uint32_t *gl, unsigned long long *gn)
+{
+    __syncthreads();
+    const unsigned m = s.n < CAP ? s.n : CAP;
+    if (threadIdx.x == 0 && m) s.base = atomicAdd(gn, (unsigned long long)m);
+    __syncthreads();
+    for (unsigned j = threadIdx.x; j < m; j += blockDim.x) gl[s.base + j] = s.buf[j];
+    __syncthreads();
+    if (threadIdx.x == 0) s.n = 0;
+    __syncthreads();
+}
+
+// whole-block rounds over [0, n): every thread of a block runs the same number of rounds
+#define BLOCK_ROUNDS(b, n) for (unsigned long long b = (unsigned long long)blockIdx.x * blockDim.x; b < (n); \
+                                b += (unsigned long long)gridDim.x * blockDim.x)
+
 __global__ void k_count_nonfinite(const float *v, uint32_t n, unsigned long long *bad)
 {
     unsigned long long local = 0;
@@ -94,15 +133,33 @@ __global__ void k_count_nonfinite(const float *v, uint32_t n, unsigned long long
 }
 
 // dense gradient of a field; with ref != nullptr also list the anchors whose code differs
+// (list, nlist) and those whose critical cells differ (clist, nclist; tier restricted)
 template <int D>
 __global__ void __launch_bounds__(TPB) k_eval_dense(const float *v, Grid G, uint64_t *out, const uint64_t *ref,
-                                                    uint32_t *list, unsigned long long *nlist)
+                                                    uint32_t *list, unsigned long long *nlist, uint32_t *clist,
+                                                    unsigned long long *nclist, int tier)
 {
-    GRID_STRIDE(p, G.n)
+    if (!ref) {
+        GRID_STRIDE(p, G.n) out[p] = anchor_code<D>(v, G, (uint32_t)p);
+        return;
+    }
+    __shared__ Stage<TPB> sm, sc;
+    st_init(sm);
+    st_init(sc);
+    BLOCK_ROUNDS(b, G.n)
     {
-        const uint64_t code = anchor_code<D>(v, G, (uint32_t)p);
-        out[p] = code;
-        if (ref && code != __ldg(ref + p)) list[atomicAdd(nlist, 1ull)] = (uint32_t)p;
+        const unsigned long long p = b + threadIdx.x;
+        if (p < G.n) {
+            const uint64_t code = anchor_code<D>(v, G, (uint32_t)p);
+            out[p] = code;
+            const uint64_t r = __ldg(ref + p);
+            if (code != r) {
+                st_push(sm, (uint32_t)p, list, nlist);
+                if (crit_sig<D>(code, tier) != crit_sig<D>(r, tier)) st_push(sc, (uint32_t)p, clist, nclist);
+            }
+        }
+        st_flush(sm, list, nlist);
+        st_flush(sc, clist, nclist);
     }
 }
 
@@ -122,10 +179,20 @@ template <int D> __global__ void __launch_bounds__(TPB) k_ctargets(Ctx c, const 
     GRID_STRIDE(i, n) ctargets_anchor<D>(c, M[i]);
 }
 
+constexpr int DIRTY_STAGE = 8192;
+
 template <int D> __global__ void k_edit(Ctx c)
 {
+    __shared__ Stage<DIRTY_STAGE> sd;
+    st_init(sd);
     const uint32_t nX = (uint32_t)c.cnt->nX, nT = (uint32_t)c.cnt->nT;
-    GRID_STRIDE(i, (unsigned long long)nX + nT) edit_item<D>(c, (uint32_t)i, nX);
+    BLOCK_ROUNDS(b, (unsigned long long)nX + nT)
+    {
+        const unsigned long long i = b + threadIdx.x;
+        if (i < (unsigned long long)nX + nT)
+            edit_item<D>(c, (uint32_t)i, nX, [&](uint32_t p) { st_push(sd, p, c.Dlist, &c.cnt->nD); });
+        st_flush(sd, c.Dlist, &c.cnt->nD);
+    }
 }
 
 template <int D> __global__ void __launch_bounds__(TPB) k_refresh(Ctx c)
@@ -134,17 +201,39 @@ template <int D> __global__ void __launch_bounds__(TPB) k_refresh(Ctx c)
     GRID_STRIDE(i, n) refresh_anchor<D>(c, c.Dlist[i]);
 }
 
-__global__ void k_rebuild(Ctx c, const uint32_t *Mcur, const unsigned long long *nMcur, unsigned long long *nMnext,
-                          unsigned long long *nSD)
+// next mismatch lists: anchors of the current lists that were not re-evaluated keep their
+// membership; re-evaluated (dirty) anchors join by their new code.  No anchor appears twice.
+template <int D>
+__global__ void k_rebuild(Ctx c, const uint32_t *Mcur, const unsigned long long *nMcur, uint32_t *Mnext,
+                          unsigned long long *nMnext, const uint32_t *Ccur, const unsigned long long *nCcur,
+                          uint32_t *Cnext, unsigned long long *nCnext, unsigned long long *nSD)
 {
-    const unsigned long long a = *nMcur, b = c.cnt->nD;
-    GRID_STRIDE(i, a + b)
+    __shared__ Stage<TPB> sm, sc, ss;
+    st_init(sm);
+    st_init(sc);
+    st_init(ss);
+    const unsigned long long a = *nMcur, b2 = *nCcur, d = c.cnt->nD;
+    BLOCK_ROUNDS(b, a + b2 + d)
     {
-        const uint32_t p = i < a ? Mcur[i] : c.Dlist[i - a];
-        if (i >= a && c.track_dirty && !test_and_set(c.sDbits, p)) c.sDlist[atomicAdd(nSD, 1ull)] = p;
-        if (__ldg(c.code_f + p) == c.code_g[p]) continue;
-        if (atomicExch(c.stamp + p, c.tag) == c.tag) continue;
-        c.Mnext[atomicAdd(nMnext, 1ull)] = p;
+        const unsigned long long i = b + threadIdx.x;
+        if (i < a + b2) {
+            const uint32_t p = i < a ? Mcur[i] : Ccur[i - a];
+            if (!((c.Dbits[p >> 5] >> (p & 31)) & 1u)) {
+                if (i < a) st_push(sm, p, Mnext, nMnext);
+                else st_push(sc, p, Cnext, nCnext);
+            }
+        } else if (i < a + b2 + d) {
+            const uint32_t p = c.Dlist[i - a - b2];
+            if (c.track_dirty && !test_and_set(c.sDbits, p)) st_push(ss, p, c.sDlist, nSD);
+            const uint64_t cf = __ldg(c.code_f + p), cg = c.code_g[p];
+            if (cf != cg) {
+                st_push(sm, p, Mnext, nMnext);
+                if (crit_sig<D>(cf, c.tier) != crit_sig<D>(cg, c.tier)) st_push(sc, p, Cnext, nCnext);
+            }
+        }
+        st_flush(sm, Mnext, nMnext);
+        st_flush(sc, Cnext, nCnext);
+        st_flush(ss, c.sDlist, nSD);
     }
 }
 
@@ -212,10 +301,32 @@ __global__ void k_sd_clear(Ctx c, unsigned long long *nSD)
     GRID_STRIDE(i, n) c.sDbits[c.sDlist[i] >> 5] = 0;
 }
 
+// count pass (out == nullptr): one atomic per block; fill pass: staged appends
 template <int D>
-__global__ void k_seeds(const uint64_t *code, Grid G, int kind, uint32_t *out, unsigned long long *count, unsigned long long cap)
+__global__ void k_seeds(const uint64_t *code, Grid G, int kind, uint32_t *out, unsigned long long *count)
 {
-    GRID_STRIDE(p, G.n) seeds_anchor<D>(code, G, (uint32_t)p, kind, out, count, cap);
+    if (!out) {
+        unsigned long long local = 0;
+        GRID_STRIDE(p, G.n) seeds_anchor<D>(code, G, (uint32_t)p, kind, [&](uint32_t) { local++; });
+        for (int o = 16; o; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+        __shared__ unsigned long long warp_sum[TPB / 32];
+        if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = local;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long t = 0;
+            for (int w = 0; w < TPB / 32; w++) t += warp_sum[w];
+            if (t) atomicAdd(count, t);
+        }
+        return;
+    }
+    __shared__ Stage<4 * TPB> st;
+    st_init(st);
+    BLOCK_ROUNDS(b, G.n)
+    {
+        const unsigned long long p = b + threadIdx.x;
+        if (p < G.n) seeds_anchor<D>(code, G, (uint32_t)p, kind, [&](uint32_t v) { st_push(st, v, out, count); });
+        st_flush(st, out, count);
+    }
 }
 
 template <int D>
@@ -502,13 +613,12 @@ struct msc_handle {
     DevBuf<float> fhat, g;
     DevBuf<uint8_t> state;
     DevBuf<uint64_t> code_g;
-    DevBuf<uint32_t> Tbits, Xbits, Dbits, Tlist, Xlist, Dlist, M0, M1, stamp;
+    DevBuf<uint32_t> Tbits, Xbits, Dbits, Tlist, Xlist, Dlist, M0, M1, C0, C1;
     DevBuf<uint32_t> vis_v, vis_top, vis_tri, ovf0, ovf1;
-    DevBuf<uint8_t> ns_v, ns_top, ns_tri, ns_dead;
+    DevBuf<int32_t> ns_v, ns_top, ns_tri, ns_dead;
     DevBuf<uint32_t> sDbits, sDlist;
     DevBuf<Counters> cnt;
-    DevBuf<unsigned long long> nM;   // [2] counts of M0, M1; [2] scratch
-    uint32_t tag = 0;
+    DevBuf<unsigned long long> nM;   // [0,1] sizes of M0, M1; [2] scratch; [3] dirty-since-S-pass; [4,5] C0, C1
     bool fix_ready = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // launch statistics
@@ -591,7 +701,8 @@ msc_status alloc_fix_state(msc_handle *h)
     CK(h->Dlist.alloc(n));
     CK(h->M0.alloc(n));
     CK(h->M1.alloc(n));
-    CK(h->stamp.alloc(n));
+    CK(h->C0.alloc(n));
+    CK(h->C1.alloc(n));
     CK(h->vis_v.alloc(words(n)));
     CK(h->vis_top.alloc(words(n * ntop)));
     if (h->D == 3) {
@@ -609,12 +720,10 @@ msc_status alloc_fix_state(msc_handle *h)
     CK(h->sDlist.alloc(n));
     CK(cudaMemset(h->sDbits.p, 0, h->sDbits.n * 4));
     CK(h->cnt.alloc(1));
-    CK(h->nM.alloc(4));
+    CK(h->nM.alloc(8));
     CK(cudaMemset(h->Tbits.p, 0, h->Tbits.n * 4));
     CK(cudaMemset(h->Xbits.p, 0, h->Xbits.n * 4));
     CK(cudaMemset(h->Dbits.p, 0, h->Dbits.n * 4));
-    CK(cudaMemset(h->stamp.p, 0, h->stamp.n * 4));
-    h->tag = 0;
     h->fix_ready = true;
     return MSC_OK;
 }
@@ -636,7 +745,6 @@ Ctx make_ctx(msc_handle *h, int tier, int qmax, int exact_fallback, float xi)
     c.code_g = h->code_g.p;
     c.Tbits = h->Tbits.p; c.Xbits = h->Xbits.p; c.Dbits = h->Dbits.p;
     c.Tlist = h->Tlist.p; c.Xlist = h->Xlist.p; c.Dlist = h->Dlist.p;
-    c.stamp = h->stamp.p;
     c.vis_v = h->vis_v.p; c.vis_top = h->vis_top.p; c.vis_tri = h->vis_tri.p;
     c.ovf_cap = (uint32_t)h->G.n + 1;
     c.cnt = h->cnt.p;
@@ -647,9 +755,10 @@ Ctx make_ctx(msc_handle *h, int tier, int qmax, int exact_fallback, float xi)
 }
 
 template <int D> msc_status eval_dense(msc_handle *h, const float *v, Grid G, uint64_t *out, const uint64_t *ref,
-                                       uint32_t *list, unsigned long long *nlist, cudaStream_t s)
+                                       uint32_t *list, unsigned long long *nlist, cudaStream_t s,
+                                       uint32_t *clist = nullptr, unsigned long long *nclist = nullptr, int tier = 4)
 {
-    KL(h, MSC_K_DENSE, s, k_eval_dense<D><<<grid_for(G.n), TPB, 0, s>>>(v, G, out, ref, list, nlist));
+    KL(h, MSC_K_DENSE, s, k_eval_dense<D><<<grid_for(G.n), TPB, 0, s>>>(v, G, out, ref, list, nlist, clist, nclist, tier));
     CK(cudaGetLastError());
     return MSC_OK;
 }
@@ -669,13 +778,13 @@ template <int D> msc_status build_seeds(msc_handle *h, cudaStream_t s)
     for (int kind = 0; kind < (D == 3 ? 3 : 2); kind++) {
         unsigned long long n = 0;
         CK(cudaMemsetAsync(cnt.p, 0, sizeof n, s));
-        KL(h, MSC_K_OTHER, s, k_seeds<D><<<grid_for(h->G.n), TPB, 0, s>>>(h->code_f.p, h->G, kind, nullptr, cnt.p, 0));
+        KL(h, MSC_K_OTHER, s, k_seeds<D><<<grid_for(h->G.n), TPB, 0, s>>>(h->code_f.p, h->G, kind, nullptr, cnt.p));
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(&n, cnt.p, sizeof n, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         CK(bufs[kind]->alloc(n));
         CK(cudaMemsetAsync(cnt.p, 0, sizeof n, s));
-        KL(h, MSC_K_OTHER, s, k_seeds<D><<<grid_for(h->G.n), TPB, 0, s>>>(h->code_f.p, h->G, kind, bufs[kind]->p, cnt.p, n));
+        KL(h, MSC_K_OTHER, s, k_seeds<D><<<grid_for(h->G.n), TPB, 0, s>>>(h->code_f.p, h->G, kind, bufs[kind]->p, cnt.p));
         CK(cudaGetLastError());
         *ns[kind] = (uint32_t)n;
     }
@@ -723,11 +832,11 @@ template <int D> msc_status s_pass_state(msc_handle *h, Ctx &c, bool &built, con
 {
     c.ovf_out = D == 3 ? h->ovf0.p : nullptr;
     if (!built) {
-        CK(cudaMemsetAsync(h->ns_v.p, 0, h->ns_v.n, s));
-        CK(cudaMemsetAsync(h->ns_top.p, 0, h->ns_top.n, s));
+        CK(cudaMemsetAsync(h->ns_v.p, 0, h->ns_v.n * 4, s));
+        CK(cudaMemsetAsync(h->ns_top.p, 0, h->ns_top.n * 4, s));
         if (D == 3) {
-            CK(cudaMemsetAsync(h->ns_tri.p, 0, h->ns_tri.n, s));
-            CK(cudaMemsetAsync(h->ns_dead.p, 0, h->ns_dead.n, s));
+            CK(cudaMemsetAsync(h->ns_tri.p, 0, h->ns_tri.n * 4, s));
+            CK(cudaMemsetAsync(h->ns_dead.p, 0, h->ns_dead.n * 4, s));
         }
         KL(h, MSC_K_SEP_INIT, s, k_node_init<D><<<grid_for(h->G.n), TPB, 0, s>>>(c));
         if (h->n_desc) KL(h, MSC_K_SEP_INIT, s, k_node_seed<D><<<grid_for(h->n_desc), TPB, 0, s>>>(c, 0, h->seeds_desc.p, h->n_desc));
@@ -773,23 +882,24 @@ template <int D>
 msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t s, FixResult &R)
 {
     Ctx c = make_ctx(h, o.tier, o.q_max, o.exact_fallback, xi);
-    unsigned long long *nMc = h->nM.p;     // nMc[0], nMc[1]
-    uint32_t *M[2] = {h->M0.p, h->M1.p};
+    unsigned long long *nMc = h->nM.p;     // nMc[0], nMc[1]: sizes of M[0], M[1]; nMc[4], nMc[5]: of C[0], C[1]
+    uint32_t *M[2] = {h->M0.p, h->M1.p};   // anchors whose code differs from f's
+    uint32_t *C[2] = {h->C0.p, h->C1.p};   // anchors whose critical cells differ from f's
     int cur = 0;
     KL(h, MSC_K_OTHER, s, k_init_g<<<grid_for(h->G.n), TPB, 0, s>>>(h->f.p, h->fhat.p, h->g.p, h->state.p, h->G.n, xi));
     CK(cudaGetLastError());
-    CK(cudaMemsetAsync(nMc, 0, 4 * sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(nMc, 0, 8 * sizeof(unsigned long long), s));
     // sets left over by an earlier call that stopped with an error
     CK(cudaMemsetAsync(h->Tbits.p, 0, h->Tbits.n * 4, s));
     CK(cudaMemsetAsync(h->Xbits.p, 0, h->Xbits.n * 4, s));
     CK(cudaMemsetAsync(h->Dbits.p, 0, h->Dbits.n * 4, s));
     CK(cudaMemsetAsync(h->sDbits.p, 0, h->sDbits.n * 4, s));
-    CKS(eval_dense<D>(h, h->g.p, h->G, h->code_g.p, h->code_f.p, M[cur], nMc + cur, s));
+    CKS(eval_dense<D>(h, h->g.p, h->G, h->code_g.p, h->code_f.p, M[cur], nMc + cur, s, C[cur], nMc + 4 + cur, o.tier));
     bool sep_built = false;
     h->items[MSC_K_DENSE] += h->G.n;
     for (;;) {
         CK(cudaMemsetAsync(h->cnt.p, 0, sizeof(Counters), s));
-        KL(h, MSC_K_CPASS, s, k_ctargets<D><<<grid_for(h->G.n / 8 + 1), TPB, 0, s>>>(c, M[cur], nMc + cur));
+        KL(h, MSC_K_CPASS, s, k_ctargets<D><<<grid_for(h->G.n / 8 + 1), TPB, 0, s>>>(c, C[cur], nMc + 4 + cur));
         CK(cudaGetLastError());
         Counters hc;
         CK(cudaMemcpyAsync(&hc, h->cnt.p, sizeof hc, cudaMemcpyDeviceToHost, s));
@@ -826,14 +936,9 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
         KL(h, MSC_K_EDIT, s, k_edit<D><<<grid_for(hc.nT + hc.nX), TPB, 0, s>>>(c));
         KL(h, MSC_K_REFRESH, s, k_refresh<D><<<grid_for(h->G.n / 4 + 1), TPB, 0, s>>>(c));
         CK(cudaMemsetAsync(nMc + nxt, 0, sizeof(unsigned long long), s));
-        c.Mnext = M[nxt];
-        c.tag = ++h->tag;
-        if (h->tag == 0xFFFFFFFFu) {   // stamps would repeat: reset them
-            CK(cudaMemsetAsync(h->stamp.p, 0, h->stamp.n * 4, s));
-            h->tag = 1;
-            c.tag = 1;
-        }
-        KL(h, MSC_K_REBUILD, s, k_rebuild<<<grid_for(h->G.n / 8 + 1), TPB, 0, s>>>(c, M[cur], nMc + cur, nMc + nxt, nMc + 3));
+        CK(cudaMemsetAsync(nMc + 4 + nxt, 0, sizeof(unsigned long long), s));
+        KL(h, MSC_K_REBUILD, s, k_rebuild<D><<<grid_for(h->G.n / 8 + 1), TPB, 0, s>>>(c, M[cur], nMc + cur, M[nxt], nMc + nxt,
+                                                                                     C[cur], nMc + 4 + cur, C[nxt], nMc + 4 + nxt, nMc + 3));
         KL(h, MSC_K_REBUILD, s, k_clear<<<grid_for(h->G.n / 8 + 1), TPB, 0, s>>>(c));
         CK(cudaGetLastError());
         cur = nxt;
@@ -1047,10 +1152,13 @@ void msc_default_options(msc_options *opt)
 uint64_t msc_device_bytes(int nx, int ny, int nz)
 {
     const uint64_t n = (uint64_t)nx * ny * nz;
-    const int D = nz > 1 ? 3 : 2;
-    uint64_t b = n * (4 + 8) + n * (4 + 4 + 1 + 8) + 3 * (n / 8) + 6 * n * 4 + n / 8 + n * (D == 3 ? 6 : 2) / 8;
-    if (D == 3) b += n * 12 / 8 + 16 * n;
-    b += n * 3 * 4;   // separatrix seeds (upper estimate)
+    const bool d3 = nz > 1;
+    const uint64_t ntop = d3 ? 6 : 2;
+    uint64_t b = 12 * n + n + 16 * n;             // f, f_hat, g; state; code_f, code_g
+    b += 4 * (n / 8 + 4) + 8 * 4 * n;             // four bitsets; eight index lists
+    b += n / 8 + ntop * n / 8 + (d3 ? 12 * n / 8 + 16 * n : 0);   // walk visited sets, spill queues
+    b += 4 * n * (1 + ntop + (d3 ? 19 : 0));      // separatrix state words
+    b += 3 * 4 * n;                               // separatrix seeds (upper estimate)
     return b;
 }
 
@@ -1074,7 +1182,7 @@ msc_status msc_prepare_original(const float *f, int nx, int ny, int nz, const ms
         CK(h->f.alloc(h->G.n));
         CK(h->code_f.alloc(h->G.n));
         CK(h->cnt.alloc(1));
-        CK(h->nM.alloc(4));
+        CK(h->nM.alloc(8));
         h->prof_on = o.profile != 0;
         CKS(upload_field(h, f, h->G.n, h->f.p, h->nM.p, s, "f"));
         CKS(eval_dense_any(h, h->D, h->f.p, h->G, h->code_f.p, nullptr, nullptr, nullptr, s));
