@@ -68,6 +68,9 @@ template <int D> struct Tab {
     // dense evaluator: window positions
     int cpos[8];                   // corner k
     int cnb[8][14];                // corner k + nb[n]
+    int cnb_ord[8][14];            // neighbour indices n of corner k by increasing window position
+    int nwin;                      // window offsets an anchor's code reads: [-1,1]^D u [0,2]^D
+    int win[64][3];
     int ce_a[19], ce_b[19];        // cube edges: corners a < b (a subset of b)
     int ce_cof[19][6];             // window positions of the cofacet extra vertices
     int ce_ncof[19];
@@ -233,11 +236,25 @@ template <int D> constexpr Tab<D> make_tab()
             t.kfac_opp[kk][j] = corner[j];
         }
     }
+    t.nwin = 0;
+    for (int z = zlo; z <= zhi; z++)
+        for (int y = -1; y <= 2; y++)
+            for (int x = -1; x <= 2; x++) {
+                const bool lowcube = x <= 1 && y <= 1 && z <= 1, highcube = x >= 0 && y >= 0 && z >= 0;
+                if (!lowcube && !highcube) continue;
+                t.win[t.nwin][0] = x; t.win[t.nwin][1] = y; t.win[t.nwin][2] = z;
+                t.nwin++;
+            }
     // dense evaluator positions
     for (int k = 0; k < T::NC; k++) {
         int cx = k & 1, cy = (k >> 1) & 1, cz = (k >> 2) & 1;
         t.cpos[k] = wpos<D>(cx, cy, cz);
         for (int n = 0; n < T::NNB; n++) t.cnb[k][n] = wpos<D>(cx + t.nb[n][0], cy + t.nb[n][1], cz + t.nb[n][2]);
+        for (int n = 0; n < T::NNB; n++) t.cnb_ord[k][n] = n;
+        for (int i = 1; i < T::NNB; i++)
+            for (int j = i; j > 0 && t.cnb[k][t.cnb_ord[k][j - 1]] > t.cnb[k][t.cnb_ord[k][j]]; j--) {
+                int u = t.cnb_ord[k][j]; t.cnb_ord[k][j] = t.cnb_ord[k][j - 1]; t.cnb_ord[k][j - 1] = u;
+            }
     }
     {
         int k = 0;
@@ -338,6 +355,9 @@ template <int N, class F> MSC_HD __forceinline__ void static_for(F &&f)
 //  tetrahedron: paired down if its highest triangle chose it; else critical (a maximum).
 // w: the WS window values (+inf outside the domain); corner_in: bit k set if cube corner
 // k of the anchor lies in the domain.  Every table index is a compile-time constant.
+// Each "lowest candidate below X" is found as the SoS-lowest candidate overall (candidates
+// visited by increasing vertex id, replaced only by a strictly smaller value) followed by
+// one comparison with X: the overall lowest is below X exactly when any candidate is.
 template <int D>
 MSC_HD __forceinline__ uint64_t eval_anchor(const float *w, unsigned corner_in)
 {
@@ -347,15 +367,15 @@ MSC_HD __forceinline__ uint64_t eval_anchor(const float *w, unsigned corner_in)
         constexpr int k = decltype(kc)::value;
         constexpr int ck = TabC<D>::T.cpos[k];
         float bv = pos_inf();
-        int bp = 1 << 20, bn = 15;
-        static_for<Tb::NNB>([&](auto nc) {
-            constexpr int n = decltype(nc)::value;
+        int bn = 15;
+        static_for<Tb::NNB>([&](auto ic) {
+            constexpr int n = TabC<D>::T.cnb_ord[k][decltype(ic)::value];
             constexpr int q = TabC<D>::T.cnb[k][n];
-            if (MSC_WLT(w, q, ck)) {
-                if (w[q] < bv || (w[q] == bv && q < bp)) { bv = w[q]; bp = q; bn = n; }
-            }
+            if (w[q] < bv) { bv = w[q]; bn = n; }
         });
-        vp[k] = bn;
+        // a neighbour -e_A (index >= NE) has the smaller vertex id, so it wins a tie
+        const bool below = bv < w[ck] || (bv == w[ck] && bn >= Tb::NE);
+        vp[k] = below ? bn : 15;
     });
     int eup[Tb::NCE];   // -2 paired down, -1 critical, >= 0 index of the cofacet taken
     static_for<Tb::NCE>([&](auto cc) {
@@ -370,11 +390,10 @@ MSC_HD __forceinline__ uint64_t eval_anchor(const float *w, unsigned corner_in)
         static_for<TabC<D>::T.ce_ncof[ce]>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
             constexpr int q = TabC<D>::T.ce_cof[ce][i];
-            if (MSC_WLT(w, q, pa) && MSC_WLT(w, q, pb)) {
-                if (w[q] < bv || (w[q] == bv && q < bp)) { bv = w[q]; bp = q; bi = i; }
-            }
+            if (w[q] < bv) { bv = w[q]; bp = q; bi = i; }
         });
-        eup[ce] = down ? -2 : bi;
+        const bool below = (bv < w[pa] || (bv == w[pa] && bp < pa)) && (bv < w[pb] || (bv == w[pb] && bp < pb));
+        eup[ce] = down ? -2 : (below ? bi : -1);
     });
     int tup[Tb::NCT];   // -2 paired down, -1 critical, >= 0 index of the cofacet tet taken
     static_for<Tb::NCT>([&](auto tc) {
@@ -396,11 +415,13 @@ MSC_HD __forceinline__ uint64_t eval_anchor(const float *w, unsigned corner_in)
         static_for<TabC<D>::T.ct_ncof[ct]>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
             constexpr int q = TabC<D>::T.ct_cof[ct][i];
-            if (MSC_WLT(w, q, pa) && MSC_WLT(w, q, pb) && MSC_WLT(w, q, pc)) {
-                if (w[q] < bv || (w[q] == bv && q < bp)) { bv = w[q]; bp = q; bi = i; }
-            }
+            if (w[q] < bv) { bv = w[q]; bp = q; bi = i; }
         });
-        tup[ct] = down ? -2 : bi;
+        // below all three vertices = below the lowest one
+        const float lv = la ? w[pa] : (lb ? w[pb] : w[pc]);
+        const int lp = la ? pa : (lb ? pb : pc);
+        const bool below = bv < lv || (bv == lv && bp < lp);
+        tup[ct] = down ? -2 : (below ? bi : -1);
     });
     uint64_t code = (uint64_t)vp[0];
     static_for<Tb::NE>([&](auto ec) {

@@ -181,11 +181,33 @@ template <int D> MSC_HD inline void load_window(const float *v, const Grid &G, i
             }
 }
 
+// window of an anchor at least one vertex from the lower and two from the upper faces
+template <int D> MSC_HD inline void load_window_interior(const float *v, const Grid &G, uint32_t p, float *w)
+{
+    constexpr int ZL = D == 3 ? -1 : 0, ZH = D == 3 ? 2 : 0;
+    const int sy = G.nx, sz = G.nx * G.ny;
+#pragma unroll
+    for (int dz = ZL; dz <= ZH; dz++)
+#pragma unroll
+        for (int dy = -1; dy <= 2; dy++)
+#pragma unroll
+            for (int dx = -1; dx <= 2; dx++) {
+                const bool lowcube = dx <= 1 && dy <= 1 && dz <= 1;
+                const bool highcube = dx >= 0 && dy >= 0 && dz >= 0;
+                if (lowcube || highcube) w[wpos<D>(dx, dy, dz)] = ld(v + (int64_t)p + dx + dy * sy + dz * sz);
+            }
+}
+
 template <int D> MSC_HD inline uint64_t anchor_code(const float *v, const Grid &G, uint32_t p)
 {
     int x, y, z;
     coords(G, p, x, y, z);
     float w[Tab<D>::WS];
+    const bool interior = x >= 1 && y >= 1 && x + 2 < G.nx && y + 2 < G.ny && (D == 2 || (z >= 1 && z + 2 < G.nz));
+    if (interior) {
+        load_window_interior<D>(v, G, p, w);
+        return eval_anchor<D>(w, (1u << Tab<D>::NC) - 1u);
+    }
     load_window<D>(v, G, x, y, z, w);
     return eval_anchor<D>(w, corner_mask<D>(G, x, y, z));
 }
@@ -379,56 +401,55 @@ MSC_HD inline float clamp_base(float f, float fh, float xi)
     return fh < lb ? lb : (fh > ub ? ub : fh);
 }
 
-// anchors whose code reads the value at v: v - (corner + neighbour offset); each newly
-// dirty anchor is handed to app (which appends it to the dirty list)
-template <int D, class App> MSC_HD inline void mark_dirty(const Ctx &c, uint32_t v, App &&app)
+// anchors whose code reads the value at v are v - o for the window offsets o; part/nparts
+// split them among cooperating threads; each newly dirty anchor is handed to app (which
+// appends it to the dirty list)
+template <int D, class App> MSC_HD inline void mark_dirty(const Ctx &c, uint32_t v, int part, int nparts, App &&app)
 {
+    const Tab<D> &T = rt_tab<D>();
     int x, y, z;
     coords(c.G, v, x, y, z);
-    constexpr int ZL = D == 3 ? -1 : 0, ZH = D == 3 ? 2 : 0;
-#pragma unroll
-    for (int dz = ZL; dz <= ZH; dz++)
-#pragma unroll
-        for (int dy = -1; dy <= 2; dy++)
-#pragma unroll
-            for (int dx = -1; dx <= 2; dx++) {
-                const bool lowcube = dx <= 1 && dy <= 1 && dz <= 1;
-                const bool highcube = dx >= 0 && dy >= 0 && dz >= 0;
-                if (!lowcube && !highcube) continue;
-                const int px = x - dx, py = y - dy, pz = z - dz;
-                if (!inside(c.G, px, py, pz)) continue;
-                const uint32_t p = vid(c.G, px, py, pz);
-                if (!test_and_set(c.Dbits, p)) app(p);
-            }
+    for (int j = part; j < T.nwin; j += nparts) {
+        const int px = x - T.win[j][0], py = y - T.win[j][1], pz = z - T.win[j][2];
+        if (!inside(c.G, px, py, pz)) continue;
+        const uint32_t p = vid(c.G, px, py, pz);
+        if (!test_and_set(c.Dbits, p)) app(p);
+    }
 }
 
-// item i < nX: restore Xlist[i] to f; else quantised step of Tlist[i - nX] unless it is
-// also restored (Eq. 2: one step of xi / 2^q_max while q < q_max and the value stays
-// >= f - xi, otherwise the floor f - xi)
-template <int D, class App> MSC_HD inline void edit_item(const Ctx &c, uint32_t i, uint32_t nX, App &&app)
+// Edit item i (read only): i < nX restores Xlist[i] to f; otherwise Tlist[i - nX] takes a
+// quantised step unless it is also restored or can no longer move.  Returns whether the
+// item changes a vertex, and the vertex.
+MSC_HD inline bool edit_decide(const Ctx &c, uint32_t i, uint32_t nX, uint32_t &v)
 {
-    uint32_t v;
     if (i < nX) {
         v = c.Xlist[i];
-        if (c.state[v] == ST_EXACT) return;
+        return c.state[v] != ST_EXACT;
+    }
+    v = c.Tlist[i - nX];
+    if ((c.Xbits[v >> 5] >> (v & 31)) & 1u) return false;
+    return c.state[v] <= c.qmax;
+}
+
+// Eq. 2 applied to a changing item: one step of xi / 2^q_max while q < q_max and the value
+// stays >= f - xi, otherwise the floor f - xi; a restore sets g = f exactly
+MSC_HD inline void edit_apply(const Ctx &c, uint32_t i, uint32_t nX, uint32_t v)
+{
+    if (i < nX) {
         c.g[v] = ld(c.f + v);
         c.state[v] = ST_EXACT;
-    } else {
-        v = c.Tlist[i - nX];
-        if ((c.Xbits[v >> 5] >> (v & 31)) & 1u) return;
-        const uint8_t st = c.state[v];
-        if (st > c.qmax) return;
-        const float fv = ld(c.f + v);
-        const float lb = sub_ru(fv, c.xi);
-        bool done = false;
-        if (st < c.qmax) {
-            const float fc = clamp_base(fv, ld(c.fhat + v), c.xi);
-            const float cand = sub_rn(fc, mul_rn((float)(st + 1), c.step));
-            if (cand >= lb) { c.g[v] = cand; c.state[v] = (uint8_t)(st + 1); done = true; }
-        }
-        if (!done) { c.g[v] = lb; c.state[v] = ST_FLOOR; }
+        return;
     }
-    mark_dirty<D>(c, v, app);
+    const uint8_t st = c.state[v];
+    const float fv = ld(c.f + v);
+    const float lb = sub_ru(fv, c.xi);
+    if (st < c.qmax) {
+        const float fc = clamp_base(fv, ld(c.fhat + v), c.xi);
+        const float cand = sub_rn(fc, mul_rn((float)(st + 1), c.step));
+        if (cand >= lb) { c.g[v] = cand; c.state[v] = (uint8_t)(st + 1); return; }
+    }
+    c.g[v] = lb;
+    c.state[v] = ST_FLOOR;
 }
 
 // one bit per cell the anchor owns: set if the cell is critical (tier 1: extrema only)

@@ -181,16 +181,25 @@ template <int D> __global__ void __launch_bounds__(TPB) k_ctargets(Ctx c, const 
 
 constexpr int DIRTY_STAGE = 8192;
 
+// one warp per edited vertex: all lanes read the item's state, lane 0 applies the edit,
+// the lanes share the dirty-anchor marks
 template <int D> __global__ void k_edit(Ctx c)
 {
     __shared__ Stage<DIRTY_STAGE> sd;
     st_init(sd);
-    const uint32_t nX = (uint32_t)c.cnt->nX, nT = (uint32_t)c.cnt->nT;
-    BLOCK_ROUNDS(b, (unsigned long long)nX + nT)
-    {
-        const unsigned long long i = b + threadIdx.x;
-        if (i < (unsigned long long)nX + nT)
-            edit_item<D>(c, (uint32_t)i, nX, [&](uint32_t p) { st_push(sd, p, c.Dlist, &c.cnt->nD); });
+    const unsigned long long nX = c.cnt->nX, items = nX + c.cnt->nT;
+    const unsigned lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (unsigned long long b = (unsigned long long)blockIdx.x * wpb; b < items; b += (unsigned long long)gridDim.x * wpb) {
+        const unsigned long long i = b + (threadIdx.x >> 5);
+        if (i < items) {
+            uint32_t v;
+            const bool changed = edit_decide(c, (uint32_t)i, (uint32_t)nX, v);
+            __syncwarp();
+            if (changed) {
+                if (lane == 0) edit_apply(c, (uint32_t)i, (uint32_t)nX, v);
+                mark_dirty<D>(c, v, (int)lane, 32, [&](uint32_t p) { st_push(sd, p, c.Dlist, &c.cnt->nD); });
+            }
+        }
         st_flush(sd, c.Dlist, &c.cnt->nD);
     }
 }
@@ -933,7 +942,7 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
         h->items[MSC_K_EDIT] += hc.nT + hc.nX;
         if (hc.nX) R.n_fb++;
         const int nxt = cur ^ 1;
-        KL(h, MSC_K_EDIT, s, k_edit<D><<<grid_for(hc.nT + hc.nX), TPB, 0, s>>>(c));
+        KL(h, MSC_K_EDIT, s, k_edit<D><<<grid_for(32 * (hc.nT + hc.nX)), TPB, 0, s>>>(c));
         KL(h, MSC_K_REFRESH, s, k_refresh<D><<<grid_for(h->G.n / 4 + 1), TPB, 0, s>>>(c));
         CK(cudaMemsetAsync(nMc + nxt, 0, sizeof(unsigned long long), s));
         CK(cudaMemsetAsync(nMc + 4 + nxt, 0, sizeof(unsigned long long), s));
