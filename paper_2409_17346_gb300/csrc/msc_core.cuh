@@ -48,6 +48,18 @@ struct Counters {
     unsigned long long rep[16];                            // verify / misc
 };
 
+// device-side state of the edit loop, so rounds can run back to back without the host
+struct LoopState {
+    int halt;                 // the current phase is over (no false case left) or an error
+    int status;               // 0 running / done, 4 max_iters reached, 6 stalled
+    int cur;                  // which of the double-buffered mismatch lists is current
+    int track_dirty;          // accumulate dirty anchors for the separatrix state
+    unsigned iters, n_c, n_s, n_fb;
+    unsigned max_iters, exact_fallback, trace_cap, ntrace;
+    unsigned long long nM[2], nC[2], nSD;
+    unsigned long long edit_items;
+};
+
 // everything a kernel of one job needs (device pointers)
 struct Ctx {
     Grid G;
@@ -67,7 +79,9 @@ struct Ctx {
     // persistent separatrix state (tier 4): one byte per node, see "separatrix state" below
     int32_t *ns_v, *ns_top, *ns_tri, *ns_dead;
     uint32_t *sDbits, *sDlist;       // anchors dirtied since the last S-pass
-    int track_dirty;
+    LoopState *ls;
+    uint32_t *Mb[2], *Cb[2];         // mismatch lists: code differs / critical cells differ
+    int64_t *trace;                  // rows (kind, |T|, |X|, sum T, sum X), ls->trace_cap rows
 };
 
 // ------------------------------------------------------------------------------------

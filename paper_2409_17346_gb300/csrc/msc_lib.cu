@@ -12,6 +12,7 @@
 // differs from f's.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -173,10 +174,42 @@ __global__ void k_init_g(const float *f, const float *fh, float *g, uint8_t *sta
     }
 }
 
-template <int D> __global__ void __launch_bounds__(TPB) k_ctargets(Ctx c, const uint32_t *M, const unsigned long long *nM)
+// ---- one edit round as a chain of kernels that read the device loop state (ls): any
+// kernel of a round whose phase is over (ls->halt) does nothing, so rounds can be queued
+// back to back (a captured graph of several rounds) and the host looks only at their end.
+
+// C-pass over the anchors whose critical cells differ from f's (current list)
+template <int D> __global__ void __launch_bounds__(TPB) k_ctargets(Ctx c)
 {
-    const unsigned long long n = *nM;
-    GRID_STRIDE(i, n) ctargets_anchor<D>(c, M[i]);
+    if (c.ls->halt) return;
+    const int cur = c.ls->cur;
+    const uint32_t *C = c.Cb[cur];
+    const unsigned long long n = c.ls->nC[cur];
+    GRID_STRIDE(i, n) ctargets_anchor<D>(c, C[i]);
+}
+
+// after a targeting pass (kind 0 C, 1 S): stop the phase when there is no false case, stop
+// with a status on a stall or at max_iters, otherwise record the round and go on
+__global__ void k_decide(Ctx c, int kind)
+{
+    if (threadIdx.x || blockIdx.x) return;
+    LoopState *ls = c.ls;
+    if (ls->halt) return;
+    const Counters *k = c.cnt;
+    if (k->ncase == 0) { ls->halt = 1; return; }
+    if (!ls->exact_fallback && k->nlive == 0) { ls->halt = 1; ls->status = MSC_ERR_STALLED; return; }
+    if (ls->iters >= ls->max_iters) { ls->halt = 1; ls->status = MSC_ERR_NOT_CONVERGED; return; }
+    if (c.trace && ls->ntrace < ls->trace_cap) {
+        int64_t *r = c.trace + 5 * (size_t)ls->ntrace;
+        r[0] = kind; r[1] = (int64_t)k->nT; r[2] = (int64_t)k->nX; r[3] = (int64_t)k->sumT; r[4] = (int64_t)k->sumX;
+    }
+    ls->ntrace++;
+    ls->iters++;
+    if (kind) ls->n_s++; else ls->n_c++;
+    if (k->nX) ls->n_fb++;
+    ls->edit_items += k->nT + k->nX;
+    ls->nM[ls->cur ^ 1] = 0;
+    ls->nC[ls->cur ^ 1] = 0;
 }
 
 constexpr int DIRTY_STAGE = 8192;
@@ -185,6 +218,7 @@ constexpr int DIRTY_STAGE = 8192;
 // the lanes share the dirty-anchor marks
 template <int D> __global__ void k_edit(Ctx c)
 {
+    if (c.ls->halt) return;
     __shared__ Stage<DIRTY_STAGE> sd;
     st_init(sd);
     const unsigned long long nX = c.cnt->nX, items = nX + c.cnt->nT;
@@ -206,22 +240,27 @@ template <int D> __global__ void k_edit(Ctx c)
 
 template <int D> __global__ void __launch_bounds__(TPB) k_refresh(Ctx c)
 {
+    if (c.ls->halt) return;
     const unsigned long long n = c.cnt->nD;
     GRID_STRIDE(i, n) refresh_anchor<D>(c, c.Dlist[i]);
 }
 
 // next mismatch lists: anchors of the current lists that were not re-evaluated keep their
 // membership; re-evaluated (dirty) anchors join by their new code.  No anchor appears twice.
-template <int D>
-__global__ void k_rebuild(Ctx c, const uint32_t *Mcur, const unsigned long long *nMcur, uint32_t *Mnext,
-                          unsigned long long *nMnext, const uint32_t *Ccur, const unsigned long long *nCcur,
-                          uint32_t *Cnext, unsigned long long *nCnext, unsigned long long *nSD)
+template <int D> __global__ void k_rebuild(Ctx c)
 {
+    if (c.ls->halt) return;
     __shared__ Stage<TPB> sm, sc, ss;
     st_init(sm);
     st_init(sc);
     st_init(ss);
-    const unsigned long long a = *nMcur, b2 = *nCcur, d = c.cnt->nD;
+    LoopState *ls = c.ls;
+    const int cur = ls->cur, nxt = cur ^ 1;
+    const uint32_t *Mcur = c.Mb[cur], *Ccur = c.Cb[cur];
+    uint32_t *Mnext = c.Mb[nxt], *Cnext = c.Cb[nxt];
+    unsigned long long *nMnext = &ls->nM[nxt], *nCnext = &ls->nC[nxt];
+    const unsigned long long a = ls->nM[cur], b2 = ls->nC[cur], d = c.cnt->nD;
+    const int track = ls->track_dirty;
     BLOCK_ROUNDS(b, a + b2 + d)
     {
         const unsigned long long i = b + threadIdx.x;
@@ -233,7 +272,7 @@ __global__ void k_rebuild(Ctx c, const uint32_t *Mcur, const unsigned long long 
             }
         } else if (i < a + b2 + d) {
             const uint32_t p = c.Dlist[i - a - b2];
-            if (c.track_dirty && !test_and_set(c.sDbits, p)) st_push(ss, p, c.sDlist, nSD);
+            if (track && !test_and_set(c.sDbits, p)) st_push(ss, p, c.sDlist, &ls->nSD);
             const uint64_t cf = __ldg(c.code_f + p), cg = c.code_g[p];
             if (cf != cg) {
                 st_push(sm, p, Mnext, nMnext);
@@ -242,12 +281,13 @@ __global__ void k_rebuild(Ctx c, const uint32_t *Mcur, const unsigned long long 
         }
         st_flush(sm, Mnext, nMnext);
         st_flush(sc, Cnext, nCnext);
-        st_flush(ss, c.sDlist, nSD);
+        st_flush(ss, c.sDlist, &ls->nSD);
     }
 }
 
 __global__ void k_clear(Ctx c)
 {
+    if (c.ls->halt) return;
     const unsigned long long nT = c.cnt->nT, nX = c.cnt->nX, nD = c.cnt->nD;
     GRID_STRIDE(i, nT + nX + nD)
     {
@@ -256,6 +296,17 @@ __global__ void k_clear(Ctx c)
         else c.Dbits[c.Dlist[i - nT - nX] >> 5] = 0;
     }
 }
+
+// end of a round: swap the mismatch lists, zero the round's counters
+__global__ void k_end(Ctx c)
+{
+    if (threadIdx.x || blockIdx.x || c.ls->halt) return;
+    c.ls->cur ^= 1;
+    memset(c.cnt, 0, sizeof(Counters));
+}
+
+__global__ void k_set_halt(LoopState *ls, int v) { ls->halt = v; }
+__global__ void k_set_track(LoopState *ls, int v) { ls->track_dirty = v; }
 
 template <int D> __global__ void k_desc(Ctx c, const uint32_t *seeds, uint32_t n)
 {
@@ -627,6 +678,9 @@ struct msc_handle {
     DevBuf<int32_t> ns_v, ns_top, ns_tri, ns_dead;
     DevBuf<uint32_t> sDbits, sDlist;
     DevBuf<Counters> cnt;
+    DevBuf<LoopState> ls;
+    DevBuf<int64_t> trace;
+    cudaStream_t cap_stream = nullptr;   // graphs are captured on this stream
     DevBuf<unsigned long long> nM;   // [0,1] sizes of M0, M1; [2] scratch; [3] dirty-since-S-pass; [4,5] C0, C1
     bool fix_ready = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -644,6 +698,7 @@ struct msc_handle {
     std::vector<cudaEvent_t> pool;
     ~msc_handle()
     {
+        if (cap_stream) cudaStreamDestroy(cap_stream);
         for (auto &p : pend) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
         for (auto e : pool) cudaEventDestroy(e);
     }
@@ -730,6 +785,7 @@ msc_status alloc_fix_state(msc_handle *h)
     CK(cudaMemset(h->sDbits.p, 0, h->sDbits.n * 4));
     CK(h->cnt.alloc(1));
     CK(h->nM.alloc(8));
+    CK(h->ls.alloc(1));
     CK(cudaMemset(h->Tbits.p, 0, h->Tbits.n * 4));
     CK(cudaMemset(h->Xbits.p, 0, h->Xbits.n * 4));
     CK(cudaMemset(h->Dbits.p, 0, h->Dbits.n * 4));
@@ -759,7 +815,10 @@ Ctx make_ctx(msc_handle *h, int tier, int qmax, int exact_fallback, float xi)
     c.cnt = h->cnt.p;
     c.ns_v = h->ns_v.p; c.ns_top = h->ns_top.p; c.ns_tri = h->ns_tri.p; c.ns_dead = h->ns_dead.p;
     c.sDbits = h->sDbits.p; c.sDlist = h->sDlist.p;
-    c.track_dirty = 0;
+    c.ls = h->ls.p;
+    c.Mb[0] = h->M0.p; c.Mb[1] = h->M1.p;
+    c.Cb[0] = h->C0.p; c.Cb[1] = h->C1.p;
+    c.trace = nullptr;
     return c;
 }
 
@@ -854,7 +913,7 @@ template <int D> msc_status s_pass_state(msc_handle *h, Ctx &c, bool &built, con
         CK(cudaGetLastError());
         h->items[MSC_K_SEP_INIT] += h->G.n;
         built = true;
-        c.track_dirty = 1;
+        k_set_track<<<1, 1, 0, s>>>(h->ls.p, 1);
     } else {
         KL(h, MSC_K_SEP_UPDATE, s, k_node_update<D><<<grid_for(h->G.n / 16 + 1), TPB, 0, s>>>(c, nSD));
         CK(cudaGetLastError());
@@ -887,70 +946,160 @@ struct FixResult {
     std::vector<msc_iter_record> trace;
 };
 
+constexpr int GRAPH_ROUNDS = 16;   // C-pass rounds queued per graph launch
+
+// A captured graph of GRAPH_ROUNDS C-pass rounds.  With profiling, every kernel node sits
+// between two event-record nodes; a node pair is counted only if its round ran.
+struct RoundGraph {
+    cudaGraphExec_t exec = nullptr;
+    struct Pair {
+        cudaEvent_t a, b;
+        int cls, round, pre;   // pre: the targeting pass and decision, which also run in the
+    };                         // round that finds no false case
+    std::vector<Pair> pairs;
+    ~RoundGraph()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        for (auto &p : pairs) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    }
+};
+
+template <int D> msc_status build_round_graph(msc_handle *h, const Ctx &c, bool profile, RoundGraph &rg)
+{
+    cudaStream_t cs = h->cap_stream;
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    auto node = [&](int cls, int round, int pre, auto &&launch) {
+        if (!profile) { launch(); return; }
+        RoundGraph::Pair p{nullptr, nullptr, cls, round, pre};
+        cudaEventCreate(&p.a);
+        cudaEventCreate(&p.b);
+        cudaEventRecordWithFlags(p.a, cs, cudaEventRecordExternal);   // an event-record node
+        launch();
+        cudaEventRecordWithFlags(p.b, cs, cudaEventRecordExternal);
+        rg.pairs.push_back(p);
+    };
+    for (int r = 0; r < GRAPH_ROUNDS; r++) {
+        node(MSC_K_CPASS, r, 1, [&] { k_ctargets<D><<<grid_for(h->G.n / 8 + 1), TPB, 0, cs>>>(c); });
+        node(MSC_K_OTHER, r, 1, [&] { k_decide<<<1, 32, 0, cs>>>(c, 0); });
+        node(MSC_K_EDIT, r, 0, [&] { k_edit<D><<<grid_for(32ull * h->G.n), TPB, 0, cs>>>(c); });
+        node(MSC_K_REFRESH, r, 0, [&] { k_refresh<D><<<grid_for(h->G.n), TPB, 0, cs>>>(c); });
+        node(MSC_K_REBUILD, r, 0, [&] { k_rebuild<D><<<grid_for(h->G.n), TPB, 0, cs>>>(c); });
+        node(MSC_K_REBUILD, r, 0, [&] { k_clear<<<grid_for(h->G.n), TPB, 0, cs>>>(c); });
+        node(MSC_K_OTHER, r, 0, [&] { k_end<<<1, 32, 0, cs>>>(c); });
+    }
+    cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    if (e != cudaSuccess) return fail(MSC_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&rg.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(MSC_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    return MSC_OK;
+}
+
+// launch counts (always) and event times (profiling) of one graph launch in which `active`
+// rounds edited and `halted` tells whether a further round found no false case
+void account_graph(msc_handle *h, RoundGraph &rg, unsigned active, bool halted)
+{
+    const unsigned long long a = active, t = active + (halted ? 1 : 0);
+    h->launches[MSC_K_CPASS] += t;
+    h->launches[MSC_K_OTHER] += t + a;
+    h->launches[MSC_K_EDIT] += a;
+    h->launches[MSC_K_REFRESH] += a;
+    h->launches[MSC_K_REBUILD] += 2 * a;
+    for (auto &p : rg.pairs) {
+        const bool ran = (unsigned)p.round < active || ((unsigned)p.round == active && halted && p.pre);
+        if (!ran) continue;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            h->ms[p.cls] += ms;
+            h->timed[p.cls]++;
+        }
+    }
+    cudaGetLastError();
+}
+
 template <int D>
 msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t s, FixResult &R)
 {
     Ctx c = make_ctx(h, o.tier, o.q_max, o.exact_fallback, xi);
-    unsigned long long *nMc = h->nM.p;     // nMc[0], nMc[1]: sizes of M[0], M[1]; nMc[4], nMc[5]: of C[0], C[1]
-    uint32_t *M[2] = {h->M0.p, h->M1.p};   // anchors whose code differs from f's
-    uint32_t *C[2] = {h->C0.p, h->C1.p};   // anchors whose critical cells differ from f's
-    int cur = 0;
+    LoopState L{};
+    L.max_iters = (unsigned)o.max_iters;
+    L.exact_fallback = (unsigned)o.exact_fallback;
+    if (o.record_trace) {
+        L.trace_cap = (unsigned)std::min<long long>(std::max(o.max_iters, 1), 1 << 22);
+        CK(h->trace.alloc(5ull * L.trace_cap));
+        c.trace = h->trace.p;
+    }
+    CK(cudaMemcpyAsync(h->ls.p, &L, sizeof L, cudaMemcpyHostToDevice, s));
     KL(h, MSC_K_OTHER, s, k_init_g<<<grid_for(h->G.n), TPB, 0, s>>>(h->f.p, h->fhat.p, h->g.p, h->state.p, h->G.n, xi));
     CK(cudaGetLastError());
-    CK(cudaMemsetAsync(nMc, 0, 8 * sizeof(unsigned long long), s));
     // sets left over by an earlier call that stopped with an error
     CK(cudaMemsetAsync(h->Tbits.p, 0, h->Tbits.n * 4, s));
     CK(cudaMemsetAsync(h->Xbits.p, 0, h->Xbits.n * 4, s));
     CK(cudaMemsetAsync(h->Dbits.p, 0, h->Dbits.n * 4, s));
     CK(cudaMemsetAsync(h->sDbits.p, 0, h->sDbits.n * 4, s));
-    CKS(eval_dense<D>(h, h->g.p, h->G, h->code_g.p, h->code_f.p, M[cur], nMc + cur, s, C[cur], nMc + 4 + cur, o.tier));
-    bool sep_built = false;
+    CK(cudaMemsetAsync(h->cnt.p, 0, sizeof(Counters), s));
+    LoopState *ls = h->ls.p;
+    CKS(eval_dense<D>(h, h->g.p, h->G, h->code_g.p, h->code_f.p, h->M0.p, &ls->nM[0], s, h->C0.p, &ls->nC[0], o.tier));
     h->items[MSC_K_DENSE] += h->G.n;
+    RoundGraph rg;
+    CKS(build_round_graph<D>(h, c, o.profile != 0, rg));
+    bool sep_built = false;
+    unsigned prev_iters = 0;
     for (;;) {
+        CK(cudaGraphLaunch(rg.exec, s));
+        CK(cudaMemcpyAsync(&L, ls, sizeof L, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        account_graph(h, rg, L.iters - prev_iters, L.halt != 0);
+        prev_iters = L.iters;
+        if (L.status == MSC_ERR_STALLED)
+            return fail(MSC_ERR_STALLED, "every false case targets a vertex that can no longer move");
+        if (L.status == MSC_ERR_NOT_CONVERGED) return fail(MSC_ERR_NOT_CONVERGED, "not converged after %d edit rounds", o.max_iters);
+        if (!L.halt) continue;               // the C-pass phase goes on
+        if (o.tier < 3) break;
+        // S-pass (Sec. 4.4) on the current lists
         CK(cudaMemsetAsync(h->cnt.p, 0, sizeof(Counters), s));
-        KL(h, MSC_K_CPASS, s, k_ctargets<D><<<grid_for(h->G.n / 8 + 1), TPB, 0, s>>>(c, C[cur], nMc + 4 + cur));
-        CK(cudaGetLastError());
+        if (o.tier >= 4) CKS(s_pass_state<D>(h, c, sep_built, c.Mb[L.cur], &ls->nM[L.cur], &ls->nSD, s));
+        else CKS(s_pass<D>(h, c, o.tier, s));
         Counters hc;
         CK(cudaMemcpyAsync(&hc, h->cnt.p, sizeof hc, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        int kind = 0;
-        if (hc.ncase == 0) {
-            if (o.tier < 3) break;
-            kind = 1;
-            if (o.tier >= 4) CKS(s_pass_state<D>(h, c, sep_built, M[cur], nMc + cur, nMc + 3, s));
-            else CKS(s_pass<D>(h, c, o.tier, s));
-            CK(cudaMemcpyAsync(&hc, h->cnt.p, sizeof hc, cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-            h->items[MSC_K_SEP_UPDATE] += hc.steps[0] + hc.steps[1] + hc.steps[2];
-            if (hc.err) return fail(MSC_ERR_OOM, "saddle-saddle spill queue overflow");
-            if (hc.ncase == 0) break;
-        }
-        if (!o.exact_fallback && hc.nlive == 0)
-            return fail(MSC_ERR_STALLED, "every false case targets a vertex at its floor (%llu cases)", hc.ncase);
-        if (R.n_c + R.n_s >= (uint32_t)o.max_iters)
-            return fail(MSC_ERR_NOT_CONVERGED, "not converged after %d edit rounds", o.max_iters);
-        if (o.record_trace) {
+        h->items[MSC_K_SEP_UPDATE] += hc.steps[0] + hc.steps[1] + hc.steps[2];
+        if (hc.err) return fail(MSC_ERR_OOM, "separatrix spill queue overflow");
+        if (hc.ncase == 0) break;
+        // the S-pass edit round, then back to C-pass rounds
+        KL(h, MSC_K_OTHER, s, k_set_halt<<<1, 1, 0, s>>>(ls, 0));
+        KL(h, MSC_K_OTHER, s, k_decide<<<1, 32, 0, s>>>(c, 1));
+        KL(h, MSC_K_EDIT, s, k_edit<D><<<grid_for(32ull * h->G.n), TPB, 0, s>>>(c));
+        KL(h, MSC_K_REFRESH, s, k_refresh<D><<<grid_for(h->G.n), TPB, 0, s>>>(c));
+        KL(h, MSC_K_REBUILD, s, k_rebuild<D><<<grid_for(h->G.n), TPB, 0, s>>>(c));
+        KL(h, MSC_K_REBUILD, s, k_clear<<<grid_for(h->G.n), TPB, 0, s>>>(c));
+        KL(h, MSC_K_OTHER, s, k_end<<<1, 32, 0, s>>>(c));
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(&L, ls, sizeof L, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        prev_iters = L.iters;
+        if (L.status == MSC_ERR_STALLED)
+            return fail(MSC_ERR_STALLED, "every false case targets a vertex that can no longer move");
+        if (L.status == MSC_ERR_NOT_CONVERGED) return fail(MSC_ERR_NOT_CONVERGED, "not converged after %d edit rounds", o.max_iters);
+    }
+    R.n_c = L.n_c;
+    R.n_s = L.n_s;
+    R.n_fb = L.n_fb;
+    h->items[MSC_K_EDIT] += L.edit_items;
+    if (o.record_trace && L.ntrace) {
+        const unsigned nt = std::min(L.ntrace, L.trace_cap);
+        std::vector<int64_t> rows(5ull * nt);
+        CK(cudaMemcpy(rows.data(), h->trace.p, rows.size() * sizeof(int64_t), cudaMemcpyDeviceToHost));
+        for (unsigned i = 0; i < nt; i++) {
             msc_iter_record r{};
-            r.kind = kind;
-            r.n_targets = (int64_t)hc.nT;
-            r.n_exact = (int64_t)hc.nX;
-            r.sum_targets = (int64_t)hc.sumT;
-            r.sum_exact = (int64_t)hc.sumX;
+            r.kind = (int32_t)rows[5 * i];
+            r.n_targets = rows[5 * i + 1];
+            r.n_exact = rows[5 * i + 2];
+            r.sum_targets = rows[5 * i + 3];
+            r.sum_exact = rows[5 * i + 4];
             R.trace.push_back(r);
         }
-        (kind ? R.n_s : R.n_c)++;
-        h->items[MSC_K_EDIT] += hc.nT + hc.nX;
-        if (hc.nX) R.n_fb++;
-        const int nxt = cur ^ 1;
-        KL(h, MSC_K_EDIT, s, k_edit<D><<<grid_for(32 * (hc.nT + hc.nX)), TPB, 0, s>>>(c));
-        KL(h, MSC_K_REFRESH, s, k_refresh<D><<<grid_for(h->G.n / 4 + 1), TPB, 0, s>>>(c));
-        CK(cudaMemsetAsync(nMc + nxt, 0, sizeof(unsigned long long), s));
-        CK(cudaMemsetAsync(nMc + 4 + nxt, 0, sizeof(unsigned long long), s));
-        KL(h, MSC_K_REBUILD, s, k_rebuild<D><<<grid_for(h->G.n / 8 + 1), TPB, 0, s>>>(c, M[cur], nMc + cur, M[nxt], nMc + nxt,
-                                                                                     C[cur], nMc + 4 + cur, C[nxt], nMc + 4 + nxt, nMc + 3));
-        KL(h, MSC_K_REBUILD, s, k_clear<<<grid_for(h->G.n / 8 + 1), TPB, 0, s>>>(c));
-        CK(cudaGetLastError());
-        cur = nxt;
     }
     return MSC_OK;
 }
@@ -1199,6 +1348,7 @@ msc_status msc_prepare_original(const float *f, int nx, int ny, int nz, const ms
         CKS(h->D == 3 ? build_seeds<3>(h, s) : build_seeds<2>(h, s));
         CK(cudaEventCreate(&h->ev0));
         CK(cudaEventCreate(&h->ev1));
+        CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
         CK(cudaStreamSynchronize(s));
         prof_flush(h);
         h->prof_on = false;
