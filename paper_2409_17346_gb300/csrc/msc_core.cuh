@@ -52,12 +52,12 @@ struct Counters {
 struct LoopState {
     int halt;                 // the current phase is over (no false case left) or an error
     int status;               // 0 running / done, 4 max_iters reached, 6 stalled
-    int cur;                  // which of the double-buffered mismatch lists is current
     int track_dirty;          // accumulate dirty anchors for the separatrix state
+    int spare;
     unsigned iters, n_c, n_s, n_fb;
     unsigned max_iters, exact_fallback, trace_cap, ntrace;
-    unsigned long long nM[2], nC[2], nSD;
-    unsigned long long edit_items;
+    unsigned long long nSD;
+    unsigned long long edit_items, refresh_items, cpass_items, cases;
 };
 
 // everything a kernel of one job needs (device pointers)
@@ -80,8 +80,10 @@ struct Ctx {
     int32_t *ns_v, *ns_top, *ns_tri, *ns_dead;
     uint32_t *sDbits, *sDlist;       // anchors dirtied since the last S-pass
     LoopState *ls;
-    uint32_t *Mb[2], *Cb[2];         // mismatch lists: code differs / critical cells differ
+    uint32_t *Mbits;                 // anchors whose code differs from f's
+    uint32_t *Cbits;                 // anchors whose critical cells differ from f's (tier restricted)
     int64_t *trace;                  // rows (kind, |T|, |X|, sum T, sum X), ls->trace_cap rows
+    unsigned long long *tally;       // when set: per-block (cases, live cases) in shared memory
 };
 
 // ------------------------------------------------------------------------------------
@@ -273,14 +275,20 @@ MSC_HD inline int lowest_of(const Verts &V, const float *vals)
 template <int D> MSC_HD inline void add_case(const Ctx &c, uint32_t t, const Verts &cell)
 {
     const Tab<D> &T = rt_tab<D>();
-    count_add(&c.cnt->ncase, 1ull);
+    const uint8_t st = c.state[t];
+    const bool live = st != ST_FLOOR && st != ST_EXACT;
+    if (c.tally) {
+        a_add(c.tally, 1ull);
+        if (live) a_add(c.tally + 1, 1ull);
+    } else {
+        count_add(&c.cnt->ncase, 1ull);
+        if (live) count_add(&c.cnt->nlive, 1ull);
+    }
     if (!test_and_set(c.Tbits, t)) {
         c.Tlist[list_slot(&c.cnt->nT)] = t;
         count_add(&c.cnt->sumT, (unsigned long long)t);
     }
-    const uint8_t st = c.state[t];
-    if (st != ST_FLOOR && st != ST_EXACT) { count_add(&c.cnt->nlive, 1ull); return; }
-    if (!c.exact_fallback) return;
+    if (live || !c.exact_fallback) return;
     for (int i = 0; i < cell.n; i++) {
         for (int n = -1; n < T.NNB; n++) {
             int xx = cell.x[i], yy = cell.y[i], zz = cell.z[i];

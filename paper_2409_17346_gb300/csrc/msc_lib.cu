@@ -135,32 +135,68 @@ __global__ void k_count_nonfinite(const float *v, uint32_t n, unsigned long long
 
 // dense gradient of a field; with ref != nullptr also list the anchors whose code differs
 // (list, nlist) and those whose critical cells differ (clist, nclist; tier restricted)
+// the anchors whose bit is set: each warp takes 32 consecutive words, compacts their set
+// bits into shared memory (ascending anchor order, warp prefix sum of popcounts) and then
+// runs f on them 32 at a time.  Needs blockDim.x == TPB.
+template <class F>
+__device__ __forceinline__ void for_each_set(const uint32_t *bits, uint32_t n, F &&f, unsigned long long *count = nullptr)
+{
+    __shared__ uint32_t q[TPB / 32][32 * 32];
+    const unsigned lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint32_t *mq = q[wib];
+    const unsigned long long nw = (n + 31) / 32;
+    const unsigned long long warp = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long nwarps = (gridDim.x * (unsigned long long)blockDim.x) >> 5;
+    for (unsigned long long w0 = warp * 32; w0 < nw; w0 += nwarps * 32) {
+        uint32_t mine = w0 + lane < nw ? bits[w0 + lane] : 0u;
+        const unsigned cnt = __popc(mine);
+        unsigned pre = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, pre, o);
+            if (lane >= (unsigned)o) pre += y;
+        }
+        const unsigned total = __shfl_sync(0xffffffffu, pre, 31);
+        if (total == 0) continue;
+        if (count && lane == 0) atomicAdd(count, (unsigned long long)total);
+        unsigned at = pre - cnt;
+        const uint32_t base = (uint32_t)((w0 + lane) * 32);
+        while (mine) {
+            const int k = __ffs(mine) - 1;
+            mine &= mine - 1;
+            mq[at++] = base + (uint32_t)k;
+        }
+        __syncwarp();
+        for (unsigned k = lane; k < total; k += 32) f(mq[k]);
+        __syncwarp();
+    }
+}
+
+// dense gradient of a field; with ref != nullptr also set the bitsets of anchors whose code
+// differs (mbits) and whose critical cells differ (cbits, tier restricted)
 template <int D>
 __global__ void __launch_bounds__(TPB) k_eval_dense(const float *v, Grid G, uint64_t *out, const uint64_t *ref,
-                                                    uint32_t *list, unsigned long long *nlist, uint32_t *clist,
-                                                    unsigned long long *nclist, int tier)
+                                                    uint32_t *mbits, uint32_t *cbits, int tier)
 {
-    if (!ref) {
-        GRID_STRIDE(p, G.n) out[p] = anchor_code<D>(v, G, (uint32_t)p);
-        return;
-    }
-    __shared__ Stage<TPB> sm, sc;
-    st_init(sm);
-    st_init(sc);
     BLOCK_ROUNDS(b, G.n)
     {
         const unsigned long long p = b + threadIdx.x;
+        bool m = false, cm = false;
         if (p < G.n) {
             const uint64_t code = anchor_code<D>(v, G, (uint32_t)p);
             out[p] = code;
-            const uint64_t r = __ldg(ref + p);
-            if (code != r) {
-                st_push(sm, (uint32_t)p, list, nlist);
-                if (crit_sig<D>(code, tier) != crit_sig<D>(r, tier)) st_push(sc, (uint32_t)p, clist, nclist);
+            if (ref) {
+                const uint64_t r = __ldg(ref + p);
+                m = code != r;
+                cm = m && crit_sig<D>(code, tier) != crit_sig<D>(r, tier);
             }
         }
-        st_flush(sm, list, nlist);
-        st_flush(sc, clist, nclist);
+        if (ref) {
+            const uint32_t wm = __ballot_sync(0xffffffffu, m), wc = __ballot_sync(0xffffffffu, cm);
+            if ((threadIdx.x & 31) == 0 && p < G.n) {
+                mbits[p >> 5] = wm;
+                cbits[p >> 5] = wc;
+            }
+        }
     }
 }
 
@@ -179,13 +215,35 @@ __global__ void k_init_g(const float *f, const float *fh, float *g, uint8_t *sta
 // back to back (a captured graph of several rounds) and the host looks only at their end.
 
 // C-pass over the anchors whose critical cells differ from f's (current list)
+// case tallies kept per block in shared memory and published once
+struct BlockTally {
+    unsigned long long v[2];
+};
+
+__device__ __forceinline__ void tally_begin(BlockTally &t, Ctx &cc)
+{
+    if (threadIdx.x < 2) t.v[threadIdx.x] = 0;
+    __syncthreads();
+    cc.tally = t.v;
+}
+
+__device__ __forceinline__ void tally_end(BlockTally &t, const Ctx &c)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (t.v[0]) atomicAdd(&c.cnt->ncase, t.v[0]);
+        if (t.v[1]) atomicAdd(&c.cnt->nlive, t.v[1]);
+    }
+}
+
 template <int D> __global__ void __launch_bounds__(TPB) k_ctargets(Ctx c)
 {
     if (c.ls->halt) return;
-    const int cur = c.ls->cur;
-    const uint32_t *C = c.Cb[cur];
-    const unsigned long long n = c.ls->nC[cur];
-    GRID_STRIDE(i, n) ctargets_anchor<D>(c, C[i]);
+    __shared__ BlockTally tally;
+    Ctx cc = c;
+    tally_begin(tally, cc);
+    for_each_set(c.Cbits, c.G.n, [&](uint32_t p) { ctargets_anchor<D>(cc, p); }, &c.ls->cpass_items);
+    tally_end(tally, c);
 }
 
 // after a targeting pass (kind 0 C, 1 S): stop the phase when there is no false case, stop
@@ -196,6 +254,7 @@ __global__ void k_decide(Ctx c, int kind)
     LoopState *ls = c.ls;
     if (ls->halt) return;
     const Counters *k = c.cnt;
+    ls->cases += k->ncase;
     if (k->ncase == 0) { ls->halt = 1; return; }
     if (!ls->exact_fallback && k->nlive == 0) { ls->halt = 1; ls->status = MSC_ERR_STALLED; return; }
     if (ls->iters >= ls->max_iters) { ls->halt = 1; ls->status = MSC_ERR_NOT_CONVERGED; return; }
@@ -208,8 +267,6 @@ __global__ void k_decide(Ctx c, int kind)
     if (kind) ls->n_s++; else ls->n_c++;
     if (k->nX) ls->n_fb++;
     ls->edit_items += k->nT + k->nX;
-    ls->nM[ls->cur ^ 1] = 0;
-    ls->nC[ls->cur ^ 1] = 0;
 }
 
 constexpr int DIRTY_STAGE = 8192;
@@ -245,44 +302,30 @@ template <int D> __global__ void __launch_bounds__(TPB) k_refresh(Ctx c)
     GRID_STRIDE(i, n) refresh_anchor<D>(c, c.Dlist[i]);
 }
 
-// next mismatch lists: anchors of the current lists that were not re-evaluated keep their
-// membership; re-evaluated (dirty) anchors join by their new code.  No anchor appears twice.
+// mismatch bitsets after a round: only re-evaluated (dirty) anchors can change membership
 template <int D> __global__ void k_rebuild(Ctx c)
 {
     if (c.ls->halt) return;
-    __shared__ Stage<TPB> sm, sc, ss;
-    st_init(sm);
-    st_init(sc);
+    __shared__ Stage<TPB> ss;
     st_init(ss);
     LoopState *ls = c.ls;
-    const int cur = ls->cur, nxt = cur ^ 1;
-    const uint32_t *Mcur = c.Mb[cur], *Ccur = c.Cb[cur];
-    uint32_t *Mnext = c.Mb[nxt], *Cnext = c.Cb[nxt];
-    unsigned long long *nMnext = &ls->nM[nxt], *nCnext = &ls->nC[nxt];
-    const unsigned long long a = ls->nM[cur], b2 = ls->nC[cur], d = c.cnt->nD;
+    const unsigned long long d = c.cnt->nD;
     const int track = ls->track_dirty;
-    BLOCK_ROUNDS(b, a + b2 + d)
+    BLOCK_ROUNDS(b, d)
     {
         const unsigned long long i = b + threadIdx.x;
-        if (i < a + b2) {
-            const uint32_t p = i < a ? Mcur[i] : Ccur[i - a];
-            if (!((c.Dbits[p >> 5] >> (p & 31)) & 1u)) {
-                if (i < a) st_push(sm, p, Mnext, nMnext);
-                else st_push(sc, p, Cnext, nCnext);
-            }
-        } else if (i < a + b2 + d) {
-            const uint32_t p = c.Dlist[i - a - b2];
+        if (i < d) {
+            const uint32_t p = c.Dlist[i];
             if (track && !test_and_set(c.sDbits, p)) st_push(ss, p, c.sDlist, &ls->nSD);
             const uint64_t cf = __ldg(c.code_f + p), cg = c.code_g[p];
-            if (cf != cg) {
-                st_push(sm, p, Mnext, nMnext);
-                if (crit_sig<D>(cf, c.tier) != crit_sig<D>(cg, c.tier)) st_push(sc, p, Cnext, nCnext);
-            }
+            const bool m = cf != cg, cm = m && crit_sig<D>(cf, c.tier) != crit_sig<D>(cg, c.tier);
+            const uint32_t bit = 1u << (p & 31);
+            if (m) atomicOr(c.Mbits + (p >> 5), bit); else atomicAnd(c.Mbits + (p >> 5), ~bit);
+            if (cm) atomicOr(c.Cbits + (p >> 5), bit); else atomicAnd(c.Cbits + (p >> 5), ~bit);
         }
-        st_flush(sm, Mnext, nMnext);
-        st_flush(sc, Cnext, nCnext);
         st_flush(ss, c.sDlist, &ls->nSD);
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ls->refresh_items, d);
 }
 
 __global__ void k_clear(Ctx c)
@@ -297,11 +340,10 @@ __global__ void k_clear(Ctx c)
     }
 }
 
-// end of a round: swap the mismatch lists, zero the round's counters
+// end of a round: zero the round's counters
 __global__ void k_end(Ctx c)
 {
     if (threadIdx.x || blockIdx.x || c.ls->halt) return;
-    c.ls->cur ^= 1;
     memset(c.cnt, 0, sizeof(Counters));
 }
 
@@ -349,10 +391,13 @@ __global__ void k_tri_spill(Ctx c, const uint32_t *items, uint32_t n)
     GRID_STRIDE(i, n) tri_propagate(c, items[2 * i], 0, true, (int)items[2 * i + 1]);
 }
 
-template <int D> __global__ void k_node_targets(Ctx c, const uint32_t *M, const unsigned long long *nM)
+template <int D> __global__ void k_node_targets(Ctx c)
 {
-    const unsigned long long n = *nM;
-    GRID_STRIDE(i, n) node_targets<D>(c, M[i]);
+    __shared__ BlockTally tally;
+    Ctx cc = c;
+    tally_begin(tally, cc);
+    for_each_set(c.Mbits, c.G.n, [&](uint32_t p) { node_targets<D>(cc, p); });
+    tally_end(tally, c);
 }
 
 __global__ void k_sd_clear(Ctx c, unsigned long long *nSD)
@@ -673,7 +718,7 @@ struct msc_handle {
     DevBuf<float> fhat, g;
     DevBuf<uint8_t> state;
     DevBuf<uint64_t> code_g;
-    DevBuf<uint32_t> Tbits, Xbits, Dbits, Tlist, Xlist, Dlist, M0, M1, C0, C1;
+    DevBuf<uint32_t> Tbits, Xbits, Dbits, Tlist, Xlist, Dlist, Mbits, Cbits;
     DevBuf<uint32_t> vis_v, vis_top, vis_tri, ovf0, ovf1;
     DevBuf<int32_t> ns_v, ns_top, ns_tri, ns_dead;
     DevBuf<uint32_t> sDbits, sDlist;
@@ -681,7 +726,7 @@ struct msc_handle {
     DevBuf<LoopState> ls;
     DevBuf<int64_t> trace;
     cudaStream_t cap_stream = nullptr;   // graphs are captured on this stream
-    DevBuf<unsigned long long> nM;   // [0,1] sizes of M0, M1; [2] scratch; [3] dirty-since-S-pass; [4,5] C0, C1
+    DevBuf<unsigned long long> nM;   // scratch counters of uploads
     bool fix_ready = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // launch statistics
@@ -763,10 +808,8 @@ msc_status alloc_fix_state(msc_handle *h)
     CK(h->Tlist.alloc(n));
     CK(h->Xlist.alloc(n));
     CK(h->Dlist.alloc(n));
-    CK(h->M0.alloc(n));
-    CK(h->M1.alloc(n));
-    CK(h->C0.alloc(n));
-    CK(h->C1.alloc(n));
+    CK(h->Mbits.alloc(words(n)));
+    CK(h->Cbits.alloc(words(n)));
     CK(h->vis_v.alloc(words(n)));
     CK(h->vis_top.alloc(words(n * ntop)));
     if (h->D == 3) {
@@ -816,25 +859,25 @@ Ctx make_ctx(msc_handle *h, int tier, int qmax, int exact_fallback, float xi)
     c.ns_v = h->ns_v.p; c.ns_top = h->ns_top.p; c.ns_tri = h->ns_tri.p; c.ns_dead = h->ns_dead.p;
     c.sDbits = h->sDbits.p; c.sDlist = h->sDlist.p;
     c.ls = h->ls.p;
-    c.Mb[0] = h->M0.p; c.Mb[1] = h->M1.p;
-    c.Cb[0] = h->C0.p; c.Cb[1] = h->C1.p;
+    c.Mbits = h->Mbits.p;
+    c.Cbits = h->Cbits.p;
     c.trace = nullptr;
+    c.tally = nullptr;
     return c;
 }
 
-template <int D> msc_status eval_dense(msc_handle *h, const float *v, Grid G, uint64_t *out, const uint64_t *ref,
-                                       uint32_t *list, unsigned long long *nlist, cudaStream_t s,
-                                       uint32_t *clist = nullptr, unsigned long long *nclist = nullptr, int tier = 4)
+template <int D> msc_status eval_dense(msc_handle *h, const float *v, Grid G, uint64_t *out, cudaStream_t s,
+                                       const uint64_t *ref = nullptr, uint32_t *mbits = nullptr,
+                                       uint32_t *cbits = nullptr, int tier = 4)
 {
-    KL(h, MSC_K_DENSE, s, k_eval_dense<D><<<grid_for(G.n), TPB, 0, s>>>(v, G, out, ref, list, nlist, clist, nclist, tier));
+    KL(h, MSC_K_DENSE, s, k_eval_dense<D><<<grid_for(G.n), TPB, 0, s>>>(v, G, out, ref, mbits, cbits, tier));
     CK(cudaGetLastError());
     return MSC_OK;
 }
 
-msc_status eval_dense_any(msc_handle *h, int D, const float *v, Grid G, uint64_t *out, const uint64_t *ref,
-                          uint32_t *list, unsigned long long *nlist, cudaStream_t s)
+msc_status eval_dense_any(msc_handle *h, int D, const float *v, Grid G, uint64_t *out, cudaStream_t s)
 {
-    return D == 3 ? eval_dense<3>(h, v, G, out, ref, list, nlist, s) : eval_dense<2>(h, v, G, out, ref, list, nlist, s);
+    return D == 3 ? eval_dense<3>(h, v, G, out, s) : eval_dense<2>(h, v, G, out, s);
 }
 
 template <int D> msc_status build_seeds(msc_handle *h, cudaStream_t s)
@@ -895,8 +938,7 @@ template <int D> msc_status s_pass(msc_handle *h, const Ctx &c0, int tier, cudaS
 
 // tier-4 S-pass from the persistent separatrix state: built once per fix, then updated at
 // the anchors dirtied since the previous S-pass; troublemakers read at the mismatch anchors
-template <int D> msc_status s_pass_state(msc_handle *h, Ctx &c, bool &built, const uint32_t *M,
-                                         unsigned long long *nM, unsigned long long *nSD, cudaStream_t s)
+template <int D> msc_status s_pass_state(msc_handle *h, Ctx &c, bool &built, unsigned long long *nSD, cudaStream_t s)
 {
     c.ovf_out = D == 3 ? h->ovf0.p : nullptr;
     if (!built) {
@@ -936,7 +978,7 @@ template <int D> msc_status s_pass_state(msc_handle *h, Ctx &c, bool &built, con
     }
     KL(h, MSC_K_SEP_UPDATE, s, k_sd_clear<<<grid_for(h->G.n / 16 + 1), TPB, 0, s>>>(c, nSD));
     CK(cudaMemsetAsync(nSD, 0, sizeof(unsigned long long), s));
-    KL(h, MSC_K_SEP_TARGETS, s, k_node_targets<D><<<grid_for(h->G.n / 16 + 1), TPB, 0, s>>>(c, M, nM));
+    KL(h, MSC_K_SEP_TARGETS, s, k_node_targets<D><<<grid_for(h->G.n / 32 + 1), TPB, 0, s>>>(c));
     CK(cudaGetLastError());
     return MSC_OK;
 }
@@ -1040,7 +1082,7 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
     CK(cudaMemsetAsync(h->sDbits.p, 0, h->sDbits.n * 4, s));
     CK(cudaMemsetAsync(h->cnt.p, 0, sizeof(Counters), s));
     LoopState *ls = h->ls.p;
-    CKS(eval_dense<D>(h, h->g.p, h->G, h->code_g.p, h->code_f.p, h->M0.p, &ls->nM[0], s, h->C0.p, &ls->nC[0], o.tier));
+    CKS(eval_dense<D>(h, h->g.p, h->G, h->code_g.p, s, h->code_f.p, h->Mbits.p, h->Cbits.p, o.tier));
     h->items[MSC_K_DENSE] += h->G.n;
     RoundGraph rg;
     CKS(build_round_graph<D>(h, c, o.profile != 0, rg));
@@ -1059,7 +1101,7 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
         if (o.tier < 3) break;
         // S-pass (Sec. 4.4) on the current lists
         CK(cudaMemsetAsync(h->cnt.p, 0, sizeof(Counters), s));
-        if (o.tier >= 4) CKS(s_pass_state<D>(h, c, sep_built, c.Mb[L.cur], &ls->nM[L.cur], &ls->nSD, s));
+        if (o.tier >= 4) CKS(s_pass_state<D>(h, c, sep_built, &ls->nSD, s));
         else CKS(s_pass<D>(h, c, o.tier, s));
         Counters hc;
         CK(cudaMemcpyAsync(&hc, h->cnt.p, sizeof hc, cudaMemcpyDeviceToHost, s));
@@ -1087,6 +1129,9 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
     R.n_s = L.n_s;
     R.n_fb = L.n_fb;
     h->items[MSC_K_EDIT] += L.edit_items;
+    h->items[MSC_K_REFRESH] += L.refresh_items;
+    h->items[MSC_K_CPASS] += L.cpass_items;
+    h->items[MSC_K_REBUILD] += L.cases;   // false cases found (reported under rebuild)
     if (o.record_trace && L.ntrace) {
         const unsigned nt = std::min(L.ntrace, L.trace_cap);
         std::vector<int64_t> rows(5ull * nt);
@@ -1145,7 +1190,7 @@ template <int D> msc_status verify_impl(msc_handle *h, const float *gdev, float 
 {
     DevBuf<uint64_t> code;
     CK(code.alloc(h->G.n));
-    CKS(eval_dense<D>(h, gdev, h->G, code.p, nullptr, nullptr, nullptr, s));
+    CKS(eval_dense<D>(h, gdev, h->G, code.p, s));
     CK(cudaMemsetAsync(h->cnt.p, 0, sizeof(Counters), s));
     KL(h, MSC_K_OTHER, s, k_decode_crit<D><<<grid_for(h->G.n), TPB, 0, s>>>(code.p, h->code_f.p, h->G, nullptr, nullptr, nullptr, 0, h->cnt.p));
     KL(h, MSC_K_OTHER, s, k_max_abs_err<<<grid_for(h->G.n), TPB, 0, s>>>(h->f.p, gdev, h->G.n, &h->cnt.p->rep[13]));
@@ -1252,7 +1297,7 @@ msc_status introspect(const float *field, Grid G, int what, int64_t *rows, int32
     CK(code.alloc(G.n));
     CK(cnt.alloc(2));
     CKS(upload_field(nullptr, field, G.n, v.p, cnt.p, s, "field"));
-    CKS(eval_dense<D>(nullptr, v.p, G, code.p, nullptr, nullptr, nullptr, s));
+    CKS(eval_dense<D>(nullptr, v.p, G, code.p, s));
     CK(cudaMemsetAsync(cnt.p, 0, 8, s));
     if (what == 0) k_decode_pairs<D><<<grid_for(G.n), TPB, 0, s>>>(code.p, G, nullptr, cnt.p, 0);
     else k_decode_crit<D><<<grid_for(G.n), TPB, 0, s>>>(code.p, nullptr, G, nullptr, nullptr, cnt.p, 0, nullptr);
@@ -1343,7 +1388,7 @@ msc_status msc_prepare_original(const float *f, int nx, int ny, int nz, const ms
         CK(h->nM.alloc(8));
         h->prof_on = o.profile != 0;
         CKS(upload_field(h, f, h->G.n, h->f.p, h->nM.p, s, "f"));
-        CKS(eval_dense_any(h, h->D, h->f.p, h->G, h->code_f.p, nullptr, nullptr, nullptr, s));
+        CKS(eval_dense_any(h, h->D, h->f.p, h->G, h->code_f.p, s));
         h->items[MSC_K_DENSE] += h->G.n;
         CKS(h->D == 3 ? build_seeds<3>(h, s) : build_seeds<2>(h, s));
         CK(cudaEventCreate(&h->ev0));
