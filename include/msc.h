@@ -196,6 +196,29 @@ msc_status msc_gradient_pairs(const float *field, int nx, int ny, int nz,
 msc_status msc_critical_cells(const float *field, int nx, int ny, int nz,
                               int64_t *rows, int32_t *dims, uint64_t cap, uint64_t *n_out);
 
+/* Largest grid (in vertices) that msc_critical_cells_static accepts. */
+#define MSC_STATIC_MAX_VERTICES (1u << 20)
+
+/* Same result as msc_critical_cells, for callers that cannot allocate device memory: for
+ * example a host application that hands this library a fixed memory budget through its
+ * own allocator, or a code path that must not call cudaMalloc/cudaFree because those
+ * calls can synchronize the device.  The paper has no counterpart to this entry point.
+ *  - field (nx*ny*nz floats), rows (cap x 4 int64) and dims (cap int32) are DEVICE
+ *    pointers on the current device, allocated and owned by the caller; host pointers are
+ *    rejected with MSC_ERR_INVALID_ARG.  *n_out (host memory) receives the number of
+ *    critical cells; at most cap rows are written, in no particular order.
+ *  - Scratch space is a fixed static device array of MSC_STATIC_MAX_VERTICES 8-byte words
+ *    plus a few counters (about 8 MiB), which every GPU that loads the library keeps until
+ *    the process exits.  Grids larger than MSC_STATIC_MAX_VERTICES vertices are rejected
+ *    with MSC_ERR_INVALID_ARG.  No device memory is allocated or freed by this call.
+ *  - The first call on a device looks up the device address of that array; make that first
+ *    call before any stream capture.
+ *  - All calls share the one array (its counters are cleared at the start of each call):
+ *    calls whose device work overlaps (other threads or streams) race and give wrong
+ *    results.  stream: a cudaStream_t (NULL = the legacy default stream). */
+msc_status msc_critical_cells_static(const float *field, int nx, int ny, int nz, int64_t *rows, int32_t *dims,
+                                     uint64_t cap, uint64_t *n_out, void *stream);
+
 /* Launch statistics accumulated on a handle since its creation or the last reset. */
 msc_status msc_get_stats(msc_handle *h, msc_stats *out);
 msc_status msc_reset_stats(msc_handle *h);

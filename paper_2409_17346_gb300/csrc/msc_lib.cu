@@ -1324,6 +1324,59 @@ msc_status introspect(const float *field, Grid G, int what, int64_t *rows, int32
 }  // namespace
 
 // ------------------------------------------------------------------------------------
+// fixed scratch of msc_critical_cells_static: gradient codes of up to
+// MSC_STATIC_MAX_VERTICES anchors, then [0] the row count, [1] the non-finite count
+// ------------------------------------------------------------------------------------
+namespace {
+constexpr size_t STATIC_WORDS = (size_t)MSC_STATIC_MAX_VERTICES + 32;
+}
+static __device__ __align__(256) unsigned long long g_static_scratch[STATIC_WORDS];
+
+namespace {
+std::mutex g_static_mu;
+void *g_static_addr[256] = {};
+
+// device address of the static scratch on the current device (looked up once per device)
+msc_status static_scratch(unsigned long long **out)
+{
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return fail(MSC_ERR_NO_DEVICE, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(MSC_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
+        g_static_addr[dev] = p;
+    }
+    *out = (unsigned long long *)g_static_addr[dev];
+    return MSC_OK;
+}
+
+template <int D>
+msc_status critical_static(const float *field, Grid G, int64_t *rows, int32_t *dims, uint64_t cap, uint64_t *n_out,
+                           cudaStream_t s)
+{
+    unsigned long long *scr;
+    CKS(static_scratch(&scr));
+    uint64_t *code = (uint64_t *)scr;
+    unsigned long long *count = scr + MSC_STATIC_MAX_VERTICES, *bad = count + 1;
+    CK(cudaMemsetAsync(count, 0, 2 * sizeof(unsigned long long), s));
+    k_count_nonfinite<<<grid_for(G.n), TPB, 0, s>>>(field, G.n, bad);
+    k_eval_dense<D><<<grid_for(G.n), TPB, 0, s>>>(field, G, code, nullptr, nullptr, nullptr, 4);
+    k_decode_crit<D><<<grid_for(G.n), TPB, 0, s>>>(code, nullptr, G, cap ? rows : nullptr, dims, count, cap, nullptr);
+    CK(cudaGetLastError());
+    unsigned long long hv[2];
+    CK(cudaMemcpyAsync(hv, count, sizeof hv, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hv[1]) return fail(MSC_ERR_INVALID_ARG, "field has %llu non-finite values", hv[1]);
+    *n_out = hv[0];
+    return MSC_OK;
+}
+}  // namespace
+
+// ------------------------------------------------------------------------------------
 // C ABI
 // ------------------------------------------------------------------------------------
 extern "C" {
@@ -1519,6 +1572,26 @@ msc_status msc_fix_batch(msc_handle **hs, const float **f_hats, const float *xis
         if (st != MSC_OK) return st;
     }
     return MSC_OK;
+}
+
+msc_status msc_critical_cells_static(const float *field, int nx, int ny, int nz, int64_t *rows, int32_t *dims,
+                                     uint64_t cap, uint64_t *n_out, void *stream)
+{
+    g_last_error.clear();
+    if (!field || !n_out) return fail(MSC_ERR_INVALID_ARG, "field and n_out must be non-NULL");
+    CKS(check_dims(nx, ny, nz));
+    const unsigned long long n = (unsigned long long)nx * ny * nz;
+    if (n > MSC_STATIC_MAX_VERTICES)
+        return fail(MSC_ERR_INVALID_ARG, "grid of %llu vertices exceeds the static scratch limit of %u vertices", n,
+                    (unsigned)MSC_STATIC_MAX_VERTICES);
+    if (cap && (!rows || !dims)) return fail(MSC_ERR_INVALID_ARG, "rows and dims must be non-NULL when cap > 0");
+    CKS(device_ready());
+    if (!is_device_ptr(field) || (cap && (!is_device_ptr(rows) || !is_device_ptr(dims))))
+        return fail(MSC_ERR_INVALID_ARG, "field, rows and dims must be device pointers");
+    Grid G{nx, ny, nz, (uint32_t)n};
+    cudaStream_t s = (cudaStream_t)stream;
+    return nz > 1 ? critical_static<3>(field, G, rows, dims, cap, n_out, s)
+                  : critical_static<2>(field, G, rows, dims, cap, n_out, s);
 }
 
 msc_status msc_get_stats(msc_handle *h, msc_stats *out)

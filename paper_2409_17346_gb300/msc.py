@@ -93,12 +93,14 @@ def load():
                                   ctypes.POINTER(Options), ctypes.POINTER(Edits), ctypes.POINTER(vp)]
     lib.msc_gradient_pairs.argtypes = [vp, i, i, i, vp, u64, ctypes.POINTER(u64)]
     lib.msc_critical_cells.argtypes = [vp, i, i, i, vp, vp, u64, ctypes.POINTER(u64)]
+    lib.msc_critical_cells_static.argtypes = [vp, i, i, i, vp, vp, u64, ctypes.POINTER(u64), vp]
     lib.msc_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
     lib.msc_reset_stats.argtypes = [vp]
     lib.msc_device_bytes.argtypes = [i, i, i]
     lib.msc_device_bytes.restype = u64
     for name in ("msc_prepare_original", "msc_fix", "msc_apply_edits", "msc_verify", "msc_fix_batch",
-                 "msc_gradient_pairs", "msc_critical_cells", "msc_get_stats", "msc_reset_stats"):
+                 "msc_gradient_pairs", "msc_critical_cells", "msc_critical_cells_static", "msc_get_stats",
+                 "msc_reset_stats"):
         getattr(lib, name).restype = i
     _lib = lib
     return lib
@@ -312,6 +314,19 @@ def critical_cells(field):
         o = np.lexsort(rows.T[::-1])
         rows, dims = rows[o], dims[o]
     return rows, dims
+
+
+STATIC_MAX_VERTICES = 1 << 20
+
+
+def critical_cells_static(field_ptr, shape, rows_ptr, dims_ptr, cap, stream=None):
+    """msc_critical_cells_static on caller-owned device buffers (integer addresses):
+    field (float32, shape), rows (cap x 4 int64), dims (cap int32).  Returns the number
+    of critical cells; at most cap rows are written, unordered."""
+    nx, ny, nz = dims_of(shape)
+    n = ctypes.c_uint64(0)
+    _check(load().msc_critical_cells_static(field_ptr, nx, ny, nz, rows_ptr, dims_ptr, cap, ctypes.byref(n), stream))
+    return n.value
 
 
 def device_bytes(shape):
