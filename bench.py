@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--tier", type=int, default=4)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving replay")
     return ap.parse_args()
 
 
@@ -111,9 +112,68 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# the kernels of each class (msc_stats); the roofline names the dominant class's kernels
+CLASS_KERNELS = {
+    "dense": "k_eval_dense", "cpass": "k_ctargets", "edit": "k_edit", "refresh": "k_refresh",
+    "rebuild": "k_rebuild, k_clear", "sep_init": "k_node_init", "sep_seed": "k_node_seed, k_tri_spill",
+    "sep_update": "k_node_update, k_tri_spill, k_sd_clear", "sep_targets": "k_node_targets",
+    "other": "k_init_g, k_decide, k_end, k_seeds, checks",
+}
+
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a class's kernel
+# from an ncu capture of this workload, for the kernels as they stand (see profiles/)
+TRAFFIC = {}
+
+
+def class_bytes(cls, tot, n, steps, ndim):
+    """Algorithmic bytes moved by the launches of one kernel class over the timed steps:
+    what the method must read and write at least, with one bit per anchor for a bitset.
+    tot: summed launches and items of the class; n: vertices; steps: timed steps."""
+    items, bit = tot["items"], n / 8.0
+    if cls == "dense":
+        # per step one launch on f (read f 4 B, write code 8 B) and one on g (read g 4 B,
+        # read f's code 8 B, write code 8 B, two mismatch bits)
+        return steps * n * (12.0 + 20.0) + steps * 2 * bit
+    if cls == "cpass":
+        # scan of the critical-difference bitset, then both codes of every listed anchor
+        return tot["launches"] * bit + 16.0 * items
+    if cls == "edit":
+        # per target: its list entry 4 B, f, f_hat, g 12 B and state 1 B read; g 4 B and
+        # state 1 B written
+        return 22.0 * items
+    if cls == "refresh":
+        # per dirty anchor: list entry 4 B, its own value 4 B, its new code 8 B
+        return 16.0 * items
+    if cls == "rebuild":
+        # per dirty anchor: list entry 4 B and both codes 16 B
+        return 20.0 * items
+    if cls == "sep_init":
+        # both codes of every anchor
+        return 16.0 * items
+    if cls in ("sep_seed", "sep_update"):
+        # per node step: the node's f code 8 B and its state word read and written 8 B
+        return 16.0 * items
+    return None
+
+
+def replica_seed(rank):
+    """Each rank fixes its own field: the workload's seed (4) plus the rank."""
+    return 4 + rank
+
+
+def max_over_ranks(v, dist, device):
+    """The maximum of a per-rank float over all ranks (the job's time is its slowest rank)."""
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload(size, rel, rank):
     from paper_2409_17346_gb300 import synth
-    f, fh, xi, tier = synth.config_case(WORKLOAD, seed=4 + rank, size=size, rel=rel)
+    f, fh, xi, tier = synth.config_case(WORKLOAD, seed=replica_seed(rank), size=size, rel=rel)
     return f, fh, xi
 
 
@@ -140,6 +200,52 @@ def cpu_baseline(f, fh, rel, budget_s=12.0):
     return dict(value=4.0 * n_done / t_done / 1e9, unit="GB/s", cores=1, kind="oracle",
                 sample="%d blocks of %d^3 vertices cut from the same f / f_hat (xi as the workload), "
                        "fixed to tier 4 by the single-threaded oracle, %.1f s" % (blocks, side, t_done))
+
+
+def pct(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = (len(xs) - 1) * q / 100.0
+    lo, hi = int(k), min(int(k) + 1, len(xs) - 1)
+    return xs[lo] + (xs[hi] - xs[lo]) * (k - lo)
+
+
+def serving_leg(msc, n_req=128, slots=8):
+    """The serving workload: n_req fix requests with Poisson arrivals (mean 20/s), sizes
+    uniform over 2D {256^2, 1024^2, 2048^2} and 3D {64^3, 128^3, 256^3}, xi in {1e-3, 1e-4}
+    x range, tier 4.  Replayed twice on the request loop: with one slot (one job at a time,
+    plain) and with `slots` slots (continuous batching).  Latency = end - submission."""
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_2409_17346_gb300 import synth
+    reqs = synth.serving_requests(n=n_req)
+    with ThreadPoolExecutor(8) as ex:
+        fields = list(ex.map(synth.serving_field, reqs))
+    total_bytes = sum(4.0 * f.size for f, _, _ in fields)
+    out = {"requests": n_req, "arrivals": "Poisson, mean 20/s (seed 5)",
+           "sizes": "2D 256^2/1024^2/2048^2, 3D 64^3/128^3/256^3", "tier": 4,
+           "latency": "job end - submission at its arrival time, s"}
+    gs = {}
+    for mode, k in (("plain", 1), ("batched", slots)):
+        with msc.Server(max_jobs=k, tier=4) as srv:
+            w = srv.submit(*fields[0][:2], fields[0][2])       # warm-up job
+            srv.wait(w)
+            t0 = time.perf_counter()
+            tickets = []
+            for r, (f, fh, xi) in zip(reqs, fields):
+                d = t0 + r["t"] - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                tickets.append(srv.submit(f, fh, xi))
+            res = [srv.wait(t) for t in tickets]
+        lat = [info["t_end"] - info["t_submit"] for _, _, info in res]
+        span = max(info["t_end"] for _, _, info in res) - min(info["t_submit"] for _, _, info in res)
+        gs[mode] = [g for g, _, _ in res]
+        out[mode] = {"slots": k, "p50_s": pct(lat, 50), "p99_s": pct(lat, 99), "mean_s": sum(lat) / len(lat),
+                     "makespan_s": span, "GB/s": total_bytes / span / 1e9}
+    out["mix_identical"] = all(np.array_equal(a.view(np.uint32), b.view(np.uint32))
+                               for a, b in zip(gs["plain"], gs["batched"]))
+    return out
 
 
 def run_reference(args):
@@ -194,7 +300,7 @@ def main():
     fhd = torch.from_numpy(fh).cuda()
     gd = torch.empty_like(fd)
 
-    def step(profile=False, stats=None):
+    def step(profile=0, stats=None):
         h = msc.Handle(fd, opts=msc.options(stream=sp, profile=profile))
         _, ed = h.fix(fhd, xi, g_out=gd, tier=args.tier, stream=sp, profile=profile)
         if stats is not None:
@@ -209,6 +315,13 @@ def main():
     h = msc.Handle(fd)
     rep = h.verify(gd, xi)
     h.close()
+    # one extra untimed step with every kernel class timed: the per-class breakdown and the
+    # choice of the dominant class, whose launches alone are then timed in the timed steps
+    brk = []
+    step(profile=True, stats=brk)
+    torch.cuda.synchronize()
+    bst = brk[0][0]
+    dom = max(msc.KERNEL_CLASSES, key=lambda k: bst[k]["ms"])
 
     stats = []
     barrier()
@@ -218,38 +331,27 @@ def main():
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.steps):
-            ed = step(profile=True, stats=stats)
+            ed = step(profile=dom, stats=stats)
         e1.record(stream)
         torch.cuda.synchronize()
     barrier()
     ms_step = e0.elapsed_time(e1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(ms_step, dist, "cuda")
     clocks = clk.summary()
 
-    # per-class device time over the timed steps; the dominant class sets the roofline
-    cls_ms = {k: sum(s[k]["ms"] for s, _ in stats) for k in msc.KERNEL_CLASSES}
-    cls_launch = {k: sum(s[k]["timed"] for s, _ in stats) for k in msc.KERNEL_CLASSES}
-    cls_items = {k: sum(s[k]["items"] for s, _ in stats) for k in msc.KERNEL_CLASSES}
     launches = sum(s[k]["launches"] for s, _ in stats for k in msc.KERNEL_CLASSES)
-    dom = max(cls_ms, key=cls_ms.get)
+    tot = {key: sum(s[dom][key] for s, _ in stats) for key in ("ms", "timed", "items", "launches")}
     peak, peak_kind = peaks()
-    roof = None
-    if dom == "dense" and cls_launch["dense"]:
-        # algorithmic bytes of one dense launch: read the field once (4 B) and write one
-        # 8-byte gradient code per vertex
-        per_launch = 12.0 * n
-        avg_s = cls_ms["dense"] / cls_launch["dense"] / 1e3
-        ach = per_launch / avg_s / 1e9
-        roof = {"bound": "hbm", "kernel": "k_eval_dense (dense discrete gradient)", "achieved": ach, "peak": peak,
-                "unit": "GB/s", "frac": ach / peak, "traffic": None, "peak_source": peak_kind,
-                "algorithmic_bytes_per_launch": per_launch, "avg_launch_ms": avg_s * 1e3}
-    else:
-        roof = {"bound": "hbm", "kernel": dom, "achieved": None, "peak": peak, "unit": "GB/s", "frac": None,
-                "traffic": None, "peak_source": peak_kind}
-
+    bytes_dom = class_bytes(dom, tot, n, args.steps, f.ndim)
+    roof = {"bound": "hbm", "kernel": "%s (%s)" % (dom, CLASS_KERNELS[dom]), "achieved": None, "peak": peak,
+            "unit": "GB/s", "frac": None, "traffic": None, "peak_source": peak_kind}
+    if bytes_dom is not None and tot["timed"]:
+        avg_ms = tot["ms"] / tot["timed"]
+        per_launch = bytes_dom / tot["launches"]
+        ach = per_launch / (avg_ms / 1e3) / 1e9
+        roof.update(achieved=ach, frac=ach / peak, algorithmic_bytes_per_launch=per_launch,
+                    avg_launch_ms=avg_ms, launches_per_step=tot["launches"] / args.steps,
+                    traffic=TRAFFIC.get(dom))
     value = world * 4.0 * n / (ms_step / 1e3) / 1e9
     iters = (ed["n_iters_c"], ed["n_iters_s"])
 
@@ -267,10 +369,7 @@ def main():
             h.close()
             t_e2e.append(time.perf_counter() - t0)
         te = statistics.median(t_e2e)
-        if dist is not None:
-            t = torch.tensor([te], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
+        te = max_over_ranks(te, dist, "cuda")
         d2h = 4 * n + n + 12 * ed2["n_lossless"]
         e2e = {"value": world * 4.0 * n / te / 1e9, "unit": "GB/s", "h2d_bytes_per_step": 8 * n,
                "d2h_bytes_per_step": d2h}
@@ -286,14 +385,19 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs (%d MB each) exceed L2; no flush" % (4 * n >> 20),
                        "verify_passed": rep["passed"],
-                       "kernel_ms_per_step": {k: v / args.steps for k, v in cls_ms.items()},
-                       "kernel_launches_per_step": {k: v / args.steps for k, v in cls_launch.items()},
-                       "kernel_items_per_step": {k: v / args.steps for k, v in cls_items.items()},
+                       "breakdown": "one extra untimed step with every kernel class timed by CUDA events",
+                       "kernel_ms_per_step": {k: bst[k]["ms"] for k in msc.KERNEL_CLASSES},
+                       "kernel_launches_per_step": {k: bst[k]["launches"] for k in msc.KERNEL_CLASSES},
+                       "kernel_items_per_step": {k: bst[k]["items"] for k in msc.KERNEL_CLASSES},
                        "launches_per_step": launches / args.steps},
             "roofline": roof, "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
         }
         if not args.no_cpu and world == 1:
             line["cpu_baseline"] = cpu_baseline(f, fh, args.rel)
+        if not args.no_serve and world == 1:
+            del fd, fhd, gd
+            torch.cuda.empty_cache()
+            line["serving"] = serving_leg(msc)
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()

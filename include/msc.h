@@ -61,8 +61,10 @@ typedef struct {
     int tile_x, tile_y, tile_z;   /* dense-stencil tile; 0 = built-in default */
     void *stream;        /* cudaStream_t for all device work of the call (NULL = default) */
     int record_trace;    /* 1: fill msc_edits.trace with one record per edit round */
-    int profile;         /* 1: time every kernel launch of the call with CUDA events on the
-                            call's stream and accumulate into the handle's msc_stats */
+    int profile;         /* bitmask of kernel classes (bit k = class k below; MSC_PROFILE_ALL =
+                            every class): the launches of those classes are timed with CUDA
+                            events on the call's stream and summed into the handle's msc_stats.
+                            0 (default) times nothing. */
 } msc_options;
 
 /* kernel classes of msc_stats */
@@ -76,17 +78,21 @@ enum {
     MSC_K_SEP_UPDATE = 6,/* separatrix state: updates around edits; full walks (tier 3) */
     MSC_K_SEP_TARGETS = 7,/* troublemakers from the separatrix state */
     MSC_K_OTHER = 8,     /* initialisation, seeds, output encoding, checks */
-    MSC_K_COUNT = 9
+    MSC_K_SEP_SEED = 9,  /* separatrix state: propagation from the seeds in the first build */
+    MSC_K_COUNT = 10
 };
+#define MSC_PROFILE_ALL ((1 << MSC_K_COUNT) - 1)
 
-/* per-handle launch statistics (msc_get_stats); times only with options.profile = 1 */
+/* per-handle launch statistics (msc_get_stats); times only for the classes in options.profile */
 typedef struct {
     uint64_t launches[12];       /* kernel launches by class, always counted */
     double ms[12];               /* summed CUDA-event duration by class (profiled calls) */
     uint64_t timed_launches[12]; /* launches that were timed */
     uint64_t items[12];          /* work items processed by class: anchors (dense, separatrix
-                                    init), edited vertices (edit), separatrix node updates
-                                    (separatrix update), mismatch anchors (separatrix targets) */
+                                    init), anchors with differing critical cells (cpass),
+                                    targeted vertices (edit), refreshed anchors (refresh),
+                                    dirty anchors (rebuild), node steps (separatrix seed and
+                                    update) */
 } msc_stats;
 
 /* one edit round: kind 0 = C-pass (false critical cells), 1 = S-pass (separatrices);
@@ -179,8 +185,11 @@ void msc_destroy(msc_handle *h);
 
 /* Batched fix (Sec. 5, time-series study): n independent jobs, job i on handle hs[i] with
  * decompressed field f_hats[i], bound xis[i], outputs outs[i] and g_outs[i] (same rules
- * as msc_fix).  The jobs share the device; their results equal n separate msc_fix calls.
- * Returns the first non-OK status, MSC_OK otherwise. */
+ * as msc_fix).  Up to 8 jobs run at once, each on its own stream driven by its own host
+ * thread, so their rounds overlap on the device; the jobs start after the work already
+ * queued on opt->stream and are all finished when the call returns.  Each job's results
+ * equal those of a separate msc_fix call.  The handles must be distinct.  Returns
+ * MSC_OK, or the status of the lowest-numbered failing job (the other jobs still run). */
 msc_status msc_fix_batch(msc_handle **hs, const float **f_hats, const float *xis, int n,
                          const msc_options *opt, msc_edits *outs, float **g_outs);
 
@@ -225,6 +234,63 @@ msc_status msc_reset_stats(msc_handle *h);
 
 /* Bytes of device memory a handle of this grid holds while fixing (for admission). */
 uint64_t msc_device_bytes(int nx, int ny, int nz);
+
+/* ---------------------------------------------------------------------------------------
+ * Serving: a request loop with continuous batching.  The paper runs one field at a time;
+ * this runtime admits fix jobs as they arrive and runs several at once on one GPU.
+ *  - A job holds msc_device_bytes of its grid from admission to completion.  A queued job
+ *    is admitted, first fit in arrival order, as soon as one of max_jobs slots is free and
+ *    its bytes fit in what mem_budget has left.  A job that keeps being passed over by
+ *    smaller ones (max_skips times) blocks admission until it fits.
+ *  - Each slot is a host thread with its own non-blocking stream: it prepares the job's
+ *    original (gradient of f, separatrix seeds), runs the whole fix loop with the job's
+ *    state resident on the device, copies g out and frees the job's memory.  Slots run
+ *    concurrently, so the rounds of different jobs overlap on the device.
+ *  - Device memory comes from the device's default stream-ordered memory pool; the server
+ *    sets that pool's release threshold to mem_budget, so freed job memory stays cached
+ *    for the next job instead of going back to the driver.
+ *  - A job's result equals that of msc_prepare_original + msc_fix on the same inputs.
+ * --------------------------------------------------------------------------------------- */
+typedef struct msc_server msc_server;
+
+typedef struct {
+    int max_jobs;          /* jobs on the device at once (slots), 1..64 */
+    int max_skips;         /* admissions that may pass a waiting job before it blocks the
+                              queue (0 = 16) */
+    uint64_t mem_budget;   /* device bytes the admitted jobs may hold together; 0 = 90% of
+                              the free device memory at creation */
+    msc_options options;   /* tier, q_max, max_iters, exact_fallback, profile for every job;
+                              stream is ignored (each slot has its own) */
+} msc_server_config;
+
+typedef struct {
+    int32_t status;        /* msc_status of the job */
+    int32_t slot;          /* slot that ran it */
+    uint64_t bytes;        /* device bytes reserved at admission */
+    double t_submit, t_start, t_end;   /* seconds since the server was created (steady clock) */
+    float loop_ms;         /* device time of the fix loop */
+    uint32_t reserved;
+} msc_job_info;
+
+/* Create a server on the current device.  cfg: NULL for defaults (8 slots, 90% of free
+ * memory, default options).  Errors: MSC_ERR_INVALID_ARG for bad settings. */
+msc_status msc_server_create(const msc_server_config *cfg, msc_server **out);
+
+/* Queue one job and return at once with its ticket.  f, f_hat (nx*ny*nz floats, host or
+ * device) and g_out (same size, host or device) stay owned by the caller and must remain
+ * valid until msc_server_wait returns for this ticket.  Errors: MSC_ERR_INVALID_ARG (dims,
+ * xi), MSC_ERR_OOM when the job alone exceeds mem_budget. */
+msc_status msc_server_submit(msc_server *srv, const float *f, const float *f_hat, int nx, int ny, int nz, float xi,
+                             float *g_out, uint64_t *ticket);
+
+/* Block until the job ends, then release it from the server.  *out receives its edits
+ * (free with msc_free_edits; NULL to discard) and *info its record (may be NULL).
+ * Returns the job's status; MSC_ERR_INVALID_ARG for an unknown ticket. */
+msc_status msc_server_wait(msc_server *srv, uint64_t ticket, msc_edits *out, msc_job_info *info);
+
+/* Finish the running jobs, cancel the queued ones and free the server.  No other call on
+ * this server (submit, wait) may run concurrently with or after this one. */
+void msc_server_destroy(msc_server *srv);
 
 #ifdef __cplusplus
 }

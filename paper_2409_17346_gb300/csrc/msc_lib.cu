@@ -27,6 +27,7 @@
 
 #include "../../include/msc.h"
 #include "msc_core.cuh"
+#include "msc_runtime.h"
 
 using namespace msc;
 
@@ -44,6 +45,16 @@ msc_status fail(msc_status s, const char *fmt, ...)
     g_last_error = buf;
     return s;
 }
+
+}  // namespace
+
+msc_status msc_rt::set_error(msc_status s, const std::string &msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+namespace {
 
 #define CK(call)                                                                              \
     do {                                                                                      \
@@ -67,13 +78,12 @@ constexpr int TPB = 256;
 
 int grid_for(unsigned long long n)
 {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
+    static const int sms = [] {
+        int dev = 0, v = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 132;
-    }
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        return v > 0 ? v : 152;
+    }();
     unsigned long long b = (n + TPB - 1) / TPB;
     unsigned long long cap = (unsigned long long)sms * 8;
     if (b > cap) b = cap;
@@ -599,6 +609,33 @@ __global__ void k_apply_lossless(const uint64_t *idx, const float *val, uint64_t
 // ------------------------------------------------------------------------------------
 // host helpers
 // ------------------------------------------------------------------------------------
+// Device buffers come from the stream-ordered allocator (the device's default memory pool),
+// ordered on the stream of the entry point that is running on this thread.  Unlike
+// cudaMalloc/cudaFree, allocating or freeing then never waits for work that other jobs
+// have queued on other streams.  Every entry point synchronizes its stream before it
+// returns, so a buffer allocated in one call is ready for any stream in a later call.
+thread_local cudaStream_t g_alloc_stream = nullptr;
+
+struct AllocOn {
+    cudaStream_t prev;
+    explicit AllocOn(cudaStream_t s) : prev(g_alloc_stream) { g_alloc_stream = s; }
+    ~AllocOn() { g_alloc_stream = prev; }
+};
+
+// The stream of an entry point: orders its allocations, and is synchronized when the entry
+// point returns, on success and on every error path alike.  Declared before the entry
+// point's buffers, so that their stream-ordered frees are queued before that final wait.
+struct EntryStream {
+    AllocOn on;
+    cudaStream_t s;
+    explicit EntryStream(cudaStream_t st) : on(st), s(st) {}
+    ~EntryStream()
+    {
+        cudaStreamSynchronize(s);
+        cudaGetLastError();
+    }
+};
+
 template <class T> struct DevBuf {
     T *p = nullptr;
     size_t n = 0;
@@ -610,14 +647,14 @@ template <class T> struct DevBuf {
     {
         if (count <= n && p) return cudaSuccess;
         release();
-        cudaError_t e = cudaMalloc((void **)&p, (count ? count : 1) * sizeof(T));
+        cudaError_t e = cudaMallocAsync((void **)&p, (count ? count : 1) * sizeof(T), g_alloc_stream);
         if (e == cudaSuccess) n = count;
         else p = nullptr;
         return e;
     }
     void release()
     {
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, g_alloc_stream);
         p = nullptr;
         n = 0;
     }
@@ -730,7 +767,8 @@ struct msc_handle {
     bool fix_ready = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // launch statistics
-    bool prof_on = false;
+    unsigned prof_mask = 0;   // kernel classes timed in the current call
+    bool last_timed = false;  // the launch opened by kbeg is being timed
     unsigned long long launches[12] = {};
     unsigned long long timed[12] = {};
     unsigned long long items[12] = {};
@@ -763,7 +801,8 @@ void kbeg(msc_handle *h, int cls, cudaStream_t s)
 {
     if (!h) return;
     h->launches[cls]++;
-    if (!h->prof_on) return;
+    h->last_timed = (h->prof_mask >> cls) & 1u;
+    if (!h->last_timed) return;
     msc_handle::Pend p{take_event(h), take_event(h), cls};
     cudaEventRecord(p.a, s);
     h->pend.push_back(p);
@@ -771,8 +810,9 @@ void kbeg(msc_handle *h, int cls, cudaStream_t s)
 
 void kend(msc_handle *h, cudaStream_t s)
 {
-    if (!h || !h->prof_on || h->pend.empty()) return;
+    if (!h || !h->last_timed || h->pend.empty()) return;
     cudaEventRecord(h->pend.back().b, s);
+    h->last_timed = false;
 }
 
 // resolve the timed launches of a finished call
@@ -825,13 +865,13 @@ msc_status alloc_fix_state(msc_handle *h)
     }
     CK(h->sDbits.alloc(words(n)));
     CK(h->sDlist.alloc(n));
-    CK(cudaMemset(h->sDbits.p, 0, h->sDbits.n * 4));
+    CK(cudaMemsetAsync(h->sDbits.p, 0, h->sDbits.n * 4, g_alloc_stream));
     CK(h->cnt.alloc(1));
     CK(h->nM.alloc(8));
     CK(h->ls.alloc(1));
-    CK(cudaMemset(h->Tbits.p, 0, h->Tbits.n * 4));
-    CK(cudaMemset(h->Xbits.p, 0, h->Xbits.n * 4));
-    CK(cudaMemset(h->Dbits.p, 0, h->Dbits.n * 4));
+    CK(cudaMemsetAsync(h->Tbits.p, 0, h->Tbits.n * 4, g_alloc_stream));
+    CK(cudaMemsetAsync(h->Xbits.p, 0, h->Xbits.n * 4, g_alloc_stream));
+    CK(cudaMemsetAsync(h->Dbits.p, 0, h->Dbits.n * 4, g_alloc_stream));
     h->fix_ready = true;
     return MSC_OK;
 }
@@ -941,6 +981,7 @@ template <int D> msc_status s_pass(msc_handle *h, const Ctx &c0, int tier, cudaS
 template <int D> msc_status s_pass_state(msc_handle *h, Ctx &c, bool &built, unsigned long long *nSD, cudaStream_t s)
 {
     c.ovf_out = D == 3 ? h->ovf0.p : nullptr;
+    const int spill_cls = built ? MSC_K_SEP_UPDATE : MSC_K_SEP_SEED;
     if (!built) {
         CK(cudaMemsetAsync(h->ns_v.p, 0, h->ns_v.n * 4, s));
         CK(cudaMemsetAsync(h->ns_top.p, 0, h->ns_top.n * 4, s));
@@ -949,9 +990,9 @@ template <int D> msc_status s_pass_state(msc_handle *h, Ctx &c, bool &built, uns
             CK(cudaMemsetAsync(h->ns_dead.p, 0, h->ns_dead.n * 4, s));
         }
         KL(h, MSC_K_SEP_INIT, s, k_node_init<D><<<grid_for(h->G.n), TPB, 0, s>>>(c));
-        if (h->n_desc) KL(h, MSC_K_SEP_INIT, s, k_node_seed<D><<<grid_for(h->n_desc), TPB, 0, s>>>(c, 0, h->seeds_desc.p, h->n_desc));
-        if (h->n_asc) KL(h, MSC_K_SEP_INIT, s, k_node_seed<D><<<grid_for(h->n_asc), TPB, 0, s>>>(c, 1, h->seeds_asc.p, h->n_asc));
-        if (D == 3 && h->n_ss) KL(h, MSC_K_SEP_INIT, s, k_node_seed<D><<<grid_for(h->n_ss), TPB, 0, s>>>(c, 2, h->seeds_ss.p, h->n_ss));
+        if (h->n_desc) KL(h, MSC_K_SEP_SEED, s, k_node_seed<D><<<grid_for(h->n_desc), TPB, 0, s>>>(c, 0, h->seeds_desc.p, h->n_desc));
+        if (h->n_asc) KL(h, MSC_K_SEP_SEED, s, k_node_seed<D><<<grid_for(h->n_asc), TPB, 0, s>>>(c, 1, h->seeds_asc.p, h->n_asc));
+        if (D == 3 && h->n_ss) KL(h, MSC_K_SEP_SEED, s, k_node_seed<D><<<grid_for(h->n_ss), TPB, 0, s>>>(c, 2, h->seeds_ss.p, h->n_ss));
         CK(cudaGetLastError());
         h->items[MSC_K_SEP_INIT] += h->G.n;
         built = true;
@@ -971,7 +1012,7 @@ template <int D> msc_status s_pass_state(msc_handle *h, Ctx &c, bool &built, uns
             const unsigned long long zero = 0;
             CK(cudaMemcpyAsync(&h->cnt.p->novf, &zero, sizeof zero, cudaMemcpyHostToDevice, s));
             c.ovf_out = out;
-            KL(h, MSC_K_SEP_UPDATE, s, k_tri_spill<<<grid_for(hc.novf), TPB, 0, s>>>(c, in, (uint32_t)hc.novf));
+            KL(h, spill_cls, s, k_tri_spill<<<grid_for(hc.novf), TPB, 0, s>>>(c, in, (uint32_t)hc.novf));
             CK(cudaGetLastError());
             std::swap(in, out);
         }
@@ -989,6 +1030,7 @@ struct FixResult {
 };
 
 constexpr int GRAPH_ROUNDS = 16;   // C-pass rounds queued per graph launch
+constexpr int BATCH_STREAMS = 8;   // jobs of a batch that run at once, one stream each
 
 // A captured graph of GRAPH_ROUNDS C-pass rounds.  With profiling, every kernel node sits
 // between two event-record nodes; a node pair is counted only if its round ran.
@@ -1006,13 +1048,13 @@ struct RoundGraph {
     }
 };
 
-template <int D> msc_status build_round_graph(msc_handle *h, const Ctx &c, bool profile, RoundGraph &rg)
+template <int D> msc_status build_round_graph(msc_handle *h, const Ctx &c, unsigned prof_mask, RoundGraph &rg)
 {
     cudaStream_t cs = h->cap_stream;
     cudaGraph_t graph = nullptr;
     CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     auto node = [&](int cls, int round, int pre, auto &&launch) {
-        if (!profile) { launch(); return; }
+        if (!((prof_mask >> cls) & 1u)) { launch(); return; }
         RoundGraph::Pair p{nullptr, nullptr, cls, round, pre};
         cudaEventCreate(&p.a);
         cudaEventCreate(&p.b);
@@ -1085,7 +1127,7 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
     CKS(eval_dense<D>(h, h->g.p, h->G, h->code_g.p, s, h->code_f.p, h->Mbits.p, h->Cbits.p, o.tier));
     h->items[MSC_K_DENSE] += h->G.n;
     RoundGraph rg;
-    CKS(build_round_graph<D>(h, c, o.profile != 0, rg));
+    CKS(build_round_graph<D>(h, c, (unsigned)o.profile & MSC_PROFILE_ALL, rg));
     bool sep_built = false;
     unsigned prev_iters = 0;
     for (;;) {
@@ -1101,12 +1143,13 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
         if (o.tier < 3) break;
         // S-pass (Sec. 4.4) on the current lists
         CK(cudaMemsetAsync(h->cnt.p, 0, sizeof(Counters), s));
+        const bool first_build = o.tier >= 4 && !sep_built;
         if (o.tier >= 4) CKS(s_pass_state<D>(h, c, sep_built, &ls->nSD, s));
         else CKS(s_pass<D>(h, c, o.tier, s));
         Counters hc;
         CK(cudaMemcpyAsync(&hc, h->cnt.p, sizeof hc, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        h->items[MSC_K_SEP_UPDATE] += hc.steps[0] + hc.steps[1] + hc.steps[2];
+        h->items[first_build ? MSC_K_SEP_SEED : MSC_K_SEP_UPDATE] += hc.steps[0] + hc.steps[1] + hc.steps[2];
         if (hc.err) return fail(MSC_ERR_OOM, "separatrix spill queue overflow");
         if (hc.ncase == 0) break;
         // the S-pass edit round, then back to C-pass rounds
@@ -1131,11 +1174,12 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
     h->items[MSC_K_EDIT] += L.edit_items;
     h->items[MSC_K_REFRESH] += L.refresh_items;
     h->items[MSC_K_CPASS] += L.cpass_items;
-    h->items[MSC_K_REBUILD] += L.cases;   // false cases found (reported under rebuild)
+    h->items[MSC_K_REBUILD] += L.refresh_items;
     if (o.record_trace && L.ntrace) {
         const unsigned nt = std::min(L.ntrace, L.trace_cap);
         std::vector<int64_t> rows(5ull * nt);
-        CK(cudaMemcpy(rows.data(), h->trace.p, rows.size() * sizeof(int64_t), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpyAsync(rows.data(), h->trace.p, rows.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
         for (unsigned i = 0; i < nt; i++) {
             msc_iter_record r{};
             r.kind = (int32_t)rows[5 * i];
@@ -1429,6 +1473,7 @@ msc_status msc_prepare_original(const float *f, int nx, int ny, int nz, const ms
     CKS(check_options(&o));
     CKS(device_ready());
     cudaStream_t s = (cudaStream_t)o.stream;
+    EntryStream es(s);
     msc_handle *h = new (std::nothrow) msc_handle();
     if (!h) return fail(MSC_ERR_OOM, "handle allocation failed");
     h->G.nx = nx; h->G.ny = ny; h->G.nz = nz;
@@ -1439,7 +1484,7 @@ msc_status msc_prepare_original(const float *f, int nx, int ny, int nz, const ms
         CK(h->code_f.alloc(h->G.n));
         CK(h->cnt.alloc(1));
         CK(h->nM.alloc(8));
-        h->prof_on = o.profile != 0;
+        h->prof_mask = (unsigned)o.profile & MSC_PROFILE_ALL;
         CKS(upload_field(h, f, h->G.n, h->f.p, h->nM.p, s, "f"));
         CKS(eval_dense_any(h, h->D, h->f.p, h->G, h->code_f.p, s));
         h->items[MSC_K_DENSE] += h->G.n;
@@ -1449,7 +1494,7 @@ msc_status msc_prepare_original(const float *f, int nx, int ny, int nz, const ms
         CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
         CK(cudaStreamSynchronize(s));
         prof_flush(h);
-        h->prof_on = false;
+        h->prof_mask = 0;
         return MSC_OK;
     };
     msc_status st = run();
@@ -1468,11 +1513,12 @@ msc_status msc_fix(msc_handle *h, const float *f_hat, float xi, const msc_option
     CKS(check_options(&o));
     if (!(xi > 0.0f) || !std::isfinite(xi)) return fail(MSC_ERR_INVALID_ARG, "xi must be finite and > 0");
     cudaStream_t s = (cudaStream_t)o.stream;
+    EntryStream es(s);
     CKS(alloc_fix_state(h));
-    h->prof_on = o.profile != 0;
+    h->prof_mask = (unsigned)o.profile & MSC_PROFILE_ALL;
     struct Flush {
         msc_handle *h;
-        ~Flush() { prof_flush(h); h->prof_on = false; }
+        ~Flush() { prof_flush(h); h->prof_mask = 0; }
     } flush_at_exit{h};
     CKS(upload_field(h, f_hat, h->G.n, h->fhat.p, h->nM.p + 2, s, "f_hat"));
     FixResult R;
@@ -1507,6 +1553,7 @@ msc_status msc_apply_edits(const float *f_hat, int nx, int ny, int nz, float xi,
     const uint32_t n = (uint32_t)((uint64_t)nx * ny * nz);
     if (e->n_vertices != n) return fail(MSC_ERR_INVALID_ARG, "edits are for %llu vertices, grid has %u", (unsigned long long)e->n_vertices, n);
     cudaStream_t s = nullptr;
+    EntryStream es(s);
     DevInput fh;
     CKS(device_input(f_hat, n, fh, s, "f_hat"));
     DevBuf<uint8_t> qm;
@@ -1534,8 +1581,9 @@ msc_status msc_verify(msc_handle *h, const float *g, float xi, msc_report *out)
     g_last_error.clear();
     if (!h || !g || !out) return fail(MSC_ERR_INVALID_ARG, "handle, g and out must be non-NULL");
     if (!(xi > 0.0f)) return fail(MSC_ERR_INVALID_ARG, "xi must be > 0");
-    CKS(alloc_fix_state(h));
     cudaStream_t s = nullptr;
+    EntryStream es(s);
+    CKS(alloc_fix_state(h));
     DevBuf<float> gd;
     CK(gd.alloc(h->G.n));
     CKS(upload_field(h, g, h->G.n, gd.p, h->nM.p + 2, s, "g"));
@@ -1559,6 +1607,7 @@ void msc_destroy(msc_handle *h)
     if (!h) return;
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
+    EntryStream es(nullptr);
     delete h;   // DevBuf members free their device memory
 }
 
@@ -1568,9 +1617,50 @@ msc_status msc_fix_batch(msc_handle **hs, const float **f_hats, const float *xis
     g_last_error.clear();
     if (n < 0 || (n > 0 && (!hs || !f_hats || !xis || !outs || !g_outs))) return fail(MSC_ERR_INVALID_ARG, "bad batch arguments");
     for (int i = 0; i < n; i++) {
-        msc_status st = msc_fix(hs[i], f_hats[i], xis[i], opt, outs + i, g_outs[i]);
-        if (st != MSC_OK) return st;
+        if (!hs[i]) return fail(MSC_ERR_INVALID_ARG, "job %d has no handle", i);
+        for (int j = 0; j < i; j++)
+            if (hs[j] == hs[i]) return fail(MSC_ERR_INVALID_ARG, "jobs %d and %d share a handle", j, i);
     }
+    if (n == 0) return MSC_OK;
+    msc_options o;
+    if (opt) o = *opt; else fill_defaults(&o);
+    CKS(check_options(&o));
+    CKS(device_ready());
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    // the jobs start after the work already queued on the caller's stream (their inputs)
+    cudaEvent_t ready = nullptr;
+    CK(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    CK(cudaEventRecord(ready, (cudaStream_t)o.stream));
+    grid_for(1);
+    std::vector<msc_status> st((size_t)n, MSC_OK);
+    std::vector<std::string> msg((size_t)n);
+    std::atomic<int> next{0};
+    auto worker = [&]() {
+        cudaStream_t ws = nullptr;
+        cudaError_t e = cudaSetDevice(dev);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ws, ready, 0);
+        for (int i; (i = next.fetch_add(1)) < n;) {
+            if (e != cudaSuccess) {
+                st[(size_t)i] = MSC_ERR_CUDA;
+                msg[(size_t)i] = cudaGetErrorString(e);
+                continue;
+            }
+            msc_options oi = o;
+            oi.stream = ws;
+            st[(size_t)i] = msc_fix(hs[i], f_hats[i], xis[i], &oi, outs + i, g_outs[i]);
+            if (st[(size_t)i] != MSC_OK) msg[(size_t)i] = g_last_error;
+        }
+        if (ws) cudaStreamDestroy(ws);
+    };
+    const int nw = std::min(n, BATCH_STREAMS);
+    std::vector<std::thread> pool;
+    for (int w = 0; w < nw; w++) pool.emplace_back(worker);
+    for (auto &t : pool) t.join();
+    cudaEventDestroy(ready);
+    for (int i = 0; i < n; i++)
+        if (st[(size_t)i] != MSC_OK) return fail(st[(size_t)i], "batch job %d: %s", i, msg[(size_t)i].c_str());
     return MSC_OK;
 }
 

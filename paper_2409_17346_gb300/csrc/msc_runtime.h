@@ -1,0 +1,10 @@
+// Host-side helpers shared by the translation units of libmsc (not part of the C ABI).
+#pragma once
+#include <string>
+
+#include "../../include/msc.h"
+
+namespace msc_rt {
+// record msg as this thread's msc_last_error and return s
+msc_status set_error(msc_status s, const std::string &msg);
+}  // namespace msc_rt

@@ -32,7 +32,23 @@ class Options(ctypes.Structure):
                 ("profile", ctypes.c_int)]
 
 
-KERNEL_CLASSES = ("dense", "cpass", "edit", "refresh", "rebuild", "sep_init", "sep_update", "sep_targets", "other")
+KERNEL_CLASSES = ("dense", "cpass", "edit", "refresh", "rebuild", "sep_init", "sep_update", "sep_targets", "other",
+                  "sep_seed")
+PROFILE_ALL = (1 << len(KERNEL_CLASSES)) - 1
+
+
+def profile_mask(profile):
+    """options.profile from True/False (all/no classes), a class name, an iterable of class
+    names, or an integer bitmask."""
+    if profile is True:
+        return PROFILE_ALL
+    if not profile:
+        return 0
+    if isinstance(profile, str):
+        return 1 << KERNEL_CLASSES.index(profile)
+    if isinstance(profile, int):
+        return profile & PROFILE_ALL
+    return sum(1 << KERNEL_CLASSES.index(k) for k in set(profile))
 
 
 class Stats(ctypes.Structure):
@@ -52,6 +68,17 @@ class Edits(ctypes.Structure):
                 ("q_map", ctypes.POINTER(ctypes.c_uint8)), ("lossless_idx", ctypes.POINTER(ctypes.c_uint64)),
                 ("lossless_val", ctypes.POINTER(ctypes.c_float)), ("n_trace", ctypes.c_uint32),
                 ("trace", ctypes.POINTER(IterRecord)), ("loop_ms", ctypes.c_double)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("max_jobs", ctypes.c_int), ("max_skips", ctypes.c_int), ("mem_budget", ctypes.c_uint64),
+                ("options", Options)]
+
+
+class JobInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("slot", ctypes.c_int32), ("bytes", ctypes.c_uint64),
+                ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double), ("t_end", ctypes.c_double),
+                ("loop_ms", ctypes.c_float), ("reserved", ctypes.c_uint32)]
 
 
 class Report(ctypes.Structure):
@@ -94,13 +121,18 @@ def load():
     lib.msc_gradient_pairs.argtypes = [vp, i, i, i, vp, u64, ctypes.POINTER(u64)]
     lib.msc_critical_cells.argtypes = [vp, i, i, i, vp, vp, u64, ctypes.POINTER(u64)]
     lib.msc_critical_cells_static.argtypes = [vp, i, i, i, vp, vp, u64, ctypes.POINTER(u64), vp]
+    lib.msc_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
+    lib.msc_server_submit.argtypes = [vp, vp, vp, i, i, i, f, vp, ctypes.POINTER(u64)]
+    lib.msc_server_wait.argtypes = [vp, u64, ctypes.POINTER(Edits), ctypes.POINTER(JobInfo)]
+    lib.msc_server_destroy.argtypes = [vp]
+    lib.msc_server_destroy.restype = None
     lib.msc_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
     lib.msc_reset_stats.argtypes = [vp]
     lib.msc_device_bytes.argtypes = [i, i, i]
     lib.msc_device_bytes.restype = u64
     for name in ("msc_prepare_original", "msc_fix", "msc_apply_edits", "msc_verify", "msc_fix_batch",
                  "msc_gradient_pairs", "msc_critical_cells", "msc_critical_cells_static", "msc_get_stats",
-                 "msc_reset_stats"):
+                 "msc_reset_stats", "msc_server_create", "msc_server_submit", "msc_server_wait"):
         getattr(lib, name).restype = i
     _lib = lib
     return lib
@@ -140,7 +172,7 @@ def options(tier=4, q_max=6, max_iters=100000, exact_fallback=1, stream=None, re
     o.tile_x, o.tile_y, o.tile_z = tile
     o.stream = ctypes.c_void_p(stream) if stream else None
     o.record_trace = int(bool(record_trace))
-    o.profile = int(bool(profile))
+    o.profile = profile_mask(profile)
     return o
 
 
@@ -279,6 +311,70 @@ def fix_batch(handles, f_hats, xis, g_outs=None, **kw):
         for i in range(n):
             lib.msc_free_edits(ctypes.byref(es[i]))
     return g_outs, outs
+
+
+class Server:
+    """msc_server: continuous batching of fix jobs on the current device.
+
+    submit() queues a job and returns its ticket at once; wait(ticket) blocks until that job
+    is done and returns (g, edits dict, info dict).  The arrays passed to submit are kept
+    alive here until their job has been waited for."""
+
+    def __init__(self, max_jobs=8, mem_budget=0, max_skips=0, **opts):
+        lib = load()
+        cfg = ServerConfig()
+        cfg.max_jobs, cfg.max_skips, cfg.mem_budget = int(max_jobs), int(max_skips), int(mem_budget)
+        cfg.options = options(**opts)
+        self._s = ctypes.c_void_p()
+        _check(lib.msc_server_create(ctypes.byref(cfg), ctypes.byref(self._s)))
+        self._jobs = {}
+
+    def submit(self, f, f_hat, xi, g_out=None):
+        lib = load()
+        if g_out is None:
+            g_out = np.zeros(np.shape(f), np.float32)
+        fp, fk = _ptr(f)
+        hp, hk = _ptr(f_hat)
+        gp, gk = _ptr(g_out)
+        nx, ny, nz = dims_of(np.shape(f))
+        t = ctypes.c_uint64(0)
+        _check(lib.msc_server_submit(self._s, fp, hp, nx, ny, nz, ctypes.c_float(xi), gp, ctypes.byref(t)))
+        self._jobs[t.value] = (g_out, (fk, hk, gk), tuple(np.shape(f)))
+        return t.value
+
+    def wait(self, ticket):
+        lib = load()
+        g_out, _keep, shape = self._jobs[ticket]
+        e = Edits()
+        info = JobInfo()
+        try:
+            st = lib.msc_server_wait(self._s, ticket, ctypes.byref(e), ctypes.byref(info))
+            del self._jobs[ticket]
+            _check(st)
+            out = _edits_to_py(e, shape)
+        finally:
+            lib.msc_free_edits(ctypes.byref(e))
+        inf = dict(status=int(info.status), slot=int(info.slot), bytes=int(info.bytes), t_submit=info.t_submit,
+                   t_start=info.t_start, t_end=info.t_end, loop_ms=float(info.loop_ms))
+        return g_out, out, inf
+
+    def close(self):
+        if self._s:
+            load().msc_server_destroy(self._s)
+            self._s = ctypes.c_void_p()
+            self._jobs.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _sorted_rows(a):

@@ -77,14 +77,12 @@ def multiscale_2d(nx=3600, ny=1800, seed=2, n_waves=64, lam_min=20.0, lam_max=90
     amp = lam / lam_max
     xs = np.arange(nx, dtype=np.float64)
     ys = np.arange(ny, dtype=np.float64)
-    f = np.zeros((ny, nx))
-    for i in range(n_waves):
-        kx = 2 * math.pi * math.cos(theta[i]) / lam[i]
-        ky = 2 * math.pi * math.sin(theta[i]) / lam[i]
-        ax = kx * xs + phase[i]
-        ay = ky * ys
-        # sin(ax + ay) = sin(ax) cos(ay) + cos(ax) sin(ay), as two outer products
-        f += amp[i] * (np.outer(np.cos(ay), np.sin(ax)) + np.outer(np.sin(ay), np.cos(ax)))
+    kx = 2 * np.pi * np.cos(theta) / lam
+    ky = 2 * np.pi * np.sin(theta) / lam
+    ax = np.outer(kx, xs) + phase[:, None]          # (waves, nx)
+    ay = np.outer(ys, ky)                           # (ny, waves)
+    # sum_i amp_i sin(ax_i + ay_i), with sin(a + b) = sin a cos b + cos a sin b: two products
+    f = (np.cos(ay) * amp) @ np.sin(ax) + (np.sin(ay) * amp) @ np.cos(ax)
     noise = np.zeros((ny, nx))
     gain = 1.0
     for lattice in (64, 32, 16, 8):
