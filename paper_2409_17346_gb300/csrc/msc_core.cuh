@@ -58,6 +58,7 @@ struct LoopState {
     unsigned max_iters, exact_fallback, trace_cap, ntrace;
     unsigned long long nSD;
     unsigned long long edit_items, refresh_items, cpass_items, cases;
+    unsigned long long nblk;  // entries of the C-block list for the next C-pass
 };
 
 // everything a kernel of one job needs (device pointers)
@@ -82,6 +83,9 @@ struct Ctx {
     LoopState *ls;
     uint32_t *Mbits;                 // anchors whose code differs from f's
     uint32_t *Cbits;                 // anchors whose critical cells differ from f's (tier restricted)
+    uint32_t *Csum;                  // one bit per block of 32 Cbits words (1024 anchors): the
+                                     // block may hold a set bit (cleared lazily when found empty)
+    uint32_t *Cblk;                  // blocks whose Csum bit is set, listed for the next C-pass
     int64_t *trace;                  // rows (kind, |T|, |X|, sum T, sum X), ls->trace_cap rows
     unsigned long long *tally;       // when set: per-block (cases, live cases) in shared memory
 };

@@ -181,11 +181,87 @@ __device__ __forceinline__ void for_each_set(const uint32_t *bits, uint32_t n, F
     }
 }
 
+// the anchors whose bit is set, visiting only the listed blocks of 32 words: one warp per
+// block compacts its set bits into shared memory and runs f on them; a block found empty
+// has its summary bit cleared.  Needs blockDim.x == TPB.
+template <class F>
+__device__ __forceinline__ void for_each_listed(const uint32_t *bits, uint32_t n, const uint32_t *blk,
+                                                unsigned long long nblk, uint32_t *sum, F &&f,
+                                                unsigned long long *count = nullptr)
+{
+    __shared__ uint32_t q[TPB / 32][32 * 32];
+    const unsigned lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint32_t *mq = q[wib];
+    const unsigned long long nw = (n + 31) / 32;
+    const unsigned long long warp = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long nwarps = (gridDim.x * (unsigned long long)blockDim.x) >> 5;
+    for (unsigned long long i = warp; i < nblk; i += nwarps) {
+        const uint32_t b = blk[i];
+        const unsigned long long w = (unsigned long long)b * 32 + lane;
+        uint32_t mine = w < nw ? bits[w] : 0u;
+        const unsigned cnt = __popc(mine);
+        unsigned pre = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, pre, o);
+            if (lane >= (unsigned)o) pre += y;
+        }
+        const unsigned total = __shfl_sync(0xffffffffu, pre, 31);
+        if (total == 0) {
+            if (lane == 0) atomicAnd(sum + (b >> 5), ~(1u << (b & 31)));
+            continue;
+        }
+        if (count && lane == 0) atomicAdd(count, (unsigned long long)total);
+        unsigned at = pre - cnt;
+        const uint32_t base = (uint32_t)(w * 32);
+        while (mine) {
+            const int k = __ffs(mine) - 1;
+            mine &= mine - 1;
+            mq[at++] = base + (uint32_t)k;
+        }
+        __syncwarp();
+        for (unsigned k = lane; k < total; k += 32) f(mq[k]);
+        __syncwarp();
+    }
+}
+
+// list the blocks whose summary bit is set (appending to blk, count in *nblk); every warp
+// of the grid takes 32 summary words at a time
+__device__ __forceinline__ void list_blocks(const uint32_t *sum, unsigned long long nsum, uint32_t *blk,
+                                            unsigned long long *nblk)
+{
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned long long warp = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long nwarps = (gridDim.x * (unsigned long long)blockDim.x) >> 5;
+    for (unsigned long long w0 = warp * 32; w0 < nsum; w0 += nwarps * 32) {
+        uint32_t mine = w0 + lane < nsum ? sum[w0 + lane] : 0u;
+        const unsigned cnt = __popc(mine);
+        unsigned pre = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, pre, o);
+            if (lane >= (unsigned)o) pre += y;
+        }
+        const unsigned total = __shfl_sync(0xffffffffu, pre, 31);
+        if (total == 0) continue;
+        unsigned long long at0 = 0;
+        if (lane == 31) at0 = atomicAdd(nblk, (unsigned long long)total);
+        at0 = __shfl_sync(0xffffffffu, at0, 31);
+        unsigned long long at = at0 + pre - cnt;
+        const uint32_t base = (uint32_t)((w0 + lane) * 32);
+        while (mine) {
+            const int k = __ffs(mine) - 1;
+            mine &= mine - 1;
+            blk[at++] = base + (uint32_t)k;
+        }
+    }
+}
+
+__host__ __device__ inline unsigned long long csum_words(uint32_t n) { return ((n + 31ull) / 32 + 1023) / 1024; }
+
 // dense gradient of a field; with ref != nullptr also set the bitsets of anchors whose code
 // differs (mbits) and whose critical cells differ (cbits, tier restricted)
 template <int D>
 __global__ void __launch_bounds__(TPB) k_eval_dense(const float *v, Grid G, uint64_t *out, const uint64_t *ref,
-                                                    uint32_t *mbits, uint32_t *cbits, int tier)
+                                                    uint32_t *mbits, uint32_t *cbits, uint32_t *csum, int tier)
 {
     BLOCK_ROUNDS(b, G.n)
     {
@@ -205,6 +281,7 @@ __global__ void __launch_bounds__(TPB) k_eval_dense(const float *v, Grid G, uint
             if ((threadIdx.x & 31) == 0 && p < G.n) {
                 mbits[p >> 5] = wm;
                 cbits[p >> 5] = wc;
+                if (wc) atomicOr(csum + (p >> 15), 1u << ((p >> 10) & 31));
             }
         }
     }
@@ -252,7 +329,8 @@ template <int D> __global__ void __launch_bounds__(TPB) k_ctargets(Ctx c)
     __shared__ BlockTally tally;
     Ctx cc = c;
     tally_begin(tally, cc);
-    for_each_set(c.Cbits, c.G.n, [&](uint32_t p) { ctargets_anchor<D>(cc, p); }, &c.ls->cpass_items);
+    for_each_listed(c.Cbits, c.G.n, c.Cblk, c.ls->nblk, c.Csum, [&](uint32_t p) { ctargets_anchor<D>(cc, p); },
+                    &c.ls->cpass_items);
     tally_end(tally, c);
 }
 
@@ -264,6 +342,7 @@ __global__ void k_decide(Ctx c, int kind)
     LoopState *ls = c.ls;
     if (ls->halt) return;
     const Counters *k = c.cnt;
+    ls->nblk = 0;          // the C-pass has read the block list; the round's end lists it anew
     ls->cases += k->ncase;
     if (k->ncase == 0) { ls->halt = 1; return; }
     if (!ls->exact_fallback && k->nlive == 0) { ls->halt = 1; ls->status = MSC_ERR_STALLED; return; }
@@ -331,13 +410,21 @@ template <int D> __global__ void k_rebuild(Ctx c)
             const bool m = cf != cg, cm = m && crit_sig<D>(cf, c.tier) != crit_sig<D>(cg, c.tier);
             const uint32_t bit = 1u << (p & 31);
             if (m) atomicOr(c.Mbits + (p >> 5), bit); else atomicAnd(c.Mbits + (p >> 5), ~bit);
-            if (cm) atomicOr(c.Cbits + (p >> 5), bit); else atomicAnd(c.Cbits + (p >> 5), ~bit);
+            if (cm) {
+                atomicOr(c.Cbits + (p >> 5), bit);
+                const uint32_t sb = 1u << ((p >> 10) & 31);
+                if (!(c.Csum[p >> 15] & sb)) atomicOr(c.Csum + (p >> 15), sb);
+            } else {
+                atomicAnd(c.Cbits + (p >> 5), ~bit);
+            }
         }
         st_flush(ss, c.sDlist, &ls->nSD);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ls->refresh_items, d);
 }
 
+// end of a round's edits: clear the round's sets through their lists, and list the blocks
+// of the critical-difference bitset that the next C-pass visits
 __global__ void k_clear(Ctx c)
 {
     if (c.ls->halt) return;
@@ -348,7 +435,10 @@ __global__ void k_clear(Ctx c)
         else if (i < nT + nX) c.Xbits[c.Xlist[i - nT] >> 5] = 0;
         else c.Dbits[c.Dlist[i - nT - nX] >> 5] = 0;
     }
+    list_blocks(c.Csum, csum_words(c.G.n), c.Cblk, &c.ls->nblk);
 }
+
+__global__ void k_list_blocks(Ctx c) { list_blocks(c.Csum, csum_words(c.G.n), c.Cblk, &c.ls->nblk); }
 
 // end of a round: zero the round's counters
 __global__ void k_end(Ctx c)
@@ -755,7 +845,7 @@ struct msc_handle {
     DevBuf<float> fhat, g;
     DevBuf<uint8_t> state;
     DevBuf<uint64_t> code_g;
-    DevBuf<uint32_t> Tbits, Xbits, Dbits, Tlist, Xlist, Dlist, Mbits, Cbits;
+    DevBuf<uint32_t> Tbits, Xbits, Dbits, Tlist, Xlist, Dlist, Mbits, Cbits, Csum, Cblk;
     DevBuf<uint32_t> vis_v, vis_top, vis_tri, ovf0, ovf1;
     DevBuf<int32_t> ns_v, ns_top, ns_tri, ns_dead;
     DevBuf<uint32_t> sDbits, sDlist;
@@ -850,6 +940,8 @@ msc_status alloc_fix_state(msc_handle *h)
     CK(h->Dlist.alloc(n));
     CK(h->Mbits.alloc(words(n)));
     CK(h->Cbits.alloc(words(n)));
+    CK(h->Csum.alloc(csum_words((uint32_t)n)));
+    CK(h->Cblk.alloc(csum_words((uint32_t)n) * 32));
     CK(h->vis_v.alloc(words(n)));
     CK(h->vis_top.alloc(words(n * ntop)));
     if (h->D == 3) {
@@ -901,6 +993,8 @@ Ctx make_ctx(msc_handle *h, int tier, int qmax, int exact_fallback, float xi)
     c.ls = h->ls.p;
     c.Mbits = h->Mbits.p;
     c.Cbits = h->Cbits.p;
+    c.Csum = h->Csum.p;
+    c.Cblk = h->Cblk.p;
     c.trace = nullptr;
     c.tally = nullptr;
     return c;
@@ -908,9 +1002,9 @@ Ctx make_ctx(msc_handle *h, int tier, int qmax, int exact_fallback, float xi)
 
 template <int D> msc_status eval_dense(msc_handle *h, const float *v, Grid G, uint64_t *out, cudaStream_t s,
                                        const uint64_t *ref = nullptr, uint32_t *mbits = nullptr,
-                                       uint32_t *cbits = nullptr, int tier = 4)
+                                       uint32_t *cbits = nullptr, uint32_t *csum = nullptr, int tier = 4)
 {
-    KL(h, MSC_K_DENSE, s, k_eval_dense<D><<<grid_for(G.n), TPB, 0, s>>>(v, G, out, ref, mbits, cbits, tier));
+    KL(h, MSC_K_DENSE, s, k_eval_dense<D><<<grid_for(G.n), TPB, 0, s>>>(v, G, out, ref, mbits, cbits, csum, tier));
     CK(cudaGetLastError());
     return MSC_OK;
 }
@@ -1124,7 +1218,9 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
     CK(cudaMemsetAsync(h->sDbits.p, 0, h->sDbits.n * 4, s));
     CK(cudaMemsetAsync(h->cnt.p, 0, sizeof(Counters), s));
     LoopState *ls = h->ls.p;
-    CKS(eval_dense<D>(h, h->g.p, h->G, h->code_g.p, s, h->code_f.p, h->Mbits.p, h->Cbits.p, o.tier));
+    CK(cudaMemsetAsync(h->Csum.p, 0, h->Csum.n * 4, s));
+    CKS(eval_dense<D>(h, h->g.p, h->G, h->code_g.p, s, h->code_f.p, h->Mbits.p, h->Cbits.p, h->Csum.p, o.tier));
+    KL(h, MSC_K_REBUILD, s, k_list_blocks<<<grid_for(h->G.n / 1024 + 1), TPB, 0, s>>>(c));
     h->items[MSC_K_DENSE] += h->G.n;
     RoundGraph rg;
     CKS(build_round_graph<D>(h, c, (unsigned)o.profile & MSC_PROFILE_ALL, rg));
@@ -1408,7 +1504,7 @@ msc_status critical_static(const float *field, Grid G, int64_t *rows, int32_t *d
     unsigned long long *count = scr + MSC_STATIC_MAX_VERTICES, *bad = count + 1;
     CK(cudaMemsetAsync(count, 0, 2 * sizeof(unsigned long long), s));
     k_count_nonfinite<<<grid_for(G.n), TPB, 0, s>>>(field, G.n, bad);
-    k_eval_dense<D><<<grid_for(G.n), TPB, 0, s>>>(field, G, code, nullptr, nullptr, nullptr, 4);
+    k_eval_dense<D><<<grid_for(G.n), TPB, 0, s>>>(field, G, code, nullptr, nullptr, nullptr, nullptr, 4);
     k_decode_crit<D><<<grid_for(G.n), TPB, 0, s>>>(code, nullptr, G, cap ? rows : nullptr, dims, count, cap, nullptr);
     CK(cudaGetLastError());
     unsigned long long hv[2];
