@@ -78,7 +78,7 @@ struct Ctx {
     uint32_t ovf_cap;
     Counters *cnt;
     // persistent separatrix state (tier 4): one byte per node, see "separatrix state" below
-    int32_t *ns_v, *ns_top, *ns_tri, *ns_dead;
+    uint32_t *ns_v, *ns_top, *ns_tri, *ns_dead;   // separatrix node words, two per uint32
     uint32_t *sDbits, *sDlist;       // anchors dirtied since the last S-pass
     LoopState *ls;
     uint32_t *Mbits;                 // anchors whose code differs from f's
@@ -501,7 +501,7 @@ template <int D> MSC_HD inline uint64_t crit_sig(uint64_t code, int tier)
     return sig;
 }
 
-// re-evaluate a dirty anchor and keep it in the mismatch list if its code differs from f's
+// re-evaluate a dirty anchor (one pass)
 template <int D> MSC_HD inline void refresh_anchor(const Ctx &c, uint32_t p)
 {
     c.code_g[p] = anchor_code<D>(c.g, c.G, p);
@@ -734,7 +734,7 @@ MSC_HD inline void ss_walk(const Ctx &c, uint32_t tri0, uint32_t entry0, bool se
 // The S-pass of Sec. 4.4 walks every separatrix of f from its saddle and stops at the first
 // pair missing from g's gradient.  The set of cells such a walk reaches depends on g only
 // through the pairs it checks, and between two S-passes g changes only around edited
-// vertices.  So the walks are kept as a state: one 32-bit word per node
+// vertices.  So the walks are kept as a state: one 16-bit word per node
 //   descending: a vertex u (its pair (u, u next_f(u)));     ascending: a top cell beta (its
 //   pair with its f-facet); saddle-saddle: a triangle t' = V_f(e) (pair (e, t')) and every
 //   edge paired down in f (a dead end of the triangle walk);
@@ -745,44 +745,64 @@ MSC_HD inline void ss_walk(const Ctx &c, uint32_t tri0, uint32_t entry0, bool se
 // mismatch.  Troublemakers are the mismatched nodes with a reached predecessor - exactly
 // the first disagreeing pairs the walks stop at.  Every change is one atomic on the node's
 // word and its before/after values decide the +-1 passed on, so concurrent updates settle
-// on the same state in any order (a count may dip below zero while a +1 is in flight; the
-// signed field holds that without touching any other node).
+// on the same state in any order).
+// Storage: two nodes per 32-bit word (node i in half i & 1), atomics on the word.  A node's
+// count is kept with a bias, so a count that dips below zero while a +1 is in flight still
+// leaves its half non-negative and never borrows from (or carries into) the other node:
+// the biased field stays inside its 14 bits for counts in [-NS_BIAS, 2^14 - 1 - NS_BIAS].
+// A fresh array is every byte NS_FILL (half 0x4040: no flags, count 0).  The helpers
+// return a node decoded as an int32: flags in bits 0-1, the unbiased count in bits 2+.
 constexpr int32_t NS_MIS = 1, NS_SEED = 2, NS_ONE = 4;
+constexpr int32_t NS_BIAS = 0x1010;
+constexpr int NS_FILL = 0x40;
 
-MSC_HD inline int32_t node_add(int32_t *ns, uint32_t i, int delta)
+__host__ __device__ constexpr size_t node_words(size_t nodes) { return (nodes + 1) / 2; }
+MSC_HD inline int32_t node_decode(uint32_t word, uint32_t i)
 {
+    const int32_t h = (int32_t)((word >> ((i & 1u) * 16)) & 0xffffu);
+    return (h & 3) | (((h >> 2) - NS_BIAS) * NS_ONE);
+}
+
+MSC_HD inline int32_t node_add(uint32_t *ns, uint32_t i, int delta)
+{
+    const uint32_t v = (uint32_t)(delta * NS_ONE) << ((i & 1u) * 16);
 #ifdef __CUDA_ARCH__
-    return atomicAdd(ns + i, delta * NS_ONE);
+    return node_decode(atomicAdd(ns + (i >> 1), v), i);
 #else
-    const int32_t o = ns[i];
-    ns[i] = o + delta * NS_ONE;
-    return o;
+    const uint32_t o = ns[i >> 1];
+    ns[i >> 1] = o + v;
+    return node_decode(o, i);
 #endif
 }
 
-MSC_HD inline int32_t node_xor(int32_t *ns, uint32_t i, int32_t m)
+MSC_HD inline int32_t node_xor(uint32_t *ns, uint32_t i, int32_t m)
 {
+    const uint32_t v = (uint32_t)m << ((i & 1u) * 16);
 #ifdef __CUDA_ARCH__
-    return atomicXor(ns + i, m);
+    return node_decode(atomicXor(ns + (i >> 1), v), i);
 #else
-    const int32_t o = ns[i];
-    ns[i] = o ^ m;
-    return o;
+    const uint32_t o = ns[i >> 1];
+    ns[i >> 1] = o ^ v;
+    return node_decode(o, i);
 #endif
 }
 
-MSC_HD inline int32_t node_or(int32_t *ns, uint32_t i, int32_t m)
+MSC_HD inline int32_t node_or(uint32_t *ns, uint32_t i, int32_t m)
 {
+    const uint32_t v = (uint32_t)m << ((i & 1u) * 16);
 #ifdef __CUDA_ARCH__
-    return atomicOr(ns + i, m);
+    return node_decode(atomicOr(ns + (i >> 1), v), i);
 #else
-    const int32_t o = ns[i];
-    ns[i] = o | m;
-    return o;
+    const uint32_t o = ns[i >> 1];
+    ns[i >> 1] = o | v;
+    return node_decode(o, i);
 #endif
 }
 
-MSC_HD inline int32_t node_load(const int32_t *ns, uint32_t i) { return ((const volatile int32_t *)ns)[i]; }
+MSC_HD inline int32_t node_load(const uint32_t *ns, uint32_t i)
+{
+    return node_decode(((const volatile uint32_t *)ns)[i >> 1], i);
+}
 
 MSC_HD inline int32_t node_count(int32_t b) { return b >> 2; }
 MSC_HD inline bool path_reached(int32_t b) { return (b & NS_SEED) || node_count(b) > 0; }
@@ -817,7 +837,7 @@ template <int D> MSC_HD inline bool asc_succ(const Ctx &c, uint32_t beta, uint32
 // the path (kind 0: descending vertices, 1: ascending top cells)
 template <int D> MSC_HD inline void path_push(const Ctx &c, int kind, uint32_t w, int delta)
 {
-    int32_t *ns = kind == 0 ? c.ns_v : c.ns_top;
+    uint32_t *ns = kind == 0 ? c.ns_v : c.ns_top;
     unsigned long long n = 0;
     for (uint32_t s = 0; s <= c.G.n * (uint32_t)Tab<D>::NTOP; s++) {
         n++;
@@ -922,7 +942,7 @@ template <int D> MSC_HD inline void node_bits(const Ctx &c, uint32_t p, bool ini
     int x, y, z;
     coords(c.G, p, x, y, z);
     auto set_path = [&](int kind, uint32_t u, bool m) {
-        int32_t *ns = kind == 0 ? c.ns_v : c.ns_top;
+        uint32_t *ns = kind == 0 ? c.ns_v : c.ns_top;
         if (init) { if (m) node_or(ns, u, NS_MIS); return; }
         if (((node_load(ns, u) & NS_MIS) != 0) == m) return;
         const int32_t o = node_xor(ns, u, NS_MIS);
@@ -972,7 +992,7 @@ template <int D> MSC_HD inline void node_seed(const Ctx &c, int kind, uint32_t u
         if (dv) tri_propagate(c, u, dv, false, 0);
         return;
     }
-    int32_t *ns = kind == 0 ? c.ns_v : c.ns_top;
+    uint32_t *ns = kind == 0 ? c.ns_v : c.ns_top;
     const int32_t o = node_or(ns, u, NS_SEED);
     if (o & NS_SEED) return;
     path_change<D>(c, kind, u, o, o | NS_SEED);
@@ -1043,38 +1063,46 @@ template <int D> MSC_HD inline void node_targets(const Ctx &c, uint32_t p)
 template <int D, class Emit> MSC_HD inline void seeds_anchor(const uint64_t *code, const Grid &G, uint32_t p, int kind,
                                                              Emit &&emit)
 {
-    const Tab<D> &T = rt_tab<D>();
+    using Tb = Tab<D>;
     int x, y, z;
     coords(G, p, x, y, z);
     const unsigned cin = corner_mask<D>(G, x, y, z);
     const uint64_t cf = ld(code + p);
     if (kind == 0 || (D == 2 && kind == 1)) {
-        for (int e = 0; e < T.NE; e++) {
-            if (!((cin >> (e + 1)) & 1u) || efield<D>(cf, e) != 0) continue;
+        static_for<Tb::NE>([&](auto ec) {
+            constexpr int e = decltype(ec)::value;
+            if (!((cin >> (e + 1)) & 1u) || efield<D>(cf, e) != 0) return;
             if (kind == 0) {
+                constexpr int A = e + 1;
                 emit(p);
-                const int A = e + 1;
                 emit(vid(G, x + (A & 1), y + ((A >> 1) & 1), z + ((A >> 2) & 1)));
-            } else {
-                for (int i = 0; i < T.necof[e]; i++) {
-                    const int bx = x + T.ecof_anc[e][i][0], by = y + T.ecof_anc[e][i][1], bz = z + T.ecof_anc[e][i][2];
-                    const int bt = T.ecof_type[e][i];
-                    if (top_exists<D>(G, bx, by, bz, bt)) emit(vid(G, bx, by, bz) * T.NTOP + bt);
-                }
+                return;
             }
-        }
+            static_for<TabC<D>::T.necof[e]>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                constexpr int ax = TabC<D>::T.ecof_anc[e][i][0], ay = TabC<D>::T.ecof_anc[e][i][1];
+                constexpr int az = TabC<D>::T.ecof_anc[e][i][2], bt = TabC<D>::T.ecof_type[e][i];
+                if (top_exists<D>(G, x + ax, y + ay, z + az, bt)) emit(vid(G, x + ax, y + ay, z + az) * Tb::NTOP + bt);
+            });
+        });
         return;
     }
     if constexpr (D == 3) {
-    for (int tt = 0; tt < T.NT; tt++) {
-        if (!((cin >> T.tB[tt]) & 1u) || tfield<D>(cf, tt) != 0) continue;
-        if (kind == 2) { emit(p * 12 + tt); continue; }
-        for (int i = 0; i < T.ntcof[tt]; i++) {
-            const int bx = x + T.tcof_anc[tt][i][0], by = y + T.tcof_anc[tt][i][1], bz = z + T.tcof_anc[tt][i][2];
-            const int bt = T.tcof_type[tt][i];
-            if (top_exists<D>(G, bx, by, bz, bt)) emit(vid(G, bx, by, bz) * T.NTOP + bt);
-        }
-    }
+        static_for<Tb::NT>([&](auto tc) {
+            constexpr int tt = decltype(tc)::value;
+            constexpr int top = TabC<D>::T.tB[tt];
+            if (!((cin >> top) & 1u) || tfield<D>(cf, tt) != 0) return;
+            if (kind == 2) {
+                emit(p * 12 + tt);
+                return;
+            }
+            static_for<TabC<D>::T.ntcof[tt]>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                constexpr int ax = TabC<D>::T.tcof_anc[tt][i][0], ay = TabC<D>::T.tcof_anc[tt][i][1];
+                constexpr int az = TabC<D>::T.tcof_anc[tt][i][2], bt = TabC<D>::T.tcof_type[tt][i];
+                if (top_exists<D>(G, x + ax, y + ay, z + az, bt)) emit(vid(G, x + ax, y + ay, z + az) * Tb::NTOP + bt);
+            });
+        });
     }
 }
 

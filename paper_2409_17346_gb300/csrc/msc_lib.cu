@@ -507,30 +507,44 @@ __global__ void k_sd_clear(Ctx c, unsigned long long *nSD)
 }
 
 // count pass (out == nullptr): one atomic per block; fill pass: staged appends
+// separatrix seeds of f, all kinds in one pass over the codes: kind 0 = 1-saddle endpoint
+// vertices (descending), 1 = top cofacets of (D-1)-saddles (ascending), 2 = 2-saddle
+// triangles (3D).  With out == nullptr only count[kind] is accumulated.
+struct SeedOut {
+    uint32_t *out[3];
+};
+
 template <int D>
-__global__ void k_seeds(const uint64_t *code, Grid G, int kind, uint32_t *out, unsigned long long *count)
+__global__ void k_seeds(const uint64_t *code, Grid G, SeedOut so, unsigned long long *count)
 {
-    if (!out) {
-        unsigned long long local = 0;
-        GRID_STRIDE(p, G.n) seeds_anchor<D>(code, G, (uint32_t)p, kind, [&](uint32_t) { local++; });
-        for (int o = 16; o; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
-        __shared__ unsigned long long warp_sum[TPB / 32];
-        if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = local;
+    constexpr int NK = D == 3 ? 3 : 2;
+    if (!so.out[0]) {
+        unsigned long long local[3] = {0, 0, 0};
+        GRID_STRIDE(p, G.n)
+        for (int k = 0; k < NK; k++) seeds_anchor<D>(code, G, (uint32_t)p, k, [&](uint32_t) { local[k]++; });
+        __shared__ unsigned long long warp_sum[3][TPB / 32];
+        for (int k = 0; k < NK; k++) {
+            unsigned long long v = local[k];
+            for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if ((threadIdx.x & 31) == 0) warp_sum[k][threadIdx.x >> 5] = v;
+        }
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < NK) {
             unsigned long long t = 0;
-            for (int w = 0; w < TPB / 32; w++) t += warp_sum[w];
-            if (t) atomicAdd(count, t);
+            for (int w = 0; w < TPB / 32; w++) t += warp_sum[threadIdx.x][w];
+            if (t) atomicAdd(count + threadIdx.x, t);
         }
         return;
     }
-    __shared__ Stage<4 * TPB> st;
-    st_init(st);
+    __shared__ Stage<2 * TPB> st[3];
+    for (int k = 0; k < NK; k++) st_init(st[k]);
     BLOCK_ROUNDS(b, G.n)
     {
         const unsigned long long p = b + threadIdx.x;
-        if (p < G.n) seeds_anchor<D>(code, G, (uint32_t)p, kind, [&](uint32_t v) { st_push(st, v, out, count); });
-        st_flush(st, out, count);
+        if (p < G.n)
+            for (int k = 0; k < NK; k++)
+                seeds_anchor<D>(code, G, (uint32_t)p, k, [&](uint32_t v) { st_push(st[k], v, so.out[k], count + k); });
+        for (int k = 0; k < NK; k++) st_flush(st[k], so.out[k], count + k);
     }
 }
 
@@ -847,7 +861,7 @@ struct msc_handle {
     DevBuf<uint64_t> code_g;
     DevBuf<uint32_t> Tbits, Xbits, Dbits, Tlist, Xlist, Dlist, Mbits, Cbits, Csum, Cblk;
     DevBuf<uint32_t> vis_v, vis_top, vis_tri, ovf0, ovf1;
-    DevBuf<int32_t> ns_v, ns_top, ns_tri, ns_dead;
+    DevBuf<uint32_t> ns_v, ns_top, ns_tri, ns_dead;
     DevBuf<uint32_t> sDbits, sDlist;
     DevBuf<Counters> cnt;
     DevBuf<LoopState> ls;
@@ -949,11 +963,11 @@ msc_status alloc_fix_state(msc_handle *h)
         CK(h->ovf0.alloc(2 * n + 2));
         CK(h->ovf1.alloc(2 * n + 2));
     }
-    CK(h->ns_v.alloc(n + 4));
-    CK(h->ns_top.alloc(n * ntop + 4));
+    CK(h->ns_v.alloc(node_words(n + 4)));
+    CK(h->ns_top.alloc(node_words(n * ntop + 4)));
     if (h->D == 3) {
-        CK(h->ns_tri.alloc(n * 12 + 4));
-        CK(h->ns_dead.alloc(n * 7 + 4));
+        CK(h->ns_tri.alloc(node_words(n * 12 + 4)));
+        CK(h->ns_dead.alloc(node_words(n * 7 + 4)));
     }
     CK(h->sDbits.alloc(words(n)));
     CK(h->sDlist.alloc(n));
@@ -1017,22 +1031,24 @@ msc_status eval_dense_any(msc_handle *h, int D, const float *v, Grid G, uint64_t
 template <int D> msc_status build_seeds(msc_handle *h, cudaStream_t s)
 {
     DevBuf<unsigned long long> cnt;
-    CK(cnt.alloc(1));
+    CK(cnt.alloc(3));
     DevBuf<uint32_t> *bufs[3] = {&h->seeds_desc, &h->seeds_asc, &h->seeds_ss};
     uint32_t *ns[3] = {&h->n_desc, &h->n_asc, &h->n_ss};
-    for (int kind = 0; kind < (D == 3 ? 3 : 2); kind++) {
-        unsigned long long n = 0;
-        CK(cudaMemsetAsync(cnt.p, 0, sizeof n, s));
-        KL(h, MSC_K_OTHER, s, k_seeds<D><<<grid_for(h->G.n), TPB, 0, s>>>(h->code_f.p, h->G, kind, nullptr, cnt.p));
-        CK(cudaGetLastError());
-        CK(cudaMemcpyAsync(&n, cnt.p, sizeof n, cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        CK(bufs[kind]->alloc(n));
-        CK(cudaMemsetAsync(cnt.p, 0, sizeof n, s));
-        KL(h, MSC_K_OTHER, s, k_seeds<D><<<grid_for(h->G.n), TPB, 0, s>>>(h->code_f.p, h->G, kind, bufs[kind]->p, cnt.p));
-        CK(cudaGetLastError());
-        *ns[kind] = (uint32_t)n;
+    unsigned long long n[3] = {0, 0, 0};
+    SeedOut so{{nullptr, nullptr, nullptr}};
+    CK(cudaMemsetAsync(cnt.p, 0, sizeof n, s));
+    KL(h, MSC_K_OTHER, s, k_seeds<D><<<grid_for(h->G.n), TPB, 0, s>>>(h->code_f.p, h->G, so, cnt.p));
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(n, cnt.p, sizeof n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int k = 0; k < 3; k++) {
+        CK(bufs[k]->alloc(n[k]));
+        so.out[k] = bufs[k]->p;
+        *ns[k] = (uint32_t)n[k];
     }
+    CK(cudaMemsetAsync(cnt.p, 0, sizeof n, s));
+    KL(h, MSC_K_OTHER, s, k_seeds<D><<<grid_for(h->G.n), TPB, 0, s>>>(h->code_f.p, h->G, so, cnt.p));
+    CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s));
     cnt.release();
     return MSC_OK;
@@ -1077,11 +1093,11 @@ template <int D> msc_status s_pass_state(msc_handle *h, Ctx &c, bool &built, uns
     c.ovf_out = D == 3 ? h->ovf0.p : nullptr;
     const int spill_cls = built ? MSC_K_SEP_UPDATE : MSC_K_SEP_SEED;
     if (!built) {
-        CK(cudaMemsetAsync(h->ns_v.p, 0, h->ns_v.n * 4, s));
-        CK(cudaMemsetAsync(h->ns_top.p, 0, h->ns_top.n * 4, s));
+        CK(cudaMemsetAsync(h->ns_v.p, NS_FILL, h->ns_v.n * 4, s));
+        CK(cudaMemsetAsync(h->ns_top.p, NS_FILL, h->ns_top.n * 4, s));
         if (D == 3) {
-            CK(cudaMemsetAsync(h->ns_tri.p, 0, h->ns_tri.n * 4, s));
-            CK(cudaMemsetAsync(h->ns_dead.p, 0, h->ns_dead.n * 4, s));
+            CK(cudaMemsetAsync(h->ns_tri.p, NS_FILL, h->ns_tri.n * 4, s));
+            CK(cudaMemsetAsync(h->ns_dead.p, NS_FILL, h->ns_dead.n * 4, s));
         }
         KL(h, MSC_K_SEP_INIT, s, k_node_init<D><<<grid_for(h->G.n), TPB, 0, s>>>(c));
         if (h->n_desc) KL(h, MSC_K_SEP_SEED, s, k_node_seed<D><<<grid_for(h->n_desc), TPB, 0, s>>>(c, 0, h->seeds_desc.p, h->n_desc));
@@ -1553,7 +1569,7 @@ uint64_t msc_device_bytes(int nx, int ny, int nz)
     uint64_t b = 12 * n + n + 16 * n;             // f, f_hat, g; state; code_f, code_g
     b += 4 * (n / 8 + 4) + 8 * 4 * n;             // four bitsets; eight index lists
     b += n / 8 + ntop * n / 8 + (d3 ? 12 * n / 8 + 16 * n : 0);   // walk visited sets, spill queues
-    b += 4 * n * (1 + ntop + (d3 ? 19 : 0));      // separatrix state words
+    b += 2 * n * (1 + ntop + (d3 ? 19 : 0));      // separatrix node words (16 bits each)
     b += 3 * 4 * n;                               // separatrix seeds (upper estimate)
     return b;
 }
