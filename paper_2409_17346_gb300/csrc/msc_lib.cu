@@ -76,7 +76,7 @@ namespace {
 
 constexpr int TPB = 256;
 
-int grid_for(unsigned long long n)
+int sm_count()
 {
     static const int sms = [] {
         int dev = 0, v = 0;
@@ -84,8 +84,32 @@ int grid_for(unsigned long long n)
         cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
         return v > 0 ? v : 152;
     }();
+    return sms;
+}
+
+// blocks of TPB threads of this kernel that fit on one SM at once (cached per kernel)
+int occ_blocks(const void *kernel)
+{
+    static std::mutex mu;
+    static std::vector<std::pair<const void *, int>> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto &kv : cache)
+        if (kv.first == kernel) return kv.second;
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, TPB, 0) != cudaSuccess || b < 1) {
+        cudaGetLastError();
+        b = 1;
+    }
+    cache.emplace_back(kernel, b);
+    return b;
+}
+
+// grid for a grid-stride kernel over n threads' worth of work: at most one full wave of the
+// blocks that can be resident at once, so no launch ends with a partly filled wave
+int grid_occ(const void *kernel, unsigned long long n)
+{
     unsigned long long b = (n + TPB - 1) / TPB;
-    unsigned long long cap = (unsigned long long)sms * 8;
+    const unsigned long long cap = (unsigned long long)sm_count() * occ_blocks(kernel);
     if (b > cap) b = cap;
     if (b < 1) b = 1;
     return (int)b;
@@ -814,7 +838,7 @@ msc_status upload_field(msc_handle *h, const float *src, size_t n, float *dst, u
     if (!src) return fail(MSC_ERR_INVALID_ARG, "%s is NULL", what);
     CK(cudaMemcpyAsync(dst, src, n * sizeof(float), is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(bad_dev, 0, sizeof(unsigned long long), s));
-    KL(h, MSC_K_OTHER, s, k_count_nonfinite<<<grid_for(n), TPB, 0, s>>>(dst, (uint32_t)n, bad_dev));
+    KL(h, MSC_K_OTHER, s, k_count_nonfinite<<<grid_occ((const void *)k_count_nonfinite, n), TPB, 0, s>>>(dst, (uint32_t)n, bad_dev));
     CK(cudaGetLastError());
     unsigned long long bad = 0;
     CK(cudaMemcpyAsync(&bad, bad_dev, sizeof bad, cudaMemcpyDeviceToHost, s));
@@ -1018,7 +1042,7 @@ template <int D> msc_status eval_dense(msc_handle *h, const float *v, Grid G, ui
                                        const uint64_t *ref = nullptr, uint32_t *mbits = nullptr,
                                        uint32_t *cbits = nullptr, uint32_t *csum = nullptr, int tier = 4)
 {
-    KL(h, MSC_K_DENSE, s, k_eval_dense<D><<<grid_for(G.n), TPB, 0, s>>>(v, G, out, ref, mbits, cbits, csum, tier));
+    KL(h, MSC_K_DENSE, s, k_eval_dense<D><<<grid_occ((const void *)k_eval_dense<D>, G.n), TPB, 0, s>>>(v, G, out, ref, mbits, cbits, csum, tier));
     CK(cudaGetLastError());
     return MSC_OK;
 }
@@ -1037,7 +1061,7 @@ template <int D> msc_status build_seeds(msc_handle *h, cudaStream_t s)
     unsigned long long n[3] = {0, 0, 0};
     SeedOut so{{nullptr, nullptr, nullptr}};
     CK(cudaMemsetAsync(cnt.p, 0, sizeof n, s));
-    KL(h, MSC_K_OTHER, s, k_seeds<D><<<grid_for(h->G.n), TPB, 0, s>>>(h->code_f.p, h->G, so, cnt.p));
+    KL(h, MSC_K_OTHER, s, k_seeds<D><<<grid_occ((const void *)k_seeds<D>, h->G.n), TPB, 0, s>>>(h->code_f.p, h->G, so, cnt.p));
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(n, cnt.p, sizeof n, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -1047,7 +1071,7 @@ template <int D> msc_status build_seeds(msc_handle *h, cudaStream_t s)
         *ns[k] = (uint32_t)n[k];
     }
     CK(cudaMemsetAsync(cnt.p, 0, sizeof n, s));
-    KL(h, MSC_K_OTHER, s, k_seeds<D><<<grid_for(h->G.n), TPB, 0, s>>>(h->code_f.p, h->G, so, cnt.p));
+    KL(h, MSC_K_OTHER, s, k_seeds<D><<<grid_occ((const void *)k_seeds<D>, h->G.n), TPB, 0, s>>>(h->code_f.p, h->G, so, cnt.p));
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s));
     cnt.release();
@@ -1060,13 +1084,13 @@ template <int D> msc_status s_pass(msc_handle *h, const Ctx &c0, int tier, cudaS
     Ctx c = c0;
     CK(cudaMemsetAsync(h->vis_v.p, 0, h->vis_v.n * 4, s));
     CK(cudaMemsetAsync(h->vis_top.p, 0, h->vis_top.n * 4, s));
-    if (h->n_desc) KL(h, MSC_K_SEP_UPDATE, s, k_desc<D><<<grid_for(h->n_desc), TPB, 0, s>>>(c, h->seeds_desc.p, h->n_desc));
-    if (h->n_asc) KL(h, MSC_K_SEP_UPDATE, s, k_asc<D><<<grid_for(h->n_asc), TPB, 0, s>>>(c, h->seeds_asc.p, h->n_asc));
+    if (h->n_desc) KL(h, MSC_K_SEP_UPDATE, s, k_desc<D><<<grid_occ((const void *)k_desc<D>, h->n_desc), TPB, 0, s>>>(c, h->seeds_desc.p, h->n_desc));
+    if (h->n_asc) KL(h, MSC_K_SEP_UPDATE, s, k_asc<D><<<grid_occ((const void *)k_asc<D>, h->n_asc), TPB, 0, s>>>(c, h->seeds_asc.p, h->n_asc));
     CK(cudaGetLastError());
     if (D == 3 && tier >= 4 && h->n_ss) {
         CK(cudaMemsetAsync(h->vis_tri.p, 0, h->vis_tri.n * 4, s));
         c.ovf_out = h->ovf0.p;
-        KL(h, MSC_K_SEP_UPDATE, s, k_ss_seed<<<grid_for(h->n_ss), TPB, 0, s>>>(c, h->seeds_ss.p, h->n_ss));
+        KL(h, MSC_K_SEP_UPDATE, s, k_ss_seed<<<grid_occ((const void *)k_ss_seed, h->n_ss), TPB, 0, s>>>(c, h->seeds_ss.p, h->n_ss));
         CK(cudaGetLastError());
         uint32_t *in = h->ovf0.p, *out = h->ovf1.p;
         for (int round = 0; round < 1 << 20; round++) {
@@ -1078,7 +1102,7 @@ template <int D> msc_status s_pass(msc_handle *h, const Ctx &c0, int tier, cudaS
             const unsigned long long zero = 0;
             CK(cudaMemcpyAsync(&h->cnt.p->novf, &zero, sizeof zero, cudaMemcpyHostToDevice, s));
             c.ovf_out = out;
-            KL(h, MSC_K_SEP_UPDATE, s, k_ss_spill<<<grid_for(hc.novf), TPB, 0, s>>>(c, in, (uint32_t)hc.novf));
+            KL(h, MSC_K_SEP_UPDATE, s, k_ss_spill<<<grid_occ((const void *)k_ss_spill, hc.novf), TPB, 0, s>>>(c, in, (uint32_t)hc.novf));
             CK(cudaGetLastError());
             std::swap(in, out);
         }
@@ -1099,16 +1123,16 @@ template <int D> msc_status s_pass_state(msc_handle *h, Ctx &c, bool &built, uns
             CK(cudaMemsetAsync(h->ns_tri.p, NS_FILL, h->ns_tri.n * 4, s));
             CK(cudaMemsetAsync(h->ns_dead.p, NS_FILL, h->ns_dead.n * 4, s));
         }
-        KL(h, MSC_K_SEP_INIT, s, k_node_init<D><<<grid_for(h->G.n), TPB, 0, s>>>(c));
-        if (h->n_desc) KL(h, MSC_K_SEP_SEED, s, k_node_seed<D><<<grid_for(h->n_desc), TPB, 0, s>>>(c, 0, h->seeds_desc.p, h->n_desc));
-        if (h->n_asc) KL(h, MSC_K_SEP_SEED, s, k_node_seed<D><<<grid_for(h->n_asc), TPB, 0, s>>>(c, 1, h->seeds_asc.p, h->n_asc));
-        if (D == 3 && h->n_ss) KL(h, MSC_K_SEP_SEED, s, k_node_seed<D><<<grid_for(h->n_ss), TPB, 0, s>>>(c, 2, h->seeds_ss.p, h->n_ss));
+        KL(h, MSC_K_SEP_INIT, s, k_node_init<D><<<grid_occ((const void *)k_node_init<D>, h->G.n), TPB, 0, s>>>(c));
+        if (h->n_desc) KL(h, MSC_K_SEP_SEED, s, k_node_seed<D><<<grid_occ((const void *)k_node_seed<D>, h->n_desc), TPB, 0, s>>>(c, 0, h->seeds_desc.p, h->n_desc));
+        if (h->n_asc) KL(h, MSC_K_SEP_SEED, s, k_node_seed<D><<<grid_occ((const void *)k_node_seed<D>, h->n_asc), TPB, 0, s>>>(c, 1, h->seeds_asc.p, h->n_asc));
+        if (D == 3 && h->n_ss) KL(h, MSC_K_SEP_SEED, s, k_node_seed<D><<<grid_occ((const void *)k_node_seed<D>, h->n_ss), TPB, 0, s>>>(c, 2, h->seeds_ss.p, h->n_ss));
         CK(cudaGetLastError());
         h->items[MSC_K_SEP_INIT] += h->G.n;
         built = true;
         k_set_track<<<1, 1, 0, s>>>(h->ls.p, 1);
     } else {
-        KL(h, MSC_K_SEP_UPDATE, s, k_node_update<D><<<grid_for(h->G.n / 16 + 1), TPB, 0, s>>>(c, nSD));
+        KL(h, MSC_K_SEP_UPDATE, s, k_node_update<D><<<grid_occ((const void *)k_node_update<D>, h->G.n / 16 + 1), TPB, 0, s>>>(c, nSD));
         CK(cudaGetLastError());
     }
     if (D == 3) {
@@ -1122,14 +1146,14 @@ template <int D> msc_status s_pass_state(msc_handle *h, Ctx &c, bool &built, uns
             const unsigned long long zero = 0;
             CK(cudaMemcpyAsync(&h->cnt.p->novf, &zero, sizeof zero, cudaMemcpyHostToDevice, s));
             c.ovf_out = out;
-            KL(h, spill_cls, s, k_tri_spill<<<grid_for(hc.novf), TPB, 0, s>>>(c, in, (uint32_t)hc.novf));
+            KL(h, spill_cls, s, k_tri_spill<<<grid_occ((const void *)k_tri_spill, hc.novf), TPB, 0, s>>>(c, in, (uint32_t)hc.novf));
             CK(cudaGetLastError());
             std::swap(in, out);
         }
     }
-    KL(h, MSC_K_SEP_UPDATE, s, k_sd_clear<<<grid_for(h->G.n / 16 + 1), TPB, 0, s>>>(c, nSD));
+    KL(h, MSC_K_SEP_UPDATE, s, k_sd_clear<<<grid_occ((const void *)k_sd_clear, h->G.n / 16 + 1), TPB, 0, s>>>(c, nSD));
     CK(cudaMemsetAsync(nSD, 0, sizeof(unsigned long long), s));
-    KL(h, MSC_K_SEP_TARGETS, s, k_node_targets<D><<<grid_for(h->G.n / 32 + 1), TPB, 0, s>>>(c));
+    KL(h, MSC_K_SEP_TARGETS, s, k_node_targets<D><<<grid_occ((const void *)k_node_targets<D>, h->G.n / 32 + 1), TPB, 0, s>>>(c));
     CK(cudaGetLastError());
     return MSC_OK;
 }
@@ -1162,6 +1186,12 @@ template <int D> msc_status build_round_graph(msc_handle *h, const Ctx &c, unsig
 {
     cudaStream_t cs = h->cap_stream;
     cudaGraph_t graph = nullptr;
+    // grid sizes (occupancy queries) before the capture begins
+    const int g_ct = grid_occ((const void *)k_ctargets<D>, h->G.n / 8 + 1);
+    const int g_ed = grid_occ((const void *)k_edit<D>, 32ull * h->G.n);
+    const int g_rf = grid_occ((const void *)k_refresh<D>, h->G.n);
+    const int g_rb = grid_occ((const void *)k_rebuild<D>, h->G.n);
+    const int g_cl = grid_occ((const void *)k_clear, h->G.n);
     CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     auto node = [&](int cls, int round, int pre, auto &&launch) {
         if (!((prof_mask >> cls) & 1u)) { launch(); return; }
@@ -1174,12 +1204,12 @@ template <int D> msc_status build_round_graph(msc_handle *h, const Ctx &c, unsig
         rg.pairs.push_back(p);
     };
     for (int r = 0; r < GRAPH_ROUNDS; r++) {
-        node(MSC_K_CPASS, r, 1, [&] { k_ctargets<D><<<grid_for(h->G.n / 8 + 1), TPB, 0, cs>>>(c); });
+        node(MSC_K_CPASS, r, 1, [&] { k_ctargets<D><<<g_ct, TPB, 0, cs>>>(c); });
         node(MSC_K_OTHER, r, 1, [&] { k_decide<<<1, 32, 0, cs>>>(c, 0); });
-        node(MSC_K_EDIT, r, 0, [&] { k_edit<D><<<grid_for(32ull * h->G.n), TPB, 0, cs>>>(c); });
-        node(MSC_K_REFRESH, r, 0, [&] { k_refresh<D><<<grid_for(h->G.n), TPB, 0, cs>>>(c); });
-        node(MSC_K_REBUILD, r, 0, [&] { k_rebuild<D><<<grid_for(h->G.n), TPB, 0, cs>>>(c); });
-        node(MSC_K_REBUILD, r, 0, [&] { k_clear<<<grid_for(h->G.n), TPB, 0, cs>>>(c); });
+        node(MSC_K_EDIT, r, 0, [&] { k_edit<D><<<g_ed, TPB, 0, cs>>>(c); });
+        node(MSC_K_REFRESH, r, 0, [&] { k_refresh<D><<<g_rf, TPB, 0, cs>>>(c); });
+        node(MSC_K_REBUILD, r, 0, [&] { k_rebuild<D><<<g_rb, TPB, 0, cs>>>(c); });
+        node(MSC_K_REBUILD, r, 0, [&] { k_clear<<<g_cl, TPB, 0, cs>>>(c); });
         node(MSC_K_OTHER, r, 0, [&] { k_end<<<1, 32, 0, cs>>>(c); });
     }
     cudaError_t e = cudaStreamEndCapture(cs, &graph);
@@ -1225,7 +1255,7 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
         c.trace = h->trace.p;
     }
     CK(cudaMemcpyAsync(h->ls.p, &L, sizeof L, cudaMemcpyHostToDevice, s));
-    KL(h, MSC_K_OTHER, s, k_init_g<<<grid_for(h->G.n), TPB, 0, s>>>(h->f.p, h->fhat.p, h->g.p, h->state.p, h->G.n, xi));
+    KL(h, MSC_K_OTHER, s, k_init_g<<<grid_occ((const void *)k_init_g, h->G.n), TPB, 0, s>>>(h->f.p, h->fhat.p, h->g.p, h->state.p, h->G.n, xi));
     CK(cudaGetLastError());
     // sets left over by an earlier call that stopped with an error
     CK(cudaMemsetAsync(h->Tbits.p, 0, h->Tbits.n * 4, s));
@@ -1236,7 +1266,7 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
     LoopState *ls = h->ls.p;
     CK(cudaMemsetAsync(h->Csum.p, 0, h->Csum.n * 4, s));
     CKS(eval_dense<D>(h, h->g.p, h->G, h->code_g.p, s, h->code_f.p, h->Mbits.p, h->Cbits.p, h->Csum.p, o.tier));
-    KL(h, MSC_K_REBUILD, s, k_list_blocks<<<grid_for(h->G.n / 1024 + 1), TPB, 0, s>>>(c));
+    KL(h, MSC_K_REBUILD, s, k_list_blocks<<<grid_occ((const void *)k_list_blocks, h->G.n / 1024 + 1), TPB, 0, s>>>(c));
     h->items[MSC_K_DENSE] += h->G.n;
     RoundGraph rg;
     CKS(build_round_graph<D>(h, c, (unsigned)o.profile & MSC_PROFILE_ALL, rg));
@@ -1267,10 +1297,10 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
         // the S-pass edit round, then back to C-pass rounds
         KL(h, MSC_K_OTHER, s, k_set_halt<<<1, 1, 0, s>>>(ls, 0));
         KL(h, MSC_K_OTHER, s, k_decide<<<1, 32, 0, s>>>(c, 1));
-        KL(h, MSC_K_EDIT, s, k_edit<D><<<grid_for(32ull * h->G.n), TPB, 0, s>>>(c));
-        KL(h, MSC_K_REFRESH, s, k_refresh<D><<<grid_for(h->G.n), TPB, 0, s>>>(c));
-        KL(h, MSC_K_REBUILD, s, k_rebuild<D><<<grid_for(h->G.n), TPB, 0, s>>>(c));
-        KL(h, MSC_K_REBUILD, s, k_clear<<<grid_for(h->G.n), TPB, 0, s>>>(c));
+        KL(h, MSC_K_EDIT, s, k_edit<D><<<grid_occ((const void *)k_edit<D>, 32ull * h->G.n), TPB, 0, s>>>(c));
+        KL(h, MSC_K_REFRESH, s, k_refresh<D><<<grid_occ((const void *)k_refresh<D>, h->G.n), TPB, 0, s>>>(c));
+        KL(h, MSC_K_REBUILD, s, k_rebuild<D><<<grid_occ((const void *)k_rebuild<D>, h->G.n), TPB, 0, s>>>(c));
+        KL(h, MSC_K_REBUILD, s, k_clear<<<grid_occ((const void *)k_clear, h->G.n), TPB, 0, s>>>(c));
         KL(h, MSC_K_OTHER, s, k_end<<<1, 32, 0, s>>>(c));
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(&L, ls, sizeof L, cudaMemcpyDeviceToHost, s));
@@ -1348,8 +1378,8 @@ template <int D> msc_status verify_impl(msc_handle *h, const float *gdev, float 
     CK(code.alloc(h->G.n));
     CKS(eval_dense<D>(h, gdev, h->G, code.p, s));
     CK(cudaMemsetAsync(h->cnt.p, 0, sizeof(Counters), s));
-    KL(h, MSC_K_OTHER, s, k_decode_crit<D><<<grid_for(h->G.n), TPB, 0, s>>>(code.p, h->code_f.p, h->G, nullptr, nullptr, nullptr, 0, h->cnt.p));
-    KL(h, MSC_K_OTHER, s, k_max_abs_err<<<grid_for(h->G.n), TPB, 0, s>>>(h->f.p, gdev, h->G.n, &h->cnt.p->rep[13]));
+    KL(h, MSC_K_OTHER, s, k_decode_crit<D><<<grid_occ((const void *)k_decode_crit<D>, h->G.n), TPB, 0, s>>>(code.p, h->code_f.p, h->G, nullptr, nullptr, nullptr, 0, h->cnt.p));
+    KL(h, MSC_K_OTHER, s, k_max_abs_err<<<grid_occ((const void *)k_max_abs_err, h->G.n), TPB, 0, s>>>(h->f.p, gdev, h->G.n, &h->cnt.p->rep[13]));
     CK(cudaGetLastError());
     Counters hc;
     CK(cudaMemcpyAsync(&hc, h->cnt.p, sizeof hc, cudaMemcpyDeviceToHost, s));
@@ -1370,8 +1400,8 @@ template <int D> msc_status verify_impl(msc_handle *h, const float *gdev, float 
         c.code_g = code.p;
         // per-separatrix pair and end checks
         CK(cudaMemsetAsync(h->cnt.p, 0, sizeof(Counters), s));
-        if (h->n_desc) KL(h, MSC_K_OTHER, s, k_verify_desc<D><<<grid_for(h->n_desc), TPB, 0, s>>>(c, h->seeds_desc.p, h->n_desc));
-        if (h->n_asc) KL(h, MSC_K_OTHER, s, k_verify_asc<D><<<grid_for(h->n_asc), TPB, 0, s>>>(c, h->seeds_asc.p, h->n_asc));
+        if (h->n_desc) KL(h, MSC_K_OTHER, s, k_verify_desc<D><<<grid_occ((const void *)k_verify_desc<D>, h->n_desc), TPB, 0, s>>>(c, h->seeds_desc.p, h->n_desc));
+        if (h->n_asc) KL(h, MSC_K_OTHER, s, k_verify_asc<D><<<grid_occ((const void *)k_verify_asc<D>, h->n_asc), TPB, 0, s>>>(c, h->seeds_asc.p, h->n_asc));
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(&hc, h->cnt.p, sizeof hc, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -1395,7 +1425,7 @@ template <int D> msc_status verify_impl(msc_handle *h, const float *gdev, float 
             CK(cudaMemsetAsync(h->cnt.p, 0, sizeof(Counters), s));
             CK(cudaMemsetAsync(h->vis_tri.p, 0, h->vis_tri.n * 4, s));
             v.ovf_out = h->ovf0.p;
-            if (h->n_ss) KL(h, MSC_K_SEP_UPDATE, s, k_ss_seed<<<grid_for(h->n_ss), TPB, 0, s>>>(v, h->seeds_ss.p, h->n_ss));
+            if (h->n_ss) KL(h, MSC_K_SEP_UPDATE, s, k_ss_seed<<<grid_occ((const void *)k_ss_seed, h->n_ss), TPB, 0, s>>>(v, h->seeds_ss.p, h->n_ss));
             CK(cudaGetLastError());
             uint32_t *in = h->ovf0.p, *o2 = h->ovf1.p;
             for (;;) {
@@ -1406,7 +1436,7 @@ template <int D> msc_status verify_impl(msc_handle *h, const float *gdev, float 
                 const unsigned long long zero = 0;
                 CK(cudaMemcpyAsync(&h->cnt.p->novf, &zero, sizeof zero, cudaMemcpyHostToDevice, s));
                 v.ovf_out = o2;
-                KL(h, MSC_K_SEP_UPDATE, s, k_ss_spill<<<grid_for(hc.novf), TPB, 0, s>>>(v, in, (uint32_t)hc.novf));
+                KL(h, MSC_K_SEP_UPDATE, s, k_ss_spill<<<grid_occ((const void *)k_ss_spill, hc.novf), TPB, 0, s>>>(v, in, (uint32_t)hc.novf));
                 CK(cudaGetLastError());
                 std::swap(in, o2);
             }
@@ -1455,8 +1485,8 @@ msc_status introspect(const float *field, Grid G, int what, int64_t *rows, int32
     CKS(upload_field(nullptr, field, G.n, v.p, cnt.p, s, "field"));
     CKS(eval_dense<D>(nullptr, v.p, G, code.p, s));
     CK(cudaMemsetAsync(cnt.p, 0, 8, s));
-    if (what == 0) k_decode_pairs<D><<<grid_for(G.n), TPB, 0, s>>>(code.p, G, nullptr, cnt.p, 0);
-    else k_decode_crit<D><<<grid_for(G.n), TPB, 0, s>>>(code.p, nullptr, G, nullptr, nullptr, cnt.p, 0, nullptr);
+    if (what == 0) k_decode_pairs<D><<<grid_occ((const void *)k_decode_pairs<D>, G.n), TPB, 0, s>>>(code.p, G, nullptr, cnt.p, 0);
+    else k_decode_crit<D><<<grid_occ((const void *)k_decode_crit<D>, G.n), TPB, 0, s>>>(code.p, nullptr, G, nullptr, nullptr, cnt.p, 0, nullptr);
     CK(cudaGetLastError());
     unsigned long long n = 0;
     CK(cudaMemcpy(&n, cnt.p, 8, cudaMemcpyDeviceToHost));
@@ -1469,8 +1499,8 @@ msc_status introspect(const float *field, Grid G, int what, int64_t *rows, int32
     CK(r.alloc(m * w));
     CK(dd.alloc(m));
     CK(cudaMemsetAsync(cnt.p, 0, 8, s));
-    if (what == 0) k_decode_pairs<D><<<grid_for(G.n), TPB, 0, s>>>(code.p, G, r.p, cnt.p, m);
-    else k_decode_crit<D><<<grid_for(G.n), TPB, 0, s>>>(code.p, nullptr, G, r.p, dd.p, cnt.p, m, nullptr);
+    if (what == 0) k_decode_pairs<D><<<grid_occ((const void *)k_decode_pairs<D>, G.n), TPB, 0, s>>>(code.p, G, r.p, cnt.p, m);
+    else k_decode_crit<D><<<grid_occ((const void *)k_decode_crit<D>, G.n), TPB, 0, s>>>(code.p, nullptr, G, r.p, dd.p, cnt.p, m, nullptr);
     CK(cudaGetLastError());
     CK(cudaMemcpy(rows, r.p, m * w * sizeof(int64_t), cudaMemcpyDeviceToHost));
     if (what == 1 && dims) CK(cudaMemcpy(dims, dd.p, m * sizeof(int32_t), cudaMemcpyDeviceToHost));
@@ -1519,9 +1549,9 @@ msc_status critical_static(const float *field, Grid G, int64_t *rows, int32_t *d
     uint64_t *code = (uint64_t *)scr;
     unsigned long long *count = scr + MSC_STATIC_MAX_VERTICES, *bad = count + 1;
     CK(cudaMemsetAsync(count, 0, 2 * sizeof(unsigned long long), s));
-    k_count_nonfinite<<<grid_for(G.n), TPB, 0, s>>>(field, G.n, bad);
-    k_eval_dense<D><<<grid_for(G.n), TPB, 0, s>>>(field, G, code, nullptr, nullptr, nullptr, nullptr, 4);
-    k_decode_crit<D><<<grid_for(G.n), TPB, 0, s>>>(code, nullptr, G, cap ? rows : nullptr, dims, count, cap, nullptr);
+    k_count_nonfinite<<<grid_occ((const void *)k_count_nonfinite, G.n), TPB, 0, s>>>(field, G.n, bad);
+    k_eval_dense<D><<<grid_occ((const void *)k_eval_dense<D>, G.n), TPB, 0, s>>>(field, G, code, nullptr, nullptr, nullptr, nullptr, 4);
+    k_decode_crit<D><<<grid_occ((const void *)k_decode_crit<D>, G.n), TPB, 0, s>>>(code, nullptr, G, cap ? rows : nullptr, dims, count, cap, nullptr);
     CK(cudaGetLastError());
     unsigned long long hv[2];
     CK(cudaMemcpyAsync(hv, count, sizeof hv, cudaMemcpyDeviceToHost, s));
@@ -1680,8 +1710,8 @@ msc_status msc_apply_edits(const float *f_hat, int nx, int ny, int nz, float xi,
         CK(cudaMemcpyAsync(li.p, e->lossless_idx, e->n_lossless * 8, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(lv.p, e->lossless_val, e->n_lossless * 4, cudaMemcpyHostToDevice, s));
     }
-    k_apply_q<<<grid_for(n), TPB, 0, s>>>(fh.p, qm.p, n, xi / (float)(1 << q_max), g.p);
-    if (e->n_lossless) k_apply_lossless<<<grid_for(e->n_lossless), TPB, 0, s>>>(li.p, lv.p, e->n_lossless, g.p);
+    k_apply_q<<<grid_occ((const void *)k_apply_q, n), TPB, 0, s>>>(fh.p, qm.p, n, xi / (float)(1 << q_max), g.p);
+    if (e->n_lossless) k_apply_lossless<<<grid_occ((const void *)k_apply_lossless, e->n_lossless), TPB, 0, s>>>(li.p, lv.p, e->n_lossless, g.p);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(g_out, g.p, (size_t)n * 4, is_device_ptr(g_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -1744,7 +1774,7 @@ msc_status msc_fix_batch(msc_handle **hs, const float **f_hats, const float *xis
     cudaEvent_t ready = nullptr;
     CK(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
     CK(cudaEventRecord(ready, (cudaStream_t)o.stream));
-    grid_for(1);
+    sm_count();
     std::vector<msc_status> st((size_t)n, MSC_OK);
     std::vector<std::string> msg((size_t)n);
     std::atomic<int> next{0};
