@@ -284,7 +284,7 @@ __host__ __device__ inline unsigned long long csum_words(uint32_t n) { return ((
 // dense gradient of a field; with ref != nullptr also set the bitsets of anchors whose code
 // differs (mbits) and whose critical cells differ (cbits, tier restricted)
 template <int D>
-__global__ void __launch_bounds__(TPB) k_eval_dense(const float *v, Grid G, uint64_t *out, const uint64_t *ref,
+__global__ void __launch_bounds__(TPB, 3) k_eval_dense(const float *v, Grid G, uint64_t *out, const uint64_t *ref,
                                                     uint32_t *mbits, uint32_t *cbits, uint32_t *csum, int tier)
 {
     BLOCK_ROUNDS(b, G.n)
@@ -408,7 +408,7 @@ template <int D> __global__ void k_edit(Ctx c)
     }
 }
 
-template <int D> __global__ void __launch_bounds__(TPB) k_refresh(Ctx c)
+template <int D> __global__ void __launch_bounds__(TPB, 3) k_refresh(Ctx c)
 {
     if (c.ls->halt) return;
     const unsigned long long n = c.cnt->nD;
