@@ -39,7 +39,32 @@ constexpr uint8_t ST_EXACT = 0xF1;   // g == f, stored losslessly (stuck-case re
 struct Grid {
     int nx, ny, nz;
     uint32_t n;
+    // reciprocals of nx and ny: v / d == (v * m) >> s for every v < 2^31 (make_grid)
+    uint64_t mx, my;
+    int sx, sy;
 };
+
+// Division by an invariant integer as a multiply and a shift (Granlund and Montgomery,
+// "Division by invariant integers using multiplication", 1994, Thm 4.2): for 31-bit
+// dividends and 2^(l-1) < d <= 2^l, m = ceil(2^(31+l) / d) gives floor(v / d) =
+// floor(v * m / 2^(31+l)); v * m < 2^63.
+__host__ __device__ inline void div_magic(uint32_t d, uint64_t &m, int &s)
+{
+    int l = 0;
+    while ((1ull << l) < d) l++;
+    s = 31 + l;
+    m = ((1ull << s) + d - 1) / d;
+}
+
+__host__ __device__ inline Grid make_grid(int nx, int ny, int nz)
+{
+    Grid G{};
+    G.nx = nx; G.ny = ny; G.nz = nz;
+    G.n = (uint32_t)((uint64_t)nx * ny * nz);
+    div_magic((uint32_t)nx, G.mx, G.sx);
+    div_magic((uint32_t)ny, G.my, G.sy);
+    return G;
+}
 
 struct Counters {
     unsigned long long ncase, nlive, nT, nX, sumT, sumX;   // targeting pass
@@ -59,6 +84,7 @@ struct LoopState {
     unsigned long long nSD;
     unsigned long long edit_items, refresh_items, cpass_items, cases;
     unsigned long long nblk;  // entries of the C-block list for the next C-pass
+    unsigned long long last_items;   // vertices the last round edited (targets + restores)
 };
 
 // everything a kernel of one job needs (device pointers)
@@ -156,10 +182,11 @@ MSC_HD inline bool sos_lt(float a, uint32_t ia, float b, uint32_t ib)
 
 MSC_HD inline void coords(const Grid &G, uint32_t v, int &x, int &y, int &z)
 {
-    x = (int)(v % (uint32_t)G.nx);
-    uint32_t t = v / (uint32_t)G.nx;
-    y = (int)(t % (uint32_t)G.ny);
-    z = (int)(t / (uint32_t)G.ny);
+    const uint32_t t = (uint32_t)(((uint64_t)v * G.mx) >> G.sx);    // v / nx
+    const uint32_t u = (uint32_t)(((uint64_t)t * G.my) >> G.sy);    // t / ny
+    x = (int)(v - t * (uint32_t)G.nx);
+    y = (int)(t - u * (uint32_t)G.ny);
+    z = (int)u;
 }
 
 MSC_HD inline bool inside(const Grid &G, int x, int y, int z)

@@ -380,6 +380,7 @@ __global__ void k_decide(Ctx c, int kind)
     if (kind) ls->n_s++; else ls->n_c++;
     if (k->nX) ls->n_fb++;
     ls->edit_items += k->nT + k->nX;
+    ls->last_items = k->nT + k->nX;
 }
 
 constexpr int DIRTY_STAGE = 8192;
@@ -1165,6 +1166,7 @@ struct FixResult {
 
 constexpr int GRAPH_ROUNDS = 16;   // C-pass rounds queued per graph launch
 constexpr int BATCH_STREAMS = 8;   // jobs of a batch that run at once, one stream each
+constexpr unsigned long long SMALL_ROUND = 8192;   // edited vertices below which rounds run small grids
 
 // A captured graph of GRAPH_ROUNDS C-pass rounds.  With profiling, every kernel node sits
 // between two event-record nodes; a node pair is counted only if its round ran.
@@ -1182,16 +1184,20 @@ struct RoundGraph {
     }
 };
 
-template <int D> msc_status build_round_graph(msc_handle *h, const Ctx &c, unsigned prof_mask, RoundGraph &rg)
+// small: one block per SM for every kernel (rounds that edit few vertices, where a launch's
+// cost is mostly its blocks starting and finding little to do); otherwise one full wave
+template <int D>
+msc_status build_round_graph(msc_handle *h, const Ctx &c, unsigned prof_mask, bool small, RoundGraph &rg)
 {
     cudaStream_t cs = h->cap_stream;
     cudaGraph_t graph = nullptr;
     // grid sizes (occupancy queries) before the capture begins
-    const int g_ct = grid_occ((const void *)k_ctargets<D>, h->G.n / 8 + 1);
-    const int g_ed = grid_occ((const void *)k_edit<D>, 32ull * h->G.n);
-    const int g_rf = grid_occ((const void *)k_refresh<D>, h->G.n);
-    const int g_rb = grid_occ((const void *)k_rebuild<D>, h->G.n);
-    const int g_cl = grid_occ((const void *)k_clear, h->G.n);
+    auto grid = [&](const void *k, unsigned long long n) { return small ? std::min(sm_count(), grid_occ(k, n)) : grid_occ(k, n); };
+    const int g_ct = grid((const void *)k_ctargets<D>, h->G.n / 8 + 1);
+    const int g_ed = grid((const void *)k_edit<D>, 32ull * h->G.n);
+    const int g_rf = grid((const void *)k_refresh<D>, h->G.n);
+    const int g_rb = grid((const void *)k_rebuild<D>, h->G.n);
+    const int g_cl = grid((const void *)k_clear, h->G.n);
     CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     auto node = [&](int cls, int round, int pre, auto &&launch) {
         if (!((prof_mask >> cls) & 1u)) { launch(); return; }
@@ -1268,11 +1274,15 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
     CKS(eval_dense<D>(h, h->g.p, h->G, h->code_g.p, s, h->code_f.p, h->Mbits.p, h->Cbits.p, h->Csum.p, o.tier));
     KL(h, MSC_K_REBUILD, s, k_list_blocks<<<grid_occ((const void *)k_list_blocks, h->G.n / 1024 + 1), TPB, 0, s>>>(c));
     h->items[MSC_K_DENSE] += h->G.n;
-    RoundGraph rg;
-    CKS(build_round_graph<D>(h, c, (unsigned)o.profile & MSC_PROFILE_ALL, rg));
+    // two captured graphs: full grids for rounds that edit many vertices, one block per SM
+    // for the long tail of rounds that edit few (chosen by the last round's size)
+    RoundGraph rg_big, rg_small;
+    CKS(build_round_graph<D>(h, c, (unsigned)o.profile & MSC_PROFILE_ALL, false, rg_big));
+    CKS(build_round_graph<D>(h, c, (unsigned)o.profile & MSC_PROFILE_ALL, true, rg_small));
     bool sep_built = false;
     unsigned prev_iters = 0;
     for (;;) {
+        RoundGraph &rg = L.iters > 0 && L.last_items < SMALL_ROUND ? rg_small : rg_big;
         CK(cudaGraphLaunch(rg.exec, s));
         CK(cudaMemcpyAsync(&L, ls, sizeof L, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -1618,8 +1628,7 @@ msc_status msc_prepare_original(const float *f, int nx, int ny, int nz, const ms
     EntryStream es(s);
     msc_handle *h = new (std::nothrow) msc_handle();
     if (!h) return fail(MSC_ERR_OOM, "handle allocation failed");
-    h->G.nx = nx; h->G.ny = ny; h->G.nz = nz;
-    h->G.n = (uint32_t)((uint64_t)nx * ny * nz);
+    h->G = make_grid(nx, ny, nz);
     h->D = nz > 1 ? 3 : 2;
     auto run = [&]() -> msc_status {
         CK(h->f.alloc(h->G.n));
@@ -1820,7 +1829,7 @@ msc_status msc_critical_cells_static(const float *field, int nx, int ny, int nz,
     CKS(device_ready());
     if (!is_device_ptr(field) || (cap && (!is_device_ptr(rows) || !is_device_ptr(dims))))
         return fail(MSC_ERR_INVALID_ARG, "field, rows and dims must be device pointers");
-    Grid G{nx, ny, nz, (uint32_t)n};
+    const Grid G = make_grid(nx, ny, nz);
     cudaStream_t s = (cudaStream_t)stream;
     return nz > 1 ? critical_static<3>(field, G, rows, dims, cap, n_out, s)
                   : critical_static<2>(field, G, rows, dims, cap, n_out, s);
@@ -1852,7 +1861,7 @@ msc_status msc_gradient_pairs(const float *field, int nx, int ny, int nz, int64_
     if (!n_out) return fail(MSC_ERR_INVALID_ARG, "n_out is NULL");
     CKS(check_dims(nx, ny, nz));
     CKS(device_ready());
-    Grid G{nx, ny, nz, (uint32_t)((uint64_t)nx * ny * nz)};
+    const Grid G = make_grid(nx, ny, nz);
     return nz > 1 ? introspect<3>(field, G, 0, rows, nullptr, cap, n_out) : introspect<2>(field, G, 0, rows, nullptr, cap, n_out);
 }
 
@@ -1863,7 +1872,7 @@ msc_status msc_critical_cells(const float *field, int nx, int ny, int nz, int64_
     if (!n_out) return fail(MSC_ERR_INVALID_ARG, "n_out is NULL");
     CKS(check_dims(nx, ny, nz));
     CKS(device_ready());
-    Grid G{nx, ny, nz, (uint32_t)((uint64_t)nx * ny * nz)};
+    const Grid G = make_grid(nx, ny, nz);
     return nz > 1 ? introspect<3>(field, G, 1, rows, dims, cap, n_out) : introspect<2>(field, G, 1, rows, dims, cap, n_out);
 }
 
