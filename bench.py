@@ -137,8 +137,9 @@ def class_bytes(cls, tot, n, steps, ndim):
         # read f's code 8 B, write code 8 B, two mismatch bits)
         return steps * n * (12.0 + 20.0) + steps * 2 * bit
     if cls == "cpass":
-        # scan of the critical-difference bitset, then both codes of every listed anchor
-        return tot["launches"] * bit + 16.0 * items
+        # the block summary of the critical-difference bitset (one bit per 1024 anchors), then
+        # both codes of every anchor whose critical cells differ
+        return tot["launches"] * n / 8192.0 + 16.0 * items
     if cls == "edit":
         # per target: its list entry 4 B, f, f_hat, g 12 B and state 1 B read; g 4 B and
         # state 1 B written
@@ -171,6 +172,11 @@ def max_over_ranks(v, dist, device):
     t = torch.tensor([float(v)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def workload_desc(shape, rel, tier):
+    return ("%s %dx%dx%d float32, 5%% constant-plateau block, base = U[-xi,xi] noise, xi=%g*range, tier %d, "
+            "q_max 6" % (WORKLOAD, *tuple(shape)[::-1], rel, tier))
 
 
 def workload(size, rel, rank):
@@ -265,7 +271,8 @@ def run_reference(args):
     v = statistics.median(vals)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": 0, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "%s %d^3, xi=%g*range, tier 4 (oracle on 12^3 sub-blocks)" % (WORKLOAD, args.size, args.rel)},
+            "config": {"workload": workload_desc(f.shape, args.rel, args.tier), "n_vertices": int(f.size),
+                       "sample": base["sample"]},
             "cpu_baseline": dict(base, value=v),
             "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -356,6 +363,15 @@ def main():
         if dom in TRAFFIC_PER_ITEM:
             roof["traffic"] = TRAFFIC_PER_ITEM[dom] * tot["items"] / tot["launches"]
             roof["traffic_source"] = "ncu dram bytes per item at 256^3, scaled by items per launch"
+    # the whole loop against the same peak: every class's algorithmic bytes in the breakdown
+    # step over the step's time (the worklist form counts its own bytes, not a dense pass's)
+    loop_bytes = 0.0
+    for k in msc.KERNEL_CLASSES:
+        b = class_bytes(k, bst[k], n, 1, f.ndim)
+        if b is not None:
+            loop_bytes += b
+    loop_gbs = loop_bytes / (ms_step / 1e3) / 1e9
+
     value = world * 4.0 * n / (ms_step / 1e3) / 1e9
     iters = (ed["n_iters_c"], ed["n_iters_s"])
 
@@ -383,8 +399,7 @@ def main():
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "%s %dx%dx%d float32, 5%% constant-plateau block, base = U[-xi,xi] noise, "
-                                   "xi=%g*range, tier %d, q_max 6" % (WORKLOAD, *f.shape[::-1], args.rel, args.tier),
+            "config": {"workload": workload_desc(f.shape, args.rel, args.tier),
                        "n_vertices": n, "xi": xi, "iters_c": iters[0], "iters_s": iters[1],
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs (%d MB each) exceed L2; no flush" % (4 * n >> 20),
@@ -393,7 +408,8 @@ def main():
                        "kernel_ms_per_step": {k: bst[k]["ms"] for k in msc.KERNEL_CLASSES},
                        "kernel_launches_per_step": {k: bst[k]["launches"] for k in msc.KERNEL_CLASSES},
                        "kernel_items_per_step": {k: bst[k]["items"] for k in msc.KERNEL_CLASSES},
-                       "launches_per_step": launches / args.steps},
+                       "launches_per_step": launches / args.steps,
+                       "loop_algorithmic_GBps": loop_gbs, "loop_frac_of_peak": loop_gbs / peak},
             "roofline": roof, "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
         }
         if not args.no_cpu and world == 1:
