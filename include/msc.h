@@ -172,6 +172,28 @@ msc_status msc_fix(msc_handle *h, const float *f_hat, float xi, const msc_option
 msc_status msc_apply_edits(const float *f_hat, int nx, int ny, int nz, float xi, int q_max,
                            const msc_edits *edits, float *g_out);
 
+/* Sec. 4.7: the edit record as a compact byte stream (the "fixed number of bits per
+ * quantised count" that the paper then hands to a dictionary coder; no such coder here).
+ * Layout, little-endian: a 32-byte header ("MSCE", version 1, q_max, b, 0, n_vertices u64,
+ * n_lossless u64, 0 u64); the q-map at b bits per vertex, b the least number of bits that
+ * holds q_max + 2 values, in groups of 8 vertices stored as b bytes (vertex 8k+j in bits
+ * [j*b, j*b+b) of group k's little-endian integer), a lossless vertex written as 2^b - 1;
+ * then the n_lossless float32 values in increasing vertex order (the vertices themselves are
+ * implied by the escape codes).  Size: 32 + ceil(n/8)*b + 4*n_lossless bytes. */
+uint64_t msc_packed_bytes(uint64_t n_vertices, uint64_t n_lossless, int q_max);
+
+/* Pack edits (as returned by msc_fix with the same q_max) into out (host or device, cap
+ * bytes); *n_out receives the record's size.  out == NULL with cap == 0 only reports the
+ * size.  Errors: MSC_ERR_INVALID_ARG for a short buffer, a count above q_max, or
+ * lossless_idx not listing exactly the q-map's lossless vertices in increasing order. */
+msc_status msc_pack_edits(const msc_edits *e, int q_max, uint8_t *out, uint64_t cap, uint64_t *n_out);
+
+/* Unpack a record of size bytes (host or device) into *out (host arrays, free with
+ * msc_free_edits after any return) and its q_max.  n_quant is recomputed; the iteration
+ * counts and the trace are not part of the record and read 0.  Errors: MSC_ERR_INVALID_ARG
+ * for a malformed record. */
+msc_status msc_unpack_edits(const uint8_t *buf, uint64_t size, msc_edits *out, int *q_max);
+
 /* Sec. 5.1 metrics: compare the MSC of g with the handle's original (critical cells by
  * dimension, every separatrix pair, separatrix terminals) and measure max |g - f|.
  * g: host or device.  Separatrix counts are computed only when the critical cells agree. */

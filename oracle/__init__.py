@@ -209,3 +209,38 @@ def edits_from_state(f, fhat, xi, state, g):
     q_map = np.where(lossless, 0xFF, st).astype(np.uint8)
     idx = np.nonzero(lossless)[0].astype(np.int64)
     return q_map, idx, gg[idx].copy()
+
+
+def packed_bytes(n, n_lossless, q_max):
+    """Size of the packed edit record (Sec. 4.7)."""
+    lib = _load()
+    lib.orc_packed_bytes.restype = ctypes.c_int64
+    return int(lib.orc_packed_bytes(ctypes.c_int64(n), ctypes.c_int64(n_lossless), q_max))
+
+
+def pack_edits(q_map, q_max, lossless_val):
+    """The edit record as bytes: header, q-map at a fixed number of bits per vertex, lossless
+    values in increasing vertex order."""
+    lib = _load()
+    qm = np.ascontiguousarray(q_map, dtype=np.uint8).reshape(-1)
+    lv = np.ascontiguousarray(lossless_val, dtype=np.float32).reshape(-1)
+    size = packed_bytes(qm.size, lv.size, q_max)
+    out = np.zeros(size, np.uint8)
+    n_out = ctypes.c_int64(0)
+    _check(lib.orc_pack_edits(_p(qm), ctypes.c_int64(qm.size), q_max, _p(lv), ctypes.c_int64(lv.size), _p(out),
+                              ctypes.c_int64(size), ctypes.byref(n_out)), "pack_edits")
+    return out
+
+
+def unpack_edits(buf):
+    """Inverse of pack_edits: (q_map, lossless_idx, lossless_val, q_max)."""
+    lib = _load()
+    b = np.ascontiguousarray(buf, dtype=np.uint8).reshape(-1)
+    n, nl, qmax = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int(0)
+    _check(lib.orc_packed_header(_p(b), ctypes.c_int64(b.size), ctypes.byref(n), ctypes.byref(nl),
+                                 ctypes.byref(qmax)), "unpack_edits")
+    qm = np.zeros(n.value, np.uint8)
+    li = np.zeros(nl.value, np.int64)
+    lv = np.zeros(nl.value, np.float32)
+    _check(lib.orc_unpack_edits(_p(b), ctypes.c_int64(b.size), _p(qm), _p(li), _p(lv)), "unpack_edits")
+    return qm, li, lv, qmax.value

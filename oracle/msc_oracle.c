@@ -967,3 +967,106 @@ int orc_apply_edits(const float *fhat, int64_t n, float xi, int qmax, const uint
     for (i64 k = 0; k < n_lossless; k++) g_out[lossless_idx[k]] = lossless_val[k];
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------- */
+/* packed edit record (Sec. 4.7: quantised counts as a fixed-bit bitstream)    */
+/* ------------------------------------------------------------------------- */
+/* Layout, little-endian:
+ *   32-byte header: "MSCE", version 1, q_max, b (bits per vertex), 0, n_vertices (u64),
+ *                   n_lossless (u64), 0 (u64);
+ *   the q-map, b bits per vertex, in groups of 8 vertices stored as b bytes each: vertex 8k+j
+ *   of group k is the bit field [j*b, j*b + b) of that group's little-endian integer;
+ *   a quantised count is stored as itself (0..q_max), a lossless vertex as 2^b - 1;
+ *   b is the least number of bits that holds q_max + 2 distinct values;
+ *   the lossless values (float32), one per lossless vertex, in increasing vertex order. */
+static int pack_bits(int qmax)
+{
+    int b = 1;
+    while ((1 << b) < qmax + 2) b++;
+    return b;
+}
+
+int64_t orc_packed_bytes(int64_t n, int64_t n_lossless, int qmax)
+{
+    return 32 + ((n + 7) / 8) * pack_bits(qmax) + 4 * n_lossless;
+}
+
+static void put_u64(uint8_t *p, uint64_t v)
+{
+    for (int i = 0; i < 8; i++) p[i] = (uint8_t)(v >> (8 * i));
+}
+
+static uint64_t get_u64(const uint8_t *p)
+{
+    uint64_t v = 0;
+    for (int i = 0; i < 8; i++) v |= (uint64_t)p[i] << (8 * i);
+    return v;
+}
+
+int orc_pack_edits(const uint8_t *q_map, int64_t n, int qmax, const float *lossless_val, int64_t n_lossless,
+                   uint8_t *out, int64_t cap, int64_t *n_out)
+{
+    if (qmax < 1 || qmax > 7 || n < 0 || n_lossless < 0) return ORC_ERR_ARG;
+    int b = pack_bits(qmax);
+    int64_t size = orc_packed_bytes(n, n_lossless, qmax);
+    *n_out = size;
+    if (cap < size) return ORC_ERR_ARG;
+    memset(out, 0, (size_t)size);
+    out[0] = 'M'; out[1] = 'S'; out[2] = 'C'; out[3] = 'E';
+    out[4] = 1; out[5] = (uint8_t)qmax; out[6] = (uint8_t)b; out[7] = 0;
+    put_u64(out + 8, (uint64_t)n);
+    put_u64(out + 16, (uint64_t)n_lossless);
+    uint8_t *bits = out + 32;
+    int64_t seen = 0;
+    for (int64_t v = 0; v < n; v++) {
+        unsigned code;
+        if (q_map[v] == 0xFF) { code = (1u << b) - 1; seen++; }
+        else if (q_map[v] <= qmax) code = q_map[v];
+        else return ORC_ERR_ARG;
+        int64_t bit = (v / 8) * 8 * b + (v % 8) * b;     /* group k starts at bit 8*b*k */
+        for (int i = 0; i < b; i++)
+            if ((code >> i) & 1u) bits[(bit + i) / 8] |= (uint8_t)(1u << ((bit + i) % 8));
+    }
+    if (seen != n_lossless) return ORC_ERR_ARG;
+    memcpy(bits + ((n + 7) / 8) * b, lossless_val, (size_t)n_lossless * 4);
+    return ORC_OK;
+}
+
+/* header fields of a packed record; returns ORC_ERR_ARG if it is not one */
+int orc_packed_header(const uint8_t *buf, int64_t size, int64_t *n, int64_t *n_lossless, int *qmax)
+{
+    if (size < 32 || memcmp(buf, "MSCE", 4) != 0 || buf[4] != 1) return ORC_ERR_ARG;
+    *qmax = buf[5];
+    *n = (int64_t)get_u64(buf + 8);
+    *n_lossless = (int64_t)get_u64(buf + 16);
+    if (*qmax < 1 || *qmax > 7 || buf[6] != pack_bits(*qmax)) return ORC_ERR_ARG;
+    if (orc_packed_bytes(*n, *n_lossless, *qmax) != size) return ORC_ERR_ARG;
+    return ORC_OK;
+}
+
+int orc_unpack_edits(const uint8_t *buf, int64_t size, uint8_t *q_map, int64_t *lossless_idx, float *lossless_val)
+{
+    int64_t n, nl;
+    int qmax;
+    if (orc_packed_header(buf, size, &n, &nl, &qmax) != ORC_OK) return ORC_ERR_ARG;
+    int b = pack_bits(qmax);
+    const uint8_t *bits = buf + 32;
+    int64_t k = 0;
+    for (int64_t v = 0; v < n; v++) {
+        int64_t bit = (v / 8) * 8 * b + (v % 8) * b;
+        unsigned code = 0;
+        for (int i = 0; i < b; i++) code |= (unsigned)((bits[(bit + i) / 8] >> ((bit + i) % 8)) & 1u) << i;
+        if (code == (1u << b) - 1) {
+            if (k >= nl) return ORC_ERR_ARG;
+            q_map[v] = 0xFF;
+            lossless_idx[k++] = v;
+        } else if ((int)code <= qmax) {
+            q_map[v] = (uint8_t)code;
+        } else {
+            return ORC_ERR_ARG;
+        }
+    }
+    if (k != nl) return ORC_ERR_ARG;
+    memcpy(lossless_val, bits + ((n + 7) / 8) * b, (size_t)nl * 4);
+    return ORC_OK;
+}

@@ -716,8 +716,70 @@ __global__ void k_lossless_write(const uint8_t *qmap, const float *g, uint32_t n
     if (flag) {
         const uint32_t pos = offsets[blockIdx.x] + warp_sums[wid] + __popc(ballot & ((1u << lane) - 1u));
         idx[pos] = i;
-        val[pos] = g[i];
+        if (val) val[pos] = g[i];
     }
+}
+
+// ---- packed edit record (Sec. 4.7): b bits per vertex in groups of 8 vertices (b bytes),
+// vertex 8k+j of group k in bits [j*b, j*b+b) of the group's little-endian integer; a
+// lossless vertex is the escape code 2^b - 1
+__global__ void k_pack_q(const uint8_t *qmap, uint64_t n, int b, uint8_t *bits)
+{
+    const uint64_t groups = (n + 7) / 8;
+    const uint32_t esc = (1u << b) - 1u;
+    GRID_STRIDE(k, groups)
+    {
+        uint32_t acc = 0;
+        for (int j = 0; j < 8; j++) {
+            const uint64_t v = 8 * k + j;
+            if (v >= n) break;
+            const uint32_t q = qmap[v];
+            acc |= (q == MSC_QMAP_LOSSLESS ? esc : q) << (j * b);
+        }
+        for (int i = 0; i < b; i++) bits[k * b + i] = (uint8_t)(acc >> (8 * i));
+    }
+}
+
+__global__ void k_unpack_q(const uint8_t *bits, uint64_t n, int b, int qmax, uint8_t *qmap, unsigned long long *bad)
+{
+    const uint64_t groups = (n + 7) / 8;
+    const uint32_t esc = (1u << b) - 1u;
+    GRID_STRIDE(k, groups)
+    {
+        uint32_t acc = 0;
+        for (int i = 0; i < b; i++) acc |= (uint32_t)bits[k * b + i] << (8 * i);
+        for (int j = 0; j < 8; j++) {
+            const uint64_t v = 8 * k + j;
+            if (v >= n) break;
+            const uint32_t code = (acc >> (j * b)) & esc;
+            if (code != esc && (int)code > qmax) atomicAdd(bad, 1ull);
+            qmap[v] = code == esc ? (uint8_t)MSC_QMAP_LOSSLESS : (uint8_t)code;
+        }
+    }
+}
+
+// per-block (1024 threads) counts of lossless entries of a q-map, and the quantised total
+__global__ void k_qcount(const uint8_t *qmap, uint64_t n, int qmax, uint32_t *block_counts,
+                         unsigned long long *nquant, unsigned long long *bad)
+{
+    const unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    const uint8_t q = i < n ? qmap[i] : 0;
+    const int lossless = i < n && q == MSC_QMAP_LOSSLESS;
+    if (i < n && !lossless && q > qmax) atomicAdd(bad, 1ull);
+    const int c = __syncthreads_count(lossless);
+    const int nq = __syncthreads_count(i < n && !lossless && q > 0);
+    if (threadIdx.x == 0) {
+        block_counts[blockIdx.x] = (uint32_t)c;
+        if (nq) atomicAdd(nquant, (unsigned long long)nq);
+    }
+}
+
+// positions where two index lists differ
+__global__ void k_count_diff(const uint64_t *a, const uint64_t *b, uint64_t n, unsigned long long *bad)
+{
+    unsigned long long local = 0;
+    GRID_STRIDE(i, n) local += a[i] != b[i];
+    if (local) atomicAdd(bad, local);
 }
 
 // decompression side: g = f_hat - fl(q * step) (one rounding each), lossless values scattered
@@ -1520,6 +1582,65 @@ msc_status introspect(const float *field, Grid G, int what, int64_t *rows, int32
 }  // namespace
 
 // ------------------------------------------------------------------------------------
+// packed edit record (Sec. 4.7)
+// ------------------------------------------------------------------------------------
+namespace {
+int pack_bits(int qmax)
+{
+    int b = 1;
+    while ((1 << b) < qmax + 2) b++;
+    return b;
+}
+
+uint64_t packed_size(uint64_t n, uint64_t nl, int qmax) { return 32 + ((n + 7) / 8) * pack_bits(qmax) + 4 * nl; }
+
+void put_u64(uint8_t *p, uint64_t v)
+{
+    for (int i = 0; i < 8; i++) p[i] = (uint8_t)(v >> (8 * i));
+}
+
+uint64_t get_u64(const uint8_t *p)
+{
+    uint64_t v = 0;
+    for (int i = 0; i < 8; i++) v |= (uint64_t)p[i] << (8 * i);
+    return v;
+}
+
+// bytes between host and/or device buffers
+cudaMemcpyKind copy_kind(const void *dst, const void *src)
+{
+    const bool dd = is_device_ptr(dst), sd = is_device_ptr(src);
+    return dd ? (sd ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice) : (sd ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost);
+}
+
+// the lossless positions of a device q-map in increasing order (idx, device), their number,
+// and the number of quantised (non-zero) counts; counts above q_max are an error
+msc_status lossless_positions(const uint8_t *qm, uint64_t n, int qmax, DevBuf<uint64_t> &idx, uint64_t *nl,
+                              uint64_t *nq, cudaStream_t s)
+{
+    const uint32_t nb = (uint32_t)((n + 1023) / 1024);
+    DevBuf<uint32_t> bc;
+    DevBuf<unsigned long long> tot;
+    CK(bc.alloc(nb));
+    CK(tot.alloc(3));
+    CK(cudaMemsetAsync(tot.p, 0, 3 * sizeof(unsigned long long), s));
+    k_qcount<<<nb, 1024, 0, s>>>(qm, n, qmax, bc.p, tot.p + 1, tot.p + 2);
+    k_scan_blocks<<<1, 1024, 0, s>>>(bc.p, nb, tot.p);
+    CK(cudaGetLastError());
+    unsigned long long t[3];
+    CK(cudaMemcpyAsync(t, tot.p, sizeof t, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (t[2]) return fail(MSC_ERR_INVALID_ARG, "q-map holds %llu counts above q_max = %d", t[2], qmax);
+    CK(idx.alloc(t[0]));
+    k_lossless_write<<<nb, 1024, 0, s>>>(qm, nullptr, (uint32_t)n, bc.p, idx.p, nullptr);
+    CK(cudaGetLastError());
+    *nl = t[0];
+    *nq = t[1];
+    return MSC_OK;
+}
+}  // namespace
+
+// ------------------------------------------------------------------------------------
 // fixed scratch of msc_critical_cells_static: gradient codes of up to
 // MSC_STATIC_MAX_VERTICES anchors, then [0] the row count, [1] the non-finite count
 // ------------------------------------------------------------------------------------
@@ -1812,6 +1933,120 @@ msc_status msc_fix_batch(msc_handle **hs, const float **f_hats, const float *xis
     cudaEventDestroy(ready);
     for (int i = 0; i < n; i++)
         if (st[(size_t)i] != MSC_OK) return fail(st[(size_t)i], "batch job %d: %s", i, msg[(size_t)i].c_str());
+    return MSC_OK;
+}
+
+uint64_t msc_packed_bytes(uint64_t n_vertices, uint64_t n_lossless, int q_max)
+{
+    if (q_max < 1 || q_max > 7) return 0;
+    return packed_size(n_vertices, n_lossless, q_max);
+}
+
+msc_status msc_pack_edits(const msc_edits *e, int q_max, uint8_t *out, uint64_t cap, uint64_t *n_out)
+{
+    g_last_error.clear();
+    if (!e || !n_out) return fail(MSC_ERR_INVALID_ARG, "edits and n_out must be non-NULL");
+    if (q_max < 1 || q_max > 7) return fail(MSC_ERR_INVALID_ARG, "q_max must be in 1..7");
+    const uint64_t n = e->n_vertices, nl = e->n_lossless;
+    if (n == 0 || n >= (1ull << 31) || !e->q_map) return fail(MSC_ERR_INVALID_ARG, "edits hold no q-map");
+    if (nl && (!e->lossless_idx || !e->lossless_val)) return fail(MSC_ERR_INVALID_ARG, "edits lack their lossless values");
+    const int b = pack_bits(q_max);
+    const uint64_t size = packed_size(n, nl, q_max), nbits = ((n + 7) / 8) * b;
+    *n_out = size;
+    if (!out && cap == 0) return MSC_OK;   // size query
+    if (!out || cap < size) return fail(MSC_ERR_INVALID_ARG, "output buffer holds %llu bytes, the record needs %llu",
+                                        (unsigned long long)cap, (unsigned long long)size);
+    CKS(device_ready());
+    cudaStream_t s = nullptr;
+    EntryStream es(s);
+    DevBuf<uint8_t> qm, bits;
+    DevBuf<uint64_t> idx, given;
+    CK(qm.alloc(n));
+    CK(cudaMemcpyAsync(qm.p, e->q_map, n, copy_kind(qm.p, e->q_map), s));
+    uint64_t cnt = 0, nq = 0;
+    CKS(lossless_positions(qm.p, n, q_max, idx, &cnt, &nq, s));
+    if (cnt != nl) return fail(MSC_ERR_INVALID_ARG, "q-map marks %llu lossless vertices, edits list %llu",
+                               (unsigned long long)cnt, (unsigned long long)nl);
+    if (nl) {
+        DevBuf<unsigned long long> bad;
+        CK(bad.alloc(1));
+        CK(cudaMemsetAsync(bad.p, 0, 8, s));
+        CK(given.alloc(nl));
+        CK(cudaMemcpyAsync(given.p, e->lossless_idx, nl * 8, copy_kind(given.p, e->lossless_idx), s));
+        k_count_diff<<<grid_occ((const void *)k_count_diff, nl), TPB, 0, s>>>(idx.p, given.p, nl, bad.p);
+        CK(cudaGetLastError());
+        unsigned long long nbad = 0;
+        CK(cudaMemcpyAsync(&nbad, bad.p, 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (nbad) return fail(MSC_ERR_INVALID_ARG, "lossless_idx does not list the lossless vertices in increasing order");
+    }
+    CK(bits.alloc(nbits));
+    k_pack_q<<<grid_occ((const void *)k_pack_q, (n + 7) / 8), TPB, 0, s>>>(qm.p, n, b, bits.p);
+    CK(cudaGetLastError());
+    uint8_t head[32] = {'M', 'S', 'C', 'E', 1, (uint8_t)q_max, (uint8_t)b, 0};
+    put_u64(head + 8, n);
+    put_u64(head + 16, nl);
+    CK(cudaMemcpyAsync(out, head, 32, copy_kind(out, head), s));
+    CK(cudaMemcpyAsync(out + 32, bits.p, nbits, copy_kind(out + 32, bits.p), s));
+    if (nl) CK(cudaMemcpyAsync(out + 32 + nbits, e->lossless_val, nl * 4, copy_kind(out + 32 + nbits, e->lossless_val), s));
+    CK(cudaStreamSynchronize(s));
+    return MSC_OK;
+}
+
+msc_status msc_unpack_edits(const uint8_t *buf, uint64_t size, msc_edits *out, int *q_max)
+{
+    g_last_error.clear();
+    if (!buf || !out || !q_max) return fail(MSC_ERR_INVALID_ARG, "buf, out and q_max must be non-NULL");
+    memset(out, 0, sizeof *out);
+    if (size < 32) return fail(MSC_ERR_INVALID_ARG, "not a packed edit record (%llu bytes)", (unsigned long long)size);
+    CKS(device_ready());
+    cudaStream_t s = nullptr;
+    EntryStream es(s);
+    uint8_t head[32];
+    CK(cudaMemcpyAsync(head, buf, 32, copy_kind(head, buf), s));
+    CK(cudaStreamSynchronize(s));
+    const int qm_max = head[5], b = head[6];
+    const uint64_t n = get_u64(head + 8), nl = get_u64(head + 16);
+    if (memcmp(head, "MSCE", 4) != 0 || head[4] != 1 || qm_max < 1 || qm_max > 7 || b != pack_bits(qm_max))
+        return fail(MSC_ERR_INVALID_ARG, "not a packed edit record (bad header)");
+    if (n == 0 || n >= (1ull << 31) || nl > n || packed_size(n, nl, qm_max) != size)
+        return fail(MSC_ERR_INVALID_ARG, "packed edit record of %llu bytes does not match its header", (unsigned long long)size);
+    const uint64_t nbits = ((n + 7) / 8) * b;
+    DevBuf<uint8_t> bits, qm;
+    DevBuf<uint64_t> idx;
+    DevBuf<unsigned long long> bad;
+    CK(bits.alloc(nbits));
+    CK(qm.alloc(n));
+    CK(bad.alloc(1));
+    CK(cudaMemcpyAsync(bits.p, buf + 32, nbits, copy_kind(bits.p, buf + 32), s));
+    CK(cudaMemsetAsync(bad.p, 0, 8, s));
+    k_unpack_q<<<grid_occ((const void *)k_unpack_q, (n + 7) / 8), TPB, 0, s>>>(bits.p, n, b, qm_max, qm.p, bad.p);
+    CK(cudaGetLastError());
+    unsigned long long nbad = 0;
+    CK(cudaMemcpyAsync(&nbad, bad.p, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (nbad) return fail(MSC_ERR_INVALID_ARG, "packed q-map holds %llu codes above q_max", nbad);
+    uint64_t cnt = 0, nq = 0;
+    CKS(lossless_positions(qm.p, n, qm_max, idx, &cnt, &nq, s));
+    if (cnt != nl) return fail(MSC_ERR_INVALID_ARG, "packed q-map marks %llu lossless vertices, header says %llu",
+                               (unsigned long long)cnt, (unsigned long long)nl);
+    out->q_map = (uint8_t *)malloc(n);
+    out->lossless_idx = (uint64_t *)malloc(nl ? nl * 8 : 8);
+    out->lossless_val = (float *)malloc(nl ? nl * 4 : 4);
+    if (!out->q_map || !out->lossless_idx || !out->lossless_val) {
+        msc_free_edits(out);
+        return fail(MSC_ERR_OOM, "host allocation of edits failed");
+    }
+    CK(cudaMemcpyAsync(out->q_map, qm.p, n, cudaMemcpyDeviceToHost, s));
+    if (nl) {
+        CK(cudaMemcpyAsync(out->lossless_idx, idx.p, nl * 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(out->lossless_val, buf + 32 + nbits, nl * 4, copy_kind(out->lossless_val, buf + 32 + nbits), s));
+    }
+    CK(cudaStreamSynchronize(s));
+    out->n_vertices = n;
+    out->n_lossless = nl;
+    out->n_quant = nq;
+    *q_max = qm_max;
     return MSC_OK;
 }
 

@@ -126,13 +126,18 @@ def load():
     lib.msc_server_wait.argtypes = [vp, u64, ctypes.POINTER(Edits), ctypes.POINTER(JobInfo)]
     lib.msc_server_destroy.argtypes = [vp]
     lib.msc_server_destroy.restype = None
+    lib.msc_packed_bytes.argtypes = [u64, u64, i]
+    lib.msc_packed_bytes.restype = u64
+    lib.msc_pack_edits.argtypes = [ctypes.POINTER(Edits), i, vp, u64, ctypes.POINTER(u64)]
+    lib.msc_unpack_edits.argtypes = [vp, u64, ctypes.POINTER(Edits), ctypes.POINTER(i)]
     lib.msc_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
     lib.msc_reset_stats.argtypes = [vp]
     lib.msc_device_bytes.argtypes = [i, i, i]
     lib.msc_device_bytes.restype = u64
     for name in ("msc_prepare_original", "msc_fix", "msc_apply_edits", "msc_verify", "msc_fix_batch",
                  "msc_gradient_pairs", "msc_critical_cells", "msc_critical_cells_static", "msc_get_stats",
-                 "msc_reset_stats", "msc_server_create", "msc_server_submit", "msc_server_wait"):
+                 "msc_reset_stats", "msc_server_create", "msc_server_submit", "msc_server_wait", "msc_pack_edits",
+                 "msc_unpack_edits"):
         getattr(lib, name).restype = i
     _lib = lib
     return lib
@@ -280,6 +285,49 @@ def apply_edits(f_hat, xi, q_max, edits, g_out=None):
     gp, gkeep = _ptr(g_out)
     _check(lib.msc_apply_edits(p, nx, ny, nz, ctypes.c_float(xi), q_max, ctypes.byref(e), gp))
     return g_out
+
+
+def _edits_struct(edits):
+    """An Edits view of an edits dict (the arrays stay owned by the dict)."""
+    qm = np.ascontiguousarray(edits["q_map"], dtype=np.uint8).reshape(-1)
+    li = np.ascontiguousarray(edits["lossless_idx"], dtype=np.uint64)
+    lv = np.ascontiguousarray(edits["lossless_val"], dtype=np.float32)
+    e = Edits()
+    e.n_vertices = qm.size
+    e.n_lossless = li.size
+    e.q_map = qm.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    e.lossless_idx = li.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+    e.lossless_val = lv.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    return e, (qm, li, lv)
+
+
+def packed_bytes(n_vertices, n_lossless, q_max):
+    return int(load().msc_packed_bytes(n_vertices, n_lossless, q_max))
+
+
+def pack_edits(edits, q_max):
+    """msc_pack_edits: the edit record as a uint8 array (Sec. 4.7 fixed-bit q-map)."""
+    lib = load()
+    e, keep = _edits_struct(edits)
+    n = ctypes.c_uint64(0)
+    _check(lib.msc_pack_edits(ctypes.byref(e), q_max, None, 0, ctypes.byref(n)))
+    out = np.zeros(n.value, np.uint8)
+    _check(lib.msc_pack_edits(ctypes.byref(e), q_max, out.ctypes.data_as(ctypes.c_void_p), out.size, ctypes.byref(n)))
+    return out
+
+
+def unpack_edits(buf, shape):
+    """msc_unpack_edits: (edits dict, q_max) from a packed record."""
+    lib = load()
+    b = np.ascontiguousarray(buf, dtype=np.uint8).reshape(-1)
+    e = Edits()
+    q = ctypes.c_int(0)
+    try:
+        _check(lib.msc_unpack_edits(b.ctypes.data_as(ctypes.c_void_p), b.size, ctypes.byref(e), ctypes.byref(q)))
+        out = _edits_to_py(e, tuple(shape))
+    finally:
+        lib.msc_free_edits(ctypes.byref(e))
+    return out, q.value
 
 
 def fix_batch(handles, f_hats, xis, g_outs=None, **kw):

@@ -654,3 +654,54 @@ def test_invalid_inputs_rejected():
     assert oracle.fix(f, bad, 0.1)["status"] == 1
     assert oracle.fix(f, f, 0.0)["status"] == 1
     assert oracle.fix(f, f, 0.1, q_max=8)["status"] == 1
+
+
+# --------------------------------------------------------------------------------------
+# packed edit record (Sec. 4.7: the quantised counts as a fixed-bit bitstream)
+# --------------------------------------------------------------------------------------
+
+def test_packed_record_hand_built():
+    """q_max = 6 needs 3 bits (values 0..6 and the lossless escape 7).  Nine vertices with
+    counts 0,1,2,3,4,5,6, lossless, 1 and one lossless value 1.5 give: the header, group 0 as
+    the 24-bit integer 0 | 1<<3 | 2<<6 | 3<<9 | 4<<12 | 5<<15 | 6<<18 | 7<<21 = 0xFAC688 in three
+    little-endian bytes, group 1 = 1, then 1.5f = 0x3FC00000."""
+    qm = np.array([0, 1, 2, 3, 4, 5, 6, 0xFF, 1], np.uint8)
+    out = oracle.pack_edits(qm, 6, np.float32([1.5]))
+    head = b"MSCE" + bytes([1, 6, 3, 0]) + (9).to_bytes(8, "little") + (1).to_bytes(8, "little") + bytes(8)
+    body = bytes([0x88, 0xC6, 0xFA, 0x01, 0x00, 0x00]) + bytes([0x00, 0x00, 0xC0, 0x3F])
+    assert out.tobytes() == head + body
+    assert oracle.packed_bytes(9, 1, 6) == len(head + body)
+
+
+@pytest.mark.parametrize("q_max", [1, 2, 3, 6, 7])
+def test_packed_record_round_trip(q_max):
+    rng = np.random.default_rng(40 + q_max)
+    n = 1000 + q_max
+    qm = rng.integers(0, q_max + 1, n).astype(np.uint8)
+    qm[rng.random(n) < 0.1] = 0xFF
+    lv = rng.standard_normal(int((qm == 0xFF).sum())).astype(np.float32)
+    buf = oracle.pack_edits(qm, q_max, lv)
+    bits = {1: 2, 2: 2, 3: 3, 6: 3, 7: 4}[q_max]
+    assert buf.size == 32 + ((n + 7) // 8) * bits + 4 * lv.size
+    qm2, li2, lv2, q2 = oracle.unpack_edits(buf)
+    assert q2 == q_max and np.array_equal(qm2, qm)
+    assert np.array_equal(li2, np.nonzero(qm == 0xFF)[0]) and np.array_equal(lv2.view(np.uint32), lv.view(np.uint32))
+
+
+def test_packed_record_rejects_bad_input():
+    with pytest.raises(RuntimeError):
+        oracle.pack_edits(np.array([0, 9], np.uint8), 6, np.zeros(0, np.float32))   # count above q_max
+    with pytest.raises(RuntimeError):
+        oracle.pack_edits(np.array([0xFF], np.uint8), 6, np.zeros(0, np.float32))   # missing value
+    buf = oracle.pack_edits(np.array([1, 2], np.uint8), 6, np.zeros(0, np.float32))
+    with pytest.raises(RuntimeError):
+        oracle.unpack_edits(buf[:-1])
+
+
+def test_packed_record_rebuilds_the_fix():
+    f, fh, xi, _ = synth.config_case("gauss2d", seed=3)
+    r = oracle.fix(f, fh, xi, tier=3)
+    qm, li, lv = oracle.edits_from_state(f, fh, xi, r["state"], r["g"])
+    qm2, li2, lv2, q = oracle.unpack_edits(oracle.pack_edits(qm, 6, lv))
+    g = oracle.apply_edits(fh, xi, q, qm2, li2, lv2)
+    assert np.array_equal(g.view(np.uint32), r["g"].view(np.uint32))
