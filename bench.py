@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving replay")
+    ap.add_argument("--study", choices=["qmax", "extreme"], default=None,
+                    help="instead of the benchmark: the q_max sweep or the extreme-noise study")
     return ap.parse_args()
 
 
@@ -256,6 +258,50 @@ def serving_leg(msc, n_req=128, slots=8):
     return out
 
 
+def run_study(args, msc):
+    """One JSON line per study.  qmax: the 512^3 workload's bound at a 256^3 size, fixed with
+    q_max = 2..7 (iterations, fix time, quantised and lossless vertices, packed record size
+    against 8-byte float edits).  extreme: the flat-base white-noise field at growing sizes
+    (iterations, fix time, share of vertices edited)."""
+    import torch
+    from paper_2409_17346_gb300 import synth
+
+    def timed_fix(f, fh, xi, **kw):
+        fd, fhd = torch.from_numpy(f).cuda(), torch.from_numpy(fh).cuda()
+        gd = torch.empty_like(fd)
+        h = msc.Handle(fd)
+        h.fix(fhd, xi, g_out=gd, **kw)                      # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, ed = h.fix(fhd, xi, g_out=gd, **kw)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        rep = h.verify(gd, xi)
+        h.close()
+        return ed, dt, rep
+
+    rows = []
+    if args.study == "qmax":
+        f, fh, xi, _ = synth.config_case(WORKLOAD, size=256, rel=args.rel)
+        for q in range(2, 8):
+            ed, dt, rep = timed_fix(f, fh, xi, tier=args.tier, q_max=q)
+            packed = msc.packed_bytes(f.size, ed["n_lossless"], q)
+            edited = ed["n_quant"] + ed["n_lossless"]
+            rows.append({"q_max": q, "iters_c": ed["n_iters_c"], "iters_s": ed["n_iters_s"], "fix_s": dt,
+                         "n_quant": ed["n_quant"], "n_lossless": ed["n_lossless"], "packed_bytes": packed,
+                         "float_edit_bytes": 8 * edited, "verify_passed": rep["passed"]})
+        desc = "q_max sweep: %s 256^3, xi=%g*range, tier %d" % (WORKLOAD, args.rel, args.tier)
+    else:
+        for n in (256, 512, 1024, 2048, 4096):
+            f, fh, xi = synth.extreme_noise_2d(n)
+            ed, dt, rep = timed_fix(f, fh, xi, tier=args.tier)
+            rows.append({"size": "%dx%d" % (n, n), "iters_c": ed["n_iters_c"], "iters_s": ed["n_iters_s"], "fix_s": dt,
+                         "edited_share": (ed["n_quant"] + ed["n_lossless"]) / f.size,
+                         "lossless_share": ed["n_lossless"] / f.size, "verify_passed": rep["passed"]})
+        desc = "extreme noise: 2D white noise in [0, xi], flat base xi/2, xi=1e-4, tier %d" % args.tier
+    print(json.dumps({"study": args.study, "config": desc, "rows": rows}))
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -288,6 +334,9 @@ def main():
     __graft_entry__.build()
     from paper_2409_17346_gb300 import msc
 
+    if args.study:
+        run_study(args, msc)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

@@ -24,7 +24,7 @@ import math
 import numpy as np
 
 __all__ = ["xi_from_range", "gaussians_2d", "multiscale_2d", "grf_3d", "add_plateaus",
-           "noise_base", "quantize_dither_base", "config_case", "serving_requests"]
+           "noise_base", "quantize_dither_base", "config_case", "serving_requests", "extreme_noise_2d"]
 
 
 def xi_from_range(f, rel):
@@ -180,6 +180,18 @@ def config_case(name, seed=None, rel=None, size=None):
         xi = xi_from_range(f, 1e-4 if rel is None else rel)
         return f, noise_base(f, xi, seed), xi, 4
     raise ValueError(name)
+
+
+def extreme_noise_2d(n, seed=9, xi=1e-4):
+    """The stress case of the paper's extreme-case study: an n x n field of white noise whose
+    whole range lies inside the error bound (values U[0, xi]), and a base-compressor output
+    that is flat (every value xi / 2), so that the local order is destroyed everywhere.
+    Returns (f, f_hat, xi); f_hat lies within xi of f at every vertex."""
+    r = np.random.Generator(np.random.PCG64(seed))
+    xi32 = np.float32(xi)
+    f = r.uniform(0.0, float(xi32), (n, n)).astype(np.float32)
+    fh = np.full_like(f, np.float32(xi32 / np.float32(2)))
+    return f, fh, float(xi32)
 
 
 def serving_requests(n=128, seed=5, rate_hz=20.0):
