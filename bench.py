@@ -120,6 +120,7 @@ CLASS_KERNELS = {
     "rebuild": "k_rebuild, k_clear", "sep_init": "k_node_init", "sep_seed": "k_node_seed, k_tri_spill",
     "sep_update": "k_node_update, k_tri_spill, k_sd_clear", "sep_targets": "k_node_targets",
     "other": "k_init_g, k_decide, k_end, k_seeds, checks",
+    "rounds": "k_rounds",
 }
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of a class's kernels per work
@@ -158,6 +159,11 @@ def class_bytes(cls, tot, n, steps, ndim):
     if cls in ("sep_seed", "sep_update"):
         # per node step: the node's f code 8 B and its state word read and written 8 B
         return 16.0 * items
+    if cls == "rounds":
+        # the persistent round kernel: per round the C block summary, and the C-pass, edit,
+        # refresh and rebuild bytes of the work it did (counted as for those classes)
+        w = tot["work"]
+        return items * n / 8192.0 + 16.0 * w["cpass"] + 22.0 * w["edit"] + (16.0 + 20.0) * w["refresh"]
     return None
 
 
@@ -399,6 +405,8 @@ def main():
 
     launches = sum(s[k]["launches"] for s, _ in stats for k in msc.KERNEL_CLASSES)
     tot = {key: sum(s[dom][key] for s, _ in stats) for key in ("ms", "timed", "items", "launches")}
+    if dom == "rounds":
+        tot["work"] = {w: sum(s["rounds"]["work"][w] for s, _ in stats) for w in ("edit", "refresh", "cpass")}
     peak, peak_kind = peaks()
     bytes_dom = class_bytes(dom, tot, n, args.steps, f.ndim)
     roof = {"bound": "hbm", "kernel": "%s (%s)" % (dom, CLASS_KERNELS[dom]), "achieved": None, "peak": peak,

@@ -79,7 +79,9 @@ enum {
     MSC_K_SEP_TARGETS = 7,/* troublemakers from the separatrix state */
     MSC_K_OTHER = 8,     /* initialisation, seeds, output encoding, checks */
     MSC_K_SEP_SEED = 9,  /* separatrix state: propagation from the seeds in the first build */
-    MSC_K_COUNT = 10
+    MSC_K_ROUNDS = 10,   /* persistent kernel running the C-pass rounds that edit few vertices
+                            (targets, edits, refresh and rebuild of each round in one launch) */
+    MSC_K_COUNT = 11
 };
 #define MSC_PROFILE_ALL ((1 << MSC_K_COUNT) - 1)
 
@@ -92,14 +94,19 @@ typedef struct {
                                     init), anchors with differing critical cells (cpass),
                                     targeted vertices (edit), refreshed anchors (refresh),
                                     dirty anchors (rebuild), node steps (separatrix seed and
-                                    update) */
+                                    update), rounds run (rounds); work done inside the
+                                    persistent round kernel is counted in round_work instead */
+    uint64_t round_work[3];      /* inside the persistent round kernel: targeted vertices,
+                                    refreshed (and rebuilt) anchors, anchors with differing
+                                    critical cells visited by the C-pass */
 } msc_stats;
 
 /* one edit round: kind 0 = C-pass (false critical cells), 1 = S-pass (separatrices);
  * T = vertices lowered by a quantised step this round, X = vertices restored to f */
 typedef struct {
     int32_t kind;
-    int32_t reserved;
+    int32_t t_us;                     /* device clock when the round's targets were counted,
+                                         microseconds after the first round's */
     int64_t n_targets, n_exact;
     int64_t sum_targets, sum_exact;   /* sums of vertex ids, an order-free digest */
 } msc_iter_record;

@@ -81,6 +81,12 @@ template <int D> struct Tab {
     int k_tri[6][4];               // tet t: cube-triangle index of the facet opposite corner
                                    //   0, kA, kB, AX (in that order)
     int k_opp_pos[6][4];           // position of that corner in the facet's cofacet list
+    // vertices within two edges of a vertex (sums of at most two neighbour offsets, the
+    // vertex itself excluded): every pair of vertices whose SoS order the pairing rules
+    // compare lies in one such set (neighbours of a vertex, cofacet candidates of an edge
+    // or triangle, vertices of a cell)
+    int nring;
+    int ring[64][3];
 };
 
 constexpr int popc3(int m) { return (m & 1) + ((m >> 1) & 1) + ((m >> 2) & 1); }
@@ -236,6 +242,19 @@ template <int D> constexpr Tab<D> make_tab()
             t.kfac_opp[kk][j] = corner[j];
         }
     }
+    t.nring = 0;
+    for (int a = -1; a < T::NNB; a++)
+        for (int b = a; b < T::NNB; b++) {
+            int o[3] = {0, 0, 0};
+            for (int i = 0; i < 3; i++) o[i] = (a >= 0 ? t.nb[a][i] : 0) + (b >= 0 ? t.nb[b][i] : 0);
+            if (o[0] == 0 && o[1] == 0 && o[2] == 0) continue;
+            bool seen = false;
+            for (int k = 0; k < t.nring; k++)
+                if (t.ring[k][0] == o[0] && t.ring[k][1] == o[1] && t.ring[k][2] == o[2]) seen = true;
+            if (seen) continue;
+            t.ring[t.nring][0] = o[0]; t.ring[t.nring][1] = o[1]; t.ring[t.nring][2] = o[2];
+            t.nring++;
+        }
     t.nwin = 0;
     for (int z = zlo; z <= zhi; z++)
         for (int y = -1; y <= 2; y++)

@@ -68,7 +68,7 @@ __host__ __device__ inline Grid make_grid(int nx, int ny, int nz)
 
 struct Counters {
     unsigned long long ncase, nlive, nT, nX, sumT, sumX;   // targeting pass
-    unsigned long long nchanged, nD, nM, novf, err, nSD;
+    unsigned long long nE, nD, nM, novf, err, nSD;
     unsigned long long steps[4];                           // cells stepped: desc, asc, saddle
     unsigned long long rep[16];                            // verify / misc
 };
@@ -85,6 +85,7 @@ struct LoopState {
     unsigned long long edit_items, refresh_items, cpass_items, cases;
     unsigned long long nblk;  // entries of the C-block list for the next C-pass
     unsigned long long last_items;   // vertices the last round edited (targets + restores)
+    unsigned long long nbl[2];       // persistent round kernel: entries of its two C-block lists
 };
 
 // everything a kernel of one job needs (device pointers)
@@ -94,11 +95,13 @@ struct Ctx {
     float xi, step;
     const float *f, *fhat;
     float *g;
+    float *gprev;                    // value before the current round, for vertices in T u X
     uint8_t *state;
     const uint64_t *code_f;
     uint64_t *code_g;
     uint32_t *Tbits, *Xbits, *Dbits;
     uint32_t *Tlist, *Xlist, *Dlist;
+    uint32_t *Elist;                 // vertices whose value the current round changed
     uint32_t *vis_v, *vis_top, *vis_tri;
     uint32_t *ovf_in, *ovf_out;      // saddle-saddle spill queues: (triangle id, entry edge) pairs
     uint32_t ovf_cap;
@@ -212,8 +215,17 @@ template <int D> MSC_HD inline unsigned corner_mask(const Grid &G, int x, int y,
     return m;
 }
 
+// a value load: through the read-only data path (NC, for arrays that no thread writes while
+// the kernel runs), or a plain coherent load (arrays that other blocks of a persistent
+// kernel write between its grid barriers)
+template <bool NC> MSC_HD __forceinline__ float ldv(const float *p)
+{
+    if constexpr (NC) return ld(p);
+    else return *p;
+}
+
 // the window of values around an anchor (+inf outside the domain)
-template <int D> MSC_HD inline void load_window(const float *v, const Grid &G, int x, int y, int z, float *w)
+template <int D, bool NC = true> MSC_HD inline void load_window(const float *v, const Grid &G, int x, int y, int z, float *w)
 {
     const float INF = pos_inf();
     constexpr int ZL = D == 3 ? -1 : 0, ZH = D == 3 ? 2 : 0;
@@ -224,12 +236,12 @@ template <int D> MSC_HD inline void load_window(const float *v, const Grid &G, i
 #pragma unroll
             for (int dx = -1; dx <= 2; dx++) {
                 const int xx = x + dx, yy = y + dy, zz = z + dz;
-                w[wpos<D>(dx, dy, dz)] = inside(G, xx, yy, zz) ? ld(v + vid(G, xx, yy, zz)) : INF;
+                w[wpos<D>(dx, dy, dz)] = inside(G, xx, yy, zz) ? ldv<NC>(v + vid(G, xx, yy, zz)) : INF;
             }
 }
 
 // window of an anchor at least one vertex from the lower and two from the upper faces
-template <int D> MSC_HD inline void load_window_interior(const float *v, const Grid &G, uint32_t p, float *w)
+template <int D, bool NC = true> MSC_HD inline void load_window_interior(const float *v, const Grid &G, uint32_t p, float *w)
 {
     constexpr int ZL = D == 3 ? -1 : 0, ZH = D == 3 ? 2 : 0;
     const int sy = G.nx, sz = G.nx * G.ny;
@@ -241,21 +253,21 @@ template <int D> MSC_HD inline void load_window_interior(const float *v, const G
             for (int dx = -1; dx <= 2; dx++) {
                 const bool lowcube = dx <= 1 && dy <= 1 && dz <= 1;
                 const bool highcube = dx >= 0 && dy >= 0 && dz >= 0;
-                if (lowcube || highcube) w[wpos<D>(dx, dy, dz)] = ld(v + (int64_t)p + dx + dy * sy + dz * sz);
+                if (lowcube || highcube) w[wpos<D>(dx, dy, dz)] = ldv<NC>(v + (int64_t)p + dx + dy * sy + dz * sz);
             }
 }
 
-template <int D> MSC_HD inline uint64_t anchor_code(const float *v, const Grid &G, uint32_t p)
+template <int D, bool NC = true> MSC_HD inline uint64_t anchor_code(const float *v, const Grid &G, uint32_t p)
 {
     int x, y, z;
     coords(G, p, x, y, z);
     float w[Tab<D>::WS];
     const bool interior = x >= 1 && y >= 1 && x + 2 < G.nx && y + 2 < G.ny && (D == 2 || (z >= 1 && z + 2 < G.nz));
     if (interior) {
-        load_window_interior<D>(v, G, p, w);
+        load_window_interior<D, NC>(v, G, p, w);
         return eval_anchor<D>(w, (1u << Tab<D>::NC) - 1u);
     }
-    load_window<D>(v, G, x, y, z, w);
+    load_window<D, NC>(v, G, x, y, z, w);
     return eval_anchor<D>(w, corner_mask<D>(G, x, y, z));
 }
 
@@ -290,12 +302,12 @@ template <int D> MSC_HD inline Verts cell_verts(const Grid &G, int x, int y, int
     return V;
 }
 
-MSC_HD inline int lowest_of(const Verts &V, const float *vals)
+template <bool NC = true> MSC_HD inline int lowest_of(const Verts &V, const float *vals)
 {
     int lo = 0;
-    float lv = ld(vals + V.id[0]);
+    float lv = ldv<NC>(vals + V.id[0]);
     for (int i = 1; i < V.n; i++) {
-        const float vi = ld(vals + V.id[i]);
+        const float vi = ldv<NC>(vals + V.id[i]);
         if (sos_lt(vi, V.id[i], lv, V.id[lo])) { lo = i; lv = vi; }
     }
     return lo;
@@ -346,7 +358,7 @@ template <int D>
 MSC_HD inline uint32_t fn_down_target(const Ctx &c, int x, int y, int z, int kind, int t, const Verts &V)
 {
     const Tab<D> &T = rt_tab<D>();
-    const int jg = lowest_of(V, c.g), jf = lowest_of(V, c.f);
+    const int jg = lowest_of<false>(V, c.g), jf = lowest_of(V, c.f);   // g: plain load (written by edits)
     if (jg != jf) return V.id[jf];
     if (kind == 1) {                       // L = the other vertex h
         const int h = 1 - jg;
@@ -470,18 +482,48 @@ template <int D, class App> MSC_HD inline void mark_dirty(const Ctx &c, uint32_t
     }
 }
 
-// Edit item i (read only): i < nX restores Xlist[i] to f; otherwise Tlist[i - nX] takes a
-// quantised step unless it is also restored or can no longer move.  Returns whether the
-// item changes a vertex, and the vertex.
-MSC_HD inline bool edit_decide(const Ctx &c, uint32_t i, uint32_t nX, uint32_t &v)
+// Edit item i: i < nX restores Xlist[i] to f; otherwise Tlist[i - nX] takes a quantised
+// step unless it is also restored or can no longer move.  Saves the vertex's value before
+// the round in gprev (every item except a target that a restore item owns, so that gprev
+// holds the pre-round value of every vertex in T u X) and returns whether the item changes
+// its vertex, and the vertex.
+MSC_HD inline bool edit_prepare(const Ctx &c, uint32_t i, uint32_t nX, uint32_t &v)
 {
     if (i < nX) {
         v = c.Xlist[i];
+        c.gprev[v] = c.g[v];
         return c.state[v] != ST_EXACT;
     }
     v = c.Tlist[i - nX];
     if ((c.Xbits[v >> 5] >> (v & 31)) & 1u) return false;
+    c.gprev[v] = c.g[v];
     return c.state[v] <= c.qmax;
+}
+
+// Whether the round changed the SoS order of the edited vertex v against any vertex u
+// within two edges of it (ring offsets `ring`, split among `nparts` cooperating threads).
+// Every pair of vertices that a pairing rule compares lies within two edges (two
+// neighbours of a vertex, two cofacet candidates of an edge or triangle, two vertices of a
+// cell), so when no such order changes, no gradient code changes.  Values before the
+// round: gprev for vertices in T u X (all saved by edit_prepare), g for the others.
+template <int D>
+MSC_HD inline bool order_changed(const Ctx &c, uint32_t v, int part, int nparts, const int (*ring)[3])
+{
+    const Tab<D> &T = rt_tab<D>();
+    int x, y, z;
+    coords(c.G, v, x, y, z);
+    const float ov = c.gprev[v], nv = c.g[v];
+    bool flip = false;
+    for (int j = part; j < T.nring; j += nparts) {
+        const int ux = x + ring[j][0], uy = y + ring[j][1], uz = z + ring[j][2];
+        if (!inside(c.G, ux, uy, uz)) continue;
+        const uint32_t u = vid(c.G, ux, uy, uz);
+        const float nu = c.g[u];
+        const bool moved = ((c.Tbits[u >> 5] | c.Xbits[u >> 5]) >> (u & 31)) & 1u;
+        const float ou = moved ? c.gprev[u] : nu;
+        flip |= sos_lt(ov, v, ou, u) != sos_lt(nv, v, nu, u);
+    }
+    return flip;
 }
 
 // Eq. 2 applied to a changing item: one step of xi / 2^q_max while q < q_max and the value

@@ -104,6 +104,18 @@ int occ_blocks(const void *kernel)
     return b;
 }
 
+// whether the current device runs cooperative launches (the persistent round kernel)
+bool coop_supported()
+{
+    static const bool ok = [] {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrCooperativeLaunch, dev);
+        return v != 0;
+    }();
+    return ok;
+}
+
 // grid for a grid-stride kernel over n threads' worth of work: at most one full wave of the
 // blocks that can be resident at once, so no launch ends with a partly filled wave
 int grid_occ(const void *kernel, unsigned long long n)
@@ -206,14 +218,17 @@ __device__ __forceinline__ void for_each_set(const uint32_t *bits, uint32_t n, F
 }
 
 // the anchors whose bit is set, visiting only the listed blocks of 32 words: one warp per
-// block compacts its set bits into shared memory and runs f on them; a block found empty
-// has its summary bit cleared.  Needs blockDim.x == TPB.
-template <class F>
-__device__ __forceinline__ void for_each_listed(const uint32_t *bits, uint32_t n, const uint32_t *blk,
-                                                unsigned long long nblk, uint32_t *sum, F &&f,
-                                                unsigned long long *count = nullptr)
+// block compacts its set bits into the warp's row of q (shared memory) and runs f on them;
+// a block found empty has its summary bit cleared, a block found non-empty is handed to
+// keep.  Needs blockDim.x == TPB.
+struct NoKeep {
+    __device__ void operator()(uint32_t) const {}
+};
+template <class F, class K = NoKeep>
+__device__ __forceinline__ void for_each_listed_in(uint32_t (*q)[32 * 32], const uint32_t *bits, uint32_t n,
+                                                   const uint32_t *blk, unsigned long long nblk, uint32_t *sum, F &&f,
+                                                   unsigned long long *count = nullptr, K &&keep = K{})
 {
-    __shared__ uint32_t q[TPB / 32][32 * 32];
     const unsigned lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     uint32_t *mq = q[wib];
     const unsigned long long nw = (n + 31) / 32;
@@ -234,7 +249,10 @@ __device__ __forceinline__ void for_each_listed(const uint32_t *bits, uint32_t n
             if (lane == 0) atomicAnd(sum + (b >> 5), ~(1u << (b & 31)));
             continue;
         }
-        if (count && lane == 0) atomicAdd(count, (unsigned long long)total);
+        if (lane == 0) {
+            if (count) atomicAdd(count, (unsigned long long)total);
+            keep(b);
+        }
         unsigned at = pre - cnt;
         const uint32_t base = (uint32_t)(w * 32);
         while (mine) {
@@ -246,6 +264,15 @@ __device__ __forceinline__ void for_each_listed(const uint32_t *bits, uint32_t n
         for (unsigned k = lane; k < total; k += 32) f(mq[k]);
         __syncwarp();
     }
+}
+
+template <class F>
+__device__ __forceinline__ void for_each_listed(const uint32_t *bits, uint32_t n, const uint32_t *blk,
+                                                unsigned long long nblk, uint32_t *sum, F &&f,
+                                                unsigned long long *count = nullptr)
+{
+    __shared__ uint32_t q[TPB / 32][32 * 32];
+    for_each_listed_in(q, bits, n, blk, nblk, sum, f, count);
 }
 
 // list the blocks whose summary bit is set (appending to blk, count in *nblk); every warp
@@ -359,21 +386,33 @@ template <int D> __global__ void __launch_bounds__(TPB) k_ctargets(Ctx c)
 }
 
 // after a targeting pass (kind 0 C, 1 S): stop the phase when there is no false case, stop
-// with a status on a stall or at max_iters, otherwise record the round and go on
-__global__ void k_decide(Ctx c, int kind)
+// with a status on a stall or at max_iters.  iters: the loop's round count when the pass
+// began.
+__device__ __forceinline__ bool round_stop(const LoopState *ls, const Counters *k, unsigned iters, int &status)
 {
-    if (threadIdx.x || blockIdx.x) return;
+    status = 0;
+    if (k->ncase == 0) return true;
+    if (!ls->exact_fallback && k->nlive == 0) { status = MSC_ERR_STALLED; return true; }
+    if (iters >= ls->max_iters) { status = MSC_ERR_NOT_CONVERGED; return true; }
+    return false;
+}
+
+// record the decision (one thread): halt with the status, or count and trace the round
+__device__ void round_record(const Ctx &c, const Counters *k, int kind, bool stop, int status)
+{
     LoopState *ls = c.ls;
-    if (ls->halt) return;
-    const Counters *k = c.cnt;
-    ls->nblk = 0;          // the C-pass has read the block list; the round's end lists it anew
     ls->cases += k->ncase;
-    if (k->ncase == 0) { ls->halt = 1; return; }
-    if (!ls->exact_fallback && k->nlive == 0) { ls->halt = 1; ls->status = MSC_ERR_STALLED; return; }
-    if (ls->iters >= ls->max_iters) { ls->halt = 1; ls->status = MSC_ERR_NOT_CONVERGED; return; }
+    if (stop) {
+        ls->halt = 1;
+        if (status) ls->status = status;
+        return;
+    }
     if (c.trace && ls->ntrace < ls->trace_cap) {
-        int64_t *r = c.trace + 5 * (size_t)ls->ntrace;
+        int64_t *r = c.trace + 6 * (size_t)ls->ntrace;
         r[0] = kind; r[1] = (int64_t)k->nT; r[2] = (int64_t)k->nX; r[3] = (int64_t)k->sumT; r[4] = (int64_t)k->sumX;
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        r[5] = (int64_t)t;
     }
     ls->ntrace++;
     ls->iters++;
@@ -383,27 +422,60 @@ __global__ void k_decide(Ctx c, int kind)
     ls->last_items = k->nT + k->nX;
 }
 
+__global__ void k_decide(Ctx c, int kind)
+{
+    if (threadIdx.x || blockIdx.x) return;
+    LoopState *ls = c.ls;
+    if (ls->halt) return;
+    ls->nblk = 0;          // the C-pass has read the block list; the round's end lists it anew
+    int status;
+    const bool stop = round_stop(ls, c.cnt, ls->iters, status);
+    round_record(c, c.cnt, kind, stop, status);
+}
+
 constexpr int DIRTY_STAGE = 8192;
 
-// one warp per edited vertex: all lanes read the item's state, lane 0 applies the edit,
-// the lanes share the dirty-anchor marks
+// one thread per edit item: save the pre-round value, apply Eq. 2 (or the restore), and
+// list the vertices whose value changed
 template <int D> __global__ void k_edit(Ctx c)
 {
     if (c.ls->halt) return;
-    __shared__ Stage<DIRTY_STAGE> sd;
-    st_init(sd);
+    __shared__ Stage<TPB> se;
+    st_init(se);
     const unsigned long long nX = c.cnt->nX, items = nX + c.cnt->nT;
+    BLOCK_ROUNDS(b, items)
+    {
+        const unsigned long long i = b + threadIdx.x;
+        if (i < items) {
+            uint32_t v;
+            if (edit_prepare(c, (uint32_t)i, (uint32_t)nX, v)) {
+                edit_apply(c, (uint32_t)i, (uint32_t)nX, v);
+                st_push(se, v, c.Elist, &c.cnt->nE);
+            }
+        }
+        st_flush(se, c.Elist, &c.cnt->nE);
+    }
+}
+
+// one warp per changed vertex: when its order against some vertex within two edges
+// changed, the lanes share the dirty-anchor marks of its window; otherwise no code can
+// change and nothing is marked
+template <int D> __global__ void k_mark(Ctx c)
+{
+    if (c.ls->halt) return;
+    __shared__ Stage<DIRTY_STAGE> sd;
+    __shared__ int ring[64][3];
+    for (int j = threadIdx.x; j < 64 * 3; j += blockDim.x) ring[j / 3][j % 3] = rt_tab<D>().ring[j / 3][j % 3];
+    st_init(sd);
+    const unsigned long long items = c.cnt->nE;
     const unsigned lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     for (unsigned long long b = (unsigned long long)blockIdx.x * wpb; b < items; b += (unsigned long long)gridDim.x * wpb) {
         const unsigned long long i = b + (threadIdx.x >> 5);
         if (i < items) {
-            uint32_t v;
-            const bool changed = edit_decide(c, (uint32_t)i, (uint32_t)nX, v);
-            __syncwarp();
-            if (changed) {
-                if (lane == 0) edit_apply(c, (uint32_t)i, (uint32_t)nX, v);
+            const uint32_t v = c.Elist[i];
+            const bool flip = order_changed<D>(c, v, (int)lane, 32, ring);
+            if (__any_sync(0xffffffffu, flip))
                 mark_dirty<D>(c, v, (int)lane, 32, [&](uint32_t p) { st_push(sd, p, c.Dlist, &c.cnt->nD); });
-            }
         }
         st_flush(sd, c.Dlist, &c.cnt->nD);
     }
@@ -414,6 +486,25 @@ template <int D> __global__ void __launch_bounds__(TPB, 3) k_refresh(Ctx c)
     if (c.ls->halt) return;
     const unsigned long long n = c.cnt->nD;
     GRID_STRIDE(i, n) refresh_anchor<D>(c, c.Dlist[i]);
+}
+
+// mismatch bits of a re-evaluated anchor p with code cg: M (code differs from f's) and C
+// (critical cells differ), and the C summary bit of p's 1024-anchor block.  Returns
+// whether this call set that summary bit.
+template <int D> __device__ __forceinline__ bool rebuild_anchor(const Ctx &c, uint32_t p, uint64_t cg)
+{
+    const uint64_t cf = __ldg(c.code_f + p);
+    const bool m = cf != cg, cm = m && crit_sig<D>(cf, c.tier) != crit_sig<D>(cg, c.tier);
+    const uint32_t bit = 1u << (p & 31);
+    if (m) atomicOr(c.Mbits + (p >> 5), bit); else atomicAnd(c.Mbits + (p >> 5), ~bit);
+    if (!cm) {
+        atomicAnd(c.Cbits + (p >> 5), ~bit);
+        return false;
+    }
+    atomicOr(c.Cbits + (p >> 5), bit);
+    const uint32_t sb = 1u << ((p >> 10) & 31);
+    if (c.Csum[p >> 15] & sb) return false;
+    return !(atomicOr(c.Csum + (p >> 15), sb) & sb);
 }
 
 // mismatch bitsets after a round: only re-evaluated (dirty) anchors can change membership
@@ -431,17 +522,7 @@ template <int D> __global__ void k_rebuild(Ctx c)
         if (i < d) {
             const uint32_t p = c.Dlist[i];
             if (track && !test_and_set(c.sDbits, p)) st_push(ss, p, c.sDlist, &ls->nSD);
-            const uint64_t cf = __ldg(c.code_f + p), cg = c.code_g[p];
-            const bool m = cf != cg, cm = m && crit_sig<D>(cf, c.tier) != crit_sig<D>(cg, c.tier);
-            const uint32_t bit = 1u << (p & 31);
-            if (m) atomicOr(c.Mbits + (p >> 5), bit); else atomicAnd(c.Mbits + (p >> 5), ~bit);
-            if (cm) {
-                atomicOr(c.Cbits + (p >> 5), bit);
-                const uint32_t sb = 1u << ((p >> 10) & 31);
-                if (!(c.Csum[p >> 15] & sb)) atomicOr(c.Csum + (p >> 15), sb);
-            } else {
-                atomicAnd(c.Cbits + (p >> 5), ~bit);
-            }
+            rebuild_anchor<D>(c, p, c.code_g[p]);
         }
         st_flush(ss, c.sDlist, &ls->nSD);
     }
@@ -474,6 +555,181 @@ __global__ void k_end(Ctx c)
 
 __global__ void k_set_halt(LoopState *ls, int v) { ls->halt = v; }
 __global__ void k_set_track(LoopState *ls, int v) { ls->track_dirty = v; }
+
+// ---- persistent C-pass rounds.  Rounds that edit few vertices cost mostly the gaps between
+// their kernels, so the rounds after the first large ones run in one cooperative launch (all
+// blocks resident), their phases separated by grid barriers:
+//   P1 targets (C-pass) | P2 decision + edits | P3 order changes -> dirty anchors |
+//   P4 refresh + mismatch bits + clearing the round's sets
+// The C-pass visits a list of 1024-anchor blocks kept in two buffers: the blocks P1 finds
+// non-empty and the blocks whose summary bit P4 newly sets form the next round's list.  The
+// round counters alternate between two Counters by round parity, so a round's counters are
+// zeroed while the round after it runs.  Data written by other blocks is read with plain
+// (coherent) loads after a barrier, never through the read-only path.
+constexpr int ROUND_STAGE = 8192;                          // dirty-anchor stage entries
+constexpr unsigned long long BAR_TIMEOUT_NS = 2000000000ull;   // 2 s
+constexpr unsigned BAR_SPIN_CAP = 1u << 28;
+
+struct GridBarrier {
+    unsigned arrive, gen;
+};
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier of a cooperative launch.  The wait is bounded: a block that waits longer
+// than BAR_TIMEOUT_NS records MSC_ERR_DEVICE_TIMEOUT in the loop state and returns false, and
+// so does every block that passes a barrier after that, so the kernel always ends.
+__device__ bool grid_sync(GridBarrier *gb, LoopState *ls)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = &gb->gen;
+        const unsigned g0 = *gen;
+        __threadfence();
+        int good = 1;
+        if (atomicAdd(&gb->arrive, 1u) == gridDim.x - 1) {
+            atomicExch(&gb->arrive, 0u);
+            __threadfence();
+            atomicAdd(&gb->gen, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            unsigned spins = 0;
+            while (*gen == g0) {
+                if (++spins >= BAR_SPIN_CAP || ((spins & 63u) == 0 && global_ns() - t0 > BAR_TIMEOUT_NS)) {
+                    good = 0;
+                    break;
+                }
+                __nanosleep(40);
+            }
+        }
+        __threadfence();
+        if (!good) {
+            atomicExch(&ls->status, (int)MSC_ERR_DEVICE_TIMEOUT);
+            atomicExch(&ls->halt, 1);
+        }
+        if (((volatile int *)&ls->status)[0] == (int)MSC_ERR_DEVICE_TIMEOUT) good = 0;
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+template <int D>
+__global__ void __launch_bounds__(TPB, 2) k_rounds(Ctx c, GridBarrier *gb, Counters *cnt2, uint32_t *blk2, unsigned max_rounds,
+                                                unsigned long long leave_items)
+{
+    __shared__ union {
+        uint32_t q[TPB / 32][32 * 32];   // P1: compacted anchors of a block, per warp
+        Stage<ROUND_STAGE> sd;           // P3: dirty anchors
+    } u;
+    __shared__ Stage<TPB> se;            // P2: changed vertices; P4: separatrix dirty anchors
+    __shared__ BlockTally tally;
+    __shared__ int ring[64][3];
+    for (int j = threadIdx.x; j < 64 * 3; j += blockDim.x) ring[j / 3][j % 3] = rt_tab<D>().ring[j / 3][j % 3];
+    LoopState *ls = c.ls;
+    uint32_t *const lists[2] = {c.Cblk, blk2};
+    const unsigned lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    const unsigned long long nthreads = (unsigned long long)gridDim.x * blockDim.x;
+    const unsigned long long gtid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    for (unsigned r = 0; r < max_rounds; r++) {
+        const int cur = (int)(r & 1u), nxt = cur ^ 1;
+        Counters *K = cnt2 + cur;
+        Ctx cc = c;
+        cc.cnt = K;
+        const unsigned iters = ls->iters;        // block 0 advances it only after barrier 1
+        // P1: false cases of the listed blocks; non-empty blocks stay listed
+        if (gtid == 0) memset(cnt2 + nxt, 0, sizeof(Counters));
+        tally_begin(tally, cc);
+        {
+            uint32_t *nl = lists[nxt];
+            unsigned long long *nn = &ls->nbl[nxt];
+            for_each_listed_in(u.q, c.Cbits, c.G.n, lists[cur], ls->nbl[cur], c.Csum,
+                               [&](uint32_t p) { ctargets_anchor<D>(cc, p); }, &ls->cpass_items,
+                               [&](uint32_t b) { nl[atomicAdd(nn, 1ull)] = b; });
+        }
+        tally_end(tally, cc);
+        if (!grid_sync(gb, ls)) return;
+        // P2: the decision, taken alike by every thread from the finished counters (block 0
+        // records it), then the edits
+        int status;
+        const bool stop = round_stop(ls, K, iters, status);
+        const unsigned long long nX = K->nX, items = nX + K->nT;
+        if (gtid == 0) round_record(cc, K, 0, stop, status);
+        if (stop) return;
+        st_init(se);
+        BLOCK_ROUNDS(b, items)
+        {
+            const unsigned long long i = b + threadIdx.x;
+            if (i < items) {
+                uint32_t v;
+                if (edit_prepare(cc, (uint32_t)i, (uint32_t)nX, v)) {
+                    edit_apply(cc, (uint32_t)i, (uint32_t)nX, v);
+                    st_push(se, v, c.Elist, &K->nE);
+                }
+            }
+            st_flush(se, c.Elist, &K->nE);
+        }
+        if (!grid_sync(gb, ls)) return;
+        // P3: edited vertices whose order changed mark their windows dirty
+        st_init(u.sd);
+        const unsigned long long nE = K->nE;
+        for (unsigned long long b = (unsigned long long)blockIdx.x * wpb; b < nE; b += (unsigned long long)gridDim.x * wpb) {
+            const unsigned long long i = b + wib;
+            if (i < nE) {
+                const uint32_t v = c.Elist[i];
+                const bool flip = order_changed<D>(cc, v, (int)lane, 32, ring);
+                if (__any_sync(0xffffffffu, flip))
+                    mark_dirty<D>(cc, v, (int)lane, 32, [&](uint32_t p) { st_push(u.sd, p, c.Dlist, &K->nD); });
+            }
+            st_flush(u.sd, c.Dlist, &K->nD);
+        }
+        if (!grid_sync(gb, ls)) return;
+        // P4: new codes and mismatch bits of the dirty anchors; clear the round's sets
+        const unsigned long long nD = K->nD, nT = K->nT;
+        const int track = ls->track_dirty;
+        st_init(se);
+        BLOCK_ROUNDS(b, nD)
+        {
+            const unsigned long long i = b + threadIdx.x;
+            if (i < nD) {
+                const uint32_t p = c.Dlist[i];
+                const uint64_t cg = anchor_code<D, false>(c.g, c.G, p);
+                c.code_g[p] = cg;
+                if (track && !test_and_set(c.sDbits, p)) st_push(se, p, c.sDlist, &ls->nSD);
+                if (rebuild_anchor<D>(cc, p, cg)) lists[nxt][atomicAdd(&ls->nbl[nxt], 1ull)] = p >> 10;
+            }
+            st_flush(se, c.sDlist, &ls->nSD);
+        }
+        for (unsigned long long i = gtid; i < nT + nX + nD; i += nthreads) {
+            if (i < nT) c.Tbits[c.Tlist[i] >> 5] = 0;
+            else if (i < nT + nX) c.Xbits[c.Xlist[i - nT] >> 5] = 0;
+            else c.Dbits[c.Dlist[i - nT - nX] >> 5] = 0;
+        }
+        if (gtid == 0) {
+            atomicAdd(&ls->refresh_items, nD);
+            ls->nbl[cur] = 0;                    // list cur was read in P1; it is the next "next"
+        }
+        if (!grid_sync(gb, ls)) return;
+        if (items >= leave_items) return;        // a large round: the next rounds run full grids
+    }
+}
+
+// entry state of k_rounds: the C-block list of the round graphs is list 0
+__global__ void k_rounds_enter(LoopState *ls, GridBarrier *gb)
+{
+    ls->nbl[0] = ls->nblk;
+    ls->nbl[1] = 0;
+    gb->arrive = 0;
+}
+
+// after k_rounds: list the C blocks again for the round graphs and the S-pass edit round
+__global__ void k_rounds_leave(LoopState *ls) { ls->nblk = 0; }
 
 template <int D> __global__ void k_desc(Ctx c, const uint32_t *seeds, uint32_t n)
 {
@@ -943,10 +1199,12 @@ struct msc_handle {
     DevBuf<uint32_t> seeds_desc, seeds_asc, seeds_ss;
     uint32_t n_desc = 0, n_asc = 0, n_ss = 0;
     // fix state (allocated on first use)
-    DevBuf<float> fhat, g;
+    DevBuf<float> fhat, g, gprev;
     DevBuf<uint8_t> state;
     DevBuf<uint64_t> code_g;
-    DevBuf<uint32_t> Tbits, Xbits, Dbits, Tlist, Xlist, Dlist, Mbits, Cbits, Csum, Cblk;
+    DevBuf<uint32_t> Tbits, Xbits, Dbits, Tlist, Xlist, Dlist, Elist, Mbits, Cbits, Csum, Cblk, Cblk2;
+    DevBuf<GridBarrier> bar;
+    int rounds_grid = 0;   // blocks of the persistent round kernel (0: one per SM)
     DevBuf<uint32_t> vis_v, vis_top, vis_tri, ovf0, ovf1;
     DevBuf<uint32_t> ns_v, ns_top, ns_tri, ns_dead;
     DevBuf<uint32_t> sDbits, sDlist;
@@ -963,6 +1221,7 @@ struct msc_handle {
     unsigned long long launches[12] = {};
     unsigned long long timed[12] = {};
     unsigned long long items[12] = {};
+    unsigned long long round_work[3] = {};   // edit, refresh, cpass items of the round kernel
     double ms[12] = {};
     struct Pend {
         cudaEvent_t a, b;
@@ -1039,10 +1298,15 @@ msc_status alloc_fix_state(msc_handle *h)
     CK(h->Tlist.alloc(n));
     CK(h->Xlist.alloc(n));
     CK(h->Dlist.alloc(n));
+    CK(h->Elist.alloc(n));
+    CK(h->gprev.alloc(n));
     CK(h->Mbits.alloc(words(n)));
     CK(h->Cbits.alloc(words(n)));
     CK(h->Csum.alloc(csum_words((uint32_t)n)));
     CK(h->Cblk.alloc(csum_words((uint32_t)n) * 32));
+    CK(h->Cblk2.alloc(csum_words((uint32_t)n) * 32));
+    CK(h->bar.alloc(1));
+    CK(cudaMemsetAsync(h->bar.p, 0, sizeof(GridBarrier), g_alloc_stream));
     CK(h->vis_v.alloc(words(n)));
     CK(h->vis_top.alloc(words(n * ntop)));
     if (h->D == 3) {
@@ -1059,7 +1323,7 @@ msc_status alloc_fix_state(msc_handle *h)
     CK(h->sDbits.alloc(words(n)));
     CK(h->sDlist.alloc(n));
     CK(cudaMemsetAsync(h->sDbits.p, 0, h->sDbits.n * 4, g_alloc_stream));
-    CK(h->cnt.alloc(1));
+    CK(h->cnt.alloc(2));   // [0]: the round graphs and the S-pass; [0], [1]: persistent rounds
     CK(h->nM.alloc(8));
     CK(h->ls.alloc(1));
     CK(cudaMemsetAsync(h->Tbits.p, 0, h->Tbits.n * 4, g_alloc_stream));
@@ -1086,6 +1350,8 @@ Ctx make_ctx(msc_handle *h, int tier, int qmax, int exact_fallback, float xi)
     c.code_g = h->code_g.p;
     c.Tbits = h->Tbits.p; c.Xbits = h->Xbits.p; c.Dbits = h->Dbits.p;
     c.Tlist = h->Tlist.p; c.Xlist = h->Xlist.p; c.Dlist = h->Dlist.p;
+    c.Elist = h->Elist.p;
+    c.gprev = h->gprev.p;
     c.vis_v = h->vis_v.p; c.vis_top = h->vis_top.p; c.vis_tri = h->vis_tri.p;
     c.ovf_cap = (uint32_t)h->G.n + 1;
     c.cnt = h->cnt.p;
@@ -1256,7 +1522,8 @@ msc_status build_round_graph(msc_handle *h, const Ctx &c, unsigned prof_mask, bo
     // grid sizes (occupancy queries) before the capture begins
     auto grid = [&](const void *k, unsigned long long n) { return small ? std::min(sm_count(), grid_occ(k, n)) : grid_occ(k, n); };
     const int g_ct = grid((const void *)k_ctargets<D>, h->G.n / 8 + 1);
-    const int g_ed = grid((const void *)k_edit<D>, 32ull * h->G.n);
+    const int g_ed = grid((const void *)k_edit<D>, h->G.n);
+    const int g_mk = grid((const void *)k_mark<D>, 32ull * h->G.n);
     const int g_rf = grid((const void *)k_refresh<D>, h->G.n);
     const int g_rb = grid((const void *)k_rebuild<D>, h->G.n);
     const int g_cl = grid((const void *)k_clear, h->G.n);
@@ -1275,6 +1542,7 @@ msc_status build_round_graph(msc_handle *h, const Ctx &c, unsigned prof_mask, bo
         node(MSC_K_CPASS, r, 1, [&] { k_ctargets<D><<<g_ct, TPB, 0, cs>>>(c); });
         node(MSC_K_OTHER, r, 1, [&] { k_decide<<<1, 32, 0, cs>>>(c, 0); });
         node(MSC_K_EDIT, r, 0, [&] { k_edit<D><<<g_ed, TPB, 0, cs>>>(c); });
+        node(MSC_K_EDIT, r, 0, [&] { k_mark<D><<<g_mk, TPB, 0, cs>>>(c); });
         node(MSC_K_REFRESH, r, 0, [&] { k_refresh<D><<<g_rf, TPB, 0, cs>>>(c); });
         node(MSC_K_REBUILD, r, 0, [&] { k_rebuild<D><<<g_rb, TPB, 0, cs>>>(c); });
         node(MSC_K_REBUILD, r, 0, [&] { k_clear<<<g_cl, TPB, 0, cs>>>(c); });
@@ -1295,7 +1563,7 @@ void account_graph(msc_handle *h, RoundGraph &rg, unsigned active, bool halted)
     const unsigned long long a = active, t = active + (halted ? 1 : 0);
     h->launches[MSC_K_CPASS] += t;
     h->launches[MSC_K_OTHER] += t + a;
-    h->launches[MSC_K_EDIT] += a;
+    h->launches[MSC_K_EDIT] += 2 * a;
     h->launches[MSC_K_REFRESH] += a;
     h->launches[MSC_K_REBUILD] += 2 * a;
     for (auto &p : rg.pairs) {
@@ -1319,7 +1587,7 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
     L.exact_fallback = (unsigned)o.exact_fallback;
     if (o.record_trace) {
         L.trace_cap = (unsigned)std::min<long long>(std::max(o.max_iters, 1), 1 << 22);
-        CK(h->trace.alloc(5ull * L.trace_cap));
+        CK(h->trace.alloc(6ull * L.trace_cap));
         c.trace = h->trace.p;
     }
     CK(cudaMemcpyAsync(h->ls.p, &L, sizeof L, cudaMemcpyHostToDevice, s));
@@ -1338,18 +1606,60 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
     h->items[MSC_K_DENSE] += h->G.n;
     // two captured graphs: full grids for rounds that edit many vertices, one block per SM
     // for the long tail of rounds that edit few (chosen by the last round's size)
+    // rounds that edit few vertices run in the persistent kernel when the device has
+    // cooperative launches, else in a graph of small grids
+    int rgrid = h->rounds_grid > 0 ? h->rounds_grid : sm_count();
+    {
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)k_rounds<D>, TPB, 0) != cudaSuccess) {
+            cudaGetLastError();
+            occ = 0;
+        }
+        rgrid = std::min(rgrid, occ * sm_count());
+    }
+    const bool persistent = coop_supported() && rgrid > 0;
     RoundGraph rg_big, rg_small;
     CKS(build_round_graph<D>(h, c, (unsigned)o.profile & MSC_PROFILE_ALL, false, rg_big));
-    CKS(build_round_graph<D>(h, c, (unsigned)o.profile & MSC_PROFILE_ALL, true, rg_small));
+    if (!persistent) CKS(build_round_graph<D>(h, c, (unsigned)o.profile & MSC_PROFILE_ALL, true, rg_small));
     bool sep_built = false;
     unsigned prev_iters = 0;
+    unsigned long long fix_work[3] = {0, 0, 0};   // items of this call done by the round kernel
     for (;;) {
-        RoundGraph &rg = L.iters > 0 && L.last_items < SMALL_ROUND ? rg_small : rg_big;
-        CK(cudaGraphLaunch(rg.exec, s));
-        CK(cudaMemcpyAsync(&L, ls, sizeof L, cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        account_graph(h, rg, L.iters - prev_iters, L.halt != 0);
-        prev_iters = L.iters;
+        const bool small = L.iters > 0 && L.last_items < SMALL_ROUND;
+        if (small && persistent) {
+            const LoopState L0 = L;
+            KL(h, MSC_K_OTHER, s, k_rounds_enter<<<1, 1, 0, s>>>(ls, h->bar.p));
+            CK(cudaMemsetAsync(h->cnt.p, 0, 2 * sizeof(Counters), s));
+            Counters *cnt2 = h->cnt.p;
+            uint32_t *blk2 = h->Cblk2.p;
+            GridBarrier *gb = h->bar.p;
+            unsigned max_rounds = 1u << 30;
+            unsigned long long leave = SMALL_ROUND;
+            void *args[] = {(void *)&c, (void *)&gb, (void *)&cnt2, (void *)&blk2, (void *)&max_rounds, (void *)&leave};
+            cudaError_t le = cudaSuccess;
+            KL(h, MSC_K_ROUNDS, s, le = cudaLaunchCooperativeKernel((const void *)k_rounds<D>, dim3(rgrid), dim3(TPB), args, 0, s));
+            if (le != cudaSuccess) return fail(MSC_ERR_CUDA, "persistent round kernel launch failed: %s", cudaGetErrorString(le));
+            KL(h, MSC_K_OTHER, s, k_rounds_leave<<<1, 1, 0, s>>>(ls));
+            KL(h, MSC_K_REBUILD, s, k_list_blocks<<<grid_occ((const void *)k_list_blocks, h->G.n / 1024 + 1), TPB, 0, s>>>(c));
+            CK(cudaMemsetAsync(h->cnt.p, 0, sizeof(Counters), s));
+            CK(cudaGetLastError());
+            CK(cudaMemcpyAsync(&L, ls, sizeof L, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            prev_iters = L.iters;
+            h->items[MSC_K_ROUNDS] += L.iters - L0.iters;
+            fix_work[0] += L.edit_items - L0.edit_items;
+            fix_work[1] += L.refresh_items - L0.refresh_items;
+            fix_work[2] += L.cpass_items - L0.cpass_items;
+            if (L.status == MSC_ERR_DEVICE_TIMEOUT)
+                return fail(MSC_ERR_DEVICE_TIMEOUT, "a grid barrier of the persistent round kernel timed out");
+        } else {
+            RoundGraph &rg = small ? rg_small : rg_big;
+            CK(cudaGraphLaunch(rg.exec, s));
+            CK(cudaMemcpyAsync(&L, ls, sizeof L, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            account_graph(h, rg, L.iters - prev_iters, L.halt != 0);
+            prev_iters = L.iters;
+        }
         if (L.status == MSC_ERR_STALLED)
             return fail(MSC_ERR_STALLED, "every false case targets a vertex that can no longer move");
         if (L.status == MSC_ERR_NOT_CONVERGED) return fail(MSC_ERR_NOT_CONVERGED, "not converged after %d edit rounds", o.max_iters);
@@ -1369,7 +1679,8 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
         // the S-pass edit round, then back to C-pass rounds
         KL(h, MSC_K_OTHER, s, k_set_halt<<<1, 1, 0, s>>>(ls, 0));
         KL(h, MSC_K_OTHER, s, k_decide<<<1, 32, 0, s>>>(c, 1));
-        KL(h, MSC_K_EDIT, s, k_edit<D><<<grid_occ((const void *)k_edit<D>, 32ull * h->G.n), TPB, 0, s>>>(c));
+        KL(h, MSC_K_EDIT, s, k_edit<D><<<grid_occ((const void *)k_edit<D>, h->G.n), TPB, 0, s>>>(c));
+        KL(h, MSC_K_EDIT, s, k_mark<D><<<grid_occ((const void *)k_mark<D>, 32ull * h->G.n), TPB, 0, s>>>(c));
         KL(h, MSC_K_REFRESH, s, k_refresh<D><<<grid_occ((const void *)k_refresh<D>, h->G.n), TPB, 0, s>>>(c));
         KL(h, MSC_K_REBUILD, s, k_rebuild<D><<<grid_occ((const void *)k_rebuild<D>, h->G.n), TPB, 0, s>>>(c));
         KL(h, MSC_K_REBUILD, s, k_clear<<<grid_occ((const void *)k_clear, h->G.n), TPB, 0, s>>>(c));
@@ -1385,22 +1696,24 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
     R.n_c = L.n_c;
     R.n_s = L.n_s;
     R.n_fb = L.n_fb;
-    h->items[MSC_K_EDIT] += L.edit_items;
-    h->items[MSC_K_REFRESH] += L.refresh_items;
-    h->items[MSC_K_CPASS] += L.cpass_items;
-    h->items[MSC_K_REBUILD] += L.refresh_items;
+    h->items[MSC_K_EDIT] += L.edit_items - fix_work[0];
+    h->items[MSC_K_REFRESH] += L.refresh_items - fix_work[1];
+    h->items[MSC_K_CPASS] += L.cpass_items - fix_work[2];
+    h->items[MSC_K_REBUILD] += L.refresh_items - fix_work[1];
+    for (int i = 0; i < 3; i++) h->round_work[i] += fix_work[i];
     if (o.record_trace && L.ntrace) {
         const unsigned nt = std::min(L.ntrace, L.trace_cap);
-        std::vector<int64_t> rows(5ull * nt);
+        std::vector<int64_t> rows(6ull * nt);
         CK(cudaMemcpyAsync(rows.data(), h->trace.p, rows.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         for (unsigned i = 0; i < nt; i++) {
             msc_iter_record r{};
-            r.kind = (int32_t)rows[5 * i];
-            r.n_targets = rows[5 * i + 1];
-            r.n_exact = rows[5 * i + 2];
-            r.sum_targets = rows[5 * i + 3];
-            r.sum_exact = rows[5 * i + 4];
+            r.kind = (int32_t)rows[6 * i];
+            r.t_us = (int32_t)std::min<int64_t>((rows[6 * i + 5] - rows[5]) / 1000, INT32_MAX);
+            r.n_targets = rows[6 * i + 1];
+            r.n_exact = rows[6 * i + 2];
+            r.sum_targets = rows[6 * i + 3];
+            r.sum_exact = rows[6 * i + 4];
             R.trace.push_back(r);
         }
     }
@@ -1696,6 +2009,11 @@ msc_status critical_static(const float *field, Grid G, int64_t *rows, int32_t *d
 // ------------------------------------------------------------------------------------
 // C ABI
 // ------------------------------------------------------------------------------------
+void msc_rt::share_device(msc_handle *h, int concurrent)
+{
+    if (h && concurrent > 1) h->rounds_grid = std::max(16, 2 * sm_count() / concurrent);
+}
+
 extern "C" {
 
 const char *msc_version(void) { return "msc-gb300 0.1 (sm_103a)"; }
@@ -1732,6 +2050,7 @@ uint64_t msc_device_bytes(int nx, int ny, int nz)
     b += n / 8 + ntop * n / 8 + (d3 ? 12 * n / 8 + 16 * n : 0);   // walk visited sets, spill queues
     b += 2 * n * (1 + ntop + (d3 ? 19 : 0));      // separatrix node words (16 bits each)
     b += 3 * 4 * n;                               // separatrix seeds (upper estimate)
+    b += 8 * n;                                   // pre-round values and list of edited vertices
     return b;
 }
 
@@ -1921,6 +2240,7 @@ msc_status msc_fix_batch(msc_handle **hs, const float **f_hats, const float *xis
             }
             msc_options oi = o;
             oi.stream = ws;
+            msc_rt::share_device(hs[i], std::min(n, BATCH_STREAMS));
             st[(size_t)i] = msc_fix(hs[i], f_hats[i], xis[i], &oi, outs + i, g_outs[i]);
             if (st[(size_t)i] != MSC_OK) msg[(size_t)i] = g_last_error;
         }
@@ -2080,6 +2400,7 @@ msc_status msc_get_stats(msc_handle *h, msc_stats *out)
         out->timed_launches[i] = h->timed[i];
         out->items[i] = h->items[i];
     }
+    for (int i = 0; i < 3; i++) out->round_work[i] = h->round_work[i];
     return MSC_OK;
 }
 
@@ -2087,6 +2408,7 @@ msc_status msc_reset_stats(msc_handle *h)
 {
     if (!h) return fail(MSC_ERR_INVALID_ARG, "handle is NULL");
     for (int i = 0; i < 12; i++) { h->launches[i] = 0; h->ms[i] = 0.0; h->timed[i] = 0; h->items[i] = 0; }
+    for (int i = 0; i < 3; i++) h->round_work[i] = 0;
     return MSC_OK;
 }
 

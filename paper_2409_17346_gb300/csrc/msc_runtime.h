@@ -7,4 +7,7 @@
 namespace msc_rt {
 // record msg as this thread's msc_last_error and return s
 msc_status set_error(msc_status s, const std::string &msg);
+// blocks of the persistent round kernel for a handle whose fixes share the device with
+// `concurrent` other jobs: a fraction of the SMs each, so that the jobs' kernels fit at once
+void share_device(msc_handle *h, int concurrent);
 }  // namespace msc_rt

@@ -98,6 +98,7 @@ struct msc_server {
                 o.stream = ws;
                 msc_handle *h = nullptr;
                 st = msc_prepare_original(j->f, j->nx, j->ny, j->nz, &o, &h);
+                msc_rt::share_device(h, cfg.max_jobs);
                 if (st == MSC_OK) st = msc_fix(h, j->fh, j->xi, &o, &j->edits, j->g_out);
                 std::string e = st == MSC_OK ? std::string() : std::string(msc_last_error());
                 msc_destroy(h);

@@ -33,7 +33,7 @@ class Options(ctypes.Structure):
 
 
 KERNEL_CLASSES = ("dense", "cpass", "edit", "refresh", "rebuild", "sep_init", "sep_update", "sep_targets", "other",
-                  "sep_seed")
+                  "sep_seed", "rounds")
 PROFILE_ALL = (1 << len(KERNEL_CLASSES)) - 1
 
 
@@ -53,11 +53,12 @@ def profile_mask(profile):
 
 class Stats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_uint64 * 12), ("ms", ctypes.c_double * 12),
-                ("timed_launches", ctypes.c_uint64 * 12), ("items", ctypes.c_uint64 * 12)]
+                ("timed_launches", ctypes.c_uint64 * 12), ("items", ctypes.c_uint64 * 12),
+                ("round_work", ctypes.c_uint64 * 3)]
 
 
 class IterRecord(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("n_targets", ctypes.c_int64),
+    _fields_ = [("kind", ctypes.c_int32), ("t_us", ctypes.c_int32), ("n_targets", ctypes.c_int64),
                 ("n_exact", ctypes.c_int64), ("sum_targets", ctypes.c_int64), ("sum_exact", ctypes.c_int64)]
 
 
@@ -196,8 +197,10 @@ def _edits_to_py(e, shape):
             r = e.trace[k]
             tr[k] = (r.kind, r.n_targets, r.n_exact, r.sum_targets, r.sum_exact)
         out["trace"] = tr
+        out["trace_t_us"] = np.array([e.trace[k].t_us for k in range(nt)], np.int64)
     else:
         out["trace"] = np.zeros((0, 5), np.int64)
+        out["trace_t_us"] = np.zeros(0, np.int64)
     return out
 
 
@@ -248,9 +251,12 @@ class Handle:
         """Launch counts and profiled CUDA-event milliseconds by kernel class."""
         st = Stats()
         _check(load().msc_get_stats(self._h, ctypes.byref(st)))
-        return {k: dict(launches=int(st.launches[i]), ms=float(st.ms[i]), timed=int(st.timed_launches[i]),
-                        items=int(st.items[i]))
-                for i, k in enumerate(KERNEL_CLASSES)}
+        out = {k: dict(launches=int(st.launches[i]), ms=float(st.ms[i]), timed=int(st.timed_launches[i]),
+                       items=int(st.items[i]))
+               for i, k in enumerate(KERNEL_CLASSES)}
+        out["rounds"]["work"] = dict(edit=int(st.round_work[0]), refresh=int(st.round_work[1]),
+                                     cpass=int(st.round_work[2]))
+        return out
 
     def reset_stats(self):
         _check(load().msc_reset_stats(self._h))

@@ -115,7 +115,7 @@ def test_server_admission_respects_memory_budget(lib):
 def test_server_admits_jobs_arriving_while_others_run(lib):
     """Continuous batching: jobs submitted from another thread while earlier ones are on the
     device; every result equals the job alone."""
-    big = synth.config_case("grf3d", seed=90, size=96, rel=1e-4)
+    big = synth.config_case("grf3d", seed=90, size=160, rel=1e-4)
     small = [synth.config_case("grf3d", seed=91 + i, size=12, rel=1e-2) for i in range(6)]
     alone_big = lib.Handle(big[0]).fix(big[1], big[2], tier=4)
     alone_small = [lib.Handle(c[0]).fix(c[1], c[2], tier=4) for c in small]
@@ -126,7 +126,7 @@ def test_server_admits_jobs_arriving_while_others_run(lib):
 
         def arrive():
             for c in small:
-                time.sleep(0.005)
+                time.sleep(0.001)
                 ts.append(srv.submit(c[0], c[1], c[2]))
 
         th = threading.Thread(target=arrive)
