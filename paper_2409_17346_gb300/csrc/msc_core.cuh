@@ -394,67 +394,78 @@ MSC_HD inline uint32_t fn_down_target(const Ctx &c, int x, int y, int z, int kin
     return L.id[lowest_of(L, c.f)];
 }
 
-// false positive: lower the extra vertex of the f-partner; false negative: lower the
-// cell's f-lowest vertex (or repair a facet, fn_down_target)
-template <int D> MSC_HD inline void ctargets_anchor(const Ctx &c, uint32_t p)
+// Cells an anchor owns, numbered for the C-pass: 0 the vertex, 1 + e the edges,
+// 1 + NE + t the triangles, 1 + NE + NT + k the tetrahedra.
+// case_mask: bit i set iff cell i exists and is critical in exactly one of f and g (the
+// tier's cells: tier 1 in 3D skips edges and triangles, tier 1 in 2D skips edges).
+template <int D> MSC_HD inline uint32_t case_mask(const Ctx &c, uint32_t p, uint64_t cf, uint64_t cg)
 {
     const Tab<D> &T = rt_tab<D>();
-    const uint64_t cf = ld(c.code_f + p), cg = c.code_g[p];
-    if (cf == cg) return;
+    if (cf == cg) return 0;
     int x, y, z;
     coords(c.G, p, x, y, z);
     const unsigned cin = corner_mask<D>(c.G, x, y, z);
-    // vertex
-    {
+    uint32_t m = crit_v(vfield<D>(cf)) != crit_v(vfield<D>(cg)) ? 1u : 0u;
+    if (c.tier >= 2)
+        for (int e = 0; e < T.NE; e++)
+            if (((cin >> (e + 1)) & 1u) && crit_c(efield<D>(cf, e)) != crit_c(efield<D>(cg, e))) m |= 1u << (1 + e);
+    if (D == 2 || c.tier >= 2)
+        for (int tt = 0; tt < T.NT; tt++)
+            if (((cin >> T.tB[tt]) & 1u) && crit_c(tfield<D>(cf, tt)) != crit_c(tfield<D>(cg, tt)))
+                m |= 1u << (1 + T.NE + tt);
+    if ((cin >> 7) & 1u)
+        for (int k = 0; k < T.NK; k++)
+            if (crit_c(kfield<D>(cf, k)) != crit_c(kfield<D>(cg, k))) m |= 1u << (1 + T.NE + T.NT + k);
+    return m;
+}
+
+// the false case of cell i of anchor p (a bit of case_mask): false positive (critical in g
+// only): lower the extra vertex of its f-partner; false negative (critical in f only): lower
+// the cell's f-lowest vertex, or repair a facet (fn_down_target)
+template <int D> MSC_HD inline void case_apply(const Ctx &c, uint32_t p, int i)
+{
+    const Tab<D> &T = rt_tab<D>();
+    const uint64_t cf = ld(c.code_f + p), cg = c.code_g[p];
+    int x, y, z;
+    coords(c.G, p, x, y, z);
+    if (i == 0) {
         const int ff = vfield<D>(cf), gf = vfield<D>(cg);
-        if (crit_v(ff) != crit_v(gf)) {
-            Verts V = cell_verts<D>(c.G, x, y, z, 0, 0);
-            const uint32_t t = crit_v(gf) ? vid(c.G, x + T.nb[ff][0], y + T.nb[ff][1], z + T.nb[ff][2]) : p;
-            add_case<D>(c, t, V);
-        }
+        Verts V = cell_verts<D>(c.G, x, y, z, 0, 0);
+        const uint32_t t = crit_v(gf) ? vid(c.G, x + T.nb[ff][0], y + T.nb[ff][1], z + T.nb[ff][2]) : p;
+        add_case<D>(c, t, V);
+        return;
     }
-    if (c.tier >= 2) {
-#pragma unroll 1
-        for (int e = 0; e < T.NE; e++) {
-            if (!((cin >> (e + 1)) & 1u)) continue;
-            const int ff = efield<D>(cf, e), gf = efield<D>(cg, e);
-            if (crit_c(ff) == crit_c(gf)) continue;
-            Verts V = cell_verts<D>(c.G, x, y, z, 1, e);
-            uint32_t t;
-            if (crit_c(gf)) {
-                t = ff == 1 ? V.id[lowest_of(V, c.f)]
-                            : vid(c.G, x + T.ecof_v[e][ff - 2][0], y + T.ecof_v[e][ff - 2][1], z + T.ecof_v[e][ff - 2][2]);
-            } else {
-                t = gf >= 2 ? V.id[lowest_of(V, c.f)] : fn_down_target<D>(c, x, y, z, 1, e, V);
-            }
-            add_case<D>(c, t, V);
-        }
+    if (i <= T.NE) {
+        const int e = i - 1;
+        const int ff = efield<D>(cf, e), gf = efield<D>(cg, e);
+        Verts V = cell_verts<D>(c.G, x, y, z, 1, e);
+        uint32_t t;
+        if (crit_c(gf))
+            t = ff == 1 ? V.id[lowest_of(V, c.f)]
+                        : vid(c.G, x + T.ecof_v[e][ff - 2][0], y + T.ecof_v[e][ff - 2][1], z + T.ecof_v[e][ff - 2][2]);
+        else
+            t = gf >= 2 ? V.id[lowest_of(V, c.f)] : fn_down_target<D>(c, x, y, z, 1, e, V);
+        add_case<D>(c, t, V);
+        return;
     }
-#pragma unroll 1
-    for (int tt = 0; tt < T.NT; tt++) {
-        if (D == 3 && c.tier < 2) break;
-        if (!((cin >> T.tB[tt]) & 1u)) continue;
+    if (i <= T.NE + T.NT) {
+        const int tt = i - 1 - T.NE;
         const int ff = tfield<D>(cf, tt), gf = tfield<D>(cg, tt);
-        if (crit_c(ff) == crit_c(gf)) continue;
         Verts V = cell_verts<D>(c.G, x, y, z, 2, tt);
         uint32_t t;
-        if (crit_c(gf)) {
+        if (crit_c(gf))
             t = ff == 1 ? V.id[lowest_of(V, c.f)]
                         : vid(c.G, x + T.tcof_v[tt][ff - 2][0], y + T.tcof_v[tt][ff - 2][1], z + T.tcof_v[tt][ff - 2][2]);
-        } else {
+        else
             t = gf >= 2 ? V.id[lowest_of(V, c.f)] : fn_down_target<D>(c, x, y, z, 2, tt, V);
-        }
         add_case<D>(c, t, V);
+        return;
     }
-#pragma unroll 1
-    for (int k = 0; k < T.NK; k++) {
-        if (!((cin >> 7) & 1u)) break;
-        const int ff = kfield<D>(cf, k), gf = kfield<D>(cg, k);
-        if (crit_c(ff) == crit_c(gf)) continue;
-        Verts V = cell_verts<D>(c.G, x, y, z, 3, k);
-        const uint32_t t = crit_c(gf) ? V.id[lowest_of(V, c.f)] : fn_down_target<D>(c, x, y, z, 3, k, V);
-        add_case<D>(c, t, V);
-    }
+    const int k = i - 1 - T.NE - T.NT;
+    const int gf = kfield<D>(cg, k);
+    Verts V = cell_verts<D>(c.G, x, y, z, 3, k);
+    const uint32_t t = crit_c(gf) ? V.id[lowest_of(V, c.f)] : fn_down_target<D>(c, x, y, z, 3, k, V);
+    add_case<D>(c, t, V);
 }
 
 // ------------------------------------------------------------------------------------

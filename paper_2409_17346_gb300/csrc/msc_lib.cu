@@ -266,6 +266,80 @@ __device__ __forceinline__ void for_each_listed_in(uint32_t (*q)[32 * 32], const
     }
 }
 
+// The C-pass over the listed blocks of the critical-difference bitset.  One warp per block
+// compacts the block's set bits (anchors, ascending) into its row of q, then compacts the
+// false cases of each group of 32 anchors (case_mask) into its row of cq, so that every lane
+// applies one case (case_apply) instead of looping over its own anchor's cells while the
+// other lanes wait.  Empty blocks have their summary bit cleared; non-empty blocks are handed
+// to keep.  Needs blockDim.x == TPB.
+constexpr int CASES_PER_ANCHOR = 26;
+template <int D, class K = NoKeep>
+__device__ __forceinline__ void cpass_listed(const Ctx &c, uint16_t (*q)[32 * 32], uint16_t (*cq)[32 * CASES_PER_ANCHOR],
+                                             const uint32_t *blk, unsigned long long nblk, unsigned long long *count,
+                                             K &&keep = K{})
+{
+    const unsigned lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint16_t *mq = q[wib];   // anchors as offsets in their 1024-anchor block
+    uint16_t *cw = cq[wib];
+    const unsigned long long nw = (c.G.n + 31ull) / 32;
+    const unsigned long long warp = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long nwarps = (gridDim.x * (unsigned long long)blockDim.x) >> 5;
+    for (unsigned long long i = warp; i < nblk; i += nwarps) {
+        const uint32_t b = blk[i];
+        const unsigned long long w = (unsigned long long)b * 32 + lane;
+        uint32_t mine = w < nw ? c.Cbits[w] : 0u;
+        const unsigned cnt = __popc(mine);
+        unsigned pre = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, pre, o);
+            if (lane >= (unsigned)o) pre += y;
+        }
+        const unsigned total = __shfl_sync(0xffffffffu, pre, 31);
+        if (total == 0) {
+            if (lane == 0) atomicAnd(c.Csum + (b >> 5), ~(1u << (b & 31)));
+            continue;
+        }
+        if (lane == 0) {
+            if (count) atomicAdd(count, (unsigned long long)total);
+            keep(b);
+        }
+        unsigned at = pre - cnt;
+        while (mine) {
+            const int k = __ffs(mine) - 1;
+            mine &= mine - 1;
+            mq[at++] = (uint16_t)(lane * 32 + (unsigned)k);
+        }
+        __syncwarp();
+        const uint32_t base = b * 1024u;
+        for (unsigned k0 = 0; k0 < total; k0 += 32) {
+            uint32_t m = 0;
+            if (k0 + lane < total) {
+                const uint32_t p = base + mq[k0 + lane];
+                m = case_mask<D>(c, p, __ldg(c.code_f + p), c.code_g[p]);
+            }
+            const unsigned nc = __popc(m);
+            unsigned cpre = nc;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, cpre, o);
+                if (lane >= (unsigned)o) cpre += y;
+            }
+            const unsigned ctot = __shfl_sync(0xffffffffu, cpre, 31);
+            unsigned ca = cpre - nc;
+            while (m) {
+                const int k = __ffs(m) - 1;
+                m &= m - 1;
+                cw[ca++] = (uint16_t)((lane << 5) | (unsigned)k);
+            }
+            __syncwarp();
+            for (unsigned j = lane; j < ctot; j += 32) {
+                const unsigned e = cw[j];
+                case_apply<D>(c, base + mq[k0 + (e >> 5)], (int)(e & 31u));
+            }
+            __syncwarp();
+        }
+    }
+}
+
 template <class F>
 __device__ __forceinline__ void for_each_listed(const uint32_t *bits, uint32_t n, const uint32_t *blk,
                                                 unsigned long long nblk, uint32_t *sum, F &&f,
@@ -378,10 +452,11 @@ template <int D> __global__ void __launch_bounds__(TPB) k_ctargets(Ctx c)
 {
     if (c.ls->halt) return;
     __shared__ BlockTally tally;
+    __shared__ uint16_t q[TPB / 32][32 * 32];
+    __shared__ uint16_t cq[TPB / 32][32 * CASES_PER_ANCHOR];
     Ctx cc = c;
     tally_begin(tally, cc);
-    for_each_listed(c.Cbits, c.G.n, c.Cblk, c.ls->nblk, c.Csum, [&](uint32_t p) { ctargets_anchor<D>(cc, p); },
-                    &c.ls->cpass_items);
+    cpass_listed<D>(cc, q, cq, c.Cblk, c.ls->nblk, &c.ls->cpass_items);
     tally_end(tally, c);
 }
 
@@ -566,7 +641,7 @@ __global__ void k_set_track(LoopState *ls, int v) { ls->track_dirty = v; }
 // round counters alternate between two Counters by round parity, so a round's counters are
 // zeroed while the round after it runs.  Data written by other blocks is read with plain
 // (coherent) loads after a barrier, never through the read-only path.
-constexpr int ROUND_STAGE = 8192;                          // dirty-anchor stage entries
+constexpr int ROUND_STAGE = 4096;                          // dirty-anchor stage entries
 constexpr unsigned long long BAR_TIMEOUT_NS = 2000000000ull;   // 2 s
 constexpr unsigned BAR_SPIN_CAP = 1u << 28;
 
@@ -625,9 +700,10 @@ __global__ void __launch_bounds__(TPB, 2) k_rounds(Ctx c, GridBarrier *gb, Count
                                                 unsigned long long leave_items)
 {
     __shared__ union {
-        uint32_t q[TPB / 32][32 * 32];   // P1: compacted anchors of a block, per warp
+        uint16_t q[TPB / 32][32 * 32];   // P1: compacted anchors of a block, per warp
         Stage<ROUND_STAGE> sd;           // P3: dirty anchors
     } u;
+    __shared__ uint16_t cq[TPB / 32][32 * CASES_PER_ANCHOR];   // P1: compacted false cases
     __shared__ Stage<TPB> se;            // P2: changed vertices; P4: separatrix dirty anchors
     __shared__ BlockTally tally;
     __shared__ int ring[64][3];
@@ -649,9 +725,8 @@ __global__ void __launch_bounds__(TPB, 2) k_rounds(Ctx c, GridBarrier *gb, Count
         {
             uint32_t *nl = lists[nxt];
             unsigned long long *nn = &ls->nbl[nxt];
-            for_each_listed_in(u.q, c.Cbits, c.G.n, lists[cur], ls->nbl[cur], c.Csum,
-                               [&](uint32_t p) { ctargets_anchor<D>(cc, p); }, &ls->cpass_items,
-                               [&](uint32_t b) { nl[atomicAdd(nn, 1ull)] = b; });
+            cpass_listed<D>(cc, u.q, cq, lists[cur], ls->nbl[cur], &ls->cpass_items,
+                            [&](uint32_t b) { nl[atomicAdd(nn, 1ull)] = b; });
         }
         tally_end(tally, cc);
         if (!grid_sync(gb, ls)) return;
