@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC_DIR = os.path.join(HERE, "csrc")
 SOURCES = [os.path.join(SRC_DIR, "msc_lib.cu"), os.path.join(SRC_DIR, "msc_server.cpp")]
-DEPS = SOURCES + [os.path.join(SRC_DIR, f) for f in ("msc_cells.cuh", "msc_core.cuh", "msc_runtime.h")] + \
+DEPS = SOURCES + [os.path.join(SRC_DIR, f) for f in ("msc_cells.cuh", "msc_core.cuh", "msc_dense.cuh", "msc_runtime.h")] + \
     [os.path.join(ROOT, "include", "msc.h")]
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmsc.so")

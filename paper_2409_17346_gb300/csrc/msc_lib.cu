@@ -27,6 +27,7 @@
 
 #include "../../include/msc.h"
 #include "msc_core.cuh"
+#include "msc_dense.cuh"
 #include "msc_runtime.h"
 
 using namespace msc;
@@ -409,6 +410,228 @@ __global__ void __launch_bounds__(TPB, 3) k_eval_dense(const float *v, Grid G, u
                 if (wc) atomicOr(csum + (p >> 15), 1u << ((p >> 10) & 31));
             }
         }
+    }
+}
+
+// Dense discrete gradient of a 3D field by z-marching tiles (msc_dense.cuh): grid
+// (ceil(nx/32), ceil(ny/8), ceil(nz/16)), 256 threads.  With ref: also the bits of the
+// anchors whose code differs from ref's (mbits) and whose critical cells differ (cbits,
+// csum); mbits and cbits must be zero on entry (a warp's anchors need not start a word).
+__global__ void __launch_bounds__(256, 3) k_eval_tile(const float *v, Grid G, uint64_t *out, const uint64_t *ref,
+                                                      uint32_t *mbits, uint32_t *cbits, uint32_t *csum, int tier)
+{
+    using namespace dense;
+    using T3 = Tab<3>;
+    __shared__ Smem S;
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * ZS;
+    const int zend = min(z0 + ZS, G.nz);
+    const float INF = pos_inf();
+    auto vs = [&](int z) { return (z - z0 + 2 * NVAL) % NVAL; };
+    auto load_plane = [&](int z) {
+        float(*P)[VX] = S.val[vs(z)];
+        const bool zin = z >= 0 && z < G.nz;
+        for (int i = tid; i < VX * VY; i += 256) {
+            const int ly = i / VX, lx = i - ly * VX;
+            const int x = x0 - 1 + lx, y = y0 - 1 + ly;
+            P[ly][lx] = (zin && x >= 0 && x < G.nx && y >= 0 && y < G.ny) ? ld(v + vid(G, x, y, z)) : INF;
+        }
+    };
+    load_plane(z0 - 1);
+    load_plane(z0);
+    const int nsteps = (zend - z0) + 3;
+    for (int j = 0; j < nsteps; j++) {
+        load_plane(z0 + j + 1);
+        __syncthreads();
+        // vertex pairs of plane zv (Sec. 4.2: the edge to the lowest lower neighbour)
+        {
+            const int zv = z0 + j;
+            const float(*Pl[3])[VX] = {S.val[vs(zv - 1)], S.val[vs(zv)], S.val[vs(zv + 1)]};
+            uint8_t(*Q)[PX] = S.vp[(zv - z0) % NVP];
+            for (int i = tid; i < PX * PY; i += 256) {
+                const int ly = i / PX, lx = i - ly * PX;
+                float bv = INF;
+                int bn = 15;
+                static_for<14>([&](auto ic) {
+                    constexpr int n = TabsC::D.vord[decltype(ic)::value];
+                    constexpr int dx = TabC<3>::T.nb[n][0], dy = TabC<3>::T.nb[n][1], dz = TabC<3>::T.nb[n][2];
+                    const float w = Pl[dz + 1][ly + 1 + dy][lx + 1 + dx];
+                    if (w < bv) { bv = w; bn = n; }
+                });
+                const float wc = Pl[1][ly + 1][lx + 1];
+                const bool below = bv < wc || (bv == wc && bn >= T3::NE);
+                Q[ly][lx] = (uint8_t)(below ? bn : 15);
+            }
+        }
+        __syncthreads();
+        // edges of plane ze: paired down with the higher end, else up with the lowest cofacet
+        // below both ends
+        if (j >= 1) {
+            const int ze = z0 + j - 1;
+            const float(*Pl[4])[VX] = {S.val[vs(ze - 1)], S.val[vs(ze)], S.val[vs(ze + 1)], S.val[vs(ze + 2)]};
+            const uint8_t(*Q[2])[PX] = {S.vp[(ze - z0) % NVP], S.vp[(ze + 1 - z0) % NVP]};
+            uint32_t(*E)[EX] = S.ef[(ze - z0) % NEDG];
+            for (int i = tid; i < EX * EY; i += 256) {
+                const int ly = i / EX, lx = i - ly * EX;
+                const float wa = Pl[1][ly + 1][lx + 1];
+                const int vpa = Q[0][ly][lx];
+                uint32_t fld = 0;
+                static_for<7>([&](auto ec) {
+                    constexpr int e = decltype(ec)::value;
+                    constexpr int bx = TabsC::D.e_b[e][0], by = TabsC::D.e_b[e][1], bz = TabsC::D.e_b[e][2];
+                    const float wb = Pl[1 + bz][ly + 1 + by][lx + 1 + bx];
+                    const bool a_hi = wb < wa;
+                    const bool down = a_hi ? (vpa == e) : ((int)Q[bz][ly + by][lx + bx] == T3::NE + e);
+                    float bv = INF;
+                    int bi = -1;
+                    static_for<TabsC::D.e_nc[e]>([&](auto icc) {
+                        constexpr int ci = decltype(icc)::value;
+                        constexpr int dx = TabsC::D.e_c[e][ci][0], dy = TabsC::D.e_c[e][ci][1], dz = TabsC::D.e_c[e][ci][2];
+                        const float w = Pl[1 + dz][ly + 1 + dy][lx + 1 + dx];
+                        if (w < bv) { bv = w; bi = ci; }
+                    });
+                    constexpr unsigned mla = TabsC::D.e_lta[e], mlb = TabsC::D.e_ltb[e];
+                    const bool lta = bi >= 0 && ((mla >> bi) & 1u);
+                    const bool ltb = bi >= 0 && ((mlb >> bi) & 1u);
+                    const bool below = (bv < wa || (bv == wa && lta)) && (bv < wb || (bv == wb && ltb));
+                    const uint32_t f = down ? 1u : (below ? 2u + (uint32_t)bi : 0u);
+                    fld |= f << (3 * e);
+                });
+                E[ly][lx] = fld;
+            }
+        }
+        __syncthreads();
+        // triangles of plane zt: paired down with the highest edge, else up with the lowest
+        // tetrahedron candidate below all three vertices
+        if (j >= 2) {
+            const int zt = z0 + j - 2;
+            const float(*Pl[4])[VX] = {S.val[vs(zt - 1)], S.val[vs(zt)], S.val[vs(zt + 1)], S.val[vs(zt + 2)]};
+            const uint32_t(*E[2])[EX] = {S.ef[(zt - z0) % NEDG], S.ef[(zt + 1 - z0) % NEDG]};
+            uint32_t(*R)[RX] = S.tf[(zt - z0) % NTRI];
+            for (int i = tid; i < RX * RY; i += 256) {
+                const int ly = i / RX, lx = i - ly * RX;
+                uint32_t fld = 0;
+                static_for<12>([&](auto tc) {
+                    constexpr int t = decltype(tc)::value;
+#define MSC_TV(s, k) TabsC::D.t_v[t][s][k]
+                    const float w0 = Pl[1 + MSC_TV(0, 2)][ly + 1 + MSC_TV(0, 1)][lx + 1 + MSC_TV(0, 0)];
+                    const float wA = Pl[1 + MSC_TV(1, 2)][ly + 1 + MSC_TV(1, 1)][lx + 1 + MSC_TV(1, 0)];
+                    const float wB = Pl[1 + MSC_TV(2, 2)][ly + 1 + MSC_TV(2, 1)][lx + 1 + MSC_TV(2, 0)];
+#undef MSC_TV
+                    const bool la = w0 <= wA && w0 <= wB;
+                    const bool lb = !la && wA <= wB;
+                    uint32_t hf[3];
+                    static_for<3>([&](auto jc) {
+                        constexpr int s = decltype(jc)::value;
+                        constexpr int hx = TabsC::D.t_he[t][s][0], hy = TabsC::D.t_he[t][s][1], hz = TabsC::D.t_he[t][s][2];
+                        constexpr int hs = 3 * TabsC::D.t_het[t][s];
+                        hf[s] = (E[hz][ly + hy][lx + hx] >> hs) & 7u;
+                    });
+                    constexpr unsigned hw0 = 2u + TabsC::D.t_hew[t][0], hw1 = 2u + TabsC::D.t_hew[t][1];
+                    constexpr unsigned hw2 = 2u + TabsC::D.t_hew[t][2];
+                    const bool down = la ? hf[0] == hw0 : (lb ? hf[1] == hw1 : hf[2] == hw2);
+                    float bv = INF;
+                    int bi = -1;
+                    static_for<2>([&](auto icc) {
+                        constexpr int ci = decltype(icc)::value;
+                        constexpr int dx = TabsC::D.t_c[t][ci][0], dy = TabsC::D.t_c[t][ci][1], dz = TabsC::D.t_c[t][ci][2];
+                        const float w = Pl[1 + dz][ly + 1 + dy][lx + 1 + dx];
+                        if (w < bv) { bv = w; bi = ci; }
+                    });
+                    const float lv = la ? w0 : (lb ? wA : wB);
+                    constexpr unsigned lt0 = TabsC::D.t_lt[t][0], lt1 = TabsC::D.t_lt[t][1], lt2 = TabsC::D.t_lt[t][2];
+                    const unsigned ltm = la ? lt0 : (lb ? lt1 : lt2);
+                    const bool below = bv < lv || (bv == lv && bi >= 0 && ((ltm >> bi) & 1u));
+                    const uint32_t f = down ? 1u : (below ? 2u + (uint32_t)bi : 0u);
+                    fld |= f << (2 * t);
+                });
+                R[ly][lx] = fld;
+            }
+        }
+        __syncthreads();
+        // codes of plane zk: tetrahedra (paired down iff their highest triangle chose them)
+        // and the fields of every cell the anchor owns
+        if (j >= 3) {
+            const int zk = z0 + j - 3;
+            const int lx = tid & 31, ly = tid >> 5;
+            const int x = x0 + lx, y = y0 + ly;
+            const bool valid = x < G.nx && y < G.ny;
+            const float(*Pl[2])[VX] = {S.val[vs(zk)], S.val[vs(zk + 1)]};
+            const uint32_t(*R[2])[RX] = {S.tf[(zk - z0) % NTRI], S.tf[(zk + 1 - z0) % NTRI]};
+            uint64_t code = 0;
+            unsigned long long p = 0;
+            if (valid) {
+                p = (unsigned long long)x + (unsigned long long)G.nx * ((unsigned long long)y + (unsigned long long)G.ny * zk);
+                const unsigned cin = corner_mask<3>(G, x, y, zk);
+                code = S.vp[(zk - z0) % NVP][ly][lx];
+                const uint32_t efl = S.ef[(zk - z0) % NEDG][ly][lx];
+                const uint32_t tfl = R[0][ly][lx];
+                static_for<7>([&](auto ec) {
+                    constexpr int e = decltype(ec)::value;
+                    if ((cin >> (e + 1)) & 1u) code |= (uint64_t)((efl >> (3 * e)) & 7u) << (4 + 3 * e);
+                });
+                static_for<12>([&](auto tc) {
+                    constexpr int t = decltype(tc)::value;
+                    constexpr int top = TabC<3>::T.tB[t];
+                    if ((cin >> top) & 1u) code |= (uint64_t)((tfl >> (2 * t)) & 3u) << (T3::TRI_BIT0 + 2 * t);
+                });
+                if ((cin >> 7) & 1u) {
+                    static_for<6>([&](auto kc) {
+                        constexpr int k = decltype(kc)::value;
+                        float w[4];
+                        static_for<4>([&](auto sc) {
+                            constexpr int s = decltype(sc)::value;
+                            constexpr int vx = TabsC::D.k_v[k][s][0], vy = TabsC::D.k_v[k][s][1], vz = TabsC::D.k_v[k][s][2];
+                            w[s] = Pl[vz][ly + 1 + vy][lx + 1 + vx];
+                        });
+                        const bool l0 = w[0] <= w[1] && w[0] <= w[2] && w[0] <= w[3];
+                        const bool l1 = !l0 && w[1] <= w[2] && w[1] <= w[3];
+                        const bool l2 = !l0 && !l1 && w[2] <= w[3];
+                        uint32_t ff[4];
+                        static_for<4>([&](auto sc) {
+                            constexpr int s = decltype(sc)::value;
+                            constexpr int fx = TabsC::D.k_f[k][s][0], fy = TabsC::D.k_f[k][s][1], fz = TabsC::D.k_f[k][s][2];
+                            constexpr int fs = 2 * TabsC::D.k_ft[k][s];
+                            ff[s] = (R[fz][ly + fy][lx + fx] >> fs) & 3u;
+                        });
+                        constexpr unsigned fw0 = 2u + TabsC::D.k_fw[k][0], fw1 = 2u + TabsC::D.k_fw[k][1];
+                        constexpr unsigned fw2 = 2u + TabsC::D.k_fw[k][2], fw3 = 2u + TabsC::D.k_fw[k][3];
+                        const bool down = l0 ? ff[0] == fw0 : l1 ? ff[1] == fw1 : l2 ? ff[2] == fw2 : ff[3] == fw3;
+                        code |= (uint64_t)down << (T3::TET_BIT0 + k);
+                    });
+                }
+                out[p] = code;
+            }
+            if (ref) {
+                bool m = false, cm = false;
+                if (valid) {
+                    const uint64_t r = __ldg(ref + p);
+                    m = code != r;
+                    cm = m && crit_sig<3>(code, tier) != crit_sig<3>(r, tier);
+                }
+                const uint32_t wm = __ballot_sync(0xffffffffu, m), wc = __ballot_sync(0xffffffffu, cm);
+                // lane k holds anchor p0 + k (lanes past the row end hold no bit)
+                const unsigned long long p0 = __shfl_sync(0xffffffffu, p, 0);
+                if (lx == 0 && (wm | wc)) {
+                    const unsigned sh = (unsigned)(p0 & 31u);
+                    const unsigned long long w0 = p0 >> 5;
+                    if (wm) {
+                        atomicOr(mbits + w0, wm << sh);
+                        if (sh && (wm >> (32 - sh))) atomicOr(mbits + w0 + 1, wm >> (32 - sh));
+                    }
+                    if (wc) {
+                        atomicOr(cbits + w0, wc << sh);
+                        if (sh && (wc >> (32 - sh))) atomicOr(cbits + w0 + 1, wc >> (32 - sh));
+                    }
+                }
+                if (cm) {
+                    const uint32_t blk = (uint32_t)(p >> 10);
+                    const unsigned peers = __match_any_sync(__activemask(), blk);
+                    if ((unsigned)(__ffs(peers) - 1) == (unsigned)lx) atomicOr(csum + (blk >> 5), 1u << (blk & 31));
+                }
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -1446,7 +1669,17 @@ template <int D> msc_status eval_dense(msc_handle *h, const float *v, Grid G, ui
                                        const uint64_t *ref = nullptr, uint32_t *mbits = nullptr,
                                        uint32_t *cbits = nullptr, uint32_t *csum = nullptr, int tier = 4)
 {
-    KL(h, MSC_K_DENSE, s, k_eval_dense<D><<<grid_occ((const void *)k_eval_dense<D>, G.n), TPB, 0, s>>>(v, G, out, ref, mbits, cbits, csum, tier));
+    if constexpr (D == 3) {
+        if (ref) {
+            CK(cudaMemsetAsync(mbits, 0, ((G.n + 31ull) / 32) * 4, s));
+            CK(cudaMemsetAsync(cbits, 0, ((G.n + 31ull) / 32) * 4, s));
+        }
+        const dim3 grid((G.nx + dense::TX - 1) / dense::TX, (G.ny + dense::TY - 1) / dense::TY,
+                        (G.nz + dense::ZS - 1) / dense::ZS);
+        KL(h, MSC_K_DENSE, s, k_eval_tile<<<grid, 256, 0, s>>>(v, G, out, ref, mbits, cbits, csum, tier));
+    } else {
+        KL(h, MSC_K_DENSE, s, k_eval_dense<D><<<grid_occ((const void *)k_eval_dense<D>, G.n), TPB, 0, s>>>(v, G, out, ref, mbits, cbits, csum, tier));
+    }
     CK(cudaGetLastError());
     return MSC_OK;
 }
