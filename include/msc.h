@@ -264,6 +264,13 @@ msc_status msc_reset_stats(msc_handle *h);
 /* Bytes of device memory a handle of this grid holds while fixing (for admission). */
 uint64_t msc_device_bytes(int nx, int ny, int nz);
 
+/* Device memory that handles free stays in the library's memory pool on that device, so
+ * that the next handle of a similar size reuses it without going back to the driver (a
+ * server limits what the pool keeps to its memory budget).  This call returns everything
+ * the pool of the current device holds unused to the driver, after waiting for the device
+ * to finish its work.  Handles that are still alive keep their memory. */
+msc_status msc_release_cached_memory(void);
+
 /* ---------------------------------------------------------------------------------------
  * Serving: a request loop with continuous batching.  The paper runs one field at a time;
  * this runtime admits fix jobs as they arrive and runs several at once on one GPU.

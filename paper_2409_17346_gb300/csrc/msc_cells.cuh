@@ -87,6 +87,13 @@ template <int D> struct Tab {
     // or triangle, vertices of a cell)
     int nring;
     int ring[64][3];
+    // ascending V-path step in f (Sec. 4.4): a top cell of type t paired with its highest
+    // facet (the one opposite its lowest vertex, slot j in cell order) continues into that
+    // facet's other cofacet, of type asc_type[t][j] at anchor offset asc_off[t][j]
+    int asc_off[6][4][3];
+    int asc_type[6][4];
+    // triangle type t whose lowest vertex is slot j: the index of the facet edge opposite it
+    int tri_opp[12][3];
 };
 
 constexpr int popc3(int m) { return (m & 1) + ((m >> 1) & 1) + ((m >> 2) & 1); }
@@ -255,6 +262,34 @@ template <int D> constexpr Tab<D> make_tab()
             t.ring[t.nring][0] = o[0]; t.ring[t.nring][1] = o[1]; t.ring[t.nring][2] = o[2];
             t.nring++;
         }
+    for (int tt = 0; tt < T::NTOP; tt++) {
+        const int nv = D + 1;
+        const int cs[4] = {0, D == 3 ? t.kA[tt] : t.tA[tt], D == 3 ? t.kB[tt] : t.tB[tt], 7};
+        for (int j = 0; j < nv; j++) {
+            int fj = 0;
+            for (int q = 0; q < nv; q++)
+                if ((D == 3 ? t.kfac_opp[tt][q] : t.tfac_opp[tt][q]) == cs[j]) fj = q;
+            const int *fo = D == 3 ? t.kfac_anc[tt][fj] : t.tfac_anc[tt][fj];
+            const int ft = D == 3 ? t.kfac_type[tt][fj] : t.tfac_type[tt][fj];
+            const int ncof = D == 3 ? t.ntcof[ft] : t.necof[ft];
+            int ib = 0;
+            for (int i = 0; i < ncof; i++) {
+                const int *an = D == 3 ? t.tcof_anc[ft][i] : t.ecof_anc[ft][i];
+                const int ty = D == 3 ? t.tcof_type[ft][i] : t.ecof_type[ft][i];
+                if (an[0] == -fo[0] && an[1] == -fo[1] && an[2] == -fo[2] && ty == tt) ib = i;
+            }
+            const int io = 1 - ib;
+            const int *an = D == 3 ? t.tcof_anc[ft][io] : t.ecof_anc[ft][io];
+            for (int k = 0; k < 3; k++) t.asc_off[tt][j][k] = fo[k] + an[k];
+            t.asc_type[tt][j] = D == 3 ? t.tcof_type[ft][io] : t.ecof_type[ft][io];
+        }
+    }
+    for (int tt = 0; tt < T::NT; tt++) {
+        const int cs[3] = {0, t.tA[tt], t.tB[tt]};
+        for (int j = 0; j < 3; j++)
+            for (int q = 0; q < 3; q++)
+                if (t.tfac_opp[tt][q] == cs[j]) t.tri_opp[tt][j] = q;
+    }
     t.nwin = 0;
     for (int z = zlo; z <= zhi; z++)
         for (int y = -1; y <= 2; y++)

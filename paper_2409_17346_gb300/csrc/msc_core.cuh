@@ -98,6 +98,8 @@ struct Ctx {
     float *gprev;                    // value before the current round, for vertices in T u X
     uint8_t *state;
     const uint64_t *code_f;
+    const uint64_t *low_f;           // 3D: per anchor, the f-lowest vertex slot of each triangle
+                                     // t (bits 2t) and tetrahedron k (bits 24 + 2k)
     uint64_t *code_g;
     uint32_t *Tbits, *Xbits, *Dbits;
     uint32_t *Tlist, *Xlist, *Dlist;
@@ -904,6 +906,22 @@ template <int D> MSC_HD inline bool desc_succ(const Ctx &c, uint32_t u, uint32_t
 // successor of top cell beta on its ascending V-path in f
 template <int D> MSC_HD inline bool asc_succ(const Ctx &c, uint32_t beta, uint32_t &nb)
 {
+    if constexpr (D == 3) {
+        // the tetrahedron's lowest vertex from the prepared slots: no vertex values to load
+        const Tab<3> &T = rt_tab<3>();
+        const uint32_t a = beta / 6;
+        const int t = (int)(beta % 6);
+        const uint64_t cf = ld(c.code_f + a), lw = ld(c.low_f + a);
+        if (kfield<3>(cf, t) == 0) return false;                 // a maximum
+        const int jl = (int)((lw >> (24 + 2 * t)) & 3u);
+        int x, y, z;
+        coords(c.G, a, x, y, z);
+        x += T.asc_off[t][jl][0]; y += T.asc_off[t][jl][1]; z += T.asc_off[t][jl][2];
+        const int t2 = T.asc_type[t][jl];
+        if (!top_exists<3>(c.G, x, y, z, t2)) return false;      // the path leaves the domain
+        nb = vid(c.G, x, y, z) * 6 + (uint32_t)t2;
+        return true;
+    }
     int x, y, z, t = (int)(beta % Tab<D>::NTOP);
     coords(c.G, beta / Tab<D>::NTOP, x, y, z);
     int fx, fy, fz, ft, ib, jl;
@@ -950,12 +968,8 @@ MSC_HD inline int tri_children(const Ctx &c, uint32_t tri, uint32_t *out, bool *
     int x, y, z;
     coords(c.G, tri / 12, x, y, z);
     int entry = -1;
-    if (tfield<3>(ld(c.code_f + tri / 12), tt) == 1) {
-        Verts V = cell_verts<3>(c.G, x, y, z, 2, tt);
-        const int jl = lowest_of(V, c.f);
-        const int corner = jl == 0 ? 0 : (jl == 1 ? T.tA[tt] : T.tB[tt]);
-        for (int j = 0; j < 3; j++) if (T.tfac_opp[tt][j] == corner) entry = j;
-    }
+    const uint64_t cf = ld(c.code_f + tri / 12), lw = ld(c.low_f + tri / 12);
+    if (tfield<3>(cf, tt) == 1) entry = T.tri_opp[tt][(lw >> (2 * tt)) & 3u];   // paired with the highest edge
     int n = 0;
     for (int j = 0; j < 3; j++) {
         if (j == entry) continue;

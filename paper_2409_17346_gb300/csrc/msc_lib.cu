@@ -418,7 +418,8 @@ __global__ void __launch_bounds__(TPB, 3) k_eval_dense(const float *v, Grid G, u
 // anchors whose code differs from ref's (mbits) and whose critical cells differ (cbits,
 // csum); mbits and cbits must be zero on entry (a warp's anchors need not start a word).
 __global__ void __launch_bounds__(256, 3) k_eval_tile(const float *v, Grid G, uint64_t *out, const uint64_t *ref,
-                                                      uint32_t *mbits, uint32_t *cbits, uint32_t *csum, int tier)
+                                                      uint32_t *mbits, uint32_t *cbits, uint32_t *csum, int tier,
+                                                      uint64_t *low)
 {
     using namespace dense;
     using T3 = Tab<3>;
@@ -601,6 +602,34 @@ __global__ void __launch_bounds__(256, 3) k_eval_tile(const float *v, Grid G, ui
                     });
                 }
                 out[p] = code;
+                if (low) {
+                    // lowest vertex slot of every triangle (bits 2t) and tetrahedron (bits 24 + 2k)
+                    uint64_t lw = 0;
+                    static_for<12>([&](auto tc) {
+                        constexpr int t = decltype(tc)::value;
+                        constexpr int az = TabsC::D.t_v[t][1][2], ay = TabsC::D.t_v[t][1][1], ax = TabsC::D.t_v[t][1][0];
+                        constexpr int bz = TabsC::D.t_v[t][2][2], by = TabsC::D.t_v[t][2][1], bx = TabsC::D.t_v[t][2][0];
+                        const float w0 = Pl[0][ly + 1][lx + 1];
+                        const float wA = Pl[az][ly + 1 + ay][lx + 1 + ax];
+                        const float wB = Pl[bz][ly + 1 + by][lx + 1 + bx];
+                        const bool la = w0 <= wA && w0 <= wB, lb = !la && wA <= wB;
+                        lw |= (uint64_t)(la ? 0 : (lb ? 1 : 2)) << (2 * t);
+                    });
+                    static_for<6>([&](auto kc) {
+                        constexpr int k = decltype(kc)::value;
+                        float w[4];
+                        static_for<4>([&](auto sc) {
+                            constexpr int s = decltype(sc)::value;
+                            constexpr int vx = TabsC::D.k_v[k][s][0], vy = TabsC::D.k_v[k][s][1], vz = TabsC::D.k_v[k][s][2];
+                            w[s] = Pl[vz][ly + 1 + vy][lx + 1 + vx];
+                        });
+                        const bool l0 = w[0] <= w[1] && w[0] <= w[2] && w[0] <= w[3];
+                        const bool l1 = !l0 && w[1] <= w[2] && w[1] <= w[3];
+                        const bool l2 = !l0 && !l1 && w[2] <= w[3];
+                        lw |= (uint64_t)(l0 ? 0 : (l1 ? 1 : (l2 ? 2 : 3))) << (24 + 2 * k);
+                    });
+                    low[p] = lw;
+                }
             }
             if (ref) {
                 bool m = false, cm = false;
@@ -1381,6 +1410,35 @@ struct EntryStream {
     }
 };
 
+// The library's own stream-ordered memory pool on each device.  Device memory that a handle
+// frees stays in the pool (release threshold: unlimited) for the next handle, so a sequence
+// of prepare / fix / destroy calls does not map and unmap its working set every time;
+// msc_release_cached_memory hands it back to the driver.
+std::mutex g_pool_mu;
+std::vector<std::pair<int, cudaMemPool_t>> g_pools;
+
+cudaMemPool_t lib_pool()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    for (auto &dp : g_pools)
+        if (dp.first == dev) return dp.second;
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) { cudaGetLastError(); pool = nullptr; }
+    if (pool) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    g_pools.emplace_back(dev, pool);
+    return pool;
+}
+
 template <class T> struct DevBuf {
     T *p = nullptr;
     size_t n = 0;
@@ -1392,7 +1450,10 @@ template <class T> struct DevBuf {
     {
         if (count <= n && p) return cudaSuccess;
         release();
-        cudaError_t e = cudaMallocAsync((void **)&p, (count ? count : 1) * sizeof(T), g_alloc_stream);
+        cudaMemPool_t pool = lib_pool();
+        const size_t bytes = (count ? count : 1) * sizeof(T);
+        cudaError_t e = pool ? cudaMallocFromPoolAsync((void **)&p, bytes, pool, g_alloc_stream)
+                             : cudaMallocAsync((void **)&p, bytes, g_alloc_stream);
         if (e == cudaSuccess) n = count;
         else p = nullptr;
         return e;
@@ -1494,6 +1555,7 @@ struct msc_handle {
     int D = 3;
     DevBuf<float> f;
     DevBuf<uint64_t> code_f;
+    DevBuf<uint64_t> low_f;   // 3D: lowest vertex slot of every triangle and tetrahedron under f
     DevBuf<uint32_t> seeds_desc, seeds_asc, seeds_ss;
     uint32_t n_desc = 0, n_asc = 0, n_ss = 0;
     // fix state (allocated on first use)
@@ -1645,6 +1707,7 @@ Ctx make_ctx(msc_handle *h, int tier, int qmax, int exact_fallback, float xi)
     c.g = h->g.p;
     c.state = h->state.p;
     c.code_f = h->code_f.p;
+    c.low_f = h->low_f.p;
     c.code_g = h->code_g.p;
     c.Tbits = h->Tbits.p; c.Xbits = h->Xbits.p; c.Dbits = h->Dbits.p;
     c.Tlist = h->Tlist.p; c.Xlist = h->Xlist.p; c.Dlist = h->Dlist.p;
@@ -1667,7 +1730,8 @@ Ctx make_ctx(msc_handle *h, int tier, int qmax, int exact_fallback, float xi)
 
 template <int D> msc_status eval_dense(msc_handle *h, const float *v, Grid G, uint64_t *out, cudaStream_t s,
                                        const uint64_t *ref = nullptr, uint32_t *mbits = nullptr,
-                                       uint32_t *cbits = nullptr, uint32_t *csum = nullptr, int tier = 4)
+                                       uint32_t *cbits = nullptr, uint32_t *csum = nullptr, int tier = 4,
+                                       uint64_t *low = nullptr)
 {
     if constexpr (D == 3) {
         if (ref) {
@@ -1676,7 +1740,7 @@ template <int D> msc_status eval_dense(msc_handle *h, const float *v, Grid G, ui
         }
         const dim3 grid((G.nx + dense::TX - 1) / dense::TX, (G.ny + dense::TY - 1) / dense::TY,
                         (G.nz + dense::ZS - 1) / dense::ZS);
-        KL(h, MSC_K_DENSE, s, k_eval_tile<<<grid, 256, 0, s>>>(v, G, out, ref, mbits, cbits, csum, tier));
+        KL(h, MSC_K_DENSE, s, k_eval_tile<<<grid, 256, 0, s>>>(v, G, out, ref, mbits, cbits, csum, tier, low));
     } else {
         KL(h, MSC_K_DENSE, s, k_eval_dense<D><<<grid_occ((const void *)k_eval_dense<D>, G.n), TPB, 0, s>>>(v, G, out, ref, mbits, cbits, csum, tier));
     }
@@ -1684,9 +1748,9 @@ template <int D> msc_status eval_dense(msc_handle *h, const float *v, Grid G, ui
     return MSC_OK;
 }
 
-msc_status eval_dense_any(msc_handle *h, int D, const float *v, Grid G, uint64_t *out, cudaStream_t s)
+msc_status eval_dense_any(msc_handle *h, int D, const float *v, Grid G, uint64_t *out, cudaStream_t s, uint64_t *low = nullptr)
 {
-    return D == 3 ? eval_dense<3>(h, v, G, out, s) : eval_dense<2>(h, v, G, out, s);
+    return D == 3 ? eval_dense<3>(h, v, G, out, s, nullptr, nullptr, nullptr, nullptr, 4, low) : eval_dense<2>(h, v, G, out, s);
 }
 
 template <int D> msc_status build_seeds(msc_handle *h, cudaStream_t s)
@@ -2317,6 +2381,13 @@ msc_status critical_static(const float *field, Grid G, int64_t *rows, int32_t *d
 // ------------------------------------------------------------------------------------
 // C ABI
 // ------------------------------------------------------------------------------------
+void msc_rt::limit_cached_memory(uint64_t bytes)
+{
+    cudaMemPool_t pool = lib_pool();
+    if (pool) cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &bytes);
+    cudaGetLastError();
+}
+
 void msc_rt::share_device(msc_handle *h, int concurrent)
 {
     if (h && concurrent > 1) h->rounds_grid = std::max(16, 2 * sm_count() / concurrent);
@@ -2381,11 +2452,12 @@ msc_status msc_prepare_original(const float *f, int nx, int ny, int nz, const ms
     auto run = [&]() -> msc_status {
         CK(h->f.alloc(h->G.n));
         CK(h->code_f.alloc(h->G.n));
+        if (h->D == 3) CK(h->low_f.alloc(h->G.n));
         CK(h->cnt.alloc(1));
         CK(h->nM.alloc(8));
         h->prof_mask = (unsigned)o.profile & MSC_PROFILE_ALL;
         CKS(upload_field(h, f, h->G.n, h->f.p, h->nM.p, s, "f"));
-        CKS(eval_dense_any(h, h->D, h->f.p, h->G, h->code_f.p, s));
+        CKS(eval_dense_any(h, h->D, h->f.p, h->G, h->code_f.p, s, h->D == 3 ? h->low_f.p : nullptr));
         h->items[MSC_K_DENSE] += h->G.n;
         CKS(h->D == 3 ? build_seeds<3>(h, s) : build_seeds<2>(h, s));
         CK(cudaEventCreate(&h->ev0));
@@ -2696,6 +2768,17 @@ msc_status msc_critical_cells_static(const float *field, int nx, int ny, int nz,
     cudaStream_t s = (cudaStream_t)stream;
     return nz > 1 ? critical_static<3>(field, G, rows, dims, cap, n_out, s)
                   : critical_static<2>(field, G, rows, dims, cap, n_out, s);
+}
+
+msc_status msc_release_cached_memory(void)
+{
+    g_last_error.clear();
+    CKS(device_ready());
+    cudaMemPool_t pool = lib_pool();
+    if (!pool) return MSC_OK;
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemPoolTrimTo(pool, 0));
+    return MSC_OK;
 }
 
 msc_status msc_get_stats(msc_handle *h, msc_stats *out)

@@ -10,4 +10,6 @@ msc_status set_error(msc_status s, const std::string &msg);
 // blocks of the persistent round kernel for a handle whose fixes share the device with
 // `concurrent` other jobs: a fraction of the SMs each, so that the jobs' kernels fit at once
 void share_device(msc_handle *h, int concurrent);
+// device memory the library's pool keeps for reuse after handles free it (the server's budget)
+void limit_cached_memory(uint64_t bytes);
 }  // namespace msc_rt

@@ -148,13 +148,8 @@ msc_status msc_server_create(const msc_server_config *cfg, msc_server **out)
         if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return msc_rt::set_error(MSC_ERR_CUDA, "cudaMemGetInfo failed");
         c.mem_budget = (uint64_t)(0.9 * (double)fr);
     }
-    // keep freed job memory in the pool for the next job
-    cudaMemPool_t pool;
-    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-        uint64_t thr = c.mem_budget;
-        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
-    }
-    cudaGetLastError();
+    // keep freed job memory (up to the budget) in the library's pool for the next job
+    msc_rt::limit_cached_memory(c.mem_budget);
     msc_server *s = new (std::nothrow) msc_server();
     if (!s) return msc_rt::set_error(MSC_ERR_OOM, "server allocation failed");
     s->cfg = c;

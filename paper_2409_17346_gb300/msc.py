@@ -483,5 +483,10 @@ def device_bytes(shape):
     return int(load().msc_device_bytes(*dims_of(shape)))
 
 
+def release_cached_memory():
+    """Return the device memory the library's pool keeps for reuse to the driver."""
+    _check(load().msc_release_cached_memory())
+
+
 def version():
     return load().msc_version().decode()

@@ -38,7 +38,8 @@ def _field(shape, kind, seed):
     return a.astype(np.float32)
 
 
-SHAPES = [(2, 2), (2, 9), (9, 2), (37, 23), (64, 300), (2, 2, 2), (2, 3, 5), (13, 9, 11), (20, 17, 33)]
+SHAPES = [(2, 2), (2, 9), (9, 2), (37, 23), (64, 300), (2, 2, 2), (2, 3, 5), (13, 9, 11), (20, 17, 33),
+          (18, 10, 67)]
 KINDS = ["normal", "equal", "binary", "signed_zero", "levels"]
 
 
@@ -292,3 +293,13 @@ def test_full_size_grf_256(lib):
 def test_full_size_kolmogorov_512(lib):
     f, fh, xi, tier = synth.config_case("kolmogorov3d")
     _full_size_check(lib, f, fh, xi, tier, n_windows=4, win=12)
+
+
+def test_fix_after_releasing_cached_memory(lib):
+    """Handles freed into the library's pool, the pool trimmed, then the same fix again."""
+    f, fh, xi, _ = synth.config_case("grf3d", seed=7, size=20, rel=1e-3)
+    g1, e1 = lib.Handle(f).fix(fh, xi, tier=4)
+    lib.release_cached_memory()
+    g2, e2 = lib.Handle(f).fix(fh, xi, tier=4)
+    assert np.array_equal(g1.view(np.uint32), g2.view(np.uint32))
+    assert (e1["n_iters_c"], e1["n_iters_s"]) == (e2["n_iters_c"], e2["n_iters_s"])
