@@ -71,6 +71,7 @@ struct Counters {
     unsigned long long nE, nD, nM, novf, err, nSD;
     unsigned long long steps[4];                           // cells stepped: desc, asc, saddle
     unsigned long long rep[16];                            // verify / misc
+    unsigned long long wnext;                              // C-pass: next listed block to take
 };
 
 // device-side state of the edit loop, so rounds can run back to back without the host
@@ -78,7 +79,8 @@ struct LoopState {
     int halt;                 // the current phase is over (no false case left) or an error
     int status;               // 0 running / done, 4 max_iters reached, 6 stalled
     int track_dirty;          // accumulate dirty anchors for the separatrix state
-    int spare;
+    int leave;                // the round graph's remaining rounds do nothing: a round edited
+                              // few vertices, and the persistent round kernel takes over
     unsigned iters, n_c, n_s, n_fb;
     unsigned max_iters, exact_fallback, trace_cap, ntrace;
     unsigned long long nSD;
@@ -86,6 +88,8 @@ struct LoopState {
     unsigned long long nblk;  // entries of the C-block list for the next C-pass
     unsigned long long last_items;   // vertices the last round edited (targets + restores)
     unsigned long long nbl[2];       // persistent round kernel: entries of its two C-block lists
+    int rounds_kernel;               // small rounds run in the persistent round kernel
+    int pad;
 };
 
 // everything a kernel of one job needs (device pointers)

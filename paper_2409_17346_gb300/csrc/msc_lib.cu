@@ -169,6 +169,45 @@ template <int CAP> __device__ __forceinline__ void st_flush(Stage<CAP> &s, uint3
     __syncthreads();
 }
 
+// Appends to a global list staged per warp in shared memory: every lane of a converged warp
+// offers at most one item per call, and the warp copies its stage to the list with one
+// global atomic when the stage fills up and once at the end - no block-wide barrier, so the
+// warps of a block never wait for one another.
+template <int CAP> struct WarpStage {
+    uint32_t buf[CAP];
+    unsigned n;
+};
+
+template <int CAP> __device__ __forceinline__ void ws_flush(WarpStage<CAP> &s, uint32_t *gl, unsigned long long *gn)
+{
+    const unsigned lane = threadIdx.x & 31;
+    __syncwarp();
+    const unsigned m = s.n;
+    if (m) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(gn, (unsigned long long)m);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        for (unsigned j = lane; j < m; j += 32) gl[base + j] = s.buf[j];
+    }
+    __syncwarp();
+    if (lane == 0) s.n = 0;
+    __syncwarp();
+}
+
+template <int CAP>
+__device__ __forceinline__ void ws_push(WarpStage<CAP> &s, bool has, uint32_t v, uint32_t *gl, unsigned long long *gn)
+{
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned mask = __ballot_sync(0xffffffffu, has);
+    if (!mask) return;
+    if (s.n + (unsigned)__popc(mask) > (unsigned)CAP) ws_flush(s, gl, gn);
+    const unsigned pos = s.n + (unsigned)__popc(mask & ((1u << lane) - 1u));
+    if (has) s.buf[pos] = v;
+    __syncwarp();
+    if (lane == 0) s.n += (unsigned)__popc(mask);
+    __syncwarp();
+}
+
 // whole-block rounds over [0, n): every thread of a block runs the same number of rounds
 #define BLOCK_ROUNDS(b, n) for (unsigned long long b = (unsigned long long)blockIdx.x * blockDim.x; b < (n); \
                                 b += (unsigned long long)gridDim.x * blockDim.x)
@@ -277,7 +316,7 @@ constexpr int CASES_PER_ANCHOR = 26;
 template <int D, class K = NoKeep>
 __device__ __forceinline__ void cpass_listed(const Ctx &c, uint16_t (*q)[32 * 32], uint16_t (*cq)[32 * CASES_PER_ANCHOR],
                                              const uint32_t *blk, unsigned long long nblk, unsigned long long *count,
-                                             K &&keep = K{})
+                                             K &&keep = K{}, unsigned long long *next = nullptr)
 {
     const unsigned lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     uint16_t *mq = q[wib];   // anchors as offsets in their 1024-anchor block
@@ -285,7 +324,16 @@ __device__ __forceinline__ void cpass_listed(const Ctx &c, uint16_t (*q)[32 * 32
     const unsigned long long nw = (c.G.n + 31ull) / 32;
     const unsigned long long warp = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
     const unsigned long long nwarps = (gridDim.x * (unsigned long long)blockDim.x) >> 5;
-    for (unsigned long long i = warp; i < nblk; i += nwarps) {
+    // with next: warps take blocks from a shared counter as they finish (blocks hold very
+    // different numbers of cases); otherwise a fixed grid-stride share
+    unsigned long long i = warp;
+    for (;; i += nwarps) {
+        if (next) {
+            unsigned long long t = 0;
+            if (lane == 0) t = atomicAdd(next, 1ull);
+            i = __shfl_sync(0xffffffffu, t, 0);
+        }
+        if (i >= nblk) break;
         const uint32_t b = blk[i];
         const unsigned long long w = (unsigned long long)b * 32 + lane;
         uint32_t mine = w < nw ? c.Cbits[w] : 0u;
@@ -674,6 +722,12 @@ __global__ void k_init_g(const float *f, const float *fh, float *g, uint8_t *sta
     }
 }
 
+constexpr unsigned long long SMALL_ROUND = 8192;   // edited vertices below which rounds run small grids
+
+// a round kernel of a captured round graph does nothing once the phase is over (halt) or
+// the rounds have become small (leave)
+__device__ __forceinline__ bool round_off(const LoopState *ls) { return ls->halt || ls->leave; }
+
 // ---- one edit round as a chain of kernels that read the device loop state (ls): any
 // kernel of a round whose phase is over (ls->halt) does nothing, so rounds can be queued
 // back to back (a captured graph of several rounds) and the host looks only at their end.
@@ -702,14 +756,21 @@ __device__ __forceinline__ void tally_end(BlockTally &t, const Ctx &c)
 
 template <int D> __global__ void __launch_bounds__(TPB) k_ctargets(Ctx c)
 {
-    if (c.ls->halt) return;
-    __shared__ BlockTally tally;
+    if (round_off(c.ls)) return;
+    __shared__ unsigned long long wt[TPB / 32][2];   // per-warp case tallies
     __shared__ uint16_t q[TPB / 32][32 * 32];
     __shared__ uint16_t cq[TPB / 32][32 * CASES_PER_ANCHOR];
+    const unsigned lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    if (lane < 2) wt[wib][lane] = 0;
+    __syncwarp();
     Ctx cc = c;
-    tally_begin(tally, cc);
-    cpass_listed<D>(cc, q, cq, c.Cblk, c.ls->nblk, &c.ls->cpass_items);
-    tally_end(tally, c);
+    cc.tally = wt[wib];
+    cpass_listed<D>(cc, q, cq, c.Cblk, c.ls->nblk, &c.ls->cpass_items, NoKeep{}, &c.cnt->wnext);
+    __syncwarp();
+    if (lane == 0) {
+        if (wt[wib][0]) atomicAdd(&c.cnt->ncase, wt[wib][0]);
+        if (wt[wib][1]) atomicAdd(&c.cnt->nlive, wt[wib][1]);
+    }
 }
 
 // after a targeting pass (kind 0 C, 1 S): stop the phase when there is no false case, stop
@@ -753,7 +814,7 @@ __global__ void k_decide(Ctx c, int kind)
 {
     if (threadIdx.x || blockIdx.x) return;
     LoopState *ls = c.ls;
-    if (ls->halt) return;
+    if (round_off(ls)) return;
     ls->nblk = 0;          // the C-pass has read the block list; the round's end lists it anew
     int status;
     const bool stop = round_stop(ls, c.cnt, ls->iters, status);
@@ -766,22 +827,25 @@ constexpr int DIRTY_STAGE = 8192;
 // list the vertices whose value changed
 template <int D> __global__ void k_edit(Ctx c)
 {
-    if (c.ls->halt) return;
-    __shared__ Stage<TPB> se;
-    st_init(se);
+    if (round_off(c.ls)) return;
+    __shared__ WarpStage<256> se[TPB / 32];
+    const unsigned lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    if (lane == 0) se[wib].n = 0;
+    __syncwarp();
     const unsigned long long nX = c.cnt->nX, items = nX + c.cnt->nT;
-    BLOCK_ROUNDS(b, items)
-    {
-        const unsigned long long i = b + threadIdx.x;
-        if (i < items) {
-            uint32_t v;
-            if (edit_prepare(c, (uint32_t)i, (uint32_t)nX, v)) {
-                edit_apply(c, (uint32_t)i, (uint32_t)nX, v);
-                st_push(se, v, c.Elist, &c.cnt->nE);
-            }
+    const unsigned long long warp = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long nwarps = (gridDim.x * (unsigned long long)blockDim.x) >> 5;
+    for (unsigned long long b = warp * 32; b < items; b += nwarps * 32) {
+        const unsigned long long i = b + lane;
+        uint32_t v = 0;
+        bool changed = false;
+        if (i < items && edit_prepare(c, (uint32_t)i, (uint32_t)nX, v)) {
+            edit_apply(c, (uint32_t)i, (uint32_t)nX, v);
+            changed = true;
         }
-        st_flush(se, c.Elist, &c.cnt->nE);
+        ws_push(se[wib], changed, v, c.Elist, &c.cnt->nE);
     }
+    ws_flush(se[wib], c.Elist, &c.cnt->nE);
 }
 
 // one warp per changed vertex: when its order against some vertex within two edges
@@ -789,28 +853,44 @@ template <int D> __global__ void k_edit(Ctx c)
 // change and nothing is marked
 template <int D> __global__ void k_mark(Ctx c)
 {
-    if (c.ls->halt) return;
-    __shared__ Stage<DIRTY_STAGE> sd;
+    if (round_off(c.ls)) return;
+    __shared__ WarpStage<512> sd[TPB / 32];
     __shared__ int ring[64][3];
     for (int j = threadIdx.x; j < 64 * 3; j += blockDim.x) ring[j / 3][j % 3] = rt_tab<D>().ring[j / 3][j % 3];
-    st_init(sd);
+    const unsigned lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    if (lane == 0) sd[wib].n = 0;
+    __syncthreads();
+    const Tab<D> &T = rt_tab<D>();
     const unsigned long long items = c.cnt->nE;
-    const unsigned lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
-    for (unsigned long long b = (unsigned long long)blockIdx.x * wpb; b < items; b += (unsigned long long)gridDim.x * wpb) {
-        const unsigned long long i = b + (threadIdx.x >> 5);
-        if (i < items) {
-            const uint32_t v = c.Elist[i];
-            const bool flip = order_changed<D>(c, v, (int)lane, 32, ring);
-            if (__any_sync(0xffffffffu, flip))
-                mark_dirty<D>(c, v, (int)lane, 32, [&](uint32_t p) { st_push(sd, p, c.Dlist, &c.cnt->nD); });
+    const unsigned long long warp = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long nwarps = (gridDim.x * (unsigned long long)blockDim.x) >> 5;
+    for (unsigned long long i = warp; i < items; i += nwarps) {
+        const uint32_t v = c.Elist[i];
+        const bool flip = order_changed<D>(c, v, (int)lane, 32, ring);
+        if (!__any_sync(0xffffffffu, flip)) continue;
+        int x, y, z;
+        coords(c.G, v, x, y, z);
+#pragma unroll
+        for (int r = 0; r < 2; r++) {            // the window has at most 64 anchors
+            const int j = (int)lane + 32 * r;
+            bool has = false;
+            uint32_t p = 0;
+            if (j < T.nwin) {
+                const int px = x - T.win[j][0], py = y - T.win[j][1], pz = z - T.win[j][2];
+                if (inside(c.G, px, py, pz)) {
+                    p = vid(c.G, px, py, pz);
+                    has = !test_and_set(c.Dbits, p);
+                }
+            }
+            ws_push(sd[wib], has, p, c.Dlist, &c.cnt->nD);
         }
-        st_flush(sd, c.Dlist, &c.cnt->nD);
     }
+    ws_flush(sd[wib], c.Dlist, &c.cnt->nD);
 }
 
 template <int D> __global__ void __launch_bounds__(TPB, 3) k_refresh(Ctx c)
 {
-    if (c.ls->halt) return;
+    if (round_off(c.ls)) return;
     const unsigned long long n = c.cnt->nD;
     GRID_STRIDE(i, n) refresh_anchor<D>(c, c.Dlist[i]);
 }
@@ -837,7 +917,7 @@ template <int D> __device__ __forceinline__ bool rebuild_anchor(const Ctx &c, ui
 // mismatch bitsets after a round: only re-evaluated (dirty) anchors can change membership
 template <int D> __global__ void k_rebuild(Ctx c)
 {
-    if (c.ls->halt) return;
+    if (round_off(c.ls)) return;
     __shared__ Stage<TPB> ss;
     st_init(ss);
     LoopState *ls = c.ls;
@@ -860,7 +940,7 @@ template <int D> __global__ void k_rebuild(Ctx c)
 // of the critical-difference bitset that the next C-pass visits
 __global__ void k_clear(Ctx c)
 {
-    if (c.ls->halt) return;
+    if (round_off(c.ls)) return;
     const unsigned long long nT = c.cnt->nT, nX = c.cnt->nX, nD = c.cnt->nD;
     GRID_STRIDE(i, nT + nX + nD)
     {
@@ -876,9 +956,12 @@ __global__ void k_list_blocks(Ctx c) { list_blocks(c.Csum, csum_words(c.G.n), c.
 // end of a round: zero the round's counters
 __global__ void k_end(Ctx c)
 {
-    if (threadIdx.x || blockIdx.x || c.ls->halt) return;
+    if (threadIdx.x || blockIdx.x || round_off(c.ls)) return;
     memset(c.cnt, 0, sizeof(Counters));
+    if (c.ls->rounds_kernel && c.ls->last_items < SMALL_ROUND) c.ls->leave = 1;
 }
+
+__global__ void k_set_leave(LoopState *ls, int v) { ls->leave = v; }
 
 __global__ void k_set_halt(LoopState *ls, int v) { ls->halt = v; }
 __global__ void k_set_track(LoopState *ls, int v) { ls->track_dirty = v; }
@@ -1050,6 +1133,7 @@ __global__ void __launch_bounds__(TPB, 2) k_rounds(Ctx c, GridBarrier *gb, Count
 // entry state of k_rounds: the C-block list of the round graphs is list 0
 __global__ void k_rounds_enter(LoopState *ls, GridBarrier *gb)
 {
+    ls->leave = 0;
     ls->nbl[0] = ls->nblk;
     ls->nbl[1] = 0;
     gb->arrive = 0;
@@ -1866,7 +1950,6 @@ struct FixResult {
 
 constexpr int GRAPH_ROUNDS = 16;   // C-pass rounds queued per graph launch
 constexpr int BATCH_STREAMS = 8;   // jobs of a batch that run at once, one stream each
-constexpr unsigned long long SMALL_ROUND = 8192;   // edited vertices below which rounds run small grids
 
 // A captured graph of GRAPH_ROUNDS C-pass rounds.  With profiling, every kernel node sits
 // between two event-record nodes; a node pair is counted only if its round ran.
@@ -1962,6 +2045,19 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
         CK(h->trace.alloc(6ull * L.trace_cap));
         c.trace = h->trace.p;
     }
+    // rounds that edit few vertices run in the persistent kernel when the device has
+    // cooperative launches, else in a graph of small grids
+    int rgrid = h->rounds_grid > 0 ? h->rounds_grid : sm_count();
+    {
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)k_rounds<D>, TPB, 0) != cudaSuccess) {
+            cudaGetLastError();
+            occ = 0;
+        }
+        rgrid = std::min(rgrid, occ * sm_count());
+    }
+    const bool persistent = coop_supported() && rgrid > 0;
+    L.rounds_kernel = persistent ? 1 : 0;
     CK(cudaMemcpyAsync(h->ls.p, &L, sizeof L, cudaMemcpyHostToDevice, s));
     KL(h, MSC_K_OTHER, s, k_init_g<<<grid_occ((const void *)k_init_g, h->G.n), TPB, 0, s>>>(h->f.p, h->fhat.p, h->g.p, h->state.p, h->G.n, xi));
     CK(cudaGetLastError());
@@ -1978,18 +2074,6 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
     h->items[MSC_K_DENSE] += h->G.n;
     // two captured graphs: full grids for rounds that edit many vertices, one block per SM
     // for the long tail of rounds that edit few (chosen by the last round's size)
-    // rounds that edit few vertices run in the persistent kernel when the device has
-    // cooperative launches, else in a graph of small grids
-    int rgrid = h->rounds_grid > 0 ? h->rounds_grid : sm_count();
-    {
-        int occ = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)k_rounds<D>, TPB, 0) != cudaSuccess) {
-            cudaGetLastError();
-            occ = 0;
-        }
-        rgrid = std::min(rgrid, occ * sm_count());
-    }
-    const bool persistent = coop_supported() && rgrid > 0;
     RoundGraph rg_big, rg_small;
     CKS(build_round_graph<D>(h, c, (unsigned)o.profile & MSC_PROFILE_ALL, false, rg_big));
     if (!persistent) CKS(build_round_graph<D>(h, c, (unsigned)o.profile & MSC_PROFILE_ALL, true, rg_small));
@@ -2026,6 +2110,7 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
                 return fail(MSC_ERR_DEVICE_TIMEOUT, "a grid barrier of the persistent round kernel timed out");
         } else {
             RoundGraph &rg = small ? rg_small : rg_big;
+            if (L.leave) KL(h, MSC_K_OTHER, s, k_set_leave<<<1, 1, 0, s>>>(ls, 0));
             CK(cudaGraphLaunch(rg.exec, s));
             CK(cudaMemcpyAsync(&L, ls, sizeof L, cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
@@ -2050,6 +2135,7 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
         if (hc.ncase == 0) break;
         // the S-pass edit round, then back to C-pass rounds
         KL(h, MSC_K_OTHER, s, k_set_halt<<<1, 1, 0, s>>>(ls, 0));
+        KL(h, MSC_K_OTHER, s, k_set_leave<<<1, 1, 0, s>>>(ls, 0));
         KL(h, MSC_K_OTHER, s, k_decide<<<1, 32, 0, s>>>(c, 1));
         KL(h, MSC_K_EDIT, s, k_edit<D><<<grid_occ((const void *)k_edit<D>, h->G.n), TPB, 0, s>>>(c));
         KL(h, MSC_K_EDIT, s, k_mark<D><<<grid_occ((const void *)k_mark<D>, 32ull * h->G.n), TPB, 0, s>>>(c));
