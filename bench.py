@@ -127,7 +127,7 @@ CLASS_KERNELS = {
 # item, from one ncu capture of the same workload at 256^3 (the capture's launches over the
 # items they processed); a launch's traffic is that figure times the launch's items.  It
 # holds for the kernels as they stand: profiles/k_node_seed_kolmogorov3d_256.md.
-TRAFFIC_PER_ITEM = {"sep_seed": (242687744 + 21242880 + 1668768768 + 574402048 + 1822034176 + 2426650112) / 131205873.0}
+TRAFFIC_PER_ITEM = {"sep_seed": (242907000 + 21325000 + 1325101000 + 339782000 + 2575775000 + 1627133000) / 131205873.0}
 
 
 def class_bytes(cls, tot, n, steps, ndim):

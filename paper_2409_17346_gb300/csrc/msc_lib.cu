@@ -1228,7 +1228,10 @@ __global__ void k_seeds(const uint64_t *code, Grid G, SeedOut so, unsigned long 
         }
         return;
     }
-    __shared__ Stage<2 * TPB> st[3];
+    // seeds are rare: the stages are flushed only once one is half full (and at the end);
+    // a push that finds its stage full goes to the list directly
+    constexpr int SCAP = 2048;
+    __shared__ Stage<SCAP> st[3];
     for (int k = 0; k < NK; k++) st_init(st[k]);
     BLOCK_ROUNDS(b, G.n)
     {
@@ -1236,8 +1239,13 @@ __global__ void k_seeds(const uint64_t *code, Grid G, SeedOut so, unsigned long 
         if (p < G.n)
             for (int k = 0; k < NK; k++)
                 seeds_anchor<D>(code, G, (uint32_t)p, k, [&](uint32_t v) { st_push(st[k], v, so.out[k], count + k); });
-        for (int k = 0; k < NK; k++) st_flush(st[k], so.out[k], count + k);
+        __syncthreads();
+        bool half = false;
+        for (int k = 0; k < NK; k++) half = half || st[k].n > SCAP / 2;
+        if (half)
+            for (int k = 0; k < NK; k++) st_flush(st[k], so.out[k], count + k);
     }
+    for (int k = 0; k < NK; k++) st_flush(st[k], so.out[k], count + k);
 }
 
 template <int D>
