@@ -99,6 +99,9 @@ typedef struct {
     uint64_t round_work[3];      /* inside the persistent round kernel: targeted vertices,
                                     refreshed (and rebuilt) anchors, anchors with differing
                                     critical cells visited by the C-pass */
+    double round_phase_ms[4];    /* persistent round kernel, device clock of its first block:
+                                    C-pass, decision and edits, order changes, refresh and
+                                    rebuild (each up to the end of its grid barrier) */
 } msc_stats;
 
 /* one edit round: kind 0 = C-pass (false critical cells), 1 = S-pass (separatrices);

@@ -90,6 +90,8 @@ struct LoopState {
     unsigned long long nbl[2];       // persistent round kernel: entries of its two C-block lists
     int rounds_kernel;               // small rounds run in the persistent round kernel
     int pad;
+    unsigned long long phase_ns[4];  // persistent round kernel: device time per phase (block 0's
+                                     // view: from one barrier's exit to the next's)
 };
 
 // everything a kernel of one job needs (device pointers)
@@ -1094,6 +1096,103 @@ template <int D> MSC_HD inline void node_seed(const Ctx &c, int kind, uint32_t u
     const int32_t o = node_or(ns, u, NS_SEED);
     if (o & NS_SEED) return;
     path_change<D>(c, kind, u, o, o | NS_SEED);
+}
+
+// The first build's propagation along descending (kind 0) or ascending (kind 1) paths, with
+// W walks interleaved per thread.  A walk is a chain of dependent memory operations (the
+// atomic on a node's word, then the f data of its successor), so one walk per thread leaves
+// the memory system idle most of the time; here a thread keeps W chains in flight and issues
+// their operations side by side.  The walks change node words only through atomics whose
+// before/after values decide what is passed on, so their interleaving does not change the
+// final state.  Seeds are this thread's share first, first + stride, ...
+template <int D, int W>
+MSC_HD inline void path_seed_walks(const Ctx &c, int kind, const uint32_t *seeds, uint32_t n, uint32_t first, uint32_t stride)
+{
+    const Tab<D> &T = rt_tab<D>();
+    constexpr uint32_t NTOP = (uint32_t)Tab<D>::NTOP;
+    uint32_t *ns = kind == 0 ? c.ns_v : c.ns_top;
+    const int64_t sy = c.G.nx, sz = (int64_t)c.G.nx * c.G.ny;
+    uint32_t node[W];
+    int delta[W];
+    bool act[W];
+    uint32_t next = first;
+    unsigned long long steps = 0;
+    // start a walk in slot k from the next seed whose seed flag changes what it passes on
+    auto refill = [&](int k) {
+        act[k] = false;
+        while (next < n) {
+            const uint32_t u = seeds[next];
+            next += stride;
+            const int32_t o = node_or(ns, u, NS_SEED);
+            if (o & NS_SEED) continue;
+            const int d = path_passes(o | NS_SEED) - path_passes(o);
+            uint32_t w;
+            if (d && (kind == 0 ? desc_succ<D>(c, u, w) : asc_succ<D>(c, u, w))) {
+                node[k] = w;
+                delta[k] = d;
+                act[k] = true;
+                return;
+            }
+        }
+    };
+#pragma unroll
+    for (int k = 0; k < W; k++) refill(k);
+    for (;;) {
+        int32_t o[W];
+        uint64_t cf[W], lw[W];
+#pragma unroll
+        for (int k = 0; k < W; k++) {
+            if (!act[k]) continue;
+            // the successor's f data, fetched beside the atomic on the node
+            const uint32_t a = kind == 0 ? node[k] : node[k] / NTOP;
+            cf[k] = ld(c.code_f + a);
+            if (D == 3 && kind == 1) lw[k] = ld(c.low_f + a);
+            o[k] = node_add(ns, node[k], delta[k]);
+        }
+        bool any = false;
+#pragma unroll
+        for (int k = 0; k < W; k++) {
+            if (!act[k]) continue;
+            steps++;
+            const int d = path_passes(o[k] + delta[k] * NS_ONE) - path_passes(o[k]);
+            bool cont = false;
+            uint32_t w = 0;
+            if (d) {
+                if (kind == 0) {
+                    const int ff = vfield<D>(cf[k]);
+                    if (ff != 15) {
+                        w = (uint32_t)((int64_t)node[k] + T.nb[ff][0] + sy * T.nb[ff][1] + sz * T.nb[ff][2]);
+                        cont = true;
+                    }
+                } else if (D == 3) {
+                    const uint32_t a = node[k] / NTOP;
+                    const int t = (int)(node[k] % NTOP);
+                    if (kfield<D>(cf[k], t) != 0) {
+                        const int jl = (int)((lw[k] >> (24 + 2 * t)) & 3u);
+                        int x, y, z;
+                        coords(c.G, a, x, y, z);
+                        x += T.asc_off[t][jl][0]; y += T.asc_off[t][jl][1]; z += T.asc_off[t][jl][2];
+                        const int t2 = T.asc_type[t][jl];
+                        if (top_exists<D>(c.G, x, y, z, t2)) {
+                            w = vid(c.G, x, y, z) * NTOP + (uint32_t)t2;
+                            cont = true;
+                        }
+                    }
+                } else {
+                    cont = asc_succ<D>(c, node[k], w);
+                }
+            }
+            if (cont) {
+                node[k] = w;
+                delta[k] = d;
+            } else {
+                refill(k);
+            }
+            any = any || act[k];
+        }
+        if (!any) break;
+    }
+    count_add(&c.cnt->steps[kind], steps);
 }
 
 // troublemakers among the pairs anchored at p (p has a code mismatch)

@@ -1048,6 +1048,13 @@ __global__ void __launch_bounds__(TPB, 2) k_rounds(Ctx c, GridBarrier *gb, Count
     const unsigned lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     const unsigned long long nthreads = (unsigned long long)gridDim.x * blockDim.x;
     const unsigned long long gtid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    unsigned long long tph = gtid == 0 ? global_ns() : 0;
+    auto phase_end = [&](int ph) {   // block 0, thread 0: time since the last barrier
+        if (gtid != 0) return;
+        const unsigned long long t = global_ns();
+        ls->phase_ns[ph] += t - tph;
+        tph = t;
+    };
     for (unsigned r = 0; r < max_rounds; r++) {
         const int cur = (int)(r & 1u), nxt = cur ^ 1;
         Counters *K = cnt2 + cur;
@@ -1065,6 +1072,7 @@ __global__ void __launch_bounds__(TPB, 2) k_rounds(Ctx c, GridBarrier *gb, Count
         }
         tally_end(tally, cc);
         if (!grid_sync(gb, ls)) return;
+        phase_end(0);
         // P2: the decision, taken alike by every thread from the finished counters (block 0
         // records it), then the edits
         int status;
@@ -1086,6 +1094,7 @@ __global__ void __launch_bounds__(TPB, 2) k_rounds(Ctx c, GridBarrier *gb, Count
             st_flush(se, c.Elist, &K->nE);
         }
         if (!grid_sync(gb, ls)) return;
+        phase_end(1);
         // P3: edited vertices whose order changed mark their windows dirty
         st_init(u.sd);
         const unsigned long long nE = K->nE;
@@ -1100,6 +1109,7 @@ __global__ void __launch_bounds__(TPB, 2) k_rounds(Ctx c, GridBarrier *gb, Count
             st_flush(u.sd, c.Dlist, &K->nD);
         }
         if (!grid_sync(gb, ls)) return;
+        phase_end(2);
         // P4: new codes and mismatch bits of the dirty anchors; clear the round's sets
         const unsigned long long nD = K->nD, nT = K->nT;
         const int track = ls->track_dirty;
@@ -1126,6 +1136,7 @@ __global__ void __launch_bounds__(TPB, 2) k_rounds(Ctx c, GridBarrier *gb, Count
             ls->nbl[cur] = 0;                    // list cur was read in P1; it is the next "next"
         }
         if (!grid_sync(gb, ls)) return;
+        phase_end(3);
         if (items >= leave_items) return;        // a large round: the next rounds run full grids
     }
 }
@@ -1169,7 +1180,11 @@ template <int D> __global__ void __launch_bounds__(TPB) k_node_init(Ctx c)
 
 template <int D> __global__ void k_node_seed(Ctx c, int kind, const uint32_t *seeds, uint32_t n)
 {
-    GRID_STRIDE(i, n) node_seed<D>(c, kind, seeds[i]);
+    if (kind == 2) {
+        GRID_STRIDE(i, n) node_seed<D>(c, kind, seeds[i]);
+        return;
+    }
+    path_seed_walks<D, 4>(c, kind, seeds, n, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 template <int D> __global__ void k_node_update(Ctx c, const unsigned long long *nSD)
@@ -1674,6 +1689,7 @@ struct msc_handle {
     unsigned long long timed[12] = {};
     unsigned long long items[12] = {};
     unsigned long long round_work[3] = {};   // edit, refresh, cpass items of the round kernel
+    unsigned long long round_phase_ns[4] = {};   // device time per phase of the round kernel
     double ms[12] = {};
     struct Pend {
         cudaEvent_t a, b;
@@ -2111,6 +2127,7 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
             CK(cudaStreamSynchronize(s));
             prev_iters = L.iters;
             h->items[MSC_K_ROUNDS] += L.iters - L0.iters;
+            for (int q = 0; q < 4; q++) h->round_phase_ns[q] += L.phase_ns[q] - L0.phase_ns[q];
             fix_work[0] += L.edit_items - L0.edit_items;
             fix_work[1] += L.refresh_items - L0.refresh_items;
             fix_work[2] += L.cpass_items - L0.cpass_items;
@@ -2886,6 +2903,7 @@ msc_status msc_get_stats(msc_handle *h, msc_stats *out)
         out->items[i] = h->items[i];
     }
     for (int i = 0; i < 3; i++) out->round_work[i] = h->round_work[i];
+    for (int i = 0; i < 4; i++) out->round_phase_ms[i] = h->round_phase_ns[i] * 1e-6;
     return MSC_OK;
 }
 
@@ -2894,6 +2912,7 @@ msc_status msc_reset_stats(msc_handle *h)
     if (!h) return fail(MSC_ERR_INVALID_ARG, "handle is NULL");
     for (int i = 0; i < 12; i++) { h->launches[i] = 0; h->ms[i] = 0.0; h->timed[i] = 0; h->items[i] = 0; }
     for (int i = 0; i < 3; i++) h->round_work[i] = 0;
+    for (int i = 0; i < 4; i++) h->round_phase_ns[i] = 0;
     return MSC_OK;
 }
 

@@ -54,7 +54,7 @@ def profile_mask(profile):
 class Stats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_uint64 * 12), ("ms", ctypes.c_double * 12),
                 ("timed_launches", ctypes.c_uint64 * 12), ("items", ctypes.c_uint64 * 12),
-                ("round_work", ctypes.c_uint64 * 3)]
+                ("round_work", ctypes.c_uint64 * 3), ("round_phase_ms", ctypes.c_double * 4)]
 
 
 class IterRecord(ctypes.Structure):
@@ -256,6 +256,8 @@ class Handle:
                for i, k in enumerate(KERNEL_CLASSES)}
         out["rounds"]["work"] = dict(edit=int(st.round_work[0]), refresh=int(st.round_work[1]),
                                      cpass=int(st.round_work[2]))
+        out["rounds"]["phase_ms"] = dict(zip(("cpass", "edit", "mark", "refresh"),
+                                             (float(v) for v in st.round_phase_ms)))
         return out
 
     def reset_stats(self):
