@@ -1195,6 +1195,83 @@ MSC_HD inline void path_seed_walks(const Ctx &c, int kind, const uint32_t *seeds
     count_add(&c.cnt->steps[kind], steps);
 }
 
+// The first build's saddle-saddle propagation with one stack per warp (in shared memory,
+// `cap` entries): the lanes take up to 32 pending (triangle, delta) items at a time, apply
+// them, and push the children that a change passes on back onto the warp's stack.  The
+// lanes stay converged, where a depth-first walk per lane leaves most of them idle.  A full
+// stack spills to the global queue that k_tri_spill drains.  Every change is an atomic on a
+// node word, so the order of the items does not change the final state.  Must be called by
+// whole warps; seeds are taken 32 at a time by each warp of the grid.
+__device__ inline void tri_seed_walks(const Ctx &c, const uint32_t *seeds, uint32_t n, uint32_t *stk, int8_t *sdl, int cap)
+{
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned long long nwarps = (gridDim.x * (unsigned long long)blockDim.x) >> 5;
+    unsigned long long next = ((blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5) * 32;
+    int sp = 0;                      // the same in every lane
+    unsigned long long steps = 0;
+    // push the live children of a triangle whose passing state changed by dv (lane-local
+    // inputs; all lanes call it)
+    auto push_children = [&](bool go, uint32_t t, int dv) {
+        uint32_t ch[3];
+        bool dead[3];
+        int k = 0;
+        if (go) k = tri_children(c, t, ch, dead);
+#pragma unroll
+        for (int r = 0; r < 3; r++) {
+            const bool live = r < k && !dead[r];
+            if (r < k && dead[r]) node_add(c.ns_dead, ch[r], dv);
+            const unsigned m = __ballot_sync(0xffffffffu, live);
+            const int cnt = __popc(m);
+            if (!cnt) continue;
+            const int pos = sp + __popc(m & ((1u << lane) - 1u));
+            if (live) {
+                if (pos < cap) { stk[pos] = ch[r]; sdl[pos] = (int8_t)dv; }
+                else ss_spill(c, ch[r], dv);
+            }
+            sp = min(sp + cnt, cap);
+        }
+        __syncwarp();
+    };
+    for (;;) {
+        if (sp < 32 && next < n) {
+            // new seeds, one per lane: a 2-saddle triangle becomes a seed
+            const unsigned long long i = next + lane;
+            next += nwarps * 32;
+            bool go = false;
+            int dv = 0;
+            uint32_t u = 0;
+            if (i < n) {
+                u = seeds[i];
+                const int32_t o = node_or(c.ns_tri, u, NS_SEED);
+                if (!(o & NS_SEED)) {
+                    dv = tri_passes(o | NS_SEED) - tri_passes(o);
+                    go = dv != 0;
+                }
+            }
+            push_children(go, u, dv);
+            continue;
+        }
+        if (sp == 0) break;
+        const int take = min(sp, 32);
+        sp -= take;
+        const bool act = (int)lane < take;
+        uint32_t t = 0;
+        int d = 0;
+        if (act) { t = stk[sp + (int)lane]; d = sdl[sp + (int)lane]; }
+        __syncwarp();
+        bool go = false;
+        int dv = 0;
+        if (act) {
+            steps++;
+            const int32_t o = node_add(c.ns_tri, t, d), nw = o + d * NS_ONE;
+            dv = tri_passes(nw) - tri_passes(o);
+            go = dv != 0;
+        }
+        push_children(go, t, dv);
+    }
+    count_add(&c.cnt->steps[2], steps);
+}
+
 // troublemakers among the pairs anchored at p (p has a code mismatch)
 template <int D> MSC_HD inline void node_targets(const Ctx &c, uint32_t p)
 {

@@ -1180,11 +1180,17 @@ template <int D> __global__ void __launch_bounds__(TPB) k_node_init(Ctx c)
 
 template <int D> __global__ void k_node_seed(Ctx c, int kind, const uint32_t *seeds, uint32_t n)
 {
-    if (kind == 2) {
-        GRID_STRIDE(i, n) node_seed<D>(c, kind, seeds[i]);
-        return;
-    }
     path_seed_walks<D, 4>(c, kind, seeds, n, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+// the first build's saddle-saddle propagation (3D): per-warp stacks in shared memory
+constexpr int SS_WARP_STACK = 384;
+__global__ void k_node_seed_ss(Ctx c, const uint32_t *seeds, uint32_t n)
+{
+    __shared__ uint32_t stk[TPB / 32][SS_WARP_STACK];
+    __shared__ int8_t sdl[TPB / 32][SS_WARP_STACK];
+    const unsigned wib = threadIdx.x >> 5;
+    tri_seed_walks(c, seeds, n, stk[wib], sdl[wib], SS_WARP_STACK);
 }
 
 template <int D> __global__ void k_node_update(Ctx c, const unsigned long long *nSD)
@@ -1935,7 +1941,7 @@ template <int D> msc_status s_pass_state(msc_handle *h, Ctx &c, bool &built, uns
         KL(h, MSC_K_SEP_INIT, s, k_node_init<D><<<grid_occ((const void *)k_node_init<D>, h->G.n), TPB, 0, s>>>(c));
         if (h->n_desc) KL(h, MSC_K_SEP_SEED, s, k_node_seed<D><<<grid_occ((const void *)k_node_seed<D>, h->n_desc), TPB, 0, s>>>(c, 0, h->seeds_desc.p, h->n_desc));
         if (h->n_asc) KL(h, MSC_K_SEP_SEED, s, k_node_seed<D><<<grid_occ((const void *)k_node_seed<D>, h->n_asc), TPB, 0, s>>>(c, 1, h->seeds_asc.p, h->n_asc));
-        if (D == 3 && h->n_ss) KL(h, MSC_K_SEP_SEED, s, k_node_seed<D><<<grid_occ((const void *)k_node_seed<D>, h->n_ss), TPB, 0, s>>>(c, 2, h->seeds_ss.p, h->n_ss));
+        if (D == 3 && h->n_ss) KL(h, MSC_K_SEP_SEED, s, k_node_seed_ss<<<grid_occ((const void *)k_node_seed_ss, 32ull * h->n_ss), TPB, 0, s>>>(c, h->seeds_ss.p, h->n_ss));
         CK(cudaGetLastError());
         h->items[MSC_K_SEP_INIT] += h->G.n;
         built = true;
