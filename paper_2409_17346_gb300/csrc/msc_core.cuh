@@ -125,6 +125,8 @@ struct Ctx {
     uint32_t *Cblk;                  // blocks whose Csum bit is set, listed for the next C-pass
     int64_t *trace;                  // rows (kind, |T|, |X|, sum T, sum X), ls->trace_cap rows
     unsigned long long *tally;       // when set: per-block (cases, live cases) in shared memory
+    int mark_only;                   // add_case only sets the target's T bit (no return value
+                                     // awaited); k_tlist lists the T bits afterwards
 };
 
 // ------------------------------------------------------------------------------------
@@ -335,7 +337,9 @@ template <int D> MSC_HD inline void add_case(const Ctx &c, uint32_t t, const Ver
         count_add(&c.cnt->ncase, 1ull);
         if (live) count_add(&c.cnt->nlive, 1ull);
     }
-    if (!test_and_set(c.Tbits, t)) {
+    if (c.mark_only) {
+        atomicOr(c.Tbits + (t >> 5), 1u << (t & 31));
+    } else if (!test_and_set(c.Tbits, t)) {
         c.Tlist[list_slot(&c.cnt->nT)] = t;
         count_add(&c.cnt->sumT, (unsigned long long)t);
     }

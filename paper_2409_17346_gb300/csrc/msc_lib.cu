@@ -773,6 +773,41 @@ template <int D> __global__ void __launch_bounds__(TPB) k_ctargets(Ctx c)
     }
 }
 
+// the T list of a round whose C-pass only set T bits (mark_only): one warp per 32 bitset
+// words, one atomic per warp for its slots and one for its sum of vertex ids
+__global__ void k_tlist(Ctx c)
+{
+    if (round_off(c.ls)) return;
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned long long nw = (c.G.n + 31ull) / 32;
+    const unsigned long long warp = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long nwarps = (gridDim.x * (unsigned long long)blockDim.x) >> 5;
+    for (unsigned long long w0 = warp * 32; w0 < nw; w0 += nwarps * 32) {
+        uint32_t mine = w0 + lane < nw ? c.Tbits[w0 + lane] : 0u;
+        const unsigned cnt = __popc(mine);
+        unsigned pre = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, pre, o);
+            if (lane >= (unsigned)o) pre += y;
+        }
+        const unsigned total = __shfl_sync(0xffffffffu, pre, 31);
+        if (total == 0) continue;
+        unsigned long long base = 0;
+        if (lane == 31) base = atomicAdd(&c.cnt->nT, (unsigned long long)total);
+        base = __shfl_sync(0xffffffffu, base, 31);
+        unsigned long long at = base + pre - cnt, sum = 0;
+        const uint32_t v0 = (uint32_t)((w0 + lane) * 32);
+        while (mine) {
+            const int k = __ffs(mine) - 1;
+            mine &= mine - 1;
+            c.Tlist[at++] = v0 + (uint32_t)k;
+            sum += v0 + (uint32_t)k;
+        }
+        for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) atomicAdd(&c.cnt->sumT, sum);
+    }
+}
+
 // after a targeting pass (kind 0 C, 1 S): stop the phase when there is no false case, stop
 // with a status on a stall or at max_iters.  iters: the loop's round count when the pass
 // began.
@@ -2007,6 +2042,9 @@ msc_status build_round_graph(msc_handle *h, const Ctx &c, unsigned prof_mask, bo
     // grid sizes (occupancy queries) before the capture begins
     auto grid = [&](const void *k, unsigned long long n) { return small ? std::min(sm_count(), grid_occ(k, n)) : grid_occ(k, n); };
     const int g_ct = grid((const void *)k_ctargets<D>, h->G.n / 8 + 1);
+    const int g_tl = grid((const void *)k_tlist, h->G.n / 32 + 1);
+    Ctx cm = c;          // the graph's C-pass marks T bits only; k_tlist lists them
+    cm.mark_only = 1;
     const int g_ed = grid((const void *)k_edit<D>, h->G.n);
     const int g_mk = grid((const void *)k_mark<D>, 32ull * h->G.n);
     const int g_rf = grid((const void *)k_refresh<D>, h->G.n);
@@ -2024,7 +2062,8 @@ msc_status build_round_graph(msc_handle *h, const Ctx &c, unsigned prof_mask, bo
         rg.pairs.push_back(p);
     };
     for (int r = 0; r < GRAPH_ROUNDS; r++) {
-        node(MSC_K_CPASS, r, 1, [&] { k_ctargets<D><<<g_ct, TPB, 0, cs>>>(c); });
+        node(MSC_K_CPASS, r, 1, [&] { k_ctargets<D><<<g_ct, TPB, 0, cs>>>(cm); });
+        node(MSC_K_CPASS, r, 1, [&] { k_tlist<<<g_tl, TPB, 0, cs>>>(cm); });
         node(MSC_K_OTHER, r, 1, [&] { k_decide<<<1, 32, 0, cs>>>(c, 0); });
         node(MSC_K_EDIT, r, 0, [&] { k_edit<D><<<g_ed, TPB, 0, cs>>>(c); });
         node(MSC_K_EDIT, r, 0, [&] { k_mark<D><<<g_mk, TPB, 0, cs>>>(c); });
@@ -2046,7 +2085,7 @@ msc_status build_round_graph(msc_handle *h, const Ctx &c, unsigned prof_mask, bo
 void account_graph(msc_handle *h, RoundGraph &rg, unsigned active, bool halted)
 {
     const unsigned long long a = active, t = active + (halted ? 1 : 0);
-    h->launches[MSC_K_CPASS] += t;
+    h->launches[MSC_K_CPASS] += 2 * t;
     h->launches[MSC_K_OTHER] += t + a;
     h->launches[MSC_K_EDIT] += 2 * a;
     h->launches[MSC_K_REFRESH] += a;
