@@ -269,9 +269,11 @@ uint64_t msc_device_bytes(int nx, int ny, int nz);
 
 /* Device memory that handles free stays in the library's memory pool on that device, so
  * that the next handle of a similar size reuses it without going back to the driver (a
- * server limits what the pool keeps to its memory budget).  This call returns everything
- * the pool of the current device holds unused to the driver, after waiting for the device
- * to finish its work.  Handles that are still alive keep their memory. */
+ * server limits what the pool keeps to its memory budget).  Likewise the page-locked host
+ * buffers of edit records that msc_free_edits gives back are kept (up to 8 GiB) for the
+ * next record.  This call returns everything the pool of the current device holds unused
+ * to the driver and frees the kept host buffers, after waiting for the device to finish its
+ * work.  Handles and edit records that are still alive keep their memory. */
 msc_status msc_release_cached_memory(void);
 
 /* ---------------------------------------------------------------------------------------

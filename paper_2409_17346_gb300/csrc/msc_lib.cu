@@ -19,7 +19,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <unordered_map>
 #include <new>
 #include <string>
 #include <thread>
@@ -1558,6 +1560,78 @@ struct EntryStream {
     }
 };
 
+// Page-locked host buffers for the edit records the library hands out.  A device-to-host
+// copy into pageable memory runs several times slower than into page-locked memory, and
+// pinning fresh memory is slow too, so the buffers msc_free_edits gives back are kept for
+// the next record (up to PINNED_IDLE_MAX bytes; msc_release_cached_memory frees them).
+constexpr size_t PINNED_IDLE_MAX = 8ull << 30;
+struct PinnedCache {
+    std::mutex mu;
+    std::unordered_map<void *, size_t> live;   // handed out, with their capacity
+    std::multimap<size_t, void *> idle;        // given back, by capacity
+    size_t idle_bytes = 0;
+};
+PinnedCache &pinned_cache()
+{
+    static PinnedCache pc;
+    return pc;
+}
+
+// a host buffer of at least `bytes` (page-locked when possible); nullptr if none
+void *host_take(size_t bytes)
+{
+    bytes = std::max<size_t>(bytes, 64);
+    PinnedCache &pc = pinned_cache();
+    {
+        std::lock_guard<std::mutex> lk(pc.mu);
+        auto it = pc.idle.lower_bound(bytes);
+        if (it != pc.idle.end() && it->first <= 2 * bytes + (1u << 20)) {
+            void *p = it->second;
+            pc.live[p] = it->first;
+            pc.idle_bytes -= it->first;
+            pc.idle.erase(it);
+            return p;
+        }
+    }
+    void *p = nullptr;
+    if (cudaMallocHost(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return malloc(bytes);   // not in the cache: freed with free()
+    }
+    std::lock_guard<std::mutex> lk(pc.mu);
+    pc.live[p] = bytes;
+    return p;
+}
+
+void host_give(void *p)
+{
+    if (!p) return;
+    PinnedCache &pc = pinned_cache();
+    std::lock_guard<std::mutex> lk(pc.mu);
+    auto it = pc.live.find(p);
+    if (it == pc.live.end()) {
+        free(p);
+        return;
+    }
+    const size_t cap = it->second;
+    pc.live.erase(it);
+    if (pc.idle_bytes + cap > PINNED_IDLE_MAX) {
+        cudaFreeHost(p);
+        return;
+    }
+    pc.idle.emplace(cap, p);
+    pc.idle_bytes += cap;
+}
+
+void host_trim()
+{
+    PinnedCache &pc = pinned_cache();
+    std::lock_guard<std::mutex> lk(pc.mu);
+    for (auto &kv : pc.idle) cudaFreeHost(kv.second);
+    pc.idle.clear();
+    pc.idle_bytes = 0;
+}
+
 // The library's own stream-ordered memory pool on each device.  Device memory that a handle
 // frees stays in the pool (release threshold: unlimited) for the next handle, so a sequence
 // of prepare / fix / destroy calls does not map and unmap its working set every time;
@@ -2274,9 +2348,9 @@ msc_status write_edits(msc_handle *h, float xi, int qmax, cudaStream_t s, msc_ed
     out->n_vertices = n;
     out->n_lossless = t[0];
     out->n_quant = t[1];
-    out->q_map = (uint8_t *)malloc(n ? n : 1);
-    out->lossless_idx = (uint64_t *)malloc(t[0] ? t[0] * 8 : 8);
-    out->lossless_val = (float *)malloc(t[0] ? t[0] * 4 : 4);
+    out->q_map = (uint8_t *)host_take(n ? n : 1);
+    out->lossless_idx = (uint64_t *)host_take(t[0] ? t[0] * 8 : 8);
+    out->lossless_val = (float *)host_take(t[0] ? t[0] * 4 : 4);
     if (!out->q_map || !out->lossless_idx || !out->lossless_val) return fail(MSC_ERR_OOM, "host allocation of edits failed");
     CK(cudaMemcpyAsync(out->q_map, qm.p, n, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(out->lossless_idx, li.p, t[0] * 8, cudaMemcpyDeviceToHost, s));
@@ -2722,9 +2796,9 @@ msc_status msc_verify(msc_handle *h, const float *g, float xi, msc_report *out)
 void msc_free_edits(msc_edits *e)
 {
     if (!e) return;
-    free(e->q_map);
-    free(e->lossless_idx);
-    free(e->lossless_val);
+    host_give(e->q_map);
+    host_give(e->lossless_idx);
+    host_give(e->lossless_val);
     free(e->trace);
     memset(e, 0, sizeof *e);
 }
@@ -2886,9 +2960,9 @@ msc_status msc_unpack_edits(const uint8_t *buf, uint64_t size, msc_edits *out, i
     CKS(lossless_positions(qm.p, n, qm_max, idx, &cnt, &nq, s));
     if (cnt != nl) return fail(MSC_ERR_INVALID_ARG, "packed q-map marks %llu lossless vertices, header says %llu",
                                (unsigned long long)cnt, (unsigned long long)nl);
-    out->q_map = (uint8_t *)malloc(n);
-    out->lossless_idx = (uint64_t *)malloc(nl ? nl * 8 : 8);
-    out->lossless_val = (float *)malloc(nl ? nl * 4 : 4);
+    out->q_map = (uint8_t *)host_take(n);
+    out->lossless_idx = (uint64_t *)host_take(nl ? nl * 8 : 8);
+    out->lossless_val = (float *)host_take(nl ? nl * 4 : 4);
     if (!out->q_map || !out->lossless_idx || !out->lossless_val) {
         msc_free_edits(out);
         return fail(MSC_ERR_OOM, "host allocation of edits failed");
@@ -2930,10 +3004,10 @@ msc_status msc_release_cached_memory(void)
 {
     g_last_error.clear();
     CKS(device_ready());
-    cudaMemPool_t pool = lib_pool();
-    if (!pool) return MSC_OK;
     CK(cudaDeviceSynchronize());
-    CK(cudaMemPoolTrimTo(pool, 0));
+    host_trim();
+    cudaMemPool_t pool = lib_pool();
+    if (pool) CK(cudaMemPoolTrimTo(pool, 0));
     return MSC_OK;
 }
 

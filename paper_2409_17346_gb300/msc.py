@@ -182,22 +182,52 @@ def options(tier=4, q_max=6, max_iters=100000, exact_fallback=1, stream=None, re
     return o
 
 
-def _edits_to_py(e, shape):
+class _EditsOwner:
+    """Owns one msc_edits record; msc_free_edits runs when the last array viewing it goes."""
+
+    def __init__(self, e):
+        self.e = e
+
+    def __del__(self):
+        try:
+            load().msc_free_edits(ctypes.byref(self.e))
+        except Exception:
+            pass
+
+
+def _view(ptr, count, ctype, dtype, owner):
+    """A numpy array over count elements at ptr; it keeps owner alive."""
+    buf = (ctype * count).from_address(ctypes.cast(ptr, ctypes.c_void_p).value)
+    buf._owner = owner
+    return np.frombuffer(buf, dtype=dtype)
+
+
+_TRACE_DTYPE = np.dtype([("kind", np.int32), ("t_us", np.int32), ("n_targets", np.int64), ("n_exact", np.int64),
+                         ("sum_targets", np.int64), ("sum_exact", np.int64)])
+
+
+def _edits_to_py(e, shape, owner=None):
+    """The record as a dict of numpy arrays: copies, or (owner given) views of the library's
+    buffers that free the record once the last of them is gone."""
     n = int(e.n_vertices)
     out = dict(n_iters_c=int(e.n_iters_c), n_iters_s=int(e.n_iters_s), n_fallback_iters=int(e.n_fallback_iters),
                n_quant=int(e.n_quant), n_lossless=int(e.n_lossless), loop_ms=float(e.loop_ms))
-    out["q_map"] = np.ctypeslib.as_array(e.q_map, shape=(n,)).copy().reshape(shape) if n else np.zeros(shape, np.uint8)
     nl = int(e.n_lossless)
-    out["lossless_idx"] = np.ctypeslib.as_array(e.lossless_idx, shape=(nl,)).copy() if nl else np.zeros(0, np.uint64)
-    out["lossless_val"] = np.ctypeslib.as_array(e.lossless_val, shape=(nl,)).copy() if nl else np.zeros(0, np.float32)
+    if owner is None:
+        out["q_map"] = np.ctypeslib.as_array(e.q_map, shape=(n,)).copy().reshape(shape) if n else np.zeros(shape, np.uint8)
+        out["lossless_idx"] = np.ctypeslib.as_array(e.lossless_idx, shape=(nl,)).copy() if nl else np.zeros(0, np.uint64)
+        out["lossless_val"] = np.ctypeslib.as_array(e.lossless_val, shape=(nl,)).copy() if nl else np.zeros(0, np.float32)
+    else:
+        out["q_map"] = _view(e.q_map, n, ctypes.c_uint8, np.uint8, owner).reshape(shape) if n else np.zeros(shape, np.uint8)
+        out["lossless_idx"] = _view(e.lossless_idx, nl, ctypes.c_uint64, np.uint64, owner) if nl else np.zeros(0, np.uint64)
+        out["lossless_val"] = _view(e.lossless_val, nl, ctypes.c_float, np.float32, owner) if nl else np.zeros(0, np.float32)
     nt = int(e.n_trace)
     if nt:
-        tr = np.zeros((nt, 5), np.int64)
-        for k in range(nt):
-            r = e.trace[k]
-            tr[k] = (r.kind, r.n_targets, r.n_exact, r.sum_targets, r.sum_exact)
-        out["trace"] = tr
-        out["trace_t_us"] = np.array([e.trace[k].t_us for k in range(nt)], np.int64)
+        raw = np.frombuffer((ctypes.c_uint8 * (nt * _TRACE_DTYPE.itemsize)).from_address(
+            ctypes.cast(e.trace, ctypes.c_void_p).value), dtype=_TRACE_DTYPE).copy()
+        out["trace"] = np.stack([raw["kind"].astype(np.int64), raw["n_targets"], raw["n_exact"], raw["sum_targets"],
+                                 raw["sum_exact"]], axis=1)
+        out["trace_t_us"] = raw["t_us"].astype(np.int64)
     else:
         out["trace"] = np.zeros((0, 5), np.int64)
         out["trace_t_us"] = np.zeros(0, np.int64)
@@ -242,10 +272,10 @@ class Handle:
         e = Edits()
         try:
             _check(lib.msc_fix(self._h, p, ctypes.c_float(xi), ctypes.byref(opts), ctypes.byref(e), gp))
-            out = _edits_to_py(e, self.shape)
-        finally:
+        except BaseException:
             lib.msc_free_edits(ctypes.byref(e))
-        return g_out, out
+            raise
+        return g_out, _edits_to_py(e, self.shape, _EditsOwner(e))
 
     def stats(self):
         """Launch counts and profiled CUDA-event milliseconds by kernel class."""
@@ -362,10 +392,15 @@ def fix_batch(handles, f_hats, xis, g_outs=None, **kw):
     es = (Edits * n)()
     try:
         _check(lib.msc_fix_batch(hp, fp, xa, n, ctypes.byref(opts), es, gp))
-        outs = [_edits_to_py(es[i], handles[i].shape) for i in range(n)]
-    finally:
+    except BaseException:
         for i in range(n):
             lib.msc_free_edits(ctypes.byref(es[i]))
+        raise
+    outs = []
+    for i in range(n):
+        e = Edits()
+        ctypes.memmove(ctypes.byref(e), ctypes.byref(es[i]), ctypes.sizeof(Edits))
+        outs.append(_edits_to_py(e, handles[i].shape, _EditsOwner(e)))
     return g_outs, outs
 
 
