@@ -116,8 +116,8 @@ class ClockSampler:
 
 # the kernels of each class (msc_stats); the roofline names the dominant class's kernels
 CLASS_KERNELS = {
-    "dense": "k_eval_dense", "cpass": "k_ctargets", "edit": "k_edit", "refresh": "k_refresh",
-    "rebuild": "k_rebuild, k_clear", "sep_init": "k_node_init", "sep_seed": "k_node_seed, k_tri_spill",
+    "dense": "k_eval_tile, k_eval_dense", "cpass": "k_ctargets, k_tlist", "edit": "k_edit, k_mark", "refresh": "k_refresh",
+    "rebuild": "k_rebuild, k_clear", "sep_init": "k_node_init", "sep_seed": "k_node_seed, k_node_seed_ss, k_tri_spill",
     "sep_update": "k_node_update, k_tri_spill, k_sd_clear", "sep_targets": "k_node_targets",
     "other": "k_init_g, k_decide, k_end, k_seeds, checks",
     "rounds": "k_rounds",
@@ -125,9 +125,10 @@ CLASS_KERNELS = {
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of a class's kernels per work
 # item, from one ncu capture of the same workload at 256^3 (the capture's launches over the
-# items they processed); a launch's traffic is that figure times the launch's items.  It
-# holds for the kernels as they stand: profiles/k_node_seed_kolmogorov3d_256.md.
-TRAFFIC_PER_ITEM = {"sep_seed": (242907000 + 21325000 + 1325101000 + 339782000 + 2575775000 + 1627133000) / 131205873.0}
+# items they processed); a launch's traffic is that figure times the launch's items.  The
+# figure is from a capture of k_node_seed and k_node_seed_ss as they stand (3 launches,
+# 131,205,873 node steps).
+TRAFFIC_PER_ITEM = {"sep_seed": (279940608 + 22409728 + 2425982976 + 441205760 + 2871237120 + 1542544128) / 131205873.0}
 
 
 def class_bytes(cls, tot, n, steps, ndim):
