@@ -65,6 +65,10 @@ typedef struct {
                             every class): the launches of those classes are timed with CUDA
                             events on the call's stream and summed into the handle's msc_stats.
                             0 (default) times nothing. */
+    int small_round;     /* edit rounds that follow a round which edited fewer than this many
+                            vertices run in the persistent round kernel, the others as captured
+                            graph nodes: 0 (default) = 8192; 1 = every round as graph nodes.
+                            Results do not depend on it. */
 } msc_options;
 
 /* kernel classes of msc_stats */

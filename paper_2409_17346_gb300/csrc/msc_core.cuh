@@ -90,6 +90,7 @@ struct LoopState {
     unsigned long long nbl[2];       // persistent round kernel: entries of its two C-block lists
     int rounds_kernel;               // small rounds run in the persistent round kernel
     int pad;
+    unsigned long long small_round;  // a round that edits fewer vertices hands the next to it
     unsigned long long phase_ns[4];  // persistent round kernel: device time per phase (block 0's
                                      // view: from one barrier's exit to the next's)
 };

@@ -995,7 +995,7 @@ __global__ void k_end(Ctx c)
 {
     if (threadIdx.x || blockIdx.x || round_off(c.ls)) return;
     memset(c.cnt, 0, sizeof(Counters));
-    if (c.ls->rounds_kernel && c.ls->last_items < SMALL_ROUND) c.ls->leave = 1;
+    if (c.ls->rounds_kernel && c.ls->last_items < c.ls->small_round) c.ls->leave = 1;
 }
 
 __global__ void k_set_leave(LoopState *ls, int v) { ls->leave = v; }
@@ -1757,6 +1757,7 @@ void fill_defaults(msc_options *o)
     o->stream = nullptr;
     o->record_trace = 0;
     o->profile = 0;
+    o->small_round = 0;
 }
 
 msc_status check_options(const msc_options *o)
@@ -1764,6 +1765,7 @@ msc_status check_options(const msc_options *o)
     if (o->tier < 1 || o->tier > 4) return fail(MSC_ERR_INVALID_ARG, "tier must be 1..4 (got %d)", o->tier);
     if (o->q_max < 1 || o->q_max > 7) return fail(MSC_ERR_INVALID_ARG, "q_max must be 1..7 (got %d)", o->q_max);
     if (o->max_iters < 0) return fail(MSC_ERR_INVALID_ARG, "max_iters must be >= 0");
+    if (o->small_round < 0) return fail(MSC_ERR_INVALID_ARG, "small_round must be >= 0");
     return MSC_OK;
 }
 
@@ -2201,6 +2203,8 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
     }
     const bool persistent = coop_supported() && rgrid > 0;
     L.rounds_kernel = persistent ? 1 : 0;
+    const unsigned long long small_thr = o.small_round > 0 ? (unsigned long long)o.small_round : SMALL_ROUND;
+    L.small_round = small_thr;
     CK(cudaMemcpyAsync(h->ls.p, &L, sizeof L, cudaMemcpyHostToDevice, s));
     KL(h, MSC_K_OTHER, s, k_init_g<<<grid_occ((const void *)k_init_g, h->G.n), TPB, 0, s>>>(h->f.p, h->fhat.p, h->g.p, h->state.p, h->G.n, xi));
     CK(cudaGetLastError());
@@ -2224,7 +2228,7 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
     unsigned prev_iters = 0;
     unsigned long long fix_work[3] = {0, 0, 0};   // items of this call done by the round kernel
     for (;;) {
-        const bool small = L.iters > 0 && L.last_items < SMALL_ROUND;
+        const bool small = L.iters > 0 && L.last_items < small_thr;
         if (small && persistent) {
             const LoopState L0 = L;
             KL(h, MSC_K_OTHER, s, k_rounds_enter<<<1, 1, 0, s>>>(ls, h->bar.p));
@@ -2233,7 +2237,7 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
             uint32_t *blk2 = h->Cblk2.p;
             GridBarrier *gb = h->bar.p;
             unsigned max_rounds = 1u << 30;
-            unsigned long long leave = SMALL_ROUND;
+            unsigned long long leave = small_thr;
             void *args[] = {(void *)&c, (void *)&gb, (void *)&cnt2, (void *)&blk2, (void *)&max_rounds, (void *)&leave};
             cudaError_t le = cudaSuccess;
             KL(h, MSC_K_ROUNDS, s, le = cudaLaunchCooperativeKernel((const void *)k_rounds<D>, dim3(rgrid), dim3(TPB), args, 0, s));

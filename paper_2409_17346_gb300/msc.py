@@ -29,7 +29,7 @@ class Options(ctypes.Structure):
     _fields_ = [("tier", ctypes.c_int), ("q_max", ctypes.c_int), ("max_iters", ctypes.c_int),
                 ("exact_fallback", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
                 ("tile_z", ctypes.c_int), ("stream", ctypes.c_void_p), ("record_trace", ctypes.c_int),
-                ("profile", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("small_round", ctypes.c_int)]
 
 
 KERNEL_CLASSES = ("dense", "cpass", "edit", "refresh", "rebuild", "sep_init", "sep_update", "sep_targets", "other",
@@ -171,7 +171,7 @@ def _ptr(a):
 
 
 def options(tier=4, q_max=6, max_iters=100000, exact_fallback=1, stream=None, record_trace=False,
-            tile=(0, 0, 0), profile=False):
+            tile=(0, 0, 0), profile=False, small_round=0):
     o = Options()
     load().msc_default_options(ctypes.byref(o))
     o.tier, o.q_max, o.max_iters, o.exact_fallback = tier, q_max, max_iters, exact_fallback
@@ -179,6 +179,7 @@ def options(tier=4, q_max=6, max_iters=100000, exact_fallback=1, stream=None, re
     o.stream = ctypes.c_void_p(stream) if stream else None
     o.record_trace = int(bool(record_trace))
     o.profile = profile_mask(profile)
+    o.small_round = small_round
     return o
 
 

@@ -73,11 +73,12 @@ FIX_CASES = [
 ]
 
 
-def _check_fix(lib, f, fh, xi, tier, q_max=6, exact_fallback=1):
+def _check_fix(lib, f, fh, xi, tier, q_max=6, exact_fallback=1, small_round=0):
     ref = oracle.fix(f, fh, xi, tier=tier, q_max=q_max, exact_fallback=exact_fallback)
     assert ref["status"] == 0
     h = lib.Handle(f)
-    g, ed = h.fix(fh, xi, tier=tier, q_max=q_max, exact_fallback=exact_fallback, record_trace=True)
+    g, ed = h.fix(fh, xi, tier=tier, q_max=q_max, exact_fallback=exact_fallback, record_trace=True,
+                  small_round=small_round)
     assert np.array_equal(g.view(np.uint32), ref["g"].view(np.uint32))
     assert (ed["n_iters_c"], ed["n_iters_s"]) == (ref["n_c"], ref["n_s"])
     assert ed["n_fallback_iters"] == ref["n_exact_iters"]
@@ -99,6 +100,32 @@ def test_fix_loop_matches_oracle(lib, idx, tier):
     name, kw = FIX_CASES[idx]
     f, fh, xi, _ = synth.config_case(name, **kw)
     _check_fix(lib, f, fh, xi, tier)
+
+
+@pytest.mark.parametrize("idx", [0, 3, 7])
+@pytest.mark.parametrize("tier", [2, 4])
+def test_fix_loop_rounds_as_graph_nodes(lib, idx, tier):
+    """Every round as captured graph nodes (the C-pass that marks T bits, then k_tlist),
+    none in the persistent round kernel: the same result, round by round."""
+    name, kw = FIX_CASES[idx]
+    f, fh, xi, _ = synth.config_case(name, **kw)
+    _check_fix(lib, f, fh, xi, tier, small_round=1)
+
+
+def test_small_rounds_run_in_the_round_kernel(lib):
+    """With the default threshold the rounds after the first run in the persistent round
+    kernel (this case edits fewer than 8192 vertices per round)."""
+    name, kw = FIX_CASES[3]
+    f, fh, xi, _ = synth.config_case(name, **kw)
+    ref = oracle.fix(f, fh, xi, tier=4)
+    h = lib.Handle(f)
+    g, ed = h.fix(fh, xi, tier=4, record_trace=True)
+    st = h.stats()
+    h.close()
+    assert np.array_equal(g.view(np.uint32), ref["g"].view(np.uint32))
+    assert np.array_equal(ed["trace"], ref["trace"][:, :5])
+    assert st["rounds"]["launches"] > 0
+    assert st["rounds"]["items"] >= ed["n_iters_c"] // 2
 
 
 @pytest.mark.parametrize("q_max", [1, 3, 7])
