@@ -280,6 +280,16 @@ uint64_t msc_device_bytes(int nx, int ny, int nz);
  * work.  Handles and edit records that are still alive keep their memory. */
 msc_status msc_release_cached_memory(void);
 
+/* Self-test of the bounded waits (not part of the method).  The persistent round kernel
+ * separates its phases with a grid barrier whose wait gives up after 2 s of device time,
+ * records MSC_ERR_DEVICE_TIMEOUT and ends the kernel, so that a block that never arrives
+ * cannot hang the device.  This call launches that barrier in a kernel where one block waits
+ * for another that never arrives, with a limit of timeout_ms (1..2000) milliseconds.  It
+ * returns MSC_ERR_DEVICE_TIMEOUT when the wait gave up and reported it (the expected outcome;
+ * the device stays usable), MSC_ERR_CUDA otherwise.  stream: a cudaStream_t (NULL = the
+ * legacy default stream). */
+msc_status msc_selftest_barrier(int timeout_ms, void *stream);
+
 /* ---------------------------------------------------------------------------------------
  * Serving: a request loop with continuous batching.  The paper runs one field at a time;
  * this runtime admits fix jobs as they arrive and runs several at once on one GPU.

@@ -1031,7 +1031,7 @@ __device__ __forceinline__ unsigned long long global_ns()
 // Grid-wide barrier of a cooperative launch.  The wait is bounded: a block that waits longer
 // than BAR_TIMEOUT_NS records MSC_ERR_DEVICE_TIMEOUT in the loop state and returns false, and
 // so does every block that passes a barrier after that, so the kernel always ends.
-__device__ bool grid_sync(GridBarrier *gb, LoopState *ls)
+__device__ bool grid_sync(GridBarrier *gb, LoopState *ls, unsigned long long timeout_ns = BAR_TIMEOUT_NS)
 {
     __shared__ int ok;
     __syncthreads();
@@ -1048,7 +1048,7 @@ __device__ bool grid_sync(GridBarrier *gb, LoopState *ls)
             const unsigned long long t0 = global_ns();
             unsigned spins = 0;
             while (*gen == g0) {
-                if (++spins >= BAR_SPIN_CAP || ((spins & 63u) == 0 && global_ns() - t0 > BAR_TIMEOUT_NS)) {
+                if (++spins >= BAR_SPIN_CAP || ((spins & 63u) == 0 && global_ns() - t0 > timeout_ns)) {
                     good = 0;
                     break;
                 }
@@ -1189,6 +1189,14 @@ __global__ void k_rounds_enter(LoopState *ls, GridBarrier *gb)
 
 // after k_rounds: list the C blocks again for the round graphs and the S-pass edit round
 __global__ void k_rounds_leave(LoopState *ls) { ls->nblk = 0; }
+
+// self-test of the bounded grid barrier: block 0 waits at a barrier that the other blocks
+// never reach (they return at once), so its wait must give up after timeout_ns
+__global__ void k_barrier_selftest(GridBarrier *gb, LoopState *ls, unsigned long long timeout_ns)
+{
+    if (blockIdx.x != 0) return;
+    grid_sync(gb, ls, timeout_ns);
+}
 
 template <int D> __global__ void k_desc(Ctx c, const uint32_t *seeds, uint32_t n)
 {
@@ -3002,6 +3010,29 @@ msc_status msc_critical_cells_static(const float *field, int nx, int ny, int nz,
     cudaStream_t s = (cudaStream_t)stream;
     return nz > 1 ? critical_static<3>(field, G, rows, dims, cap, n_out, s)
                   : critical_static<2>(field, G, rows, dims, cap, n_out, s);
+}
+
+msc_status msc_selftest_barrier(int timeout_ms, void *stream)
+{
+    g_last_error.clear();
+    if (timeout_ms < 1 || timeout_ms > 2000) return fail(MSC_ERR_INVALID_ARG, "timeout_ms must be 1..2000");
+    CKS(device_ready());
+    cudaStream_t s = (cudaStream_t)stream;
+    EntryStream es(s);
+    DevBuf<GridBarrier> gb;
+    DevBuf<LoopState> ls;
+    CK(gb.alloc(1));
+    CK(ls.alloc(1));
+    CK(cudaMemsetAsync(gb.p, 0, sizeof(GridBarrier), s));
+    CK(cudaMemsetAsync(ls.p, 0, sizeof(LoopState), s));
+    k_barrier_selftest<<<2, 32, 0, s>>>(gb.p, ls.p, (unsigned long long)timeout_ms * 1000000ull);
+    CK(cudaGetLastError());
+    LoopState L{};
+    CK(cudaMemcpyAsync(&L, ls.p, sizeof L, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (L.status == MSC_ERR_DEVICE_TIMEOUT && L.halt)
+        return fail(MSC_ERR_DEVICE_TIMEOUT, "the barrier wait gave up as it should");
+    return fail(MSC_ERR_CUDA, "the barrier wait did not report its timeout (status %d)", L.status);
 }
 
 msc_status msc_release_cached_memory(void)

@@ -135,6 +135,8 @@ def load():
     lib.msc_reset_stats.argtypes = [vp]
     lib.msc_device_bytes.argtypes = [i, i, i]
     lib.msc_device_bytes.restype = u64
+    lib.msc_selftest_barrier.argtypes = [i, vp]
+    lib.msc_release_cached_memory.argtypes = []
     for name in ("msc_prepare_original", "msc_fix", "msc_apply_edits", "msc_verify", "msc_fix_batch",
                  "msc_gradient_pairs", "msc_critical_cells", "msc_critical_cells_static", "msc_get_stats",
                  "msc_reset_stats", "msc_server_create", "msc_server_submit", "msc_server_wait", "msc_pack_edits",
@@ -519,6 +521,11 @@ def critical_cells_static(field_ptr, shape, rows_ptr, dims_ptr, cap, stream=None
 
 def device_bytes(shape):
     return int(load().msc_device_bytes(*dims_of(shape)))
+
+
+def selftest_barrier(timeout_ms=100):
+    """Status of msc_selftest_barrier (MSC_ERR_DEVICE_TIMEOUT = 5 is the expected outcome)."""
+    return int(load().msc_selftest_barrier(int(timeout_ms), None))
 
 
 def release_cached_memory():
