@@ -1087,22 +1087,6 @@ template <int D> MSC_HD inline void node_bits(const Ctx &c, uint32_t p, bool ini
     }
 }
 
-// seeds: kind 0 descending vertex, 1 ascending top cell, 2 2-saddle triangle
-template <int D> MSC_HD inline void node_seed(const Ctx &c, int kind, uint32_t u)
-{
-    if (kind == 2) {
-        const int32_t o = node_or(c.ns_tri, u, NS_SEED);
-        if (o & NS_SEED) return;
-        const int dv = tri_passes(o | NS_SEED) - tri_passes(o);
-        if (dv) tri_propagate(c, u, dv, false, 0);
-        return;
-    }
-    uint32_t *ns = kind == 0 ? c.ns_v : c.ns_top;
-    const int32_t o = node_or(ns, u, NS_SEED);
-    if (o & NS_SEED) return;
-    path_change<D>(c, kind, u, o, o | NS_SEED);
-}
-
 // The first build's propagation along descending (kind 0) or ascending (kind 1) paths, with
 // W walks interleaved per thread.  A walk is a chain of dependent memory operations (the
 // atomic on a node's word, then the f data of its successor), so one walk per thread leaves

@@ -259,54 +259,10 @@ __device__ __forceinline__ void for_each_set(const uint32_t *bits, uint32_t n, F
     }
 }
 
-// the anchors whose bit is set, visiting only the listed blocks of 32 words: one warp per
-// block compacts its set bits into the warp's row of q (shared memory) and runs f on them;
-// a block found empty has its summary bit cleared, a block found non-empty is handed to
-// keep.  Needs blockDim.x == TPB.
+// a no-op for the keep argument of cpass_listed
 struct NoKeep {
     __device__ void operator()(uint32_t) const {}
 };
-template <class F, class K = NoKeep>
-__device__ __forceinline__ void for_each_listed_in(uint32_t (*q)[32 * 32], const uint32_t *bits, uint32_t n,
-                                                   const uint32_t *blk, unsigned long long nblk, uint32_t *sum, F &&f,
-                                                   unsigned long long *count = nullptr, K &&keep = K{})
-{
-    const unsigned lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    uint32_t *mq = q[wib];
-    const unsigned long long nw = (n + 31) / 32;
-    const unsigned long long warp = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
-    const unsigned long long nwarps = (gridDim.x * (unsigned long long)blockDim.x) >> 5;
-    for (unsigned long long i = warp; i < nblk; i += nwarps) {
-        const uint32_t b = blk[i];
-        const unsigned long long w = (unsigned long long)b * 32 + lane;
-        uint32_t mine = w < nw ? bits[w] : 0u;
-        const unsigned cnt = __popc(mine);
-        unsigned pre = cnt;
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned y = __shfl_up_sync(0xffffffffu, pre, o);
-            if (lane >= (unsigned)o) pre += y;
-        }
-        const unsigned total = __shfl_sync(0xffffffffu, pre, 31);
-        if (total == 0) {
-            if (lane == 0) atomicAnd(sum + (b >> 5), ~(1u << (b & 31)));
-            continue;
-        }
-        if (lane == 0) {
-            if (count) atomicAdd(count, (unsigned long long)total);
-            keep(b);
-        }
-        unsigned at = pre - cnt;
-        const uint32_t base = (uint32_t)(w * 32);
-        while (mine) {
-            const int k = __ffs(mine) - 1;
-            mine &= mine - 1;
-            mq[at++] = base + (uint32_t)k;
-        }
-        __syncwarp();
-        for (unsigned k = lane; k < total; k += 32) f(mq[k]);
-        __syncwarp();
-    }
-}
 
 // The C-pass over the listed blocks of the critical-difference bitset.  One warp per block
 // compacts the block's set bits (anchors, ascending) into its row of q, then compacts the
@@ -389,15 +345,6 @@ __device__ __forceinline__ void cpass_listed(const Ctx &c, uint16_t (*q)[32 * 32
             __syncwarp();
         }
     }
-}
-
-template <class F>
-__device__ __forceinline__ void for_each_listed(const uint32_t *bits, uint32_t n, const uint32_t *blk,
-                                                unsigned long long nblk, uint32_t *sum, F &&f,
-                                                unsigned long long *count = nullptr)
-{
-    __shared__ uint32_t q[TPB / 32][32 * 32];
-    for_each_listed_in(q, bits, n, blk, nblk, sum, f, count);
 }
 
 // list the blocks whose summary bit is set (appending to blk, count in *nblk); every warp
@@ -858,7 +805,6 @@ __global__ void k_decide(Ctx c, int kind)
     round_record(c, c.cnt, kind, stop, status);
 }
 
-constexpr int DIRTY_STAGE = 8192;
 
 // one thread per edit item: save the pre-round value, apply Eq. 2 (or the restore), and
 // list the vertices whose value changed
