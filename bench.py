@@ -123,6 +123,15 @@ CLASS_KERNELS = {
     "rounds": "k_rounds",
 }
 
+# what limits each class, from the ncu captures of its kernels (issue, stalls, DRAM throughput)
+CLASS_LIMITER = {
+    "sep_seed": "memory latency: dependent chains of node atomics and successor loads (path walks issue at "
+                "15-18%, DRAM well below peak); the saddle-saddle walk is issue-bound",
+    "rounds": "latency: four grid barriers and short dependent phases per round",
+    "dense": "instruction issue (78-82% SM throughput, ~3% of DRAM peak)",
+    "cpass": "memory latency of the case lookups",
+}
+
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of a class's kernels per work
 # item, from one ncu capture of the same workload at 256^3 (the capture's launches over the
 # items they processed); a launch's traffic is that figure times the launch's items.  The
@@ -412,6 +421,8 @@ def main():
     bytes_dom = class_bytes(dom, tot, n, args.steps, f.ndim)
     roof = {"bound": "hbm", "kernel": "%s (%s)" % (dom, CLASS_KERNELS[dom]), "achieved": None, "peak": peak,
             "unit": "GB/s", "frac": None, "traffic": None, "peak_source": peak_kind}
+    if dom in CLASS_LIMITER:
+        roof["limiter"] = CLASS_LIMITER[dom]
     if bytes_dom is not None and tot["timed"]:
         avg_ms = tot["ms"] / tot["timed"]
         per_launch = bytes_dom / tot["launches"]
