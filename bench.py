@@ -477,6 +477,7 @@ def main():
                        "kernel_ms_per_step": {k: bst[k]["ms"] for k in msc.KERNEL_CLASSES},
                        "kernel_launches_per_step": {k: bst[k]["launches"] for k in msc.KERNEL_CLASSES},
                        "kernel_items_per_step": {k: bst[k]["items"] for k in msc.KERNEL_CLASSES},
+                       "round_kernel_phase_ms": bst["rounds"].get("phase_ms"),
                        "launches_per_step": launches / args.steps,
                        "loop_algorithmic_GBps": loop_gbs, "loop_frac_of_peak": loop_gbs / peak},
             "roofline": roof, "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
