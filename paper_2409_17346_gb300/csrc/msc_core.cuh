@@ -1262,6 +1262,9 @@ __device__ inline void tri_seed_walks(const Ctx &c, const uint32_t *seeds, uint3
 }
 
 // troublemakers among the pairs anchored at p (p has a code mismatch)
+// A pair's node carries the mismatch bit exactly when the pair's code field differs between
+// f and g (node_bits keeps it so for every anchor whose code changed), so only the node words
+// of differing pairs are read.
 template <int D> MSC_HD inline void node_targets(const Ctx &c, uint32_t p)
 {
     const Tab<D> &T = rt_tab<D>();
@@ -1270,7 +1273,7 @@ template <int D> MSC_HD inline void node_targets(const Ctx &c, uint32_t p)
     int x, y, z;
     coords(c.G, p, x, y, z);
     const int vf = vfield<D>(cf);
-    if (vf != 15) {
+    if (vf != 15 && vfield<D>(cg) != vf) {
         const int32_t b = node_load(c.ns_v, p);
         if ((b & NS_MIS) && path_reached(b)) {
             Verts V;
@@ -1283,7 +1286,7 @@ template <int D> MSC_HD inline void node_targets(const Ctx &c, uint32_t p)
     const int nfac = D == 3 ? T.NT : T.NE;
     for (int ft = 0; ft < nfac; ft++) {
         const int ff = facet_field<D>(cf, ft);
-        if (ff < 2) continue;
+        if (ff < 2 || facet_field<D>(cg, ft) == ff) continue;
         const int i = ff - 2;
         const int *an = D == 3 ? T.tcof_anc[ft][i] : T.ecof_anc[ft][i];
         const int bt = D == 3 ? T.tcof_type[ft][i] : T.ecof_type[ft][i];
@@ -1297,7 +1300,7 @@ template <int D> MSC_HD inline void node_targets(const Ctx &c, uint32_t p)
     if constexpr (D == 3) {
         for (int et = 0; et < T.NE; et++) {
             const int ef = efield<D>(cf, et);
-            if (ef == 0) continue;
+            if (ef == 0 || efield<D>(cg, et) == ef) continue;
             if (ef == 1) {
                 const int32_t b = node_load(c.ns_dead, p * 7 + (uint32_t)et);
                 if ((b & NS_MIS) && node_count(b) > 0) {
