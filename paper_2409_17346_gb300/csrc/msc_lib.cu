@@ -1,15 +1,20 @@
 // libmsc: kernels, fix-loop driver and the C ABI declared in include/msc.h.
 //
 // Device layout of one job (one original field f, N vertices):
-//   f, f_hat, g           float[N]        resident for the job's lifetime
+//   f, f_hat, g, gprev    float[N]        resident for the job's lifetime; gprev holds the
+//                                         pre-round value of the round's edited vertices
 //   state                 uint8[N]        0..q_max quantised count, 0xF0 floor, 0xF1 exact
 //   code_f, code_g        uint64[N]       packed gradient of the cells each anchor owns
+//   low_f                 uint64[N]       (3D) f-lowest vertex slot of each triangle, tetrahedron
 //   T/X/D bitsets         uint32[N/32]    targets, restores, dirty anchors (cleared per round)
-//   T/X/D lists, M lists  uint32[N]       the same sets compacted, mismatch anchors
-//   visited bitsets       N, 6N (3D) or 2N, 12N (3D) bits for the separatrix walks
+//   T/X/D/E lists         uint32[N]       the same sets compacted; E = vertices a round changed
+//   M/C bitsets           uint32[N/32]    anchors whose code / critical cells differ from f's
+//   node words            16 bits per separatrix node (vertex, top cell, triangle, dead edge)
+//   visited bitsets       N, 6N (3D) or 2N, 12N (3D) bits for the tier-3 walks
 // The loop is incremental: after the initial dense gradient of g, a round re-evaluates only
-// anchors whose window contains an edited vertex, and targets only anchors whose code
-// differs from f's.
+// the anchors around edited vertices whose SoS order against a vertex within two edges
+// changed, and targets only anchors whose critical cells differ from f's.  Large rounds run
+// as captured graphs of per-step kernels, small ones in one persistent cooperative kernel.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -678,11 +683,12 @@ constexpr unsigned long long SMALL_ROUND = 8192;   // edited vertices below whic
 __device__ __forceinline__ bool round_off(const LoopState *ls) { return ls->halt || ls->leave; }
 
 // ---- one edit round as a chain of kernels that read the device loop state (ls): any
-// kernel of a round whose phase is over (ls->halt) does nothing, so rounds can be queued
-// back to back (a captured graph of several rounds) and the host looks only at their end.
+// kernel of a round whose phase is over (ls->halt) or whose rounds have become small
+// (ls->leave) does nothing, so rounds can be queued back to back (a captured graph of
+// several rounds) and the host looks only at their end.
 
-// C-pass over the anchors whose critical cells differ from f's (current list)
-// case tallies kept per block in shared memory and published once
+// case tallies of the persistent round kernel's C-pass, kept per block in shared memory and
+// published once (k_ctargets keeps them per warp)
 struct BlockTally {
     unsigned long long v[2];
 };
