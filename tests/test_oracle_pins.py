@@ -705,3 +705,66 @@ def test_packed_record_rebuilds_the_fix():
     qm2, li2, lv2, q = oracle.unpack_edits(oracle.pack_edits(qm, 6, lv))
     g = oracle.apply_edits(fh, xi, q, qm2, li2, lv2)
     assert np.array_equal(g.view(np.uint32), r["g"].view(np.uint32))
+
+
+def _nb_and_ring_offsets(ndim):
+    """Neighbour offsets of the Freudenthal grid and the offsets within two edges."""
+    if ndim == 2:
+        nb = [(1, 0, 0), (0, 1, 0), (1, 1, 0)]
+    else:
+        nb = [(A & 1, (A >> 1) & 1, (A >> 2) & 1) for A in range(1, 8)]
+    nb = nb + [tuple(-c for c in o) for o in nb]
+    ring = set(nb) | {tuple(a[i] + b[i] for i in range(3)) for a in nb for b in nb}
+    ring.discard((0, 0, 0))
+    return set(nb), ring
+
+
+def test_gradient_depends_only_on_orders_within_two_edges():
+    """Every comparison the pairing rules make (Sec. 4.2) is between two vertices within two
+    edges of each other: two neighbours of a vertex, two cofacet candidates of an edge or a
+    triangle, two vertices of a cell.  So moving one vertex's value without crossing any
+    vertex within two edges (in SoS order) leaves the gradient unchanged, checked here both
+    with the closed-form rules and by brute force on Eq. 1.  Crossing a single vertex two
+    edges away that is not a neighbour does change it on some fields, so the neighbours
+    alone would not do.  (The GPU loop skips the refresh of edits that cross nothing.)"""
+    rng = np.random.default_rng(23)
+    kept = changed = tried = 0
+    for trial in range(240):
+        ndim = 2 if trial % 2 else 3
+        shape = tuple(int(s) for s in (rng.integers(4, 7, 2) if ndim == 2 else rng.integers(3, 6, 3)))
+        a = rng.standard_normal(shape).astype(np.float32)
+        flat = a.reshape(-1)
+        nx, ny = shape[-1], shape[-2]
+        nz = 1 if ndim == 2 else shape[0]
+        nbs, ring = _nb_and_ring_offsets(ndim)
+        v = int(rng.integers(0, flat.size))
+        x, y, z = v % nx, (v // nx) % ny, v // (nx * ny)
+        parts = []
+        for o in ring:
+            X, Y, Z = x + o[0], y + o[1], z + o[2]
+            if 0 <= X < nx and 0 <= Y < ny and 0 <= Z < nz:
+                parts.append((X + nx * (Y + ny * Z), o in nbs))
+        key = lambda u: (float(flat[u]), u)
+        brute = trial % 4 == 0
+        # a new value strictly between the nearest partners below and above: no order changes
+        lo = max([float(flat[u]) for u, _ in parts if key(u) < key(v)] + [float(flat[v]) - 4])
+        hi = min([float(flat[u]) for u, _ in parts if key(u) > key(v)] + [float(flat[v]) + 4])
+        w = np.float32(rng.uniform(lo, hi)) if lo < hi else None
+        if w is not None and lo < w < hi:
+            g = flat.copy()
+            g[v] = w
+            assert np.array_equal(oracle.gradient_pairs(g.reshape(shape), brute=brute),
+                                  oracle.gradient_pairs(a, brute=brute)), trial
+            kept += 1
+        # just past the nearest non-neighbour partner above, with no neighbour in between
+        far = sorted([u for u, isnb in parts if not isnb and key(u) > key(v)], key=key)
+        if far and not [p for p, isnb in parts if isnb and key(v) < key(p) <= key(far[0])]:
+            u = far[0]
+            hi2 = min([float(flat[p]) for p, _ in parts if key(p) > key(u)] + [float(flat[u]) + 1])
+            w = np.float32((float(flat[u]) + hi2) / 2)
+            if float(flat[u]) < w < hi2:
+                g = flat.copy()
+                g[v] = w
+                tried += 1
+                changed += not np.array_equal(oracle.gradient_pairs(g.reshape(shape)), oracle.gradient_pairs(a))
+    assert kept > 200 and tried > 100 and changed > 0
