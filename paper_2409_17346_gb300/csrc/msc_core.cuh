@@ -339,7 +339,11 @@ template <int D> MSC_HD inline void add_case(const Ctx &c, uint32_t t, const Ver
         if (live) count_add(&c.cnt->nlive, 1ull);
     }
     if (c.mark_only) {
+#ifdef __CUDA_ARCH__
         atomicOr(c.Tbits + (t >> 5), 1u << (t & 31));
+#else
+        a_or(c.Tbits + (t >> 5), 1u << (t & 31));
+#endif
     } else if (!test_and_set(c.Tbits, t)) {
         c.Tlist[list_slot(&c.cnt->nT)] = t;
         count_add(&c.cnt->sumT, (unsigned long long)t);
