@@ -27,3 +27,107 @@ extern "C" int host_gradient_pairs(const float *field, int nx, int ny, int nz, i
     else pairs_of<2>(field, G, rows, cap, n_out);
     return 0;
 }
+
+// one C-pass (Sec. 4.3) of the CUDA path's case logic (case_mask, case_apply, add_case) on
+// (f, g, state), run anchor by anchor on the host: the target set T and restore set X as
+// vertex flags, and the numbers of cases and of cases whose target can still move
+template <int D>
+static void cpass_of(const float *f, const float *g, const uint8_t *state, const msc::Grid &G, int tier,
+                     int exact_fallback, uint8_t *T_out, uint8_t *X_out, uint64_t *ncase, uint64_t *nlive)
+{
+    using namespace msc;
+    const uint32_t n = G.n;
+    std::vector<uint64_t> cf(n), cg(n);
+    for (uint32_t p = 0; p < n; p++) {
+        cf[p] = anchor_code<D>(f, G, p);
+        cg[p] = anchor_code<D>(g, G, p);
+    }
+    std::vector<uint32_t> Tbits((n + 31) / 32), Xbits((n + 31) / 32), Tlist(n), Xlist(n);
+    std::vector<uint8_t> st(state, state + n);
+    Counters cnt{};
+    Ctx c{};
+    c.G = G;
+    c.tier = tier;
+    c.exact_fallback = exact_fallback;
+    c.f = f;
+    c.g = const_cast<float *>(g);
+    c.state = st.data();
+    c.code_f = cf.data();
+    c.code_g = cg.data();
+    c.Tbits = Tbits.data();
+    c.Xbits = Xbits.data();
+    c.Tlist = Tlist.data();
+    c.Xlist = Xlist.data();
+    c.cnt = &cnt;
+    for (uint32_t p = 0; p < n; p++) {
+        uint32_t m = case_mask<D>(c, p, cf[p], cg[p]);
+        while (m) {
+            const int i = __builtin_ctz(m);
+            m &= m - 1;
+            case_apply<D>(c, p, i);
+        }
+    }
+    for (uint32_t v = 0; v < n; v++) {
+        T_out[v] = (Tbits[v >> 5] >> (v & 31)) & 1u;
+        X_out[v] = (Xbits[v >> 5] >> (v & 31)) & 1u;
+    }
+    *ncase = cnt.ncase;
+    *nlive = cnt.nlive;
+}
+
+extern "C" int host_cpass(const float *f, const float *g, const uint8_t *state, int nx, int ny, int nz, int tier,
+                          int exact_fallback, uint8_t *T_out, uint8_t *X_out, uint64_t *ncase, uint64_t *nlive)
+{
+    const msc::Grid G = msc::make_grid(nx, ny, nz);
+    if (nz > 1) cpass_of<3>(f, g, state, G, tier, exact_fallback, T_out, X_out, ncase, nlive);
+    else cpass_of<2>(f, g, state, G, tier, exact_fallback, T_out, X_out, ncase, nlive);
+    return 0;
+}
+
+// every anchor's packed gradient code
+extern "C" int host_codes(const float *field, int nx, int ny, int nz, uint64_t *out)
+{
+    const msc::Grid G = msc::make_grid(nx, ny, nz);
+    for (uint32_t p = 0; p < G.n; p++) out[p] = nz > 1 ? msc::anchor_code<3>(field, G, p) : msc::anchor_code<2>(field, G, p);
+    return 0;
+}
+
+// the round's refresh set as the edit and mark kernels build it: every vertex v with
+// moved[v] != 0 went from g_old[v] to g_new[v] in the round (gprev = g_old there); the
+// anchors in the window of each moved vertex whose order against a vertex within two
+// edges changed (order_changed) are flagged in dirty_out
+template <int D>
+static void dirty_of(const float *g_old, const float *g_new, const uint8_t *moved, const msc::Grid &G, uint8_t *dirty_out)
+{
+    using namespace msc;
+    const Tab<D> &T = rt_tab<D>();
+    const uint32_t n = G.n;
+    std::vector<uint32_t> Tbits((n + 31) / 32), Xbits((n + 31) / 32);
+    std::vector<float> gprev(g_old, g_old + n), g(g_new, g_new + n);
+    for (uint32_t v = 0; v < n; v++)
+        if (moved[v]) Tbits[v >> 5] |= 1u << (v & 31);
+    Ctx c{};
+    c.G = G;
+    c.g = g.data();
+    c.gprev = gprev.data();
+    c.Tbits = Tbits.data();
+    c.Xbits = Xbits.data();
+    for (uint32_t v = 0; v < n; v++) {
+        if (!moved[v] || !order_changed<D>(c, v, 0, 1, T.ring)) continue;
+        int x, y, z;
+        coords(G, v, x, y, z);
+        for (int j = 0; j < T.nwin; j++) {
+            const int px = x - T.win[j][0], py = y - T.win[j][1], pz = z - T.win[j][2];
+            if (inside(G, px, py, pz)) dirty_out[vid(G, px, py, pz)] = 1;
+        }
+    }
+}
+
+extern "C" int host_dirty(const float *g_old, const float *g_new, const uint8_t *moved, int nx, int ny, int nz,
+                          uint8_t *dirty_out)
+{
+    const msc::Grid G = msc::make_grid(nx, ny, nz);
+    if (nz > 1) dirty_of<3>(g_old, g_new, moved, G, dirty_out);
+    else dirty_of<2>(g_old, g_new, moved, G, dirty_out);
+    return 0;
+}

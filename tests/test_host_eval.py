@@ -1,8 +1,11 @@
-"""The CUDA path's per-anchor gradient evaluator (eval_anchor and its compile-time cell
-tables) and its pair decoder, compiled for the host, against the oracle on CPU: a check of
-the device logic that needs no GPU (the GPU parity tests check the kernels themselves).
-The same fields as the GPU gradient tests: random, all-equal, binary, signed-zero and
-few-level values on 2D and 3D grids, boundary anchors included."""
+"""Device logic of the CUDA path compiled for the host and checked on CPU, with no GPU (the
+GPU parity tests check the kernels themselves):
+  * the per-anchor gradient evaluator (eval_anchor and its compile-time cell tables) and the
+    pair decoder, against the oracle's gradient;
+  * the C-pass case logic (case_mask, case_apply, add_case), against the oracle's targeting
+    pass: the same target set, restore set and number of cases;
+  * the order-change filter of the edit round (order_changed, the window marks): every anchor
+    whose code an edit changes is in the refresh set it builds."""
 import ctypes
 import os
 import shutil
@@ -32,9 +35,17 @@ def lib():
                                "-O2", "-Xcompiler", "-fPIC", "-shared", "-o", tmp, SRC])
         os.replace(tmp, OUT)
     h = ctypes.CDLL(OUT)
-    h.host_gradient_pairs.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
-                                      ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]
+    vp, i = ctypes.c_void_p, ctypes.c_int
+    h.host_gradient_pairs.argtypes = [vp, i, i, i, vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]
+    h.host_cpass.argtypes = [vp, vp, vp, i, i, i, i, i, vp, vp, ctypes.POINTER(ctypes.c_uint64),
+                             ctypes.POINTER(ctypes.c_uint64)]
+    h.host_codes.argtypes = [vp, i, i, i, vp]
+    h.host_dirty.argtypes = [vp, vp, vp, i, i, i, vp]
     return h
+
+
+def _dims(shape):
+    return shape[-1], shape[-2], (shape[0] if len(shape) == 3 else 1)
 
 
 def _pairs(lib, a):
@@ -69,3 +80,53 @@ def test_device_evaluator_matches_oracle_gradient(lib, shape, kind):
     rng = np.random.default_rng(zlib.crc32(repr((shape, kind)).encode()))
     a = _field(shape, kind, rng)
     assert np.array_equal(_pairs(lib, a), oracle.gradient_pairs(a))
+
+
+@pytest.mark.parametrize("shape", [(6, 7), (9, 5), (4, 5, 6), (3, 4, 3)])
+@pytest.mark.parametrize("tier", [1, 2, 3, 4])
+@pytest.mark.parametrize("fallback", [0, 1])
+def test_device_cpass_matches_oracle_targets(lib, shape, tier, fallback):
+    rng = np.random.default_rng(zlib.crc32(repr((shape, tier, fallback)).encode()))
+    f = rng.standard_normal(shape).astype(np.float32)
+    g = (f + rng.standard_normal(shape) * 0.6).astype(np.float32)
+    # quantised states, floors and restores, so that live and stuck cases both occur
+    st = rng.choice(np.array([0, 1, 3, 6, 0xF0, 0xF1], np.uint8), size=f.size, p=[.4, .2, .1, .1, .1, .1])
+    st = np.ascontiguousarray(st, np.uint8)
+    T = np.zeros(f.size, np.uint8)
+    X = np.zeros(f.size, np.uint8)
+    nc, nl = ctypes.c_uint64(), ctypes.c_uint64()
+    lib.host_cpass(f.ctypes.data, g.ctypes.data, st.ctypes.data, *_dims(shape), tier, fallback, T.ctypes.data,
+                   X.ctypes.data, ctypes.byref(nc), ctypes.byref(nl))
+    cases, markX = oracle.targets(f, g, st, 0, tier, fallback)
+    To = np.zeros(f.size, np.uint8)
+    if len(cases):
+        To[np.unique(cases[:, 0])] = 1
+    assert nc.value == len(cases)
+    assert np.array_equal(T, To)
+    assert np.array_equal(X, (markX != 0).astype(np.uint8))
+    live = [t for t in cases[:, 0] if st[t] not in (0xF0, 0xF1)]
+    assert nl.value == len(live)
+
+
+def test_order_change_filter_never_misses_a_changed_code(lib):
+    """Random rounds: a fifth of the vertices lowered, by small or large amounts, so that
+    moved vertices are often compared with other moved ones (each at its pre-round value).
+    Every anchor whose code changed must be in the refresh set; the set must also leave many
+    anchors out, or the filter would be doing nothing."""
+    rng = np.random.default_rng(3)
+    skipped = []
+    for trial in range(200):
+        shape = (tuple(int(s) for s in rng.integers(4, 9, 2)) if trial % 2 else tuple(int(s) for s in rng.integers(3, 7, 3)))
+        a = rng.standard_normal(shape).astype(np.float32)
+        moved = np.ascontiguousarray(rng.random(shape) < 0.2, np.uint8)
+        step = np.where(rng.random(shape) < 0.7, rng.random(shape) * 0.05, rng.random(shape)).astype(np.float32)
+        b = np.where(moved == 1, a - step, a).astype(np.float32)
+        c0 = np.zeros(a.size, np.uint64)
+        c1 = np.zeros(a.size, np.uint64)
+        lib.host_codes(a.ctypes.data, *_dims(shape), c0.ctypes.data)
+        lib.host_codes(b.ctypes.data, *_dims(shape), c1.ctypes.data)
+        dirty = np.zeros(a.size, np.uint8)
+        lib.host_dirty(a.ctypes.data, b.ctypes.data, moved.ctypes.data, *_dims(shape), dirty.ctypes.data)
+        assert not np.any((c0 != c1) & (dirty == 0)), trial
+        skipped.append(1.0 - dirty.mean())
+    assert np.mean(skipped) > 0.1
