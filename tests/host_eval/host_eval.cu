@@ -131,3 +131,101 @@ extern "C" int host_dirty(const float *g_old, const float *g_new, const uint8_t 
     else dirty_of<2>(g_old, g_new, moved, G, dirty_out);
     return 0;
 }
+
+// The S-pass of the separatrix state (tier 4), run on the host with the CUDA path's device
+// functions: the first build (node_bits, path_seed_walks, tri_propagate) on g1, then, when
+// g2 differs, the incremental update of every anchor whose code changed (node_bits), then
+// the troublemakers (node_targets).  Outputs the target and restore sets and the case count.
+template <int D>
+static int spass_of(const float *f, const float *g1, const float *g2, const uint8_t *state, const msc::Grid &G,
+                    int exact_fallback, uint8_t *T_out, uint8_t *X_out, uint64_t *ncase)
+{
+    using namespace msc;
+    const Tab<D> &T = rt_tab<D>();
+    const uint32_t n = G.n;
+    constexpr int NTOP = Tab<D>::NTOP;
+    std::vector<uint64_t> cf(n), c1(n), c2(n), low(n, 0);
+    for (uint32_t p = 0; p < n; p++) {
+        cf[p] = anchor_code<D>(f, G, p);
+        c1[p] = anchor_code<D>(g1, G, p);
+        c2[p] = anchor_code<D>(g2, G, p);
+        if (D == 3) {
+            // f-lowest vertex slot of each existing triangle (bits 2t) and tetrahedron (24 + 2k)
+            int x, y, z;
+            coords(G, p, x, y, z);
+            const unsigned cin = corner_mask<D>(G, x, y, z);
+            for (int t = 0; t < T.NT; t++)
+                if ((cin >> T.tB[t]) & 1u) low[p] |= (uint64_t)lowest_of(cell_verts<D>(G, x, y, z, 2, t), f) << (2 * t);
+            if ((cin >> 7) & 1u)
+                for (int k = 0; k < T.NK; k++)
+                    low[p] |= (uint64_t)lowest_of(cell_verts<D>(G, x, y, z, 3, k), f) << (24 + 2 * k);
+        }
+    }
+    std::vector<uint32_t> seeds[3];
+    for (uint32_t p = 0; p < n; p++)
+        for (int kind = 0; kind < (D == 3 ? 3 : 2); kind++)
+            seeds_anchor<D>(cf.data(), G, p, kind, [&](uint32_t u) { seeds[kind].push_back(u); });
+    std::vector<uint32_t> ns_v(node_words(n + 4)), ns_top(node_words((size_t)n * NTOP + 4));
+    std::vector<uint32_t> ns_tri(node_words((size_t)n * 12 + 4)), ns_dead(node_words((size_t)n * 7 + 4));
+    for (auto *a : {&ns_v, &ns_top, &ns_tri, &ns_dead}) std::fill(a->begin(), a->end(), 0x40404040u);
+    std::vector<uint32_t> ovf(2 * ((size_t)n * 12 + 4));
+    std::vector<uint32_t> Tbits((n + 31) / 32), Xbits((n + 31) / 32), Tlist(n), Xlist(n);
+    std::vector<uint8_t> st(state, state + n);
+    Counters cnt{};
+    Ctx c{};
+    c.G = G;
+    c.tier = 4;
+    c.exact_fallback = exact_fallback;
+    c.f = f;
+    c.g = const_cast<float *>(g2);
+    c.state = st.data();
+    c.code_f = cf.data();
+    c.low_f = low.data();
+    c.code_g = c1.data();
+    c.Tbits = Tbits.data(); c.Xbits = Xbits.data(); c.Tlist = Tlist.data(); c.Xlist = Xlist.data();
+    c.cnt = &cnt;
+    c.ns_v = ns_v.data(); c.ns_top = ns_top.data(); c.ns_tri = ns_tri.data(); c.ns_dead = ns_dead.data();
+    c.ovf_out = ovf.data();
+    c.ovf_cap = (uint32_t)(ovf.size() / 2);
+    auto drain = [&]() {
+        while (cnt.novf) {
+            std::vector<uint32_t> items(ovf.begin(), ovf.begin() + 2 * cnt.novf);
+            cnt.novf = 0;
+            for (size_t i = 0; i < items.size(); i += 2) tri_propagate(c, items[i], 0, true, (int)items[i + 1]);
+        }
+        return cnt.err == 0;
+    };
+    // first build on g1
+    for (uint32_t p = 0; p < n; p++) node_bits<D>(c, p, true);
+    for (int kind = 0; kind < 2; kind++)
+        path_seed_walks<D, 4>(c, kind, seeds[kind].data(), (uint32_t)seeds[kind].size(), 0, 1);
+    if (D == 3)
+        for (uint32_t u : seeds[2]) {
+            const int32_t o = node_or(c.ns_tri, u, NS_SEED);
+            if (o & NS_SEED) continue;
+            const int dv = tri_passes(o | NS_SEED) - tri_passes(o);
+            if (dv) tri_propagate(c, u, dv, false, 0);
+        }
+    if (!drain()) return 1;
+    // the update to g2: every anchor whose code changed
+    c.code_g = c2.data();
+    for (uint32_t p = 0; p < n; p++)
+        if (c1[p] != c2[p]) node_bits<D>(c, p, false);
+    if (!drain()) return 1;
+    cnt = Counters{};
+    for (uint32_t p = 0; p < n; p++) node_targets<D>(c, p);
+    for (uint32_t v = 0; v < n; v++) {
+        T_out[v] = (Tbits[v >> 5] >> (v & 31)) & 1u;
+        X_out[v] = (Xbits[v >> 5] >> (v & 31)) & 1u;
+    }
+    *ncase = cnt.ncase;
+    return 0;
+}
+
+extern "C" int host_spass(const float *f, const float *g1, const float *g2, const uint8_t *state, int nx, int ny,
+                          int nz, int exact_fallback, uint8_t *T_out, uint8_t *X_out, uint64_t *ncase)
+{
+    const msc::Grid G = msc::make_grid(nx, ny, nz);
+    return nz > 1 ? spass_of<3>(f, g1, g2, state, G, exact_fallback, T_out, X_out, ncase)
+                  : spass_of<2>(f, g1, g2, state, G, exact_fallback, T_out, X_out, ncase);
+}

@@ -5,7 +5,10 @@ GPU parity tests check the kernels themselves):
   * the C-pass case logic (case_mask, case_apply, add_case), against the oracle's targeting
     pass: the same target set, restore set and number of cases;
   * the order-change filter of the edit round (order_changed, the window marks): every anchor
-    whose code an edit changes is in the refresh set it builds."""
+    whose code an edit changes is in the refresh set it builds;
+  * the separatrix state of the S-pass (node_bits, the interleaved path walks, the
+    saddle-saddle propagation, its incremental update, node_targets), against the oracle's
+    S-pass: the same troublemaker targets and restores."""
 import ctypes
 import os
 import shutil
@@ -16,6 +19,7 @@ import numpy as np
 import pytest
 
 import oracle
+from paper_2409_17346_gb300 import synth
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "host_eval", "host_eval.cu")
@@ -41,6 +45,7 @@ def lib():
                              ctypes.POINTER(ctypes.c_uint64)]
     h.host_codes.argtypes = [vp, i, i, i, vp]
     h.host_dirty.argtypes = [vp, vp, vp, i, i, i, vp]
+    h.host_spass.argtypes = [vp, vp, vp, vp, i, i, i, i, vp, vp, ctypes.POINTER(ctypes.c_uint64)]
     return h
 
 
@@ -130,3 +135,37 @@ def test_order_change_filter_never_misses_a_changed_code(lib):
         assert not np.any((c0 != c1) & (dirty == 0)), trial
         skipped.append(1.0 - dirty.mean())
     assert np.mean(skipped) > 0.1
+
+
+SPASS_CASES = [("gauss2d", dict(seed=9, size=(23, 41), rel=1e-2)), ("multiscale2d", dict(size=(40, 56), rel=1e-2)),
+               ("grf3d", dict(size=9, rel=1e-2)), ("kolmogorov3d", dict(size=10, rel=3e-3)),
+               ("grf3d", dict(size=13, rel=1e-2))]
+
+
+@pytest.mark.parametrize("idx", range(len(SPASS_CASES)))
+def test_device_separatrix_state_matches_oracle_spass(lib, idx):
+    """Fields whose critical cells already equal f's (the oracle's tier-2 fix of two different
+    base fields), so that the S-pass has troublemakers to find.  The state is built on one
+    field and, in two of the three runs, updated to the other incrementally; either way its
+    troublemakers must be the oracle's S-pass targets (the case counts differ by convention:
+    the oracle counts paths, the state counts nodes)."""
+    name, kw = SPASS_CASES[idx]
+    f, fh, xi, _ = synth.config_case(name, **kw)
+    fh2 = (f + np.random.default_rng(1).uniform(-xi, xi, f.shape)).astype(np.float32)
+    r1, r2 = oracle.fix(f, fh, xi, tier=2), oracle.fix(f, fh2, xi, tier=2)
+    for g1, g2, st in ((r1["g"], r1["g"], r1["state"]), (r1["g"], r2["g"], r2["state"]),
+                       (r2["g"], r1["g"], r1["state"])):
+        g1, g2 = np.ascontiguousarray(g1, np.float32), np.ascontiguousarray(g2, np.float32)
+        st = np.ascontiguousarray(st, np.uint8).reshape(-1)
+        T = np.zeros(f.size, np.uint8)
+        X = np.zeros(f.size, np.uint8)
+        nc = ctypes.c_uint64()
+        assert lib.host_spass(f.ctypes.data, g1.ctypes.data, g2.ctypes.data, st.ctypes.data, *_dims(f.shape), 1,
+                              T.ctypes.data, X.ctypes.data, ctypes.byref(nc)) == 0
+        cases, markX = oracle.targets(f, g2, st, 1, 4, 1)
+        To = np.zeros(f.size, np.uint8)
+        if len(cases):
+            To[np.unique(cases[:, 0])] = 1
+        assert np.array_equal(T, To)
+        assert np.array_equal(X, (markX != 0).astype(np.uint8))
+        assert (nc.value > 0) == (len(cases) > 0)
