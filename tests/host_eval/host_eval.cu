@@ -2,10 +2,35 @@
 // compile-time cell tables) and pair decoder, for the CPU test that compares them with the
 // oracle: test infrastructure, not part of the library.
 #define MSC_HOST_EMULATION 1
+#include <cfenv>
 #include <cstdint>
 #include <vector>
 
 #include "../../paper_2409_17346_gb300/csrc/msc_core.cuh"
+
+// the directed roundings that the device takes from __fsub_ru / __fadd_rd, here from the
+// host's IEEE rounding modes (built with -frounding-math)
+#ifndef __CUDA_ARCH__
+float msc::emu_sub_ru(float a, float b)
+{
+    const int old = std::fegetround();
+    std::fesetround(FE_UPWARD);
+    volatile float x = a, y = b;
+    volatile float r = x - y;
+    std::fesetround(old);
+    return r;
+}
+
+float msc::emu_add_rd(float a, float b)
+{
+    const int old = std::fegetround();
+    std::fesetround(FE_DOWNWARD);
+    volatile float x = a, y = b;
+    volatile float r = x + y;
+    std::fesetround(old);
+    return r;
+}
+#endif
 
 template <int D>
 static void pairs_of(const float *field, const msc::Grid &G, int64_t *rows, uint64_t cap, uint64_t *n_out)
@@ -228,4 +253,34 @@ extern "C" int host_spass(const float *f, const float *g1, const float *g2, cons
     const msc::Grid G = msc::make_grid(nx, ny, nz);
     return nz > 1 ? spass_of<3>(f, g1, g2, state, G, exact_fallback, T_out, X_out, ncase)
                   : spass_of<2>(f, g1, g2, state, G, exact_fallback, T_out, X_out, ncase);
+}
+
+// Eq. 2 as the edit kernel applies it: out_g[v * (q_max + 2) + k] and out_state[...] after
+// k = 0 (the re-clamped base) .. q_max + 1 edits of vertex v
+extern "C" int host_edit_sequence(const float *f, const float *fhat, uint32_t n, float xi, int q_max, float *out_g,
+                                  uint8_t *out_state)
+{
+    using namespace msc;
+    std::vector<float> g(n);
+    std::vector<uint8_t> st(n, 0);
+    Ctx c{};
+    c.f = f;
+    c.fhat = fhat;
+    c.g = g.data();
+    c.state = st.data();
+    c.xi = xi;
+    c.qmax = q_max;
+    c.step = xi / (float)(1 << q_max);
+    const int K = q_max + 2;
+    for (uint32_t v = 0; v < n; v++) {
+        g[v] = clamp_base(f[v], fhat[v], xi);
+        out_g[(size_t)v * K] = g[v];
+        out_state[(size_t)v * K] = 0;
+        for (int k = 1; k < K; k++) {
+            if (st[v] <= q_max) edit_apply(c, 1, 0, v);   // a quantised-step item (not a restore)
+            out_g[(size_t)v * K + k] = g[v];
+            out_state[(size_t)v * K + k] = st[v];
+        }
+    }
+    return 0;
 }

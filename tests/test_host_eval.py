@@ -8,7 +8,10 @@ GPU parity tests check the kernels themselves):
     whose code an edit changes is in the refresh set it builds;
   * the separatrix state of the S-pass (node_bits, the interleaved path walks, the
     saddle-saddle propagation, its incremental update, node_targets), against the oracle's
-    S-pass: the same troublemaker targets and restores."""
+    S-pass: the same troublemaker targets and restores;
+  * the edit arithmetic of Eq. 2 (clamp_base, edit_apply), with the directed roundings taken
+    from the host's IEEE rounding modes, against the oracle's values (its own TwoSum-based
+    rounding) bit for bit."""
 import ctypes
 import os
 import shutil
@@ -36,7 +39,7 @@ def lib():
         os.makedirs(os.path.dirname(OUT), exist_ok=True)
         tmp = OUT + ".tmp.%d" % os.getpid()
         subprocess.check_call([nvcc, "-std=c++17", "--expt-relaxed-constexpr", "-gencode=arch=compute_103a,code=sm_103a",
-                               "-O2", "-Xcompiler", "-fPIC", "-shared", "-o", tmp, SRC])
+                               "-O2", "-Xcompiler", "-fPIC,-frounding-math", "-shared", "-o", tmp, SRC])
         os.replace(tmp, OUT)
     h = ctypes.CDLL(OUT)
     vp, i = ctypes.c_void_p, ctypes.c_int
@@ -46,6 +49,7 @@ def lib():
     h.host_codes.argtypes = [vp, i, i, i, vp]
     h.host_dirty.argtypes = [vp, vp, vp, i, i, i, vp]
     h.host_spass.argtypes = [vp, vp, vp, vp, i, i, i, i, vp, vp, ctypes.POINTER(ctypes.c_uint64)]
+    h.host_edit_sequence.argtypes = [vp, vp, ctypes.c_uint32, ctypes.c_float, i, vp, vp]
     return h
 
 
@@ -169,3 +173,36 @@ def test_device_separatrix_state_matches_oracle_spass(lib, idx):
         assert np.array_equal(T, To)
         assert np.array_equal(X, (markX != 0).astype(np.uint8))
         assert (nc.value > 0) == (len(cases) > 0)
+
+
+@pytest.mark.parametrize("q_max", [1, 3, 6, 7])
+def test_device_edit_arithmetic_matches_oracle(lib, q_max):
+    """Every edit a vertex can take, from the re-clamped base through q_max quantised steps to
+    the floor, on values of three magnitudes, signed zeros, subnormals, bases 2 xi away (so the
+    clamp matters) and bases equal to f."""
+    rng = np.random.default_rng(100 + q_max)
+    for xi in (1e-4, 1e-2, 0.5):
+        n = 3000
+        f = (rng.standard_normal(n) * rng.choice([1e-3, 1.0, 1e3], n)).astype(np.float32)
+        f[:20], f[20:40], f[40:60] = np.float32(0.0), np.float32(-0.0), np.float32(1e-40)
+        xi = float(np.float32(xi))
+        fh = (f + rng.uniform(-2 * xi, 2 * xi, n)).astype(np.float32)
+        fh[60:80] = f[60:80]
+        K = q_max + 2
+        g = np.zeros(n * K, np.float32)
+        st = np.zeros(n * K, np.uint8)
+        lib.host_edit_sequence(f.ctypes.data, fh.ctypes.data, n, xi, q_max, g.ctypes.data, st.ctypes.data)
+        g, st = g.reshape(n, K), st.reshape(n, K)
+        lb, ub, fc, qv = oracle.edit_values(f, fh, xi, q_max)
+        assert np.array_equal(g[:, 0].view(np.uint32), fc.view(np.uint32))
+        was_floor = np.zeros(n, bool)
+        for k in range(1, K):
+            quant, floor = st[:, k] == k, st[:, k] == 0xF0
+            assert np.all(quant | floor)
+            if k <= q_max:
+                assert np.array_equal(g[quant, k].view(np.uint32), qv[quant, k].view(np.uint32))
+                assert np.all(qv[quant, k] >= lb[quant])
+                first = floor & ~was_floor
+                assert np.all(qv[first, k] < lb[first])       # the floor only when the step would pass it
+            assert np.array_equal(g[floor, k].view(np.uint32), lb[floor].view(np.uint32))
+            was_floor |= floor
