@@ -284,3 +284,54 @@ extern "C" int host_edit_sequence(const float *f, const float *fhat, uint32_t n,
     }
     return 0;
 }
+
+// The tier-3 S-pass (terminal mode) with the CUDA path's walks (desc_walk, asc_walk and
+// their visited sets) on (f, g, state): the target and restore sets
+template <int D>
+static void spass_t3_of(const float *f, const float *g, const uint8_t *state, const msc::Grid &G, int exact_fallback,
+                        uint8_t *T_out, uint8_t *X_out)
+{
+    using namespace msc;
+    constexpr int NTOP = Tab<D>::NTOP;
+    const uint32_t n = G.n;
+    std::vector<uint64_t> cf(n), cg(n);
+    for (uint32_t p = 0; p < n; p++) {
+        cf[p] = anchor_code<D>(f, G, p);
+        cg[p] = anchor_code<D>(g, G, p);
+    }
+    std::vector<uint32_t> seeds[2];
+    for (uint32_t p = 0; p < n; p++)
+        for (int kind = 0; kind < 2; kind++) seeds_anchor<D>(cf.data(), G, p, kind, [&](uint32_t u) { seeds[kind].push_back(u); });
+    std::vector<uint32_t> vis_v((n + 31) / 32), vis_top(((size_t)n * NTOP + 31) / 32);
+    std::vector<uint32_t> Tbits((n + 31) / 32), Xbits((n + 31) / 32), Tlist(n), Xlist(n);
+    std::vector<uint8_t> st(state, state + n);
+    Counters cnt{};
+    Ctx c{};
+    c.G = G;
+    c.tier = 3;
+    c.exact_fallback = exact_fallback;
+    c.f = f;
+    c.g = const_cast<float *>(g);
+    c.state = st.data();
+    c.code_f = cf.data();
+    c.code_g = cg.data();
+    c.Tbits = Tbits.data(); c.Xbits = Xbits.data(); c.Tlist = Tlist.data(); c.Xlist = Xlist.data();
+    c.vis_v = vis_v.data();
+    c.vis_top = vis_top.data();
+    c.cnt = &cnt;
+    for (uint32_t u : seeds[0]) desc_walk<D>(c, u);
+    for (uint32_t b : seeds[1]) asc_walk<D>(c, b);
+    for (uint32_t v = 0; v < n; v++) {
+        T_out[v] = (Tbits[v >> 5] >> (v & 31)) & 1u;
+        X_out[v] = (Xbits[v >> 5] >> (v & 31)) & 1u;
+    }
+}
+
+extern "C" int host_spass_t3(const float *f, const float *g, const uint8_t *state, int nx, int ny, int nz,
+                             int exact_fallback, uint8_t *T_out, uint8_t *X_out)
+{
+    const msc::Grid G = msc::make_grid(nx, ny, nz);
+    if (nz > 1) spass_t3_of<3>(f, g, state, G, exact_fallback, T_out, X_out);
+    else spass_t3_of<2>(f, g, state, G, exact_fallback, T_out, X_out);
+    return 0;
+}

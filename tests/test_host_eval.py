@@ -8,7 +8,8 @@ GPU parity tests check the kernels themselves):
     whose code an edit changes is in the refresh set it builds;
   * the separatrix state of the S-pass (node_bits, the interleaved path walks, the
     saddle-saddle propagation, its incremental update, node_targets), against the oracle's
-    S-pass: the same troublemaker targets and restores;
+    S-pass: the same troublemaker targets and restores; likewise the terminal-mode walks of
+    tier 3 (desc_walk, asc_walk);
   * the edit arithmetic of Eq. 2 (clamp_base, edit_apply), with the directed roundings taken
     from the host's IEEE rounding modes, against the oracle's values (its own TwoSum-based
     rounding) bit for bit."""
@@ -50,6 +51,7 @@ def lib():
     h.host_dirty.argtypes = [vp, vp, vp, i, i, i, vp]
     h.host_spass.argtypes = [vp, vp, vp, vp, i, i, i, i, vp, vp, ctypes.POINTER(ctypes.c_uint64)]
     h.host_edit_sequence.argtypes = [vp, vp, ctypes.c_uint32, ctypes.c_float, i, vp, vp]
+    h.host_spass_t3.argtypes = [vp, vp, vp, i, i, i, i, vp, vp]
     return h
 
 
@@ -206,3 +208,21 @@ def test_device_edit_arithmetic_matches_oracle(lib, q_max):
                 assert np.all(qv[first, k] < lb[first])       # the floor only when the step would pass it
             assert np.array_equal(g[floor, k].view(np.uint32), lb[floor].view(np.uint32))
             was_floor |= floor
+
+
+@pytest.mark.parametrize("idx", range(len(SPASS_CASES)))
+def test_device_tier3_walks_match_oracle_spass(lib, idx):
+    name, kw = SPASS_CASES[idx]
+    f, fh, xi, _ = synth.config_case(name, **kw)
+    r = oracle.fix(f, fh, xi, tier=2)
+    g = np.ascontiguousarray(r["g"], np.float32)
+    st = np.ascontiguousarray(r["state"], np.uint8).reshape(-1)
+    T = np.zeros(f.size, np.uint8)
+    X = np.zeros(f.size, np.uint8)
+    lib.host_spass_t3(f.ctypes.data, g.ctypes.data, st.ctypes.data, *_dims(f.shape), 1, T.ctypes.data, X.ctypes.data)
+    cases, markX = oracle.targets(f, g, st, 1, 3, 1)
+    To = np.zeros(f.size, np.uint8)
+    if len(cases):
+        To[np.unique(cases[:, 0])] = 1
+    assert np.array_equal(T, To)
+    assert np.array_equal(X, (markX != 0).astype(np.uint8))
