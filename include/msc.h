@@ -256,13 +256,22 @@ msc_status msc_critical_cells(const float *field, int nx, int ny, int nz,
  *    plus a few counters (about 8 MiB), which every GPU that loads the library keeps until
  *    the process exits.  Grids larger than MSC_STATIC_MAX_VERTICES vertices are rejected
  *    with MSC_ERR_INVALID_ARG.  No device memory is allocated or freed by this call.
- *  - The first call on a device looks up the device address of that array; make that first
- *    call before any stream capture.
+ *  - Every call looks up the device address of that array (cudaGetSymbolAddress) on the
+ *    current device, queues its kernels on stream, then waits for that stream before it
+ *    returns, on success and on every error path alike.
  *  - All calls share the one array (its counters are cleared at the start of each call):
  *    calls whose device work overlaps (other threads or streams) race and give wrong
- *    results.  stream: a cudaStream_t (NULL = the legacy default stream). */
+ *    results.  stream: a cudaStream_t (NULL = the legacy default stream).
+ *  - Device pointers of another device are rejected with MSC_ERR_INVALID_ARG before any
+ *    kernel is launched.  On any status other than MSC_OK the contents of rows and dims
+ *    are undefined. */
 msc_status msc_critical_cells_static(const float *field, int nx, int ny, int nz, int64_t *rows, int32_t *dims,
                                      uint64_t cap, uint64_t *n_out, void *stream);
+
+/* Bytes of the library's device memory pool on the current device that are allocated to
+ * live buffers right now (cudaMemPoolAttrUsedMemCurrent); memory the pool keeps for reuse
+ * is not counted.  Lets a caller check that a sequence of calls allocated nothing. */
+msc_status msc_pool_used_bytes(uint64_t *used);
 
 /* Launch statistics accumulated on a handle since its creation or the last reset. */
 msc_status msc_get_stats(msc_handle *h, msc_stats *out);

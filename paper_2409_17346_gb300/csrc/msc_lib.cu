@@ -2529,25 +2529,32 @@ constexpr size_t STATIC_WORDS = (size_t)MSC_STATIC_MAX_VERTICES + 32;
 static __device__ __align__(256) unsigned long long g_static_scratch[STATIC_WORDS];
 
 namespace {
-std::mutex g_static_mu;
-void *g_static_addr[256] = {};
-
-// device address of the static scratch on the current device (looked up once per device)
+// device address of the static scratch on the current device.  Looked up on every call:
+// the lookup is cheap, and an address kept from an earlier call would be stale after the
+// device's context was torn down and the module loaded again.
 msc_status static_scratch(unsigned long long **out)
 {
-    int dev = 0;
-    CK(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 256) return fail(MSC_ERR_NO_DEVICE, "device ordinal %d out of range", dev);
-    std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_addr[dev]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess || !p)
-            return fail(MSC_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
-        g_static_addr[dev] = p;
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return fail(MSC_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
     }
-    *out = (unsigned long long *)g_static_addr[dev];
+    *out = (unsigned long long *)p;
     return MSC_OK;
+}
+
+// true iff p is device memory of the current device, or managed memory
+bool on_current_device(const void *p)
+{
+    cudaPointerAttributes a;
+    int dev = -1;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 template <int D>
@@ -2556,6 +2563,16 @@ msc_status critical_static(const float *field, Grid G, int64_t *rows, int32_t *d
 {
     unsigned long long *scr;
     CKS(static_scratch(&scr));
+    // waits for the stream on every return path, so that no kernel of this call is still
+    // writing the scratch or the caller's rows when it returns
+    struct SyncOnExit {
+        cudaStream_t s;
+        ~SyncOnExit()
+        {
+            cudaStreamSynchronize(s);
+            cudaGetLastError();
+        }
+    } sync_on_exit{s};
     uint64_t *code = (uint64_t *)scr;
     unsigned long long *count = scr + MSC_STATIC_MAX_VERTICES, *bad = count + 1;
     CK(cudaMemsetAsync(count, 0, 2 * sizeof(unsigned long long), s));
@@ -2956,8 +2973,8 @@ msc_status msc_critical_cells_static(const float *field, int nx, int ny, int nz,
                     (unsigned)MSC_STATIC_MAX_VERTICES);
     if (cap && (!rows || !dims)) return fail(MSC_ERR_INVALID_ARG, "rows and dims must be non-NULL when cap > 0");
     CKS(device_ready());
-    if (!is_device_ptr(field) || (cap && (!is_device_ptr(rows) || !is_device_ptr(dims))))
-        return fail(MSC_ERR_INVALID_ARG, "field, rows and dims must be device pointers");
+    if (!on_current_device(field) || (cap && (!on_current_device(rows) || !on_current_device(dims))))
+        return fail(MSC_ERR_INVALID_ARG, "field, rows and dims must be device pointers on the current device");
     const Grid G = make_grid(nx, ny, nz);
     cudaStream_t s = (cudaStream_t)stream;
     return nz > 1 ? critical_static<3>(field, G, rows, dims, cap, n_out, s)
@@ -2995,6 +3012,20 @@ msc_status msc_release_cached_memory(void)
     host_trim();
     cudaMemPool_t pool = lib_pool();
     if (pool) CK(cudaMemPoolTrimTo(pool, 0));
+    return MSC_OK;
+}
+
+msc_status msc_pool_used_bytes(uint64_t *used)
+{
+    g_last_error.clear();
+    if (!used) return fail(MSC_ERR_INVALID_ARG, "used is NULL");
+    *used = 0;
+    CKS(device_ready());
+    cudaMemPool_t pool = lib_pool();
+    if (!pool) return fail(MSC_ERR_CUDA, "the library's memory pool could not be created");
+    uint64_t v = 0;
+    CK(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &v));
+    *used = (uint64_t)v;
     return MSC_OK;
 }
 

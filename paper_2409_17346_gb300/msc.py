@@ -137,10 +137,11 @@ def load():
     lib.msc_device_bytes.restype = u64
     lib.msc_selftest_barrier.argtypes = [i, vp]
     lib.msc_release_cached_memory.argtypes = []
+    lib.msc_pool_used_bytes.argtypes = [ctypes.POINTER(u64)]
     for name in ("msc_prepare_original", "msc_fix", "msc_apply_edits", "msc_verify", "msc_fix_batch",
                  "msc_gradient_pairs", "msc_critical_cells", "msc_critical_cells_static", "msc_get_stats",
                  "msc_reset_stats", "msc_server_create", "msc_server_submit", "msc_server_wait", "msc_pack_edits",
-                 "msc_unpack_edits"):
+                 "msc_unpack_edits", "msc_pool_used_bytes", "msc_release_cached_memory", "msc_selftest_barrier"):
         getattr(lib, name).restype = i
     _lib = lib
     return lib
@@ -531,6 +532,13 @@ def selftest_barrier(timeout_ms=100):
 def release_cached_memory():
     """Return the device memory the library's pool keeps for reuse to the driver."""
     _check(load().msc_release_cached_memory())
+
+
+def pool_used_bytes():
+    """Bytes of the library's device memory pool (current device) held by live buffers."""
+    n = ctypes.c_uint64(0)
+    _check(load().msc_pool_used_bytes(ctypes.byref(n)))
+    return n.value
 
 
 def version():

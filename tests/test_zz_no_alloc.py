@@ -1,6 +1,7 @@
 """msc_critical_cells_static, the entry point that allocates no device memory, agrees
 with msc_critical_cells (which allocates its own scratch) on caller-owned device
-buffers, on two calls in a row."""
+buffers, on two calls in a row, and leaves both torch's allocator and the library's
+memory pool exactly as it found them."""
 import numpy as np
 import pytest
 
@@ -77,3 +78,24 @@ def test_static_rejects_oversize_and_host_pointers(lib):
     host = np.zeros((8, 8), np.float32)
     with pytest.raises(lib.MscError, match="device pointers"):
         lib.critical_cells_static(host.ctypes.data, host.shape, 0, 0, 0)
+
+
+def test_static_allocates_nothing(lib):
+    """After a first call, further calls change neither torch's allocated bytes nor the
+    bytes of the library's pool that live buffers hold."""
+    import torch
+    f = synth.config_case("grf3d", seed=7, size=20)[0]
+    fd = torch.from_numpy(f).cuda()
+    rows = torch.empty((4096, 4), dtype=torch.int64, device="cuda")
+    dims = torch.empty((4096,), dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    first = lib.critical_cells_static(fd.data_ptr(), f.shape, rows.data_ptr(), dims.data_ptr(), 4096, stream)
+    torch.cuda.synchronize()
+    torch_before = torch.cuda.memory_allocated()
+    pool_before = lib.pool_used_bytes()
+    for _ in range(3):
+        n = lib.critical_cells_static(fd.data_ptr(), f.shape, rows.data_ptr(), dims.data_ptr(), 4096, stream)
+        assert n == first
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == torch_before
+    assert lib.pool_used_bytes() == pool_before
