@@ -111,6 +111,21 @@ def separatrices(field, kind):
     return out[: n.value]
 
 
+def saddle_connectors(field):
+    """The saddle-saddle walk of a 3D field's gradient from every 2-saddle.  Rows of 13:
+    2-saddle (4 ids), kind (0 = 1-saddle edge reached, 1 = pair (edge, triangle) crossed,
+    2 = dead-end edge paired down with a vertex), edge (4 ids), other cell (4 ids)."""
+    lib = _load()
+    f = _f32(field)
+    nx, ny, nz = _dims(f)
+    n = ctypes.c_int64(0)
+    _check(lib.orc_saddle_connectors(_p(f), nx, ny, nz, None, ctypes.c_int64(0), ctypes.byref(n)), "saddle_connectors")
+    out = np.zeros((max(n.value, 1), 13), dtype=np.int64)
+    _check(lib.orc_saddle_connectors(_p(f), nx, ny, nz, _p(out), ctypes.c_int64(n.value), ctypes.byref(n)),
+           "saddle_connectors")
+    return out[: n.value]
+
+
 def targets(f, g, state=None, pass_=0, tier=4, exact_fallback=1):
     """One targeting pass (0 = C-pass, 1 = S-pass) on (f, g, state).  Returns
     (cases: rows (target vertex, case cell 4 ids), markX: uint8 per vertex)."""

@@ -416,7 +416,21 @@ typedef struct {
     i64 ncase, nlive;
     /* optional record of (target, case cell) for the case tests */
     i64 *rec; i64 rec_cap, rec_n;
+    /* optional record of the saddle-saddle walk, rows (2-saddle, kind, edge, other):
+     * kind 0 = 1-saddle edge reached, 1 = pair (edge, other triangle) crossed,
+     * 2 = dead-end edge paired down with vertex other */
+    i64 *walk; i64 walk_cap, walk_n;
 } loopctx;
+
+static void walk_note(loopctx *c, i64 t0, i64 kind, i64 e, i64 other)
+{
+    if (!c->walk) return;
+    if (c->walk_n < c->walk_cap) {
+        i64 *r = c->walk + 4 * c->walk_n;
+        r[0] = t0; r[1] = kind; r[2] = e; r[3] = other;
+    }
+    c->walk_n++;
+}
 
 static int stuck(const loopctx *c, i64 t) { return c->state[t] == ST_FLOOR || c->state[t] == ST_EXACT; }
 
@@ -518,8 +532,9 @@ static i64 saddle_saddle(loopctx *c, i64 t0, i64 *stamp, i64 stampval, i64 *queu
             i64 e = fc[i];
             if (e == entry) continue;
             i64 pe = c->prf[e];
-            if (pe == -1) continue;
+            if (pe == -1) { walk_note(c, t0, 0, e, -1); continue; }
             if (cell_dim(g, pe) == 0) {
+                walk_note(c, t0, 2, e, pe);
                 i64 q = c->prg[e];
                 if (q == -1 || cell_dim(g, q) != 0) {
                     add_case(c, extra_vertex(g, e, pe), e);
@@ -528,6 +543,7 @@ static i64 saddle_saddle(loopctx *c, i64 t0, i64 *stamp, i64 stampval, i64 *queu
                 continue;
             }
             if (pe == t) continue;
+            walk_note(c, t0, 1, e, pe);
             if (c->prg[e] != pe) {
                 add_case(c, extra_vertex(g, pe, e), pe);
                 found++;
@@ -786,6 +802,50 @@ int orc_separatrices(const float *field, int nx, int ny, int nz, int kind,
     free(pr); free(pb.L); free(pb.U);
     *n_out = n;
     return ORC_OK;
+}
+
+/* The saddle-saddle walk of a 3D field's own gradient (Sec. 3.1, Sec. 4.4), as the S-pass
+ * runs it with V_g = V_f: one row of 13 per item examined from each 2-saddle,
+ * (2-saddle 4 ids, kind, edge 4 ids, other 4 ids) with kind 0 = 1-saddle edge reached
+ * (other -1), 1 = pair (edge, other triangle) crossed, 2 = dead-end edge paired down with
+ * vertex other.  Items reached along several routes appear once per route examined. */
+int orc_saddle_connectors(const float *field, int nx, int ny, int nz, int64_t *out, int64_t cap, int64_t *n_out)
+{
+    grid_t g;
+    if (grid_init(&g, nx, ny, nz) || g.dim != 3 || !valid_field(field, (i64)nx * ny * nz)) return ORC_ERR_ARG;
+    i64 ncell = g.n * g.K;
+    loopctx c = {0};
+    c.g = &g; c.f = field; c.gv = (float *)field;
+    c.prf = malloc(ncell * sizeof(i64));
+    c.markT = calloc(g.n, 1);
+    c.markX = calloc(g.n, 1);
+    c.state = calloc(g.n, 1);
+    c.walk = malloc(4 * (cap > 0 ? cap : 1) * sizeof(i64));
+    c.walk_cap = cap;
+    i64 *stamp = malloc(ncell * sizeof(i64));
+    i64 *queue = malloc(2 * ncell * sizeof(i64) + 16);
+    int rc = ORC_OK;
+    if (!c.prf || !c.markT || !c.markX || !c.state || !c.walk || !stamp || !queue) { rc = ORC_ERR_OOM; goto done; }
+    gradient_rules(&g, field, c.prf);
+    c.prg = c.prf;
+    for (i64 i = 0; i < ncell; i++) stamp[i] = -1;
+    for (i64 id = 0; id < ncell; id++) {
+        if (cell_dim(&g, id) != 2 || c.prf[id] != -1) continue;
+        if (saddle_saddle(&c, id, stamp, id, queue) != 0) { rc = ORC_ERR_INTERNAL; goto done; }
+    }
+    for (i64 i = 0; i < c.walk_n && i < cap; i++) {
+        const i64 *r = c.walk + 4 * i;
+        int64_t *o = out + 13 * i;
+        write_cell(&g, r[0], o);
+        o[4] = r[1];
+        write_cell(&g, r[2], o + 5);
+        if (r[3] >= 0) write_cell(&g, r[3], o + 9);
+        else for (int k = 0; k < 4; k++) o[9 + k] = -1;
+    }
+    *n_out = c.walk_n;
+done:
+    free(c.prf); free(c.markT); free(c.markX); free(c.state); free(c.walk); free(stamp); free(queue);
+    return rc;
 }
 
 /* One targeting pass on (f, g, state): pass 0 = C-pass, 1 = S-pass.  Writes the case list

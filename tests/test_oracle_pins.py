@@ -468,6 +468,162 @@ def test_fn_max_2d_repairs_facet():
     assert _case_target(F_MAX, g, (4, 7, 8)) == 5
 
 
+# 3D cases on a 3 x 2 x 2 grid (nx = 3, ny = 2, nz = 2), vertex id = x + 3 y + 6 z:
+#   0 (0,0,0)  1 (1,0,0)  2 (2,0,0)  3 (0,1,0)  4 (1,1,0)  5 (2,1,0)
+#   6 (0,0,1)  7 (1,0,1)  8 (2,0,1)  9 (0,1,1) 10 (1,1,1) 11 (2,1,1)
+# Each field below is f with one (or two) vertices moved; the docstrings derive the pairs
+# involved from the rules of Sec. 4.2 by hand, and the expected vertex from Sec. 4.3/4.4.
+
+def _g3(f, moves):
+    g = np.float32(f).copy()
+    for v, val in moves.items():
+        g[v] = val
+    return g.reshape(2, 2, 3)
+
+
+def _crit_set(field):
+    rows, _ = oracle.critical_cells(field)
+    return {tuple(int(x) for x in r if x >= 0) for r in rows}
+
+
+def test_fp_2saddle_edge_type_and_fp_1saddle_triangle_type_3d():
+    """f: edge {0,4} (values 4, 5) is not paired down (V(0) = {0,7}, V(4) = {4,5}) and its
+    only cofacet whose extra vertex lies below both ends is {0,1,4} (vertex 1, value 3), so
+    triangle {0,1,4} is paired with edge {0,4}.  Raising vertex 1 to 4.5 breaks the
+    condition f_1 < f_0, f_4: the edge becomes an FP1saddle (triangle type, Sec. 4.3: lower
+    the triangle's vertex l = 1) and the triangle an FP2saddle of the edge type (lower
+    the vertex k = 1 that the pairing requires below the edge)."""
+    f = np.float32([4, 3, 10, 9, 5, 1, 6, 0, 2, 8, 11, 7])
+    g = _g3(f, {1: 4.5})
+    f = f.reshape(2, 2, 3)
+    P = _pairs_dict(f)
+    assert P[(0, 4)] == (0, 1, 4) and (0, 4) in _crit_set(g) and (0, 1, 4) in _crit_set(g)
+    assert _case_target(f, g, (0, 1, 4)) == 1
+    assert _case_target(f, g, (0, 4)) == 1
+
+
+def test_fp_2saddle_tet_type_and_fp_max_3d():
+    """f: triangle {7,10,11} (values 5, 10, 7) is claimed by none of its edges ({7,10}
+    pairs with {6,7,10}, {7,11} with {7,8,11}, {10,11} with {4,10,11}) and its one tet
+    {1,7,10,11} has extra vertex 1 (value 4) below all three, so it pairs with that tet.
+    Raising vertex 1 to 5.5 (above vertex 7) breaks the pair: the triangle is an
+    FP2saddle of the tetrahedron type and the tet an FPmax (3D); Sec. 4.3 lowers l = 1
+    for both."""
+    f = np.float32([11, 4, 3, 9, 1, 8, 2, 5, 0, 6, 10, 7])
+    g = _g3(f, {1: 5.5})
+    f = f.reshape(2, 2, 3)
+    assert _pairs_dict(f)[(7, 10, 11)] == (1, 7, 10, 11)
+    assert {(7, 10, 11), (1, 7, 10, 11)} <= _crit_set(g)
+    assert _case_target(f, g, (7, 10, 11)) == 1
+    assert _case_target(f, g, (1, 7, 10, 11)) == 1
+
+
+def test_fn_2saddle_tet_type_and_fn_max_3d():
+    """f: triangle {4,10,11} (values 4, 10, 6) and tet {1,4,10,11} are critical (a
+    2-saddle and a maximum).  Raising vertex 4 to 5.5 puts the tet's vertex 1 (value 5)
+    below all of the triangle, so g pairs them.  FN2saddle paired with a tetrahedron: edit
+    i, j or k (Sec. 4.3), here the triangle's lowest vertex in f, 4.  FNmax (3D) paired with
+    triangle ijk: edit i, j or k, again the f-lowest, 4."""
+    f = np.float32([1, 5, 7, 9, 4, 0, 2, 3, 8, 11, 10, 6])
+    g = _g3(f, {4: 5.5})
+    f = f.reshape(2, 2, 3)
+    assert {(4, 10, 11), (1, 4, 10, 11)} <= _crit_set(f)
+    assert _pairs_dict(g)[(4, 10, 11)] == (1, 4, 10, 11)
+    assert _case_target(f, g, (4, 10, 11)) == 4
+    assert _case_target(f, g, (1, 4, 10, 11)) == 4
+
+
+def test_fn_2saddle_edge_type_and_fn_1saddle_triangle_type_3d():
+    """f: edge {0,4} and triangle {0,1,4} are critical (vertex 1, value 3, is not below
+    vertex 0, value 2).  Raising vertex 0 to 3.5 makes g pair the edge with the triangle.
+    FN2saddle paired with edge ij: edit i or j; FN1saddle paired with triangle ijl: edit i
+    or j (Sec. 4.3).  Both cases take vertex 0, the lowest of the edge in f."""
+    f = np.float32([2, 3, 11, 8, 7, 1, 4, 0, 5, 9, 10, 6])
+    g = _g3(f, {0: 3.5})
+    f = f.reshape(2, 2, 3)
+    assert {(0, 4), (0, 1, 4)} <= _crit_set(f)
+    assert _pairs_dict(g)[(0, 4)] == (0, 1, 4)
+    assert _case_target(f, g, (0, 1, 4)) == 0
+    assert _case_target(f, g, (0, 4)) == 0
+
+
+def test_fn_2saddle_edge_type_repairs_facet_3d():
+    """f: edge {7,10} (values 10, 8) pairs with triangle {7,10,11}: of its cofacets'
+    extra vertices below both ends (11: 5, 6: 6, 1: 7) vertex 11 is the lowest.  Triangle
+    {6,7,10} is then a 2-saddle.  Raising vertex 11 to 6.5 lets vertex 6 win: g pairs
+    {7,10} with {6,7,10} (an FN2saddle of the edge type) and {7,10,11} becomes critical
+    (an FP2saddle, lower k = 11).  For the FN case the paper allows i or j (7 or 10), but
+    vertex 6, the triangle's lowest in f, is already below both in g, so the reading
+    repairs the facet's f-pair ({7,10}, {7,10,11}) instead: it lowers 11 as well."""
+    f = np.float32([11, 7, 4, 9, 2, 3, 6, 10, 1, 0, 8, 5])
+    g = _g3(f, {11: 6.5})
+    f = f.reshape(2, 2, 3)
+    assert _pairs_dict(f)[(7, 10)] == (7, 10, 11) and (6, 7, 10) in _crit_set(f)
+    assert _pairs_dict(g)[(7, 10)] == (6, 7, 10)
+    assert _case_target(f, g, (6, 7, 10)) == 11
+    assert _case_target(f, g, (7, 10, 11)) == 11
+
+
+def test_one_dim_troublemaker_2d():
+    """1-dimensional troublemaker (Sec. 4.4) on a 4 x 4 grid (id = x + 4 y).  In f, edge
+    {2,6} (values 10, 8) is not paired down and pairs with triangle {1,2,6}: vertex 1
+    (value 6) is below both ends, vertex 7 of the other cofacet {2,6,7} (value 9) is not.
+    The pair lies on an ascending separatrix.  In g vertex 1 rises to 9.5 and vertex 7
+    falls to 2.5, so the edge pairs with {2,6,7} (the paper's ijl) while every critical
+    cell stays: the S-pass lowers k = 1, and that is its only troublemaker."""
+    f = np.float32([2, 6, 10, 11, 13, 4, 8, 9, 7, 3, 5, 0, 1, 15, 14, 12]).reshape(4, 4)
+    g = f.copy().reshape(-1)
+    g[1], g[7] = 9.5, 2.5
+    g = g.reshape(4, 4)
+    assert _pairs_dict(f)[(2, 6)] == (1, 2, 6) and _pairs_dict(g)[(2, 6)] == (2, 6, 7)
+    assert len(oracle.targets(f, g, pass_=0)[0]) == 0
+    cases, _ = oracle.targets(f, g, pass_=1, tier=4)
+    assert [int(c[0]) for c in cases] == [1]
+    assert _case_target(f, g, (1, 2, 6), pass_=1) == 1
+
+
+def test_two_dim_troublemaker_3d():
+    """2-dimensional troublemaker (Sec. 4.4).  In f, triangle {0,3,10} (values 8, 9, 11)
+    pairs with tet {0,3,9,10}: vertex 9 (value 7) lies below all three, vertex 4 of the
+    other tet {0,3,4,10} (value 10) does not.  The pair lies on an ascending separatrix.
+    In g vertex 9 rises to 9.5 and vertex 4 falls to 6.5, so the triangle pairs with
+    {0,3,4,10} (the paper's ijkq) and no critical cell changes: the S-pass lowers l = 9,
+    its only troublemaker."""
+    f = np.float32([8, 0, 6, 9, 10, 3, 4, 5, 2, 7, 11, 1])
+    g = _g3(f, {4: 6.5, 9: 9.5})
+    f = f.reshape(2, 2, 3)
+    assert _pairs_dict(f)[(0, 3, 10)] == (0, 3, 9, 10) and _pairs_dict(g)[(0, 3, 10)] == (0, 3, 4, 10)
+    assert len(oracle.targets(f, g, pass_=0)[0]) == 0
+    cases, _ = oracle.targets(f, g, pass_=1, tier=4)
+    assert [int(c[0]) for c in cases] == [9]
+    assert _case_target(f, g, (0, 3, 9, 10), pass_=1) == 9
+
+
+def test_one_dim_troublemaker_on_saddle_connector_3d():
+    """1-dimensional troublemaker on a saddle-saddle connector (Sec. 4.4) on a 3 x 3 x 3
+    grid (id = x + 3 y + 9 z).  In f, edge {15,16} (values 22, 24) pairs with triangle
+    {15,16,25}: its extra vertex 25 (value 12) is the lowest below both ends, ahead of
+    vertex 12 (value 13, triangle {12,15,16}); the walk from a 2-saddle crosses this pair.
+    Lowering vertex 12 to 11.5 makes g pair the edge with {12,15,16}: the troublemaker is
+    the edge, and the S-pass lowers k = 25.  (Triangle {12,15,16}, paired in f with tet
+    {12,15,16,25} on an ascending path, is re-paired with the edge in g; that 2-dim
+    troublemaker names vertex 25 too.)"""
+    f = np.float32([11, 0, 9, 23, 26, 5, 17, 25, 19, 20, 18, 7, 13, 8, 14, 22, 24, 10, 3, 21, 16, 4, 6, 15,
+                    1, 12, 2])
+    g = f.copy()
+    g[12] = 11.5
+    f, g = f.reshape(3, 3, 3), g.reshape(3, 3, 3)
+    assert _pairs_dict(f)[(15, 16)] == (15, 16, 25) and _pairs_dict(g)[(15, 16)] == (12, 15, 16)
+    crossed = {(tuple(int(x) for x in r[5:9] if x >= 0), tuple(int(x) for x in r[9:13] if x >= 0))
+               for r in oracle.saddle_connectors(f) if r[4] == 1}
+    assert ((15, 16), (15, 16, 25)) in crossed
+    assert len(oracle.targets(f, g, pass_=0)[0]) == 0
+    cases, _ = oracle.targets(f, g, pass_=1, tier=4)
+    assert {int(c[0]) for c in cases} == {25}
+    assert _case_target(f, g, (15, 16, 25), pass_=1) == 25
+    assert _case_target(f, g, (12, 15, 16, 25), pass_=1) == 25
+
+
 @pytest.mark.parametrize("shape", [(6, 7), (4, 4, 4), (3, 5, 4)])
 def test_case_rules_on_random_fields(shape):
     """For every false case of every dimension: an FP case lowers the extra vertex of the
@@ -768,3 +924,173 @@ def test_gradient_depends_only_on_orders_within_two_edges():
                 tried += 1
                 changed += not np.array_equal(oracle.gradient_pairs(g.reshape(shape)), oracle.gradient_pairs(a))
     assert kept > 200 and tried > 100 and changed > 0
+
+
+# --------------------------------------------------------------------------------------
+# saddle-saddle connectors (Sec. 3.1 V-paths, Sec. 4.4): brute-force enumeration of every
+# alternating triangle -> facet edge -> paired triangle sequence from each 2-saddle
+# --------------------------------------------------------------------------------------
+
+def _facets(cell):
+    return [cell[:i] + cell[i + 1:] for i in range(len(cell))]
+
+
+def _brute_connector_paths(P, crit, saddle, limit=200000):
+    """Every V-path of a gradient (pair dict P) from 2-saddle triangle `saddle`, by plain
+    recursion without a visited set (V is acyclic, so every path ends).  A path is a list
+    of items: ("cross", e, t') for a facet edge e paired up with another triangle t',
+    ("dead", e, v) for a facet edge paired down with vertex v (the path ends there), and
+    ("saddle", e, None) for a critical facet edge (a 1-saddle: the path ends there)."""
+    paths = []
+
+    def rec(t, prefix):
+        if len(paths) > limit:
+            raise RuntimeError("too many V-paths")
+        for e in _facets(t):
+            if e in crit:
+                paths.append(prefix + [("saddle", e, None)])
+                continue
+            p = P[e]
+            if len(p) == 1:
+                paths.append(prefix + [("dead", e, p)])
+                continue
+            if p == t:           # e is the pair that brought the path into t
+                continue
+            rec(p, prefix + [("cross", e, p)])
+
+    rec(saddle, [])
+    return paths
+
+
+def _connector_fields():
+    rng = np.random.default_rng(61)
+    out = []
+    for shape in [(3, 3, 3), (4, 3, 4), (4, 4, 4), (5, 4, 3), (5, 5, 5)]:
+        out.append(("normal", rng.standard_normal(shape).astype(np.float32)))
+        out.append(("binary", rng.integers(0, 2, shape).astype(np.float32)))
+        out.append(("few_levels", rng.integers(0, 4, shape).astype(np.float32)))
+    return out
+
+
+@pytest.mark.parametrize("idx", range(15))
+def test_saddle_connectors_match_brute_force(idx):
+    """From every 2-saddle, the oracle's walk reaches exactly the 1-saddles, crosses
+    exactly the (edge, triangle) pairs and stops at exactly the dead-end edges that the
+    enumeration of every V-path of V_f from that 2-saddle does (per 2-saddle, so a walk
+    that shared visited marks between 2-saddles, crossed a pair backwards or skipped a
+    dead end would differ)."""
+    kind, f = _connector_fields()[idx]
+    nz, ny, nx = f.shape
+    P = _pairs_dict(f)
+    cells = _rows_to_sets(oracle.cells(nx, ny, nz))
+    crit = {c for c in cells if c not in P}
+    t = lambda q: tuple(int(x) for x in q if x >= 0)
+    got = {}
+    for r in oracle.saddle_connectors(f):
+        got.setdefault(t(r[0:4]), set()).add((int(r[4]), t(r[5:9]), t(r[9:13])))
+    want = {}
+    code = {"saddle": 0, "cross": 1, "dead": 2}
+    for s in sorted(c for c in crit if len(c) == 3):
+        items = set()
+        for path in _brute_connector_paths(P, crit, s):
+            for what, e, other in path:
+                items.add((code[what], e, other if other is not None else ()))
+        want[s] = items
+    assert set(got) == set(want)
+    for s in want:
+        assert got[s] == want[s], s
+    if kind == "normal" and f.size >= 64:
+        assert any(any(k == 1 for k, _, _ in v) for v in want.values())
+
+
+def _brute_s_cases(f, g):
+    """The S-pass at tier 4 restated from exhaustive path enumeration on the pair lists of
+    f and g (Sec. 4.4): along every separatrix of f, the first pair (L, U) that g's
+    gradient does not have is a troublemaker, and the vertex U \\ L is lowered.  On a
+    saddle-saddle path a dead-end edge e paired down with v in f is kept as long as g also
+    pairs e down; otherwise its f-pair (v, e) is the troublemaker.  Returns the set of
+    (target vertex, case cell)."""
+    nz, ny, nx = f.shape if f.ndim == 3 else (1,) + f.shape
+    dims = (nx, ny, nz)
+    Pf, Pg = _pairs_dict(f), _pairs_dict(g)
+    cells = _rows_to_sets(oracle.cells(*dims))
+    crit = {c for c in cells if c not in Pf}
+    top = 3 if nz > 1 else 2
+    cof = {c: [] for c in cells}
+    for U in cells:
+        for L in _facets(U):
+            if L:
+                cof[L].append(U)
+    extra = lambda U, L: (set(U) - set(L)).pop()
+    cases = set()
+
+    def first_bad(pairs):
+        for L, U in pairs:
+            if Pg.get(L) != U:
+                cases.add((extra(U, L), U))
+                return
+
+    for s in sorted(crit):
+        if len(s) == 2:                                  # descending, one per endpoint
+            for start in s:
+                pairs, u = [], (start,)
+                while u not in crit:
+                    e = Pf[u]
+                    pairs.append((u, e))
+                    u = (extra(e, u),)
+                first_bad(pairs)
+        if len(s) == top:                                # ascending, one per top cofacet
+            for beta in cof[s]:
+                pairs, b = [], beta
+                while b not in crit:
+                    a = Pf[b]
+                    pairs.append((a, b))
+                    nxt = [c for c in cof[a] if c != b]
+                    if not nxt:
+                        break
+                    b = nxt[0]
+                first_bad(pairs)
+        if top == 3 and len(s) == 3:                     # saddle-saddle, every V-path
+            for path in _brute_connector_paths(Pf, crit, s):
+                for what, e, other in path:
+                    if what == "cross" and Pg.get(e) != other:
+                        cases.add((extra(other, e), other))
+                        break
+                    if what == "dead" and len(Pg.get(e, ())) != 1:
+                        cases.add((extra(e, other), e))
+                        break
+    return cases
+
+
+@pytest.mark.parametrize("shape", [(4, 4, 4), (5, 4, 3), (3, 5, 5), (7, 9)])
+def test_s_pass_targets_match_path_enumeration(shape):
+    """On perturbed copies of random fields whose critical cells are unchanged, the
+    oracle's S-pass (tier 4) names exactly the troublemakers that exhaustive path
+    enumeration finds: the first disagreeing pair on every descending, ascending and
+    saddle-saddle path of f."""
+    rng = np.random.default_rng(67 + len(shape))
+    checked = saddle_hits = 0
+    for trial in range(6000):
+        if checked >= 12 and (saddle_hits >= 3 or len(shape) == 2):
+            break
+        if trial % 2 == 0:       # ties: a small move re-orders only equal values
+            f = rng.integers(0, 4, shape).astype(np.float32)
+            scale = 0.4
+        else:
+            f = rng.standard_normal(shape).astype(np.float32)
+            scale = 1.0
+        g = f.copy().reshape(-1)
+        for v in rng.choice(f.size, size=int(rng.integers(1, 3)), replace=False):
+            g[v] = g[v] + np.float32(rng.uniform(-scale, scale))
+        g = g.reshape(shape)
+        if len(oracle.targets(f, g, pass_=0)[0]):
+            continue                                     # the S-pass runs only after the C-loop
+        cases, _ = oracle.targets(f, g, pass_=1, tier=4)
+        got = {(int(r[0]), tuple(int(x) for x in r[1:] if x >= 0)) for r in cases}
+        want = _brute_s_cases(f, g)
+        assert got == want, (trial, got ^ want)
+        checked += bool(want)
+        saddle_hits += any(len(c) == 3 for _, c in want)
+    assert checked >= 12
+    if len(shape) == 3:
+        assert saddle_hits >= 3
