@@ -128,6 +128,11 @@ struct Ctx {
     unsigned long long *tally;       // when set: per-block (cases, live cases) in shared memory
     int mark_only;                   // add_case only sets the target's T bit (no return value
                                      // awaited); k_tlist lists the T bits afterwards
+    // verification of saddle-saddle connectors: triangles from which the walk found a
+    // troublemaker (bitset over triangle ids, plus a list of them, ss_cap entries)
+    uint32_t *ss_bad, *ss_list;
+    unsigned long long *ss_n;
+    uint32_t ss_cap;
 };
 
 // ------------------------------------------------------------------------------------
@@ -774,6 +779,15 @@ MSC_HD inline void ss_push_global(const Ctx &c, uint32_t tri, uint32_t entry)
     else a_add(&c.cnt->err, 1ull);
 }
 
+// verification: record that the walk found a troublemaker among the facets of triangle tri
+MSC_HD inline void ss_note_bad(const Ctx &c, uint32_t tri)
+{
+    if (!c.ss_bad || test_and_set(c.ss_bad, tri)) return;
+    const unsigned long long i = list_slot(c.ss_n);
+    if (i < c.ss_cap) c.ss_list[i] = tri;
+    else a_add(&c.cnt->err, 1ull);
+}
+
 // start: (triangle id = anchor * 12 + type, entry edge id = anchor * 7 + type or ~0u);
 // fresh seeds are marked visited here, spilled items were marked when first pushed
 MSC_HD inline void ss_walk(const Ctx &c, uint32_t tri0, uint32_t entry0, bool seed)
@@ -803,6 +817,7 @@ MSC_HD inline void ss_walk(const Ctx &c, uint32_t tri0, uint32_t entry0, bool se
                 if (eg != 1) {
                     Verts V = cell_verts<3>(c.G, ex, ey, ez, 1, et);
                     add_case<3>(c, V.id[lowest_of(V, c.f)], V);
+                    ss_note_bad(c, tri);
                 }
                 continue;
             }
@@ -813,6 +828,7 @@ MSC_HD inline void ss_walk(const Ctx &c, uint32_t tri0, uint32_t entry0, bool se
                 Verts V = cell_verts<3>(c.G, tx, ty, tz, 2, t2);
                 const uint32_t tv = vid(c.G, ex + T.ecof_v[et][i][0], ey + T.ecof_v[et][i][1], ez + T.ecof_v[et][i][2]);
                 add_case<3>(c, tv, V);
+                ss_note_bad(c, tri);
                 continue;
             }
             const uint32_t tri2 = vid(c.G, tx, ty, tz) * 12 + (uint32_t)t2;
@@ -823,6 +839,38 @@ MSC_HD inline void ss_walk(const Ctx &c, uint32_t tri0, uint32_t entry0, bool se
         }
     }
     count_add(&c.cnt->steps[2], nvis);
+}
+
+// verification: a triangle t' = V_f(e) reached by the walk leads to a troublemaker, so do
+// the reached triangles that cross into it: every reached triangle with facet e other than
+// t' (its crossing (e, t') is the same pair, present in g since t' was reached).  e is the
+// facet of t' opposite its f-lowest vertex.  A 2-saddle has no entry and no predecessor.
+// Newly marked predecessors are appended to out.
+MSC_HD inline void ss_back_step(const Ctx &c, uint32_t tri, uint32_t *out, unsigned long long *nout, uint32_t cap)
+{
+    const Tab<3> &T = rt_tab<3>();
+    const int tt = (int)(tri % 12);
+    int x, y, z;
+    coords(c.G, tri / 12, x, y, z);
+    if (tfield<3>(ld(c.code_f + tri / 12), tt) != 1) return;      // a 2-saddle (critical) root
+    Verts V = cell_verts<3>(c.G, x, y, z, 2, tt);
+    const int k = T.tri_opp[tt][lowest_of(V, c.f)];
+    const int ex = x + T.tfac_anc[tt][k][0], ey = y + T.tfac_anc[tt][k][1], ez = z + T.tfac_anc[tt][k][2];
+    const int et = T.tfac_type[tt][k];
+    for (int i = 0; i < T.necof[et]; i++) {
+        const int tx = ex + T.ecof_anc[et][i][0], ty = ey + T.ecof_anc[et][i][1], tz = ez + T.ecof_anc[et][i][2];
+        const int t2 = T.ecof_type[et][i];
+        const int top = T.tB[t2];
+        if (!inside(c.G, tx, ty, tz) || !inside(c.G, tx + (top & 1), ty + ((top >> 1) & 1), tz + ((top >> 2) & 1)))
+            continue;
+        const uint32_t p = vid(c.G, tx, ty, tz) * 12 + (uint32_t)t2;
+        if (p == tri) continue;
+        if (!((c.vis_tri[p >> 5] >> (p & 31)) & 1u)) continue;     // not reached by the walk
+        if (test_and_set(c.ss_bad, p)) continue;
+        const unsigned long long j = list_slot(nout);
+        if (j < cap) out[j] = p;
+        else a_add(&c.cnt->err, 1ull);
+    }
 }
 
 // ------------------------------------------------------------------------------------

@@ -1170,6 +1170,22 @@ __global__ void k_ss_spill(Ctx c, const uint32_t *items, uint32_t n)
     GRID_STRIDE(i, n) ss_walk(c, items[2 * i], items[2 * i + 1], false);
 }
 
+// verification of saddle-saddle connectors: one backward step from each listed triangle
+__global__ void k_ss_back(Ctx c, const uint32_t *in, uint32_t n, uint32_t *out, unsigned long long *nout, uint32_t cap)
+{
+    GRID_STRIDE(i, n) ss_back_step(c, in[i], out, nout, cap);
+}
+
+// 2-saddles whose connectors reach a troublemaker, counted into *n
+__global__ void k_ss_count(Ctx c, const uint32_t *seeds, uint32_t n, unsigned long long *cnt)
+{
+    GRID_STRIDE(i, n)
+    {
+        const uint32_t t = seeds[i];
+        count_add(cnt, (c.ss_bad[t >> 5] >> (t & 31)) & 1u);
+    }
+}
+
 template <int D> __global__ void __launch_bounds__(TPB) k_node_init(Ctx c)
 {
     GRID_STRIDE(p, c.G.n) node_bits<D>(c, (uint32_t)p, true);
@@ -2370,9 +2386,18 @@ template <int D> msc_status verify_impl(msc_handle *h, const float *gdev, float 
             DevBuf<uint8_t> st;
             CK(st.alloc(h->G.n));
             CK(cudaMemsetAsync(st.p, 0, h->G.n, s));
+            // per 2-saddle: the walk marks the triangles whose facets hold a troublemaker,
+            // then backward steps mark every reached triangle that leads to one
+            DevBuf<uint32_t> bad, bl0, bl1;
+            DevBuf<unsigned long long> bn;
+            const uint32_t bcap = (uint32_t)h->G.n + 1;
+            CK(bad.alloc(words(h->G.n * 12))); CK(bl0.alloc(bcap)); CK(bl1.alloc(bcap)); CK(bn.alloc(4));
+            CK(cudaMemsetAsync(bad.p, 0, bad.n * 4, s));
+            CK(cudaMemsetAsync(bn.p, 0, 4 * sizeof(unsigned long long), s));
             Ctx v = c;
             v.Tlist = tl.p; v.Tbits = tb.p; v.Xlist = xl.p; v.Xbits = xb.p; v.state = st.p;
             v.exact_fallback = 0;
+            v.ss_bad = bad.p; v.ss_list = bl0.p; v.ss_n = bn.p; v.ss_cap = bcap;
             CK(cudaMemsetAsync(h->cnt.p, 0, sizeof(Counters), s));
             CK(cudaMemsetAsync(h->vis_tri.p, 0, h->vis_tri.n * 4, s));
             v.ovf_out = h->ovf0.p;
@@ -2391,7 +2416,30 @@ template <int D> msc_status verify_impl(msc_handle *h, const float *gdev, float 
                 CK(cudaGetLastError());
                 std::swap(in, o2);
             }
-            out->sep_mismatch[2] = hc.ncase;
+            uint32_t *bin = bl0.p, *bout = bl1.p;
+            for (int side = 0;; side ^= 1) {
+                unsigned long long nb[4];
+                CK(cudaMemcpyAsync(nb, bn.p, sizeof nb, cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                unsigned long long err = 0;
+                CK(cudaMemcpyAsync(&err, &h->cnt.p->err, sizeof err, cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                if (err) return fail(MSC_ERR_OOM, "saddle-saddle verification list overflow");
+                const unsigned long long m = nb[side];
+                if (m == 0) break;
+                CK(cudaMemsetAsync(bn.p + (side ^ 1), 0, sizeof(unsigned long long), s));
+                KL(h, MSC_K_OTHER, s, k_ss_back<<<grid_occ((const void *)k_ss_back, m), TPB, 0, s>>>(v, bin, (uint32_t)m, bout, bn.p + (side ^ 1), bcap));
+                CK(cudaGetLastError());
+                CK(cudaMemsetAsync(bn.p + side, 0, sizeof(unsigned long long), s));
+                std::swap(bin, bout);
+            }
+            CK(cudaMemsetAsync(bn.p + 2, 0, sizeof(unsigned long long), s));
+            if (h->n_ss) KL(h, MSC_K_OTHER, s, k_ss_count<<<grid_occ((const void *)k_ss_count, h->n_ss), TPB, 0, s>>>(v, h->seeds_ss.p, h->n_ss, bn.p + 2));
+            CK(cudaGetLastError());
+            unsigned long long nbad = 0;
+            CK(cudaMemcpyAsync(&nbad, bn.p + 2, sizeof nbad, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            out->sep_mismatch[2] = nbad;
         }
     }
     unsigned long long sep = 0;
