@@ -27,6 +27,16 @@ def _load():
     return _lib
 
 
+def set_threads(n):
+    """Number of threads the oracle's parallel loops use (results do not depend on it)."""
+    _load().orc_set_threads(int(n))
+
+
+def threads():
+    """Number of threads the oracle's parallel loops use."""
+    return int(_load().orc_threads())
+
+
 def _p(a):
     return a.ctypes.data_as(ctypes.c_void_p)
 

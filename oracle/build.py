@@ -2,7 +2,8 @@
 
 The oracle is plain C built with IEEE semantics kept intact: no fast-math and no
 floating-point contraction, so that every float operation is one correctly rounded
-IEEE operation, exactly as the edit arithmetic (Eq. 2) is written.
+IEEE operation, exactly as the edit arithmetic (Eq. 2) is written.  Its per-cell loops
+are OpenMP loops (-fopenmp); their results do not depend on the number of threads.
 """
 import os
 import subprocess
@@ -19,7 +20,7 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
         return LIB
     tmp = LIB + ".tmp.%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
            "-fno-fast-math", "-Wall", "-Wno-unused-function", SRC, "-o", tmp, "-lm"]
     subprocess.check_call(cmd)
     os.replace(tmp, LIB)

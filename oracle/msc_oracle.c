@@ -36,6 +36,12 @@
  *    extremum connectivity); T4 compares every pair along every separatrix, including
  *    saddle-saddle connectors in 3D.
  *
+ * Threads: the per-cell loops (pairing within one dimension, the C-pass, the separatrices of
+ * the S-pass) run as OpenMP loops over cells or paths.  Within a dimension each cell's pairing
+ * reads only pairings of the dimension below, and the target sets are sets, so every result
+ * is the same for any number of threads (a CPU test checks 1 thread against several); a
+ * pass that records its case list or walk (test exports) runs on one thread.
+ *
  * Parity unpinned: exact iteration counts and edit sequences have no printed worked loop;
  * they are pinned only through the invariants (monotone edits, bound, termination, final
  * MSC equality) that the tests check.
@@ -44,6 +50,9 @@
 #include <stdlib.h>
 #include <string.h>
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef int64_t i64;
 
@@ -102,6 +111,13 @@ static int grid_init(grid_t *g, int nx, int ny, int nz)
 
 static void vcoord(const grid_t *g, i64 v, int *x, int *y, int *z)
 {
+    if (g->n <= (i64)UINT32_MAX) {        /* the same quotients in 32-bit arithmetic */
+        uint32_t u = (uint32_t)v, t = u / (uint32_t)g->nx;
+        *x = (int)(u - t * (uint32_t)g->nx);
+        *y = (int)(t % (uint32_t)g->ny);
+        *z = (int)(t / (uint32_t)g->ny);
+        return;
+    }
     *x = (int)(v % g->nx);
     *y = (int)((v / g->nx) % g->ny);
     *z = (int)(v / ((i64)g->nx * g->ny));
@@ -126,6 +142,15 @@ static int adjacent(const grid_t *g, i64 u, i64 v)
     return pos || neg;
 }
 
+/* the same test as adjacent(), on the coordinate difference itself */
+static int adjacent_offset(int dx, int dy, int dz)
+{
+    if (dx == 0 && dy == 0 && dz == 0) return 0;
+    int pos = dx >= 0 && dy >= 0 && dz >= 0;
+    int neg = dx <= 0 && dy <= 0 && dz <= 0;
+    return pos || neg;
+}
+
 static int neighbours(const grid_t *g, i64 v, i64 out[26])
 {
     int x, y, z, n = 0;
@@ -133,8 +158,9 @@ static int neighbours(const grid_t *g, i64 v, i64 out[26])
     for (int dz = -1; dz <= 1; dz++)
         for (int dy = -1; dy <= 1; dy++)
             for (int dx = -1; dx <= 1; dx++) {
+                if (!adjacent_offset(dx, dy, dz)) continue;
                 i64 w = vindex(g, x + dx, y + dy, z + dz);
-                if (w >= 0 && adjacent(g, v, w)) out[n++] = w;
+                if (w >= 0) out[n++] = w;
             }
     return n;
 }
@@ -261,6 +287,7 @@ static i64 lowest_vertex(const grid_t *g, i64 id, const float *f)
 static void pairing_init(const grid_t *g, i64 *pr)
 {
     i64 ncell = g->n * g->K;
+#pragma omp parallel for schedule(static)
     for (i64 id = 0; id < ncell; id++) pr[id] = cell_exists(g, id) ? -1 : -2;
 }
 
@@ -272,6 +299,10 @@ static void gradient_rules(const grid_t *g, const float *f, i64 *pr)
 {
     pairing_init(g, pr);
     for (int d = 0; d < g->dim; d++) {
+        /* cells of dimension d decide independently: each reads pr of its own (set by the
+         * pass of dimension d - 1) and writes pr of itself and of one cofacet, which no other
+         * cell of dimension d takes (the pairs form a matching) */
+#pragma omp parallel for schedule(dynamic, 4096)
         for (i64 id = 0; id < g->n * g->K; id++) {
             if (cell_dim(g, id) != d || pr[id] != -1) continue;
             i64 v[5], nb[26];
@@ -436,23 +467,34 @@ static int stuck(const loopctx *c, i64 t) { return c->state[t] == ST_FLOOR || c-
 
 /* one false case: lower vertex t (set semantics, Sec. 4.8.3 read as "each vertex edited at
  * most once per iteration"); a stuck case restores the closed 1-rings of its cell to f. */
+static void set_mark(uint8_t *m, i64 i)
+{
+#pragma omp atomic write
+    m[i] = 1;
+}
+
 static void add_case(loopctx *c, i64 t, i64 case_cell)
 {
-    c->markT[t] = 1;
+    set_mark(c->markT, t);
+#pragma omp atomic
     c->ncase++;
     if (c->rec && c->rec_n < c->rec_cap) {
         c->rec[2 * c->rec_n] = t;
         c->rec[2 * c->rec_n + 1] = case_cell;
         c->rec_n++;
     }
-    if (!stuck(c, t)) { c->nlive++; return; }
+    if (!stuck(c, t)) {
+#pragma omp atomic
+        c->nlive++;
+        return;
+    }
     if (!c->exact_fallback) return;
     i64 v[4], nb[26];
     int nv = cell_verts(c->g, case_cell, v);
     for (int i = 0; i < nv; i++) {
-        c->markX[v[i]] = 1;
+        set_mark(c->markX, v[i]);
         int nn = neighbours(c->g, v[i], nb);
-        for (int j = 0; j < nn; j++) c->markX[nb[j]] = 1;
+        for (int j = 0; j < nn; j++) set_mark(c->markX, nb[j]);
     }
 }
 
@@ -466,6 +508,7 @@ static void add_case(loopctx *c, i64 t, i64 case_cell)
 static void c_targets(loopctx *c, int tier)
 {
     const grid_t *g = c->g;
+#pragma omp parallel for schedule(dynamic, 4096) if (!c->rec)
     for (i64 id = 0; id < g->n * g->K; id++) {
         if (c->prf[id] == -2) continue;
         int d = cell_dim(g, id);
@@ -517,14 +560,30 @@ static int check_path(loopctx *c, int tier, const pathbuf *p, i64 fterm, i64 gte
  * V_g are crossed; the first disagreeing pairs reached are the troublemakers.  A dead-end
  * edge that V_g pairs upward is repaired through its f-pair (v, e).  Returns the number of
  * troublemakers found. */
-static i64 saddle_saddle(loopctx *c, i64 t0, i64 *stamp, i64 stampval, i64 *queue)
+typedef struct { i64 *v; i64 cap; } i64queue;
+
+/* make room for entries [0, need) of a growable queue; -1 when out of memory */
+static int q_reserve(i64queue *q, i64 need)
+{
+    if (need <= q->cap) return 0;
+    i64 nc = q->cap ? q->cap : 1024;
+    while (nc < need) nc *= 2;
+    i64 *nv = realloc(q->v, nc * sizeof(i64));
+    if (!nv) return -1;
+    q->v = nv;
+    q->cap = nc;
+    return 0;
+}
+
+static i64 saddle_saddle(loopctx *c, i64 t0, i64 *stamp, i64 stampval, i64queue *Q)
 {
     const grid_t *g = c->g;
     i64 qh = 0, qt = 0, found = 0;
-    queue[qt] = t0; queue[qt + 1] = -1; qt += 2;
+    if (q_reserve(Q, 2)) return -1;
+    Q->v[qt] = t0; Q->v[qt + 1] = -1; qt += 2;
     stamp[t0] = stampval;
     while (qh < qt) {
-        i64 t = queue[qh], entry = queue[qh + 1];
+        i64 t = Q->v[qh], entry = Q->v[qh + 1];
         qh += 2;
         i64 fc[4];
         int n = facets(g, t, fc);
@@ -551,60 +610,101 @@ static i64 saddle_saddle(loopctx *c, i64 t0, i64 *stamp, i64 stampval, i64 *queu
             }
             if (stamp[pe] != stampval) {
                 stamp[pe] = stampval;
-                queue[qt] = pe; queue[qt + 1] = e; qt += 2;
+                if (q_reserve(Q, qt + 2)) return -1;
+                Q->v[qt] = pe; Q->v[qt + 1] = e; qt += 2;
             }
         }
     }
     return found;
 }
 
+static void report_add(i64 *report, int k, i64 v)
+{
+    if (!report || !v) return;
+#pragma omp atomic
+    report[k] += v;
+}
+
 static int s_targets(loopctx *c, int tier, i64 *report)
 {
     const grid_t *g = c->g;
     i64 ncell = g->n * g->K;
-    pathbuf pb = {0};
+    int err = ORC_OK;
+    const int serial = c->rec != NULL;   /* the recorded case list keeps the serial order */
     /* descending separatrices of every 1-saddle edge, one per endpoint */
-    for (i64 id = 0; id < ncell; id++) {
-        if (cell_dim(g, id) != 1 || c->prf[id] != -1) continue;
-        i64 v[4];
-        cell_verts(g, id, v);
-        for (int s = 0; s < 2; s++) {
-            pb.n = 0;
-            i64 ft = trace_desc(g, c->prf, v[s], &pb);
-            i64 gt = trace_desc(g, c->prg, v[s], NULL);
-            if (ft < -1 || gt < -1) { free(pb.L); free(pb.U); return ORC_ERR_INTERNAL; }
-            int bad = check_path(c, tier, &pb, ft, gt);
-            if (report) { report[0] += bad; report[3] += ft != gt; }
-        }
-    }
-    /* ascending separatrices of every (D-1)-saddle, one per top-dimensional cofacet */
-    for (i64 id = 0; id < ncell; id++) {
-        if (cell_dim(g, id) != g->dim - 1 || c->prf[id] != -1) continue;
-        i64 cf[16];
-        int n = cofacets(g, id, cf);
-        for (int i = 0; i < n; i++) {
-            pb.n = 0;
-            i64 ft = trace_asc(g, c->prf, cf[i], &pb);
-            i64 gt = trace_asc(g, c->prg, cf[i], NULL);
-            if (ft < -1 || gt < -1) { free(pb.L); free(pb.U); return ORC_ERR_INTERNAL; }
-            int bad = check_path(c, tier, &pb, ft, gt);
-            if (report) { report[1] += bad; report[4] += ft != gt; }
-        }
-    }
-    free(pb.L); free(pb.U);
-    if (g->dim == 3 && tier >= 4) {
-        i64 *stamp = malloc(ncell * sizeof(i64));
-        i64 *queue = malloc(2 * ncell * sizeof(i64) + 16);
-        if (!stamp || !queue) { free(stamp); free(queue); return ORC_ERR_OOM; }
-        for (i64 i = 0; i < ncell; i++) stamp[i] = -1;
+#pragma omp parallel if (!serial)
+    {
+        pathbuf pb = {0};
+#pragma omp for schedule(dynamic, 256)
         for (i64 id = 0; id < ncell; id++) {
-            if (cell_dim(g, id) != 2 || c->prf[id] != -1) continue;
-            i64 found = saddle_saddle(c, id, stamp, id, queue);
-            if (report) report[2] += found > 0;
+            if (cell_dim(g, id) != 1 || c->prf[id] != -1) continue;
+            i64 v[4];
+            cell_verts(g, id, v);
+            for (int s = 0; s < 2; s++) {
+                pb.n = 0;
+                i64 ft = trace_desc(g, c->prf, v[s], &pb);
+                i64 gt = trace_desc(g, c->prg, v[s], NULL);
+                if (ft < -1 || gt < -1) {
+#pragma omp atomic write
+                    err = ORC_ERR_INTERNAL;
+                    continue;
+                }
+                int bad = check_path(c, tier, &pb, ft, gt);
+                report_add(report, 0, bad);
+                report_add(report, 3, ft != gt);
+            }
         }
-        free(stamp); free(queue);
+        /* ascending separatrices of every (D-1)-saddle, one per top-dimensional cofacet */
+#pragma omp for schedule(dynamic, 256)
+        for (i64 id = 0; id < ncell; id++) {
+            if (cell_dim(g, id) != g->dim - 1 || c->prf[id] != -1) continue;
+            i64 cf[16];
+            int n = cofacets(g, id, cf);
+            for (int i = 0; i < n; i++) {
+                pb.n = 0;
+                i64 ft = trace_asc(g, c->prf, cf[i], &pb);
+                i64 gt = trace_asc(g, c->prg, cf[i], NULL);
+                if (ft < -1 || gt < -1) {
+#pragma omp atomic write
+                    err = ORC_ERR_INTERNAL;
+                    continue;
+                }
+                int bad = check_path(c, tier, &pb, ft, gt);
+                report_add(report, 1, bad);
+                report_add(report, 4, ft != gt);
+            }
+        }
+        free(pb.L); free(pb.U);
     }
-    return ORC_OK;
+    if (err) return err;
+    if (g->dim == 3 && tier >= 4) {
+        /* each 2-saddle walks with its own visited marks: one stamp array per thread,
+         * stamped with the 2-saddle's id */
+#pragma omp parallel if (!serial && !c->walk)
+        {
+            i64 *stamp = malloc(ncell * sizeof(i64));
+            i64queue q = {0};
+            if (!stamp) {
+#pragma omp atomic write
+                err = ORC_ERR_OOM;
+            } else {
+                for (i64 i = 0; i < ncell; i++) stamp[i] = -1;
+            }
+#pragma omp for schedule(dynamic, 64)
+            for (i64 id = 0; id < ncell; id++) {
+                if (!stamp || cell_dim(g, id) != 2 || c->prf[id] != -1) continue;
+                i64 found = saddle_saddle(c, id, stamp, id, &q);
+                if (found < 0) {
+#pragma omp atomic write
+                    err = ORC_ERR_OOM;
+                    continue;
+                }
+                report_add(report, 2, found > 0);
+            }
+            free(stamp); free(q.v);
+        }
+    }
+    return err;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -823,15 +923,15 @@ int orc_saddle_connectors(const float *field, int nx, int ny, int nz, int64_t *o
     c.walk = malloc(4 * (cap > 0 ? cap : 1) * sizeof(i64));
     c.walk_cap = cap;
     i64 *stamp = malloc(ncell * sizeof(i64));
-    i64 *queue = malloc(2 * ncell * sizeof(i64) + 16);
+    i64queue q = {0};
     int rc = ORC_OK;
-    if (!c.prf || !c.markT || !c.markX || !c.state || !c.walk || !stamp || !queue) { rc = ORC_ERR_OOM; goto done; }
+    if (!c.prf || !c.markT || !c.markX || !c.state || !c.walk || !stamp) { rc = ORC_ERR_OOM; goto done; }
     gradient_rules(&g, field, c.prf);
     c.prg = c.prf;
     for (i64 i = 0; i < ncell; i++) stamp[i] = -1;
     for (i64 id = 0; id < ncell; id++) {
         if (cell_dim(&g, id) != 2 || c.prf[id] != -1) continue;
-        if (saddle_saddle(&c, id, stamp, id, queue) != 0) { rc = ORC_ERR_INTERNAL; goto done; }
+        if (saddle_saddle(&c, id, stamp, id, &q) != 0) { rc = ORC_ERR_INTERNAL; goto done; }
     }
     for (i64 i = 0; i < c.walk_n && i < cap; i++) {
         const i64 *r = c.walk + 4 * i;
@@ -844,7 +944,7 @@ int orc_saddle_connectors(const float *field, int nx, int ny, int nz, int64_t *o
     }
     *n_out = c.walk_n;
 done:
-    free(c.prf); free(c.markT); free(c.markX); free(c.state); free(c.walk); free(stamp); free(queue);
+    free(c.prf); free(c.markT); free(c.markX); free(c.state); free(c.walk); free(stamp); free(q.v);
     return rc;
 }
 
@@ -1129,4 +1229,23 @@ int orc_unpack_edits(const uint8_t *buf, int64_t size, uint8_t *q_map, int64_t *
     if (k != nl) return ORC_ERR_ARG;
     memcpy(lossless_val, bits + ((n + 7) / 8) * b, (size_t)nl * 4);
     return ORC_OK;
+}
+
+/* threads used by the oracle's parallel loops: set (n >= 1) and query */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }

@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <condition_variable>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -1608,6 +1609,196 @@ void host_trim()
     pc.idle_bytes = 0;
 }
 
+// ------------------------------------------------------------------------------------
+// copies between pageable host memory and the device
+// ------------------------------------------------------------------------------------
+// A cudaMemcpy from or to pageable host memory runs at a few GB/s.  The library instead moves
+// such data through page-locked staging chunks: host threads copy one chunk between the
+// caller's memory and a staging buffer while the copy engine moves another between the
+// staging buffer and the device.
+
+// A fixed pool of host threads that copy disjoint parts of one buffer.
+class HostCopyPool {
+  public:
+    static HostCopyPool &get()
+    {
+        static HostCopyPool pool;
+        return pool;
+    }
+    // dst[0, n) = src[0, n), split over the pool's threads and the caller
+    void copy(void *dst, const void *src, size_t n)
+    {
+        constexpr size_t PART = 1u << 20;
+        const size_t parts = (n + PART - 1) / PART;
+        if (workers_.empty() || parts < 2) {
+            memcpy(dst, src, n);
+            return;
+        }
+        std::lock_guard<std::mutex> one(job_mu_);     // one job at a time
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            dst_ = (char *)dst;
+            src_ = (const char *)src;
+            n_ = n;
+            part_ = PART;
+            parts_ = parts;
+            next_.store(0);
+            left_.store(parts);
+            gen_++;
+        }
+        cv_.notify_all();
+        run_parts();
+        std::unique_lock<std::mutex> lk(mu_);
+        done_cv_.wait(lk, [&] { return left_.load() == 0; });
+    }
+    ~HostCopyPool()
+    {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        for (auto &t : workers_) t.join();
+    }
+
+  private:
+    HostCopyPool()
+    {
+        const unsigned hc = std::thread::hardware_concurrency();
+        const unsigned n = hc > 2 ? std::min(7u, hc - 1) : 0;
+        for (unsigned i = 0; i < n; i++) workers_.emplace_back([this] { loop(); });
+    }
+    void run_parts()
+    {
+        for (;;) {
+            const size_t i = next_.fetch_add(1);
+            if (i >= parts_) return;
+            const size_t off = i * part_, len = std::min(part_, n_ - off);
+            memcpy(dst_ + off, src_ + off, len);
+            if (left_.fetch_sub(1) == 1) {
+                std::lock_guard<std::mutex> lk(mu_);
+                done_cv_.notify_all();
+            }
+        }
+    }
+    void loop()
+    {
+        uint64_t seen = 0;
+        for (;;) {
+            {
+                std::unique_lock<std::mutex> lk(mu_);
+                cv_.wait(lk, [&] { return stop_ || gen_ != seen; });
+                if (stop_) return;
+                seen = gen_;
+            }
+            run_parts();
+        }
+    }
+    std::vector<std::thread> workers_;
+    std::mutex job_mu_, mu_;
+    std::condition_variable cv_, done_cv_;
+    char *dst_ = nullptr;
+    const char *src_ = nullptr;
+    size_t n_ = 0, part_ = 1, parts_ = 0;
+    std::atomic<size_t> next_{0}, left_{0};
+    uint64_t gen_ = 0;
+    bool stop_ = false;
+};
+
+enum class MemKind { Device, PinnedHost, PageableHost };
+
+MemKind mem_kind(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return MemKind::PageableHost;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return MemKind::Device;
+    if (a.type == cudaMemoryTypeHost) return MemKind::PinnedHost;
+    return MemKind::PageableHost;
+}
+
+constexpr size_t STAGE_CHUNK = 32u << 20;   // bytes per staging chunk
+constexpr int STAGE_BUFS = 3;               // chunks in flight
+
+struct Staging {
+    void *buf[STAGE_BUFS] = {};
+    cudaEvent_t ev[STAGE_BUFS] = {};
+    bool pinned_ok = true;
+    ~Staging()
+    {
+        for (int i = 0; i < STAGE_BUFS; i++) {
+            if (ev[i]) { cudaEventSynchronize(ev[i]); cudaEventDestroy(ev[i]); }
+            host_give(buf[i]);
+        }
+        cudaGetLastError();
+    }
+    cudaError_t init(size_t chunk)
+    {
+        for (int i = 0; i < STAGE_BUFS; i++) {
+            buf[i] = host_take(chunk);
+            if (!buf[i]) return cudaErrorMemoryAllocation;
+            cudaError_t e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+};
+
+// n bytes from src (host or device) to device memory dst, ordered on stream s.  From pageable
+// host memory the call returns once src may be reused (every chunk has been staged).
+cudaError_t copy_to_device(void *dst, const void *src, size_t n, cudaStream_t s)
+{
+    const MemKind k = mem_kind(src);
+    if (k == MemKind::Device) return cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToDevice, s);
+    if (k == MemKind::PinnedHost || n <= STAGE_CHUNK) return cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, s);
+    Staging st;
+    cudaError_t e = st.init(STAGE_CHUNK);
+    if (e != cudaSuccess) return e;
+    HostCopyPool &pool = HostCopyPool::get();
+    for (size_t off = 0, i = 0; off < n; off += STAGE_CHUNK, i++) {
+        const int b = (int)(i % STAGE_BUFS);
+        const size_t len = std::min(STAGE_CHUNK, n - off);
+        if ((e = cudaEventSynchronize(st.ev[b])) != cudaSuccess) return e;    // its last copy is done
+        pool.copy(st.buf[b], (const char *)src + off, len);
+        if ((e = cudaMemcpyAsync((char *)dst + off, st.buf[b], len, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(st.ev[b], s)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// n bytes from device memory src to dst (host or device), ordered on stream s.  To pageable
+// host memory the call waits for the copy and returns when dst holds the data.
+cudaError_t copy_from_device(void *dst, const void *src, size_t n, cudaStream_t s)
+{
+    const MemKind k = mem_kind(dst);
+    if (k == MemKind::Device) return cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToDevice, s);
+    if (k == MemKind::PinnedHost || n <= STAGE_CHUNK) return cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, s);
+    Staging st;
+    cudaError_t e = st.init(STAGE_CHUNK);
+    if (e != cudaSuccess) return e;
+    HostCopyPool &pool = HostCopyPool::get();
+    const size_t nchunk = (n + STAGE_CHUNK - 1) / STAGE_CHUNK;
+    auto drain = [&](size_t j) -> cudaError_t {    // chunk j has been queued: move it out
+        const int b = (int)(j % STAGE_BUFS);
+        cudaError_t r = cudaEventSynchronize(st.ev[b]);
+        if (r != cudaSuccess) return r;
+        pool.copy((char *)dst + j * STAGE_CHUNK, st.buf[b], std::min(STAGE_CHUNK, n - j * STAGE_CHUNK));
+        return cudaSuccess;
+    };
+    for (size_t i = 0; i < nchunk; i++) {
+        const int b = (int)(i % STAGE_BUFS);
+        if (i >= (size_t)STAGE_BUFS && (e = drain(i - STAGE_BUFS)) != cudaSuccess) return e;
+        const size_t off = i * STAGE_CHUNK, len = std::min(STAGE_CHUNK, n - off);
+        if ((e = cudaMemcpyAsync(st.buf[b], (const char *)src + off, len, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(st.ev[b], s)) != cudaSuccess) return e;
+    }
+    for (size_t j = nchunk > (size_t)STAGE_BUFS ? nchunk - STAGE_BUFS : 0; j < nchunk; j++)
+        if ((e = drain(j)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
 // The library's own stream-ordered memory pool on each device.  Device memory that a handle
 // frees stays in the pool (release threshold: unlimited) for the next handle, so a sequence
 // of prepare / fix / destroy calls does not map and unmap its working set every time;
@@ -1712,7 +1903,7 @@ msc_status upload_field(msc_handle *h, const float *src, size_t n, float *dst, u
                         const char *what)
 {
     if (!src) return fail(MSC_ERR_INVALID_ARG, "%s is NULL", what);
-    CK(cudaMemcpyAsync(dst, src, n * sizeof(float), is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    CK(copy_to_device(dst, src, n * sizeof(float), s));
     CK(cudaMemsetAsync(bad_dev, 0, sizeof(unsigned long long), s));
     KL(h, MSC_K_OTHER, s, k_count_nonfinite<<<grid_occ((const void *)k_count_nonfinite, n), TPB, 0, s>>>(dst, (uint32_t)n, bad_dev));
     CK(cudaGetLastError());
@@ -2466,7 +2657,7 @@ msc_status device_input(const float *src, size_t n, DevInput &d, cudaStream_t s,
     if (!src) return fail(MSC_ERR_INVALID_ARG, "%s is NULL", what);
     if (is_device_ptr(src)) { d.p = src; return MSC_OK; }
     CK(d.own.alloc(n));
-    CK(cudaMemcpyAsync(d.own.p, src, n * sizeof(float), cudaMemcpyHostToDevice, s));
+    CK(copy_to_device(d.own.p, src, n * sizeof(float), s));
     d.p = d.own.p;
     return MSC_OK;
 }
@@ -2756,7 +2947,7 @@ msc_status msc_fix(msc_handle *h, const float *f_hat, float xi, const msc_option
     msc_status st = h->D == 3 ? fix_loop<3>(h, xi, o, s, R) : fix_loop<2>(h, xi, o, s, R);
     if (st != MSC_OK) return st;
     CK(cudaEventRecord(h->ev1, s));
-    CK(cudaMemcpyAsync(g_out, h->g.p, (size_t)h->G.n * 4, is_device_ptr(g_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    CK(copy_from_device(g_out, h->g.p, (size_t)h->G.n * 4, s));
     CKS(write_edits(h, xi, o.q_max, s, out));
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
@@ -2801,7 +2992,7 @@ msc_status msc_apply_edits(const float *f_hat, int nx, int ny, int nz, float xi,
     k_apply_q<<<grid_occ((const void *)k_apply_q, n), TPB, 0, s>>>(fh.p, qm.p, n, xi / (float)(1 << q_max), g.p);
     if (e->n_lossless) k_apply_lossless<<<grid_occ((const void *)k_apply_lossless, e->n_lossless), TPB, 0, s>>>(li.p, lv.p, e->n_lossless, g.p);
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(g_out, g.p, (size_t)n * 4, is_device_ptr(g_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    CK(copy_from_device(g_out, g.p, (size_t)n * 4, s));
     CK(cudaStreamSynchronize(s));
     return MSC_OK;
 }

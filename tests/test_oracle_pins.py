@@ -1094,3 +1094,28 @@ def test_s_pass_targets_match_path_enumeration(shape):
     assert checked >= 12
     if len(shape) == 3:
         assert saddle_hits >= 3
+
+
+# --------------------------------------------------------------------------------------
+# the oracle's parallel loops: results independent of the number of threads
+# --------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name,kw", [("kolmogorov3d", dict(size=14, rel=1e-3)),
+                                     ("multiscale2d", dict(size=(40, 72), rel=3e-3))])
+def test_results_do_not_depend_on_threads(name, kw):
+    f, fh, xi, _ = synth.config_case(name, **kw)
+    n0 = oracle.threads()
+    try:
+        oracle.set_threads(1)
+        one = oracle.fix(f, fh, xi, tier=4)
+        vone = oracle.verify(f, np.clip(fh, f - xi, f + xi).astype(np.float32))
+        oracle.set_threads(max(4, n0))
+        many = oracle.fix(f, fh, xi, tier=4)
+        vmany = oracle.verify(f, np.clip(fh, f - xi, f + xi).astype(np.float32))
+    finally:
+        oracle.set_threads(n0)
+    assert one["status"] == many["status"] == 0
+    assert np.array_equal(one["g"].view(np.uint32), many["g"].view(np.uint32))
+    assert np.array_equal(one["state"], many["state"])
+    assert np.array_equal(one["trace"], many["trace"])
+    assert vone == vmany
