@@ -128,6 +128,30 @@ def test_small_rounds_run_in_the_round_kernel(lib):
     assert st["rounds"]["items"] >= ed["n_iters_c"] // 2
 
 
+# Larger cases, at the default round threshold: their first rounds edit 8192 vertices or
+# more, so the loop takes the captured-graph rounds and then hands over to the persistent
+# round kernel by itself; grids span many tiles, multi-wave launches and many listed
+# 1024-anchor C-blocks, and separatrices cross many tiles.
+LARGE_CASES = [
+    ("kolmogorov3d", dict(size=64, rel=1e-4), 4, True),
+    ("kolmogorov3d", dict(size=64, rel=1e-3), 4, True),
+    ("kolmogorov3d", dict(size=48, rel=1e-3), 3, False),
+    ("multiscale2d", dict(size=(512, 1024), rel=1e-3), 3, True),
+    ("multiscale2d", dict(size=(512, 1024), rel=1e-2), 4, True),
+]
+
+
+@pytest.mark.parametrize("idx", range(len(LARGE_CASES)))
+def test_fix_loop_matches_oracle_large(lib, idx):
+    name, kw, tier, big_rounds = LARGE_CASES[idx]
+    f, fh, xi, _ = synth.config_case(name, **kw)
+    g, ed = _check_fix(lib, f, fh, xi, tier)
+    tr = ed["trace"]
+    if big_rounds:
+        assert int((tr[:, 1] + tr[:, 2] >= 8192).sum()) >= 3
+    assert ed["n_iters_c"] > 100
+
+
 @pytest.mark.parametrize("q_max", [1, 3, 7])
 def test_fix_q_max_range(lib, q_max):
     f, fh, xi, _ = synth.config_case("gauss2d", seed=4, size=(30, 33), rel=1e-2)
