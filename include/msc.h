@@ -44,7 +44,8 @@ typedef enum {
     MSC_ERR_DEVICE_TIMEOUT = 5,  /* a bounded device-side wait gave up */
     MSC_ERR_STALLED = 6,         /* every false case targets a vertex that cannot move and
                                     exact_fallback is off */
-    MSC_ERR_NO_DEVICE = 7        /* no CUDA device, or the library was not built for it */
+    MSC_ERR_NO_DEVICE = 7,       /* no CUDA device, or the library was not built for it */
+    MSC_ERR_CANCELLED = 8        /* a serving job cancelled by msc_server_cancel */
 } msc_status;
 
 /* per-vertex edit states (the value of msc_edits.q_map[v] is derived from these) */
@@ -289,6 +290,14 @@ uint64_t msc_device_bytes(int nx, int ny, int nz);
  * work.  Handles and edit records that are still alive keep their memory. */
 msc_status msc_release_cached_memory(void);
 
+/* Fault injection for tests (not part of the method; off by default).  After `after`
+ * further device allocations succeed, the next `count` device allocations of the library
+ * fail as if the device were out of memory (the call that needed them returns MSC_ERR_OOM
+ * and frees what it had allocated); later allocations succeed again.  The failure is made
+ * on the host: no device call fails and the device is not touched.  count = 0 turns the
+ * injection off.  Process-wide; returns the number of failures injected so far. */
+uint64_t msc_inject_alloc_failures(uint64_t after, uint64_t count);
+
 /* Self-test of the bounded waits (not part of the method).  The persistent round kernel
  * separates its phases with a grid barrier whose wait gives up after 2 s of device time,
  * records MSC_ERR_DEVICE_TIMEOUT and ends the kernel, so that a block that never arrives
@@ -351,6 +360,13 @@ msc_status msc_server_submit(msc_server *srv, const float *f, const float *f_hat
  * (free with msc_free_edits; NULL to discard) and *info its record (may be NULL).
  * Returns the job's status; MSC_ERR_INVALID_ARG for an unknown ticket. */
 msc_status msc_server_wait(msc_server *srv, uint64_t ticket, msc_edits *out, msc_job_info *info);
+
+/* Cancel a job.  A queued job is taken off the queue at once; a running job stops at the
+ * next point where its fix loop returns to the host (between round launches), frees its
+ * state and ends.  Either way msc_server_wait then returns MSC_ERR_CANCELLED for it (a
+ * running job that finishes before it reaches such a point keeps its own status).  Returns
+ * MSC_OK, or MSC_ERR_INVALID_ARG for an unknown ticket or a job that has already ended. */
+msc_status msc_server_cancel(msc_server *srv, uint64_t ticket);
 
 /* Finish the running jobs, cancel the queued ones and free the server.  No other call on
  * this server (submit, wait) may run concurrently with or after this one. */

@@ -1516,6 +1516,7 @@ __global__ void k_apply_lossless(const uint64_t *idx, const float *val, uint64_t
 // have queued on other streams.  Every entry point synchronizes its stream before it
 // returns, so a buffer allocated in one call is ready for any stream in a later call.
 thread_local cudaStream_t g_alloc_stream = nullptr;
+thread_local const std::atomic<int> *g_cancel = nullptr;   // set by a serving slot for its job
 
 struct AllocOn {
     cudaStream_t prev;
@@ -1828,6 +1829,25 @@ cudaMemPool_t lib_pool()
     return pool;
 }
 
+// allocation-failure injection (msc_inject_alloc_failures): the count of allocations still
+// allowed before failures start, and the failures left to inject
+std::atomic<uint64_t> g_inject_after{0}, g_inject_left{0}, g_injected{0};
+
+bool inject_alloc_failure()
+{
+    if (g_inject_left.load(std::memory_order_relaxed) == 0) return false;
+    uint64_t a = g_inject_after.load();
+    while (a > 0)
+        if (g_inject_after.compare_exchange_weak(a, a - 1)) return false;
+    uint64_t l = g_inject_left.load();
+    while (l > 0)
+        if (g_inject_left.compare_exchange_weak(l, l - 1)) {
+            g_injected.fetch_add(1);
+            return true;
+        }
+    return false;
+}
+
 template <class T> struct DevBuf {
     T *p = nullptr;
     size_t n = 0;
@@ -1839,6 +1859,7 @@ template <class T> struct DevBuf {
     {
         if (count <= n && p) return cudaSuccess;
         release();
+        if (inject_alloc_failure()) return cudaErrorMemoryAllocation;
         cudaMemPool_t pool = lib_pool();
         const size_t bytes = (count ? count : 1) * sizeof(T);
         cudaError_t e = pool ? cudaMallocFromPoolAsync((void **)&p, bytes, pool, g_alloc_stream)
@@ -2395,6 +2416,7 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
     unsigned prev_iters = 0;
     unsigned long long fix_work[3] = {0, 0, 0};   // items of this call done by the round kernel
     for (;;) {
+        if (g_cancel && g_cancel->load()) return fail(MSC_ERR_CANCELLED, "the job was cancelled");
         const bool small = L.iters > 0 && L.last_items < small_thr;
         if (small && persistent) {
             const LoopState L0 = L;
@@ -2838,6 +2860,8 @@ void msc_rt::limit_cached_memory(uint64_t bytes)
     cudaGetLastError();
 }
 
+void msc_rt::set_cancel_flag(const std::atomic<int> *flag) { g_cancel = flag; }
+
 void msc_rt::share_device(msc_handle *h, int concurrent)
 {
     if (h && concurrent > 1) h->rounds_grid = std::max(16, 2 * sm_count() / concurrent);
@@ -2854,6 +2878,7 @@ const char *msc_status_string(msc_status s)
     case MSC_ERR_INVALID_ARG: return "MSC_ERR_INVALID_ARG";
     case MSC_ERR_OOM: return "MSC_ERR_OOM";
     case MSC_ERR_CUDA: return "MSC_ERR_CUDA";
+    case MSC_ERR_CANCELLED: return "MSC_ERR_CANCELLED";
     case MSC_ERR_NOT_CONVERGED: return "MSC_ERR_NOT_CONVERGED";
     case MSC_ERR_DEVICE_TIMEOUT: return "MSC_ERR_DEVICE_TIMEOUT";
     case MSC_ERR_STALLED: return "MSC_ERR_STALLED";
@@ -3252,6 +3277,14 @@ msc_status msc_release_cached_memory(void)
     cudaMemPool_t pool = lib_pool();
     if (pool) CK(cudaMemPoolTrimTo(pool, 0));
     return MSC_OK;
+}
+
+uint64_t msc_inject_alloc_failures(uint64_t after, uint64_t count)
+{
+    g_inject_left.store(0);
+    g_inject_after.store(after);
+    g_inject_left.store(count);
+    return g_injected.load();
 }
 
 msc_status msc_pool_used_bytes(uint64_t *used)

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstdint>
@@ -33,7 +34,9 @@ struct Job {
     float xi = 0.f;
     uint64_t bytes = 0;
     int skips = 0;
+    bool running = false;
     bool done = false;
+    std::atomic<int> cancel{0};
     msc_status status = MSC_OK;
     std::string err;
     msc_edits edits{};
@@ -87,6 +90,7 @@ struct msc_server {
                 j = *it;
                 pending.erase(it);
                 reserved += j->bytes;
+                j->running = true;
             }
             j->info.slot = slot;
             j->info.t_start = seconds_since(t0);
@@ -97,9 +101,12 @@ struct msc_server {
                 msc_options o = cfg.options;
                 o.stream = ws;
                 msc_handle *h = nullptr;
-                st = msc_prepare_original(j->f, j->nx, j->ny, j->nz, &o, &h);
+                msc_rt::set_cancel_flag(&j->cancel);
+                if (j->cancel.load()) st = msc_rt::set_error(MSC_ERR_CANCELLED, "the job was cancelled");
+                else st = msc_prepare_original(j->f, j->nx, j->ny, j->nz, &o, &h);
                 msc_rt::share_device(h, cfg.max_jobs);
                 if (st == MSC_OK) st = msc_fix(h, j->fh, j->xi, &o, &j->edits, j->g_out);
+                msc_rt::set_cancel_flag(nullptr);
                 std::string e = st == MSC_OK ? std::string() : std::string(msc_last_error());
                 msc_destroy(h);
                 if (st != MSC_OK) msc_rt::set_error(st, e);
@@ -211,6 +218,31 @@ msc_status msc_server_wait(msc_server *srv, uint64_t ticket, msc_edits *out, msc
     if (st != MSC_OK) msc_rt::set_error(st, j->err);
     delete j;
     return st;
+}
+
+msc_status msc_server_cancel(msc_server *srv, uint64_t ticket)
+{
+    if (!srv) return msc_rt::set_error(MSC_ERR_INVALID_ARG, "server is NULL");
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        auto it = srv->jobs.find(ticket);
+        if (it == srv->jobs.end()) return msc_rt::set_error(MSC_ERR_INVALID_ARG, "unknown ticket");
+        Job *j = it->second;
+        if (j->done) return msc_rt::set_error(MSC_ERR_INVALID_ARG, "the job has already ended");
+        j->cancel.store(1);
+        if (!j->running) {                      // still queued: it never starts
+            srv->pending.erase(std::find(srv->pending.begin(), srv->pending.end(), j));
+            j->status = MSC_ERR_CANCELLED;
+            j->err = "the job was cancelled before it started";
+            j->info.status = MSC_ERR_CANCELLED;
+            j->info.slot = -1;
+            j->info.t_start = j->info.t_end = seconds_since(srv->t0);
+            j->done = true;
+        }
+    }
+    srv->cv_done.notify_all();
+    srv->cv_work.notify_all();
+    return MSC_OK;
 }
 
 void msc_server_destroy(msc_server *srv)

@@ -15,7 +15,7 @@ from . import build as _build
 MSC_OK = 0
 STATUS_NAMES = {0: "MSC_OK", 1: "MSC_ERR_INVALID_ARG", 2: "MSC_ERR_OOM", 3: "MSC_ERR_CUDA",
                 4: "MSC_ERR_NOT_CONVERGED", 5: "MSC_ERR_DEVICE_TIMEOUT", 6: "MSC_ERR_STALLED",
-                7: "MSC_ERR_NO_DEVICE"}
+                7: "MSC_ERR_NO_DEVICE", 8: "MSC_ERR_CANCELLED"}
 QMAP_LOSSLESS = 0xFF
 
 
@@ -138,10 +138,14 @@ def load():
     lib.msc_selftest_barrier.argtypes = [i, vp]
     lib.msc_release_cached_memory.argtypes = []
     lib.msc_pool_used_bytes.argtypes = [ctypes.POINTER(u64)]
+    lib.msc_inject_alloc_failures.argtypes = [u64, u64]
+    lib.msc_inject_alloc_failures.restype = u64
+    lib.msc_server_cancel.argtypes = [vp, u64]
     for name in ("msc_prepare_original", "msc_fix", "msc_apply_edits", "msc_verify", "msc_fix_batch",
                  "msc_gradient_pairs", "msc_critical_cells", "msc_critical_cells_static", "msc_get_stats",
                  "msc_reset_stats", "msc_server_create", "msc_server_submit", "msc_server_wait", "msc_pack_edits",
-                 "msc_unpack_edits", "msc_pool_used_bytes", "msc_release_cached_memory", "msc_selftest_barrier"):
+                 "msc_unpack_edits", "msc_pool_used_bytes", "msc_release_cached_memory", "msc_selftest_barrier",
+                 "msc_server_cancel"):
         getattr(lib, name).restype = i
     _lib = lib
     return lib
@@ -437,6 +441,10 @@ class Server:
         self._jobs[t.value] = (g_out, (fk, hk, gk), tuple(np.shape(f)))
         return t.value
 
+    def cancel(self, ticket):
+        """Cancel a queued or running job; its wait() then raises MscError (MSC_ERR_CANCELLED)."""
+        _check(load().msc_server_cancel(self._s, ctypes.c_uint64(ticket)))
+
     def wait(self, ticket):
         lib = load()
         g_out, _keep, shape = self._jobs[ticket]
@@ -532,6 +540,12 @@ def selftest_barrier(timeout_ms=100):
 def release_cached_memory():
     """Return the device memory the library's pool keeps for reuse to the driver."""
     _check(load().msc_release_cached_memory())
+
+
+def inject_alloc_failures(after, count):
+    """Test hook: after `after` more device allocations succeed, the next `count` fail as if
+    the device were out of memory (count 0 turns it off).  Returns failures injected so far."""
+    return int(load().msc_inject_alloc_failures(int(after), int(count)))
 
 
 def pool_used_bytes():
