@@ -40,9 +40,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--size", type=int, default=512)
-    ap.add_argument("--rel", type=float, default=1e-4)
-    ap.add_argument("--tier", type=int, default=4)
+    ap.add_argument("--config", type=int, default=4, choices=[1, 2, 3, 4],
+                    help="workload: 1 gauss2d 64^2, 2 multiscale2d 1800x3600, 3 grf3d 256^3 x 8 (batched), "
+                         "4 kolmogorov3d 512^3 (default; --rel 1e-3 for its second bound)")
+    ap.add_argument("--size", type=int, default=None, help="shrink the config's grid (side; 2D: ny, nx = 2 ny)")
+    ap.add_argument("--rel", type=float, default=None, help="relative error bound (default: the config's)")
+    ap.add_argument("--tier", type=int, default=None, help="tier (default: the config's)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving replay")
@@ -192,40 +195,83 @@ def max_over_ranks(v, dist, device):
     return float(t.item())
 
 
-def workload_desc(shape, rel, tier):
-    return ("%s %dx%dx%d float32, 5%% constant-plateau block, base = U[-xi,xi] noise, xi=%g*range, tier %d, "
-            "q_max 6" % (WORKLOAD, *tuple(shape)[::-1], rel, tier))
+# The five configurations of the workload (the first four are single fields; the fifth is the
+# serving replay, reported with every config-4 line): generator, relative bound, tier, and the
+# description that names the workload in the JSON line.
+CONFIGS = {
+    1: dict(name="gauss2d", size=(64, 64), rel=1e-3, tier=3, seed=1,
+            desc="gauss2d 64x64 float32: 8 Gaussians + N(0,1e-3) noise, base = U[-xi,xi] noise, xi=%g*range, "
+                 "tier %d, q_max 6"),
+    2: dict(name="multiscale2d", size=(1800, 3600), rel=1e-3, tier=4, seed=2,
+            desc="multiscale2d 1800x3600 float32: 64 plane waves + 4-octave value noise, base = 2xi bins + U[-xi,xi] "
+                 "dither, xi=%g*range, tier %d, q_max 6"),
+    3: dict(name="grf3d", size=256, rel=1e-4, tier=4, seed=30, batch=8,
+            desc="grf3d 256x256x256 float32 x 8 fields (seeds 30-37), P(k)~k^-3, base = U[-xi,xi] noise, "
+                 "xi=%g*range, tier %d, q_max 6"),
+    4: dict(name=WORKLOAD, size=512, rel=1e-4, tier=4, seed=4,
+            desc=WORKLOAD + " 512x512x512 float32, 5%% constant-plateau block, base = U[-xi,xi] noise, "
+                            "xi=%g*range, tier %d, q_max 6"),
+}
 
 
-def workload(size, rel, rank):
+def config_of(args):
+    c = dict(CONFIGS[args.config])
+    if args.rel is not None:
+        c["rel"] = args.rel
+    if args.size is not None:
+        c["size"] = args.size if c["name"] in ("grf3d", WORKLOAD) else (args.size, 2 * args.size)
+    if args.tier is not None:
+        c["tier"] = args.tier
+    return c
+
+
+def workload_desc(cfg, shape):
+    d = cfg["desc"] % (cfg["rel"], cfg["tier"])
+    if tuple(shape) != (tuple(cfg["size"]) if isinstance(cfg["size"], tuple) else (cfg["size"],) * 3):
+        d += " (run at %s)" % "x".join(str(x) for x in tuple(shape)[::-1])
+    return d
+
+
+def workload(cfg, rank, k=0):
+    """(f, f_hat, xi) of the config's field k (of a batch), replica `rank`."""
     from paper_2409_17346_gb300 import synth
-    f, fh, xi, tier = synth.config_case(WORKLOAD, seed=replica_seed(rank), size=size, rel=rel)
+    f, fh, xi, _ = synth.config_case(cfg["name"], seed=cfg["seed"] + rank + k, size=cfg["size"], rel=cfg["rel"])
     return f, fh, xi
 
 
-def cpu_baseline(f, fh, rel, budget_s=12.0):
-    """The oracle (single thread, as it stands) on sub-blocks of the same fields with the
-    same xi; returns field GB/s over the sample."""
+def cpu_block(shape, small=False):
+    """Side lengths of the oracle's sample block: the whole field if it is small, else a
+    window of about 64^3 (3D) or 512x1024 (2D) vertices (32^3 / 128x256 when small)."""
+    if len(shape) == 3:
+        b = 32 if small else 64
+        return tuple(min(b, s) for s in shape)
+    b = (128, 256) if small else (512, 1024)
+    return tuple(min(x, s) for x, s in zip(b, shape))
+
+
+def cpu_baseline(f, fh, xi, tier, budget_s=20.0, small=False, max_blocks=64):
+    """The oracle as it stands (its OpenMP loops on every host core) on windows cut from the
+    same f and f_hat with the same xi and tier, until budget_s of CPU time is spent (at least
+    one window); returns field GB/s over the sample."""
     import oracle
-    from paper_2409_17346_gb300 import synth
-    xi = synth.xi_from_range(f, rel)
-    side = 12
+    blk = cpu_block(f.shape, small)
     n_done, t_done, blocks = 0, 0.0, 0
     rng = np.random.default_rng(0)
-    t_start = time.perf_counter()
-    while time.perf_counter() - t_start < budget_s and blocks < 64:
-        o = [int(rng.integers(0, s - side)) for s in f.shape]
-        sl = tuple(slice(a, a + side) for a in o)
+    while blocks < max_blocks and (blocks == 0 or t_done < budget_s):
+        o = [int(rng.integers(0, s - b + 1)) for s, b in zip(f.shape, blk)]
+        sl = tuple(slice(a, a + b) for a, b in zip(o, blk))
         fb, fhb = np.ascontiguousarray(f[sl]), np.ascontiguousarray(fh[sl])
         t0 = time.perf_counter()
-        r = oracle.fix(fb, fhb, xi, tier=4)
+        r = oracle.fix(fb, fhb, xi, tier=tier)
         t_done += time.perf_counter() - t0
         assert r["status"] == 0
         n_done += fb.size
         blocks += 1
-    return dict(value=4.0 * n_done / t_done / 1e9, unit="GB/s", cores=1, kind="oracle",
-                sample="%d blocks of %d^3 vertices cut from the same f / f_hat (xi as the workload), "
-                       "fixed to tier 4 by the single-threaded oracle, %.1f s" % (blocks, side, t_done))
+    cores = oracle.threads()
+    return dict(value=4.0 * n_done / t_done / 1e9, unit="GB/s", cores=cores, kind="oracle",
+                sample="%d window(s) of %s vertices cut from the same f / f_hat (xi as the workload), fixed to "
+                       "tier %d by the oracle on %d threads, %.1f s" % (blocks, "x".join(map(str, blk[::-1])),
+                                                                        tier, cores, t_done))
 
 
 def pct(xs, q):
@@ -276,8 +322,9 @@ def serving_leg(msc, n_req=128, slots=8):
 
 def run_study(args, msc):
     """One JSON line per study.  qmax: the 512^3 workload's bound at a 256^3 size, fixed with
-    q_max = 2..7 (iterations, fix time, quantised and lossless vertices, packed record size
-    against 8-byte float edits).  extreme: the flat-base white-noise field at growing sizes
+    q_max = 2..7 (iterations, fix time, quantised and lossless vertices, packed record size and
+    its coded size), beside the floating-edit loop (iterations, time, key-value record size
+    and its coded size).  extreme: the flat-base white-noise field at growing sizes
     (iterations, fix time, share of vertices edited)."""
     import torch
     from paper_2409_17346_gb300 import synth
@@ -297,16 +344,34 @@ def run_study(args, msc):
         return ed, dt, rep
 
     rows = []
+    if args.rel is None:
+        args.rel = 1e-4
+    if args.tier is None:
+        args.tier = 4
     if args.study == "qmax":
         f, fh, xi, _ = synth.config_case(WORKLOAD, size=256, rel=args.rel)
+        coder = msc.load().msc_coded_bound(16) > 0
+
+        def coded(rec):
+            return int(len(msc.code_record(rec, 3))) if coder else None
+
         for q in range(2, 8):
             ed, dt, rep = timed_fix(f, fh, xi, tier=args.tier, q_max=q)
-            packed = msc.packed_bytes(f.size, ed["n_lossless"], q)
-            edited = ed["n_quant"] + ed["n_lossless"]
-            rows.append({"q_max": q, "iters_c": ed["n_iters_c"], "iters_s": ed["n_iters_s"], "fix_s": dt,
-                         "n_quant": ed["n_quant"], "n_lossless": ed["n_lossless"], "packed_bytes": packed,
-                         "float_edit_bytes": 8 * edited, "verify_passed": rep["passed"]})
-        desc = "q_max sweep: %s 256^3, xi=%g*range, tier %d" % (WORKLOAD, args.rel, args.tier)
+            packed = msc.pack_edits(ed, q)
+            row = {"q_max": q, "iters_c": ed["n_iters_c"], "iters_s": ed["n_iters_s"], "fix_s": dt,
+                   "n_quant": ed["n_quant"], "n_lossless": ed["n_lossless"], "packed_bytes": int(packed.size),
+                   "packed_coded_bytes": coded(packed), "verify_passed": rep["passed"]}
+            if q <= 6:
+                # the floating edits the paper compares against: the same loop without the
+                # q_max cap, every edited vertex stored as an (index, value) pair
+                edf, dtf, repf = timed_fix(f, fh, xi, tier=args.tier, q_max=q, edit_mode=1)
+                kv = msc.pack_edits_kv(edf)
+                row.update({"float_iters_c": edf["n_iters_c"], "float_iters_s": edf["n_iters_s"], "float_fix_s": dtf,
+                            "float_edited": edf["n_lossless"], "float_kv_bytes": int(kv.size),
+                            "float_kv_coded_bytes": coded(kv), "float_verify_passed": repf["passed"]})
+            rows.append(row)
+        desc = ("q_max sweep: %s 256^3, xi=%g*range, tier %d; records coded by zstd level 3"
+                % (WORKLOAD, args.rel, args.tier))
     else:
         for n in (256, 512, 1024, 2048, 4096):
             f, fh, xi = synth.extreme_noise_2d(n)
@@ -319,25 +384,102 @@ def run_study(args, msc):
 
 
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    """The reference arm: the oracle as it stands, on the host's cores, on bounded windows of
+    the same workload (the rank-0 process only; other ranks exit without work)."""
+    if int(os.environ.get("RANK", "0")) != 0:
         return
-    f, fh, xi = workload(args.size, args.rel, 0)
+    cfg = config_of(args)
+    f, fh, xi = workload(cfg, 0)
+    # each step a window budget that keeps the whole run to a few minutes
+    per_step = max(2.0, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
-        cpu_baseline(f, fh, args.rel, budget_s=2.0)
+        cpu_baseline(f, fh, xi, cfg["tier"], budget_s=per_step, small=True)
     vals = []
     base = None
     for _ in range(args.steps):
-        base = cpu_baseline(f, fh, args.rel, budget_s=8.0)
+        base = cpu_baseline(f, fh, xi, cfg["tier"], budget_s=per_step, small=True)
         vals.append(base["value"])
     v = statistics.median(vals)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": 0, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload_desc(f.shape, args.rel, args.tier), "n_vertices": int(f.size),
+            "config": {"workload": workload_desc(cfg, f.shape), "n_vertices": int(f.size),
                        "sample": base["sample"]},
             "cpu_baseline": dict(base, value=v),
             "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def run_batch(args, cfg, msc, torch, world, rank, local, dist):
+    """Config 3: a batch of fields (timesteps) fixed together.  A step prepares every field's
+    original and fixes the batch in one msc_fix_batch call; the same fields fixed one after
+    another (prepare + fix each) are timed beside it.  value = all fields' bytes / step time."""
+    B = cfg["batch"]
+    tier = cfg["tier"]
+    fields = [workload(cfg, rank, k) for k in range(B)]
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    fds = [torch.from_numpy(f).cuda() for f, _, _ in fields]
+    fhds = [torch.from_numpy(fh).cuda() for _, fh, _ in fields]
+    gds = [torch.empty_like(x) for x in fds]
+    xis = [xi for _, _, xi in fields]
+    n = sum(f.size for f, _, _ in fields)
+
+    def batched():
+        hs = [msc.Handle(fd, opts=msc.options(stream=sp)) for fd in fds]
+        _, eds = msc.fix_batch(hs, fhds, xis, g_outs=gds, tier=tier, stream=sp)
+        for h in hs:
+            h.close()
+        return eds
+
+    def sequential():
+        eds = []
+        for fd, fhd, gd, xi in zip(fds, fhds, gds, xis):
+            h = msc.Handle(fd, opts=msc.options(stream=sp))
+            _, ed = h.fix(fhd, xi, g_out=gd, tier=tier, stream=sp)
+            h.close()
+            eds.append(ed)
+        return eds
+
+    def timed(fn, steps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps, out
+
+    for _ in range(args.warmup):
+        batched()
+        sequential()
+    g_seq = [gd.cpu().numpy() for gd in gds]
+    with ClockSampler(local) as clk:
+        ms_b, eds = timed(batched, args.steps)
+    clocks = clk.summary()
+    identical = all(np.array_equal(gd.cpu().numpy().view(np.uint32), g.view(np.uint32)) for gd, g in zip(gds, g_seq))
+    ms_s, _ = timed(sequential, args.steps)
+    ms_b = max_over_ranks(ms_b, None if dist is None else dist, "cuda")
+    passed = True
+    for fd, gd, xi in zip(fds, gds, xis):
+        h = msc.Handle(fd)
+        passed = passed and h.verify(gd, xi)["passed"]
+        h.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": world * 4.0 * n / (ms_b / 1e3) / 1e9, "unit": "GB/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": workload_desc(cfg, fields[0][0].shape), "config": 3, "fields": B,
+                           "n_vertices": n, "iters": [[e["n_iters_c"], e["n_iters_s"]] for e in eds],
+                           "verify_passed": passed, "batched_equals_sequential": identical,
+                           "sequential_ms_per_step": ms_s, "sequential_GBps": 4.0 * n / (ms_s / 1e3) / 1e9,
+                           "speedup_vs_sequential": ms_s / ms_b,
+                           "l2": "inputs (%d MB each) exceed L2; no flush" % (4 * fields[0][0].size >> 20)},
+                "clocks": clocks}
+        if not args.no_cpu and world == 1:
+            f, fh, xi = fields[0]
+            line["cpu_baseline"] = cpu_baseline(f, fh, xi, tier)
+        print(json.dumps(line))
 
 
 def main():
@@ -366,7 +508,14 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    f, fh, xi = workload(args.size, args.rel, rank)
+    cfg = config_of(args)
+    if cfg.get("batch"):
+        run_batch(args, cfg, msc, torch, world, rank, local, dist)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    tier = cfg["tier"]
+    f, fh, xi = workload(cfg, rank)
     n = f.size
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
@@ -376,7 +525,7 @@ def main():
 
     def step(profile=0, stats=None):
         h = msc.Handle(fd, opts=msc.options(stream=sp, profile=profile))
-        _, ed = h.fix(fhd, xi, g_out=gd, tier=args.tier, stream=sp, profile=profile)
+        _, ed = h.fix(fhd, xi, g_out=gd, tier=tier, stream=sp, profile=profile)
         if stats is not None:
             stats.append((h.stats(), ed))
         h.close()
@@ -454,7 +603,7 @@ def main():
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             h = msc.Handle(f)
-            _, ed2 = h.fix(fh, xi, g_out=g_host, tier=args.tier)
+            _, ed2 = h.fix(fh, xi, g_out=g_host, tier=tier)
             h.close()
             t_e2e.append(time.perf_counter() - t0)
         te = statistics.median(t_e2e)
@@ -468,7 +617,7 @@ def main():
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload_desc(f.shape, args.rel, args.tier),
+            "config": {"workload": workload_desc(cfg, f.shape), "config": args.config,
                        "n_vertices": n, "xi": xi, "iters_c": iters[0], "iters_s": iters[1],
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs (%d MB each) exceed L2; no flush" % (4 * n >> 20),
@@ -478,13 +627,14 @@ def main():
                        "kernel_launches_per_step": {k: bst[k]["launches"] for k in msc.KERNEL_CLASSES},
                        "kernel_items_per_step": {k: bst[k]["items"] for k in msc.KERNEL_CLASSES},
                        "round_kernel_phase_ms": bst["rounds"].get("phase_ms"),
+                       "dense_tile": msc.tile_report(f.shape) if f.ndim == 3 else None,
                        "launches_per_step": launches / args.steps,
                        "loop_algorithmic_GBps": loop_gbs, "loop_frac_of_peak": loop_gbs / peak},
             "roofline": roof, "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
         }
         if not args.no_cpu and world == 1:
-            line["cpu_baseline"] = cpu_baseline(f, fh, args.rel)
-        if not args.no_serve and world == 1:
+            line["cpu_baseline"] = cpu_baseline(f, fh, xi, tier)
+        if not args.no_serve and world == 1 and args.config == 4:
             del fd, fhd, gd
             torch.cuda.empty_cache()
             line["serving"] = serving_leg(msc)

@@ -45,7 +45,8 @@ typedef enum {
     MSC_ERR_STALLED = 6,         /* every false case targets a vertex that cannot move and
                                     exact_fallback is off */
     MSC_ERR_NO_DEVICE = 7,       /* no CUDA device, or the library was not built for it */
-    MSC_ERR_CANCELLED = 8        /* a serving job cancelled by msc_server_cancel */
+    MSC_ERR_CANCELLED = 8,       /* a serving job cancelled by msc_server_cancel */
+    MSC_ERR_UNAVAILABLE = 9      /* a runtime dependency is missing (the zstd library) */
 } msc_status;
 
 /* per-vertex edit states (the value of msc_edits.q_map[v] is derived from these) */
@@ -59,7 +60,9 @@ typedef struct {
     int exact_fallback;  /* 1 (default): a false case whose target vertex cannot move any
                             more (already at its floor f - xi, or restored) restores the
                             closed 1-rings of the case cell's vertices to f exactly */
-    int tile_x, tile_y, tile_z;   /* dense-stencil tile; 0 = built-in default */
+    int tile_x, tile_y, tile_z;   /* tile of the dense gradient of 3D fields: 32 x {4,8,16} x {8,16,32}
+                                     anchors as instantiated (msc_tile_report lists them);
+                                     0, 0, 0 (default) = the autotuned shape */
     void *stream;        /* cudaStream_t for all device work of the call (NULL = default) */
     int record_trace;    /* 1: fill msc_edits.trace with one record per edit round */
     int profile;         /* bitmask of kernel classes (bit k = class k below; MSC_PROFILE_ALL =
@@ -70,7 +73,16 @@ typedef struct {
                             vertices run in the persistent round kernel, the others as captured
                             graph nodes: 0 (default) = 8192; 1 = every round as graph nodes.
                             Results do not depend on it. */
+    int edit_mode;       /* MSC_EDITS_QUANTIZED (0, default): Eq. 2, at most q_max steps of
+                            xi / 2^q_max, then the floor; MSC_EDITS_FLOAT (1): the floating
+                            edits the paper compares against (Sec. 4.7): the same steps with no
+                            cap on their number (a vertex snaps to the floor only when the next
+                            step would pass f - xi), and every edited vertex stored losslessly
+                            as an (index, value) pair; q_max must then be 1..6 */
 } msc_options;
+
+#define MSC_EDITS_QUANTIZED 0
+#define MSC_EDITS_FLOAT 1
 
 /* kernel classes of msc_stats */
 enum {
@@ -162,7 +174,7 @@ const char *msc_status_string(msc_status s);
 const char *msc_last_error(void);
 
 /* Fill *opt with defaults: tier 4, q_max 6, max_iters 100000, exact_fallback 1,
- * tiles 0, stream NULL, record_trace 0, profile 0. */
+ * tiles 0, stream NULL, record_trace 0, profile 0, small_round 0, edit_mode quantized. */
 void msc_default_options(msc_options *opt);
 
 /* Sec. 4.2 (discrete gradient of f), Sec. 3.1 (critical cells, gradient paths): compute
@@ -208,6 +220,36 @@ msc_status msc_pack_edits(const msc_edits *e, int q_max, uint8_t *out, uint64_t 
  * counts and the trace are not part of the record and read 0.  Errors: MSC_ERR_INVALID_ARG
  * for a malformed record. */
 msc_status msc_unpack_edits(const uint8_t *buf, uint64_t size, msc_edits *out, int *q_max);
+
+/* Floating edits as key-value pairs (Sec. 4.7: the form that stores every edit as a float,
+ * with its vertex index).  Layout, little-endian: a 32-byte header ("MSCE", version 2, 0, 0,
+ * 0, n_vertices u64, n_pairs u64, 0 u64), the n_pairs vertex ids as u32 in increasing order,
+ * then the n_pairs float32 values.  Size: 32 + 8 * n_pairs bytes. */
+uint64_t msc_kv_bytes(uint64_t n_pairs);
+
+/* Pack the edits of a fix run with edit_mode MSC_EDITS_FLOAT (n_quant must be 0) as
+ * key-value pairs into out (host memory, cap bytes); *n_out receives the size (out NULL and
+ * cap 0 only report it).  Errors: MSC_ERR_INVALID_ARG for quantised counts, a short buffer or
+ * lossless_idx not increasing. */
+msc_status msc_pack_edits_kv(const msc_edits *e, uint8_t *out, uint64_t cap, uint64_t *n_out);
+
+/* Unpack a key-value record (host memory) into *out (q_map 0 or MSC_QMAP_LOSSLESS, the pairs;
+ * free with msc_free_edits after any return).  msc_apply_edits then rebuilds g from it. */
+msc_status msc_unpack_edits_kv(const uint8_t *buf, uint64_t size, msc_edits *out);
+
+/* Sec. 4.7 / Sec. 5.5: the lossless coder the paper applies to edit records (ZSTD).  The
+ * system's zstd library is loaded on first use; every call returns MSC_ERR_UNAVAILABLE (and
+ * msc_coded_bound 0) where it cannot be loaded.  All buffers are host memory.
+ *  msc_coded_bound: the largest coded size of a size-byte record (the size out must have).
+ *  msc_code_record: code rec[0, size) as one zstd frame at level 1..22 (3 is zstd's default)
+ *    into out; *n_out receives the coded size.
+ *  msc_decoded_size: the record size stored in a coded frame's header.
+ *  msc_decode_record: decode a frame into out (at least msc_decoded_size bytes).
+ * Errors: MSC_ERR_INVALID_ARG for a bad level, a short buffer or a damaged frame. */
+uint64_t msc_coded_bound(uint64_t size);
+msc_status msc_code_record(const uint8_t *rec, uint64_t size, int level, uint8_t *out, uint64_t cap, uint64_t *n_out);
+msc_status msc_decoded_size(const uint8_t *in, uint64_t size, uint64_t *n_out);
+msc_status msc_decode_record(const uint8_t *in, uint64_t size, uint8_t *out, uint64_t cap, uint64_t *n_out);
 
 /* Sec. 5.1 metrics: compare the MSC of g with the handle's original (critical cells by
  * dimension, every separatrix pair, separatrix terminals) and measure max |g - f|.
@@ -273,6 +315,15 @@ msc_status msc_critical_cells_static(const float *field, int nx, int ny, int nz,
  * live buffers right now (cudaMemPoolAttrUsedMemCurrent); memory the pool keeps for reuse
  * is not counted.  Lets a caller check that a sequence of calls allocated nothing. */
 msc_status msc_pool_used_bytes(uint64_t *used);
+
+/* The tile autotuner of the dense 3D gradient.  The first dense pass of a grid shape on a
+ * device (with the tile options 0) times every instantiated tile shape once on its input and
+ * keeps the fastest for that (device, nx, ny, nz); every shape gives the same result.  This
+ * reports, for the current device and a grid: *n = the number of shapes, shapes[3*i ..] the
+ * anchors per block along x, y, z of shape i and ms[i] its time on the tuning pass (up to cap
+ * shapes), chosen[0..2] the shape kept (all 0, and ms 0, if the grid was not tuned yet).
+ * Any of chosen, shapes, ms may be NULL. */
+msc_status msc_tile_report(int nx, int ny, int nz, int *chosen, int *shapes, float *ms, int cap, int *n);
 
 /* Launch statistics accumulated on a handle since its creation or the last reset. */
 msc_status msc_get_stats(msc_handle *h, msc_stats *out);

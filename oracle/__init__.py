@@ -154,9 +154,10 @@ def targets(f, g, state=None, pass_=0, tier=4, exact_fallback=1):
     return out[: min(n.value, cap)], markX
 
 
-def fix(f, fhat, xi, tier=4, q_max=6, max_iters=100000, exact_fallback=1, trace_cap=1 << 20):
-    """The whole fix loop.  Returns a dict with g, state, n_c, n_s, n_exact_iters,
-    trace (rows: kind, |T|, |X|, sum T, sum X, #cases) and status."""
+def fix(f, fhat, xi, tier=4, q_max=6, max_iters=100000, exact_fallback=1, trace_cap=1 << 20, edit_mode=0):
+    """The whole fix loop.  edit_mode 0: quantised edits (Eq. 2); 1: floating edits (no cap
+    on the number of steps, Sec. 4.7).  Returns a dict with g, state, n_c, n_s,
+    n_exact_iters, trace (rows: kind, |T|, |X|, sum T, sum X, #cases) and status."""
     lib = _load()
     f = _f32(f)
     fhat = _f32(fhat)
@@ -169,7 +170,7 @@ def fix(f, fhat, xi, tier=4, q_max=6, max_iters=100000, exact_fallback=1, trace_
     trace = np.zeros((trace_cap, 6), dtype=np.int64)
     ntr = ctypes.c_int64(0)
     rc = lib.orc_fix(_p(f), _p(fhat), nx, ny, nz, ctypes.c_float(xi), tier, q_max, max_iters,
-                     exact_fallback, _p(g), _p(state), _p(counts), _p(trace),
+                     exact_fallback, edit_mode, _p(g), _p(state), _p(counts), _p(trace),
                      ctypes.c_int64(trace_cap), ctypes.byref(ntr))
     return dict(status=rc, g=g, state=state, n_c=int(counts[0]), n_s=int(counts[1]),
                 n_exact_iters=int(counts[2]), trace=trace[: min(ntr.value, trace_cap)])
@@ -193,17 +194,19 @@ def verify(f, g):
     return out
 
 
-def edit_values(f, fhat, xi, q_max=6):
-    """Closed-form pieces of Eq. 2: (lb, ub, clamped base, values after q = 0..q_max steps)."""
+def edit_values(f, fhat, xi, q_max=6, n_steps=None):
+    """Closed-form pieces of Eq. 2: (lb, ub, clamped base, values after q = 0 .. n_steps - 1
+    steps of xi / 2^q_max); n_steps defaults to q_max + 1."""
     lib = _load()
     f = _f32(f).reshape(-1)
     fhat = _f32(fhat).reshape(-1)
     n = f.size
+    nq = q_max + 1 if n_steps is None else int(n_steps)
     lb = np.zeros(n, np.float32)
     ub = np.zeros(n, np.float32)
     fc = np.zeros(n, np.float32)
-    qv = np.zeros((n, q_max + 1), np.float32)
-    _check(lib.orc_edit_values(_p(f), _p(fhat), ctypes.c_int64(n), ctypes.c_float(xi), q_max,
+    qv = np.zeros((n, nq), np.float32)
+    _check(lib.orc_edit_values(_p(f), _p(fhat), ctypes.c_int64(n), ctypes.c_float(xi), q_max, nq,
                                _p(lb), _p(ub), _p(fc), _p(qv)), "edit_values")
     return lb, ub, fc, qv
 
@@ -221,16 +224,17 @@ def apply_edits(fhat, xi, q_max, q_map, lossless_idx, lossless_val):
     return g
 
 
-def edits_from_state(f, fhat, xi, state, g):
+def edits_from_state(f, fhat, xi, state, g, edit_mode=0):
     """The stored form of the edits (Sec. 4.7): q per quantised vertex; 0xFF and the exact
-    final value for floor, exact, or re-clamped vertices."""
+    final value for floor, exact, or re-clamped vertices.  Floating edits (edit_mode 1) store
+    every edited vertex that way."""
     f = _f32(f).reshape(-1)
     fhat = _f32(fhat).reshape(-1)
     st = np.asarray(state, dtype=np.uint8).reshape(-1)
     gg = _f32(g).reshape(-1)
     _, _, fc, _ = edit_values(f, fhat, xi, 1)
     clamped = fc.view(np.uint32) != fhat.view(np.uint32)
-    lossless = (st > 7) | clamped
+    lossless = (st > (0 if edit_mode else 7)) | clamped
     q_map = np.where(lossless, 0xFF, st).astype(np.uint8)
     idx = np.nonzero(lossless)[0].astype(np.int64)
     return q_map, idx, gg[idx].copy()

@@ -760,8 +760,13 @@ static float quant_value(float fc, int q, float step)
 }
 
 /* Eq. 2: one more quantised step while q < qmax and the result stays >= f - xi,
- * otherwise snap to the floor f - xi. */
-static int apply_edits(loopctx *c, float xi, int qmax)
+ * otherwise snap to the floor f - xi.  Floating edits (Sec. 4.7, the form the paper
+ * compares against): every edit is stored as a float, so the count q needs no bound; the
+ * same steps continue until the next one would pass f - xi (qcap = QCAP_FLOAT, more steps
+ * than fit between f + xi and f - xi). */
+#define QCAP_FLOAT 0xEF
+
+static int apply_edits(loopctx *c, float xi, int qmax, int qcap)
 {
     const grid_t *g = c->g;
     float step = xi / (float)(1 << qmax);
@@ -771,11 +776,11 @@ static int apply_edits(loopctx *c, float xi, int qmax)
             if (c->state[v] != ST_EXACT) { c->gv[v] = c->f[v]; c->state[v] = ST_EXACT; changed++; }
             continue;
         }
-        if (!c->markT[v] || c->state[v] > qmax) continue;
+        if (!c->markT[v] || c->state[v] > qcap) continue;
         int q = c->state[v];
         float lb = lower_bound(c->f[v], xi);
         float fc = clamped_base(c->f[v], c->fhat[v], xi);
-        if (q < qmax) {
+        if (q < qcap) {
             float cand = quant_value(fc, q + 1, step);
             if (cand >= lb) { c->gv[v] = cand; c->state[v] = (uint8_t)(q + 1); changed++; continue; }
         }
@@ -985,17 +990,20 @@ done:
     return rc;
 }
 
-/* The whole fix loop (Sec. 4.2-4.7).  Outputs: g, per-vertex state (0..qmax quantised
- * count, 0xF0 floor, 0xF1 exact), counts, and one trace row per iteration:
+/* The whole fix loop (Sec. 4.2-4.7).  edit_mode 0: quantised edits (Eq. 2); 1: floating
+ * edits (no cap on the step count, Sec. 4.7).  Outputs: g, per-vertex state (the step count
+ * q, 0xF0 floor, 0xF1 exact), counts, and one trace row per iteration:
  * (kind 0=C/1=S, |T|, |X|, sum of T ids, sum of X ids, number of cases). */
 int orc_fix(const float *f, const float *fhat, int nx, int ny, int nz, float xi,
-            int tier, int qmax, int max_iters, int exact_fallback,
+            int tier, int qmax, int max_iters, int exact_fallback, int edit_mode,
             float *g_out, uint8_t *state_out, int32_t *counts /* n_c, n_s, n_exact_iters */,
             int64_t *trace, int64_t trace_cap, int64_t *n_trace)
 {
     grid_t g;
     if (grid_init(&g, nx, ny, nz)) return ORC_ERR_ARG;
     if (!(xi > 0.0f) || !isfinite(xi) || qmax < 1 || qmax > 7 || tier < 1 || tier > 4) return ORC_ERR_ARG;
+    if (edit_mode < 0 || edit_mode > 1 || (edit_mode == 1 && qmax > 6)) return ORC_ERR_ARG;
+    const int qcap = edit_mode == 1 ? QCAP_FLOAT : qmax;
     if (!valid_field(f, g.n) || !valid_field(fhat, g.n)) return ORC_ERR_ARG;
     i64 ncell = g.n * g.K;
     loopctx c = {0};
@@ -1035,7 +1043,7 @@ int orc_fix(const float *f, const float *fhat, int nx, int ny, int nz, float xi,
             if (c.markT[v]) { nT++; sT += v; }
             if (c.markX[v]) { nX++; sX += v; }
         }
-        apply_edits(&c, xi, qmax);
+        apply_edits(&c, xi, qmax, qcap);
         counts[kind]++;
         if (nX) counts[2]++;
         if (*n_trace < trace_cap) {
@@ -1101,16 +1109,16 @@ done:
 
 /* edit arithmetic exposed for the closed-form pins: lb, ub, clamped base and the value
  * after q quantised steps, for each input */
-int orc_edit_values(const float *f, const float *fhat, int64_t n, float xi, int qmax,
-                    float *lb, float *ub, float *fc, float *qvals /* n x (qmax+1) */)
+int orc_edit_values(const float *f, const float *fhat, int64_t n, float xi, int qmax, int nq,
+                    float *lb, float *ub, float *fc, float *qvals /* n x nq: q = 0 .. nq-1 */)
 {
-    if (!(xi > 0.0f) || qmax < 1 || qmax > 7) return ORC_ERR_ARG;
+    if (!(xi > 0.0f) || qmax < 1 || qmax > 7 || nq < 1 || nq > 256) return ORC_ERR_ARG;
     float step = xi / (float)(1 << qmax);
     for (i64 i = 0; i < n; i++) {
         lb[i] = lower_bound(f[i], xi);
         ub[i] = upper_bound(f[i], xi);
         fc[i] = clamped_base(f[i], fhat[i], xi);
-        for (int q = 0; q <= qmax; q++) qvals[i * (qmax + 1) + q] = quant_value(fc[i], q, step);
+        for (int q = 0; q < nq; q++) qvals[i * nq + q] = quant_value(fc[i], q, step);
     }
     return ORC_OK;
 }

@@ -10,7 +10,8 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC_DIR = os.path.join(HERE, "csrc")
-SOURCES = [os.path.join(SRC_DIR, "msc_lib.cu"), os.path.join(SRC_DIR, "msc_server.cpp")]
+SOURCES = [os.path.join(SRC_DIR, "msc_lib.cu"), os.path.join(SRC_DIR, "msc_server.cpp"),
+           os.path.join(SRC_DIR, "msc_coder.cpp")]
 DEPS = SOURCES + [os.path.join(SRC_DIR, f) for f in ("msc_cells.cuh", "msc_core.cuh", "msc_dense.cuh", "msc_runtime.h")] + \
     [os.path.join(ROOT, "include", "msc.h")]
 OUT_DIR = os.path.join(HERE, "_build")
@@ -37,7 +38,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             return LIB
     tmp = LIB + ".tmp.%d" % os.getpid()
     cmd = [nvcc_path(), "-std=c++17", "--expt-relaxed-constexpr", ARCH, "-O3", "-lineinfo",
-           "-Xcompiler", "-fPIC", "-shared", "-o", tmp] + SOURCES
+           "-Xcompiler", "-fPIC", "-shared", "-o", tmp] + SOURCES + ["-ldl"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     subprocess.check_call(cmd)

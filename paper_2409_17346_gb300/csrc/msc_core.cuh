@@ -99,6 +99,8 @@ struct LoopState {
 struct Ctx {
     Grid G;
     int tier, qmax, exact_fallback;
+    int qcap;                        // quantised steps a vertex may take before the floor:
+                                     // q_max (Eq. 2), or no cap in floating-edit mode
     float xi, step;
     const float *f, *fhat;
     float *g;
@@ -530,7 +532,7 @@ MSC_HD inline bool edit_prepare(const Ctx &c, uint32_t i, uint32_t nX, uint32_t 
     v = c.Tlist[i - nX];
     if ((c.Xbits[v >> 5] >> (v & 31)) & 1u) return false;
     c.gprev[v] = c.g[v];
-    return c.state[v] <= c.qmax;
+    return c.state[v] <= c.qcap;
 }
 
 // Whether the round changed the SoS order of the edited vertex v against any vertex u
@@ -559,8 +561,9 @@ MSC_HD inline bool order_changed(const Ctx &c, uint32_t v, int part, int nparts,
     return flip;
 }
 
-// Eq. 2 applied to a changing item: one step of xi / 2^q_max while q < q_max and the value
-// stays >= f - xi, otherwise the floor f - xi; a restore sets g = f exactly
+// Eq. 2 applied to a changing item: one step of xi / 2^q_max while q < q_max (q < qcap in
+// floating-edit mode) and the value stays >= f - xi, otherwise the floor f - xi; a restore
+// sets g = f exactly
 MSC_HD inline void edit_apply(const Ctx &c, uint32_t i, uint32_t nX, uint32_t v)
 {
     if (i < nX) {
@@ -571,7 +574,7 @@ MSC_HD inline void edit_apply(const Ctx &c, uint32_t i, uint32_t nX, uint32_t v)
     const uint8_t st = c.state[v];
     const float fv = ld(c.f + v);
     const float lb = sub_ru(fv, c.xi);
-    if (st < c.qmax) {
+    if (st < c.qcap) {
         const float fc = clamp_base(fv, ld(c.fhat + v), c.xi);
         const float cand = sub_rn(fc, mul_rn((float)(st + 1), c.step));
         if (cand >= lb) { c.g[v] = cand; c.state[v] = (uint8_t)(st + 1); return; }

@@ -1,4 +1,4 @@
-// Dense discrete gradient of a whole 3D field, one z-slab of a 32 x 8 anchor tile per block.
+// Dense discrete gradient of a whole 3D field, one z-slab of a 32 x TY anchor tile per block.
 //
 // The per-anchor evaluator (eval_anchor) recomputes, for every anchor, the vertex pairs of
 // the 8 corners of its cube and the pairings of the 19 cube edges and 18 cube triangles that
@@ -21,11 +21,17 @@
 namespace msc {
 namespace dense {
 
-constexpr int TX = 32, TY = 8, ZS = 16;          // tile of anchors, planes per block
-constexpr int VX = TX + 5, VY = TY + 5;          // values: x0-1 .. x0+TX+3
-constexpr int PX = TX + 3, PY = TY + 3;          // vertex pairs: x0 .. x0+TX+2
-constexpr int EX = TX + 2, EY = TY + 2;          // edges: x0 .. x0+TX+1
-constexpr int RX = TX + 1, RY = TY + 1;          // triangles: x0 .. x0+TX
+// Tile shapes: 32 anchors along x (a warp per row, so the per-warp ballots of the mismatch
+// bits cover whole rows) by TY rows, one block of 32 * TY threads, marching up ZS planes.
+// The autotuner in the library times the instantiated shapes per grid and keeps the fastest;
+// every shape gives the same codes.
+template <int TY_, int ZS_> struct Tile {
+    static constexpr int TX = 32, TY = TY_, ZS = ZS_, NT = 32 * TY_;
+    static constexpr int VX = TX + 5, VY = TY + 5;   // values: x0-1 .. x0+TX+3
+    static constexpr int PX = TX + 3, PY = TY + 3;   // vertex pairs: x0 .. x0+TX+2
+    static constexpr int EX = TX + 2, EY = TY + 2;   // edges: x0 .. x0+TX+1
+    static constexpr int RX = TX + 1, RY = TY + 1;   // triangles: x0 .. x0+TX
+};
 constexpr int NVAL = 5, NVP = 4, NEDG = 3, NTRI = 2;   // ring depths
 
 constexpr bool pos_lt(const int *a, const int *b)   // vertex-id order of two offsets
@@ -143,11 +149,11 @@ constexpr bool reach_ok()
 }
 static_assert(reach_ok(), "pairing rule reach exceeds the dense tile's margins");
 
-struct Smem {
-    float val[NVAL][VY][VX];
-    uint8_t vp[NVP][PY][PX];
-    uint32_t ef[NEDG][EY][EX];
-    uint32_t tf[NTRI][RY][RX];
+template <class TL> struct Smem {
+    float val[NVAL][TL::VY][TL::VX];
+    uint8_t vp[NVP][TL::PY][TL::PX];
+    uint32_t ef[NEDG][TL::EY][TL::EX];
+    uint32_t tf[NTRI][TL::RY][TL::RX];
 };
 
 }  // namespace dense

@@ -26,6 +26,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <unordered_map>
 #include <new>
@@ -417,16 +418,21 @@ __global__ void __launch_bounds__(TPB, 3) k_eval_dense(const float *v, Grid G, u
 }
 
 // Dense discrete gradient of a 3D field by z-marching tiles (msc_dense.cuh): grid
-// (ceil(nx/32), ceil(ny/8), ceil(nz/16)), 256 threads.  With ref: also the bits of the
+// (ceil(nx/32), ceil(ny/TY), ceil(nz/ZS)), 32 * TY threads.  With ref: also the bits of the
 // anchors whose code differs from ref's (mbits) and whose critical cells differ (cbits,
 // csum); mbits and cbits must be zero on entry (a warp's anchors need not start a word).
-__global__ void __launch_bounds__(256, 3) k_eval_tile(const float *v, Grid G, uint64_t *out, const uint64_t *ref,
-                                                      uint32_t *mbits, uint32_t *cbits, uint32_t *csum, int tier,
-                                                      uint64_t *low)
+template <int TY, int ZS, int MINB>
+__global__ void __launch_bounds__(32 * TY, MINB) k_eval_tile(const float *v, Grid G, uint64_t *out, const uint64_t *ref,
+                                                            uint32_t *mbits, uint32_t *cbits, uint32_t *csum, int tier,
+                                                            uint64_t *low)
 {
     using namespace dense;
     using T3 = Tab<3>;
-    __shared__ Smem S;
+    using TL = Tile<TY, ZS>;
+    constexpr int TX = TL::TX, NT = TL::NT;
+    constexpr int VX = TL::VX, VY = TL::VY, PX = TL::PX, PY = TL::PY, EX = TL::EX, EY = TL::EY, RX = TL::RX,
+                  RY = TL::RY;
+    __shared__ Smem<TL> S;
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * ZS;
     const int zend = min(z0 + ZS, G.nz);
@@ -435,7 +441,7 @@ __global__ void __launch_bounds__(256, 3) k_eval_tile(const float *v, Grid G, ui
     auto load_plane = [&](int z) {
         float(*P)[VX] = S.val[vs(z)];
         const bool zin = z >= 0 && z < G.nz;
-        for (int i = tid; i < VX * VY; i += 256) {
+        for (int i = tid; i < VX * VY; i += NT) {
             const int ly = i / VX, lx = i - ly * VX;
             const int x = x0 - 1 + lx, y = y0 - 1 + ly;
             P[ly][lx] = (zin && x >= 0 && x < G.nx && y >= 0 && y < G.ny) ? ld(v + vid(G, x, y, z)) : INF;
@@ -452,7 +458,7 @@ __global__ void __launch_bounds__(256, 3) k_eval_tile(const float *v, Grid G, ui
             const int zv = z0 + j;
             const float(*Pl[3])[VX] = {S.val[vs(zv - 1)], S.val[vs(zv)], S.val[vs(zv + 1)]};
             uint8_t(*Q)[PX] = S.vp[(zv - z0) % NVP];
-            for (int i = tid; i < PX * PY; i += 256) {
+            for (int i = tid; i < PX * PY; i += NT) {
                 const int ly = i / PX, lx = i - ly * PX;
                 float bv = INF;
                 int bn = 15;
@@ -475,7 +481,7 @@ __global__ void __launch_bounds__(256, 3) k_eval_tile(const float *v, Grid G, ui
             const float(*Pl[4])[VX] = {S.val[vs(ze - 1)], S.val[vs(ze)], S.val[vs(ze + 1)], S.val[vs(ze + 2)]};
             const uint8_t(*Q[2])[PX] = {S.vp[(ze - z0) % NVP], S.vp[(ze + 1 - z0) % NVP]};
             uint32_t(*E)[EX] = S.ef[(ze - z0) % NEDG];
-            for (int i = tid; i < EX * EY; i += 256) {
+            for (int i = tid; i < EX * EY; i += NT) {
                 const int ly = i / EX, lx = i - ly * EX;
                 const float wa = Pl[1][ly + 1][lx + 1];
                 const int vpa = Q[0][ly][lx];
@@ -512,7 +518,7 @@ __global__ void __launch_bounds__(256, 3) k_eval_tile(const float *v, Grid G, ui
             const float(*Pl[4])[VX] = {S.val[vs(zt - 1)], S.val[vs(zt)], S.val[vs(zt + 1)], S.val[vs(zt + 2)]};
             const uint32_t(*E[2])[EX] = {S.ef[(zt - z0) % NEDG], S.ef[(zt + 1 - z0) % NEDG]};
             uint32_t(*R)[RX] = S.tf[(zt - z0) % NTRI];
-            for (int i = tid; i < RX * RY; i += 256) {
+            for (int i = tid; i < RX * RY; i += NT) {
                 const int ly = i / RX, lx = i - ly * RX;
                 uint32_t fld = 0;
                 static_for<12>([&](auto tc) {
@@ -1359,7 +1365,7 @@ __global__ void k_qmap(const float *f, const float *fh, const uint8_t *state, ui
     if (i < n) {
         const uint8_t st = state[i];
         const float fc = clamp_base(f[i], fh[i], xi);
-        lossless = st > qmax || __float_as_uint(fc) != __float_as_uint(fh[i]);
+        lossless = st > qmax || __float_as_uint(fc) != __float_as_uint(fh[i]);   // qmax 0: every edited vertex
         quant = !lossless && st > 0;
         qmap[i] = lossless ? (uint8_t)MSC_QMAP_LOSSLESS : st;
     }
@@ -1946,6 +1952,7 @@ void fill_defaults(msc_options *o)
     o->record_trace = 0;
     o->profile = 0;
     o->small_round = 0;
+    o->edit_mode = MSC_EDITS_QUANTIZED;
 }
 
 msc_status check_options(const msc_options *o)
@@ -1954,6 +1961,10 @@ msc_status check_options(const msc_options *o)
     if (o->q_max < 1 || o->q_max > 7) return fail(MSC_ERR_INVALID_ARG, "q_max must be 1..7 (got %d)", o->q_max);
     if (o->max_iters < 0) return fail(MSC_ERR_INVALID_ARG, "max_iters must be >= 0");
     if (o->small_round < 0) return fail(MSC_ERR_INVALID_ARG, "small_round must be >= 0");
+    if (o->edit_mode != MSC_EDITS_QUANTIZED && o->edit_mode != MSC_EDITS_FLOAT)
+        return fail(MSC_ERR_INVALID_ARG, "edit_mode must be 0 (quantized) or 1 (float)");
+    if (o->edit_mode == MSC_EDITS_FLOAT && o->q_max > 6)
+        return fail(MSC_ERR_INVALID_ARG, "floating edits need q_max <= 6 (got %d)", o->q_max);
     return MSC_OK;
 }
 
@@ -1977,6 +1988,8 @@ struct msc_handle {
     DevBuf<uint32_t> Tbits, Xbits, Dbits, Tlist, Xlist, Dlist, Elist, Mbits, Cbits, Csum, Cblk, Cblk2;
     DevBuf<GridBarrier> bar;
     int rounds_grid = 0;   // blocks of the persistent round kernel (0: one per SM)
+    int tile_req = -1;     // tile shape of the dense 3D gradient the current call asks for (-1: tuned)
+    int tile_used = -1;    // the shape its last dense pass ran with
     DevBuf<uint32_t> vis_v, vis_top, vis_tri, ovf0, ovf1;
     DevBuf<uint32_t> ns_v, ns_top, ns_tri, ns_dead;
     DevBuf<uint32_t> sDbits, sDlist;
@@ -2106,12 +2119,17 @@ msc_status alloc_fix_state(msc_handle *h)
     return MSC_OK;
 }
 
-Ctx make_ctx(msc_handle *h, int tier, int qmax, int exact_fallback, float xi)
+// steps a vertex may take before the floor: q_max (Eq. 2), or, for floating edits, more than
+// the 2^(q_max+1) steps of xi / 2^q_max that fit between f + xi and f - xi (no cap)
+constexpr int FLOAT_EDIT_CAP = 0xEF;
+
+Ctx make_ctx(msc_handle *h, int tier, int qmax, int exact_fallback, float xi, int edit_mode = MSC_EDITS_QUANTIZED)
 {
     Ctx c{};
     c.G = h->G;
     c.tier = tier;
     c.qmax = qmax;
+    c.qcap = edit_mode == MSC_EDITS_FLOAT ? FLOAT_EDIT_CAP : qmax;
     c.exact_fallback = exact_fallback;
     c.xi = xi;
     c.step = xi / (float)(1 << qmax);
@@ -2141,6 +2159,108 @@ Ctx make_ctx(msc_handle *h, int tier, int qmax, int exact_fallback, float xi)
     return c;
 }
 
+// ------------------------------------------------------------------------------------
+// tile shapes of k_eval_tile and their autotuner
+// ------------------------------------------------------------------------------------
+// The shapes instantiated: 32 x TY anchors per block, ZS planes per z-slab.  Deeper slabs
+// recompute fewer halo planes (3 per slab) but give fewer blocks; taller tiles share more of
+// their halo rows but hold more shared memory per block.  The first dense pass of a 3D grid
+// shape on a device times every shape once on its input (all shapes write the same codes) and
+// keeps the fastest for that (device, nx, ny, nz); msc_options.tile_* picks one instead.
+using TileFn = void (*)(const float *, Grid, uint64_t *, const uint64_t *, uint32_t *, uint32_t *, uint32_t *, int,
+                        uint64_t *);
+struct TileShape {
+    int ty, zs, nt;
+    TileFn fn;
+};
+const TileShape TILE_SHAPES[] = {
+    {8, 16, 256, k_eval_tile<8, 16, 3>},
+    {8, 8, 256, k_eval_tile<8, 8, 3>},
+    {8, 32, 256, k_eval_tile<8, 32, 3>},
+    {4, 16, 128, k_eval_tile<4, 16, 6>},
+    {16, 16, 512, k_eval_tile<16, 16, 1>},
+};
+constexpr int N_TILE_SHAPES = (int)(sizeof(TILE_SHAPES) / sizeof(TILE_SHAPES[0]));
+
+struct TileTuning {
+    int best = 0;
+    float ms[N_TILE_SHAPES] = {};
+};
+std::mutex g_tile_mu;
+std::map<std::tuple<int, int, int, int>, TileTuning> g_tile_tuned;
+
+// the shape index the options ask for: -1 = tuned, else an instantiated shape
+msc_status tile_request(const msc_options &o, int *req)
+{
+    *req = -1;
+    if (!o.tile_x && !o.tile_y && !o.tile_z) return MSC_OK;
+    for (int i = 0; i < N_TILE_SHAPES; i++)
+        if (o.tile_x == 32 && o.tile_y == TILE_SHAPES[i].ty && o.tile_z == TILE_SHAPES[i].zs) {
+            *req = i;
+            return MSC_OK;
+        }
+    return fail(MSC_ERR_INVALID_ARG, "tile %dx%dx%d is not instantiated (32 x {4,8,16} x {8,16,32} as listed by "
+                "msc_tile_report; 0 = tuned)", o.tile_x, o.tile_y, o.tile_z);
+}
+
+void launch_tile(int i, const float *v, Grid G, uint64_t *out, cudaStream_t s, const uint64_t *ref, uint32_t *mbits,
+                 uint32_t *cbits, uint32_t *csum, int tier, uint64_t *low)
+{
+    const TileShape &t = TILE_SHAPES[i];
+    const dim3 grid((G.nx + 31) / 32, (G.ny + t.ty - 1) / t.ty, (G.nz + t.zs - 1) / t.zs);
+    t.fn<<<grid, t.nt, 0, s>>>(v, G, out, ref, mbits, cbits, csum, tier, low);
+}
+
+// the dense gradient of a 3D grid with the requested tile shape, or the tuned one (tuning it
+// on the first pass of this grid shape on this device)
+msc_status eval_tile(msc_handle *h, const float *v, Grid G, uint64_t *out, cudaStream_t s, const uint64_t *ref,
+                     uint32_t *mbits, uint32_t *cbits, uint32_t *csum, int tier, uint64_t *low)
+{
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    int shape = h ? h->tile_req : -1;     // no handle (introspection calls): the tuned shape
+    if (shape < 0) {
+        const auto key = std::make_tuple(dev, G.nx, G.ny, G.nz);
+        {
+            std::lock_guard<std::mutex> lk(g_tile_mu);
+            auto it = g_tile_tuned.find(key);
+            if (it != g_tile_tuned.end()) shape = it->second.best;
+        }
+        if (shape < 0) {
+            // one untimed launch, then every shape once; each writes the same codes to out
+            TileTuning tt;
+            cudaEvent_t e[N_TILE_SHAPES + 1];
+            for (int i = 0; i <= N_TILE_SHAPES; i++) CK(cudaEventCreate(&e[i]));
+            launch_tile(0, v, G, out, s, ref, mbits, cbits, csum, tier, low);
+            CK(cudaEventRecord(e[0], s));
+            for (int i = 0; i < N_TILE_SHAPES; i++) {
+                launch_tile(i, v, G, out, s, ref, mbits, cbits, csum, tier, low);
+                CK(cudaEventRecord(e[i + 1], s));
+            }
+            CK(cudaGetLastError());
+            CK(cudaEventSynchronize(e[N_TILE_SHAPES]));
+            for (int i = 0; i < N_TILE_SHAPES; i++) {
+                CK(cudaEventElapsedTime(&tt.ms[i], e[i], e[i + 1]));
+                if (tt.ms[i] < tt.ms[tt.best]) tt.best = i;
+            }
+            for (int i = 0; i <= N_TILE_SHAPES; i++) cudaEventDestroy(e[i]);
+            {
+                std::lock_guard<std::mutex> lk(g_tile_mu);
+                g_tile_tuned.emplace(key, tt);
+            }
+            if (h) {
+                h->launches[MSC_K_DENSE] += N_TILE_SHAPES + 1;
+                h->tile_used = tt.best;
+            }
+            return MSC_OK;
+        }
+    }
+    if (h) h->tile_used = shape;
+    KL(h, MSC_K_DENSE, s, launch_tile(shape, v, G, out, s, ref, mbits, cbits, csum, tier, low));
+    CK(cudaGetLastError());
+    return MSC_OK;
+}
+
 template <int D> msc_status eval_dense(msc_handle *h, const float *v, Grid G, uint64_t *out, cudaStream_t s,
                                        const uint64_t *ref = nullptr, uint32_t *mbits = nullptr,
                                        uint32_t *cbits = nullptr, uint32_t *csum = nullptr, int tier = 4,
@@ -2151,9 +2271,7 @@ template <int D> msc_status eval_dense(msc_handle *h, const float *v, Grid G, ui
             CK(cudaMemsetAsync(mbits, 0, ((G.n + 31ull) / 32) * 4, s));
             CK(cudaMemsetAsync(cbits, 0, ((G.n + 31ull) / 32) * 4, s));
         }
-        const dim3 grid((G.nx + dense::TX - 1) / dense::TX, (G.ny + dense::TY - 1) / dense::TY,
-                        (G.nz + dense::ZS - 1) / dense::ZS);
-        KL(h, MSC_K_DENSE, s, k_eval_tile<<<grid, 256, 0, s>>>(v, G, out, ref, mbits, cbits, csum, tier, low));
+        CKS(eval_tile(h, v, G, out, s, ref, mbits, cbits, csum, tier, low));
     } else {
         KL(h, MSC_K_DENSE, s, k_eval_dense<D><<<grid_occ((const void *)k_eval_dense<D>, G.n), TPB, 0, s>>>(v, G, out, ref, mbits, cbits, csum, tier));
     }
@@ -2369,7 +2487,7 @@ void account_graph(msc_handle *h, RoundGraph &rg, unsigned active, bool halted)
 template <int D>
 msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t s, FixResult &R)
 {
-    Ctx c = make_ctx(h, o.tier, o.q_max, o.exact_fallback, xi);
+    Ctx c = make_ctx(h, o.tier, o.q_max, o.exact_fallback, xi, o.edit_mode);
     LoopState L{};
     L.max_iters = (unsigned)o.max_iters;
     L.exact_fallback = (unsigned)o.exact_fallback;
@@ -2879,6 +2997,7 @@ const char *msc_status_string(msc_status s)
     case MSC_ERR_OOM: return "MSC_ERR_OOM";
     case MSC_ERR_CUDA: return "MSC_ERR_CUDA";
     case MSC_ERR_CANCELLED: return "MSC_ERR_CANCELLED";
+    case MSC_ERR_UNAVAILABLE: return "MSC_ERR_UNAVAILABLE";
     case MSC_ERR_NOT_CONVERGED: return "MSC_ERR_NOT_CONVERGED";
     case MSC_ERR_DEVICE_TIMEOUT: return "MSC_ERR_DEVICE_TIMEOUT";
     case MSC_ERR_STALLED: return "MSC_ERR_STALLED";
@@ -2903,7 +3022,7 @@ uint64_t msc_device_bytes(int nx, int ny, int nz)
     b += 4 * (n / 8 + 4) + 8 * 4 * n;             // four bitsets; eight index lists
     b += n / 8 + ntop * n / 8 + (d3 ? 12 * n / 8 + 16 * n : 0);   // walk visited sets, spill queues
     b += 2 * n * (1 + ntop + (d3 ? 19 : 0));      // separatrix node words (16 bits each)
-    b += 3 * 4 * n;                               // separatrix seeds (upper estimate)
+    b += (d3 ? 6 : 3) * 4 * n;                    // separatrix seeds (upper estimate)
     b += 8 * n;                                   // pre-round values and list of edited vertices
     return b;
 }
@@ -2924,6 +3043,10 @@ msc_status msc_prepare_original(const float *f, int nx, int ny, int nz, const ms
     if (!h) return fail(MSC_ERR_OOM, "handle allocation failed");
     h->G = make_grid(nx, ny, nz);
     h->D = nz > 1 ? 3 : 2;
+    {
+        const msc_status ts = tile_request(o, &h->tile_req);
+        if (ts != MSC_OK) { delete h; return ts; }
+    }
     auto run = [&]() -> msc_status {
         CK(h->f.alloc(h->G.n));
         CK(h->code_f.alloc(h->G.n));
@@ -2960,6 +3083,7 @@ msc_status msc_fix(msc_handle *h, const float *f_hat, float xi, const msc_option
     if (!(xi > 0.0f) || !std::isfinite(xi)) return fail(MSC_ERR_INVALID_ARG, "xi must be finite and > 0");
     cudaStream_t s = (cudaStream_t)o.stream;
     EntryStream es(s);
+    CKS(tile_request(o, &h->tile_req));
     CKS(alloc_fix_state(h));
     h->prof_mask = (unsigned)o.profile & MSC_PROFILE_ALL;
     struct Flush {
@@ -2973,7 +3097,9 @@ msc_status msc_fix(msc_handle *h, const float *f_hat, float xi, const msc_option
     if (st != MSC_OK) return st;
     CK(cudaEventRecord(h->ev1, s));
     CK(copy_from_device(g_out, h->g.p, (size_t)h->G.n * 4, s));
-    CKS(write_edits(h, xi, o.q_max, s, out));
+    // floating edits: every edited vertex is stored losslessly (state > 0 reads as above a
+    // q_max of 0)
+    CKS(write_edits(h, xi, o.edit_mode == MSC_EDITS_FLOAT ? 0 : o.q_max, s, out));
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
     out->loop_ms = ms;
@@ -3222,6 +3348,97 @@ msc_status msc_unpack_edits(const uint8_t *buf, uint64_t size, msc_edits *out, i
     out->n_lossless = nl;
     out->n_quant = nq;
     *q_max = qm_max;
+    return MSC_OK;
+}
+
+msc_status msc_tile_report(int nx, int ny, int nz, int *chosen, int *shapes, float *ms, int cap, int *n)
+{
+    g_last_error.clear();
+    if (!n) return fail(MSC_ERR_INVALID_ARG, "n is NULL");
+    *n = N_TILE_SHAPES;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); dev = 0; }
+    TileTuning tt;
+    bool tuned = false;
+    {
+        std::lock_guard<std::mutex> lk(g_tile_mu);
+        auto it = g_tile_tuned.find(std::make_tuple(dev, nx, ny, nz));
+        if (it != g_tile_tuned.end()) { tt = it->second; tuned = true; }
+    }
+    for (int i = 0; i < N_TILE_SHAPES && i < cap; i++) {
+        if (shapes) { shapes[3 * i] = 32; shapes[3 * i + 1] = TILE_SHAPES[i].ty; shapes[3 * i + 2] = TILE_SHAPES[i].zs; }
+        if (ms) ms[i] = tuned ? tt.ms[i] : 0.f;
+    }
+    if (chosen) {
+        chosen[0] = tuned ? 32 : 0;
+        chosen[1] = tuned ? TILE_SHAPES[tt.best].ty : 0;
+        chosen[2] = tuned ? TILE_SHAPES[tt.best].zs : 0;
+    }
+    return MSC_OK;
+}
+
+uint64_t msc_kv_bytes(uint64_t n_pairs) { return 32 + 8 * n_pairs; }
+
+msc_status msc_pack_edits_kv(const msc_edits *e, uint8_t *out, uint64_t cap, uint64_t *n_out)
+{
+    g_last_error.clear();
+    if (!e || !n_out) return fail(MSC_ERR_INVALID_ARG, "edits and n_out must be non-NULL");
+    if (e->n_quant) return fail(MSC_ERR_INVALID_ARG, "%llu quantised counts: only floating edits (every edited vertex "
+                                "stored as a value) form key-value pairs", (unsigned long long)e->n_quant);
+    if (e->n_vertices == 0 || e->n_vertices >= (1ull << 31) || e->n_lossless > e->n_vertices)
+        return fail(MSC_ERR_INVALID_ARG, "bad edit record sizes");
+    if (e->n_lossless && (!e->lossless_idx || !e->lossless_val)) return fail(MSC_ERR_INVALID_ARG, "edits lack their pairs");
+    const uint64_t nl = e->n_lossless, size = msc_kv_bytes(nl);
+    *n_out = size;
+    if (!out && cap == 0) return MSC_OK;
+    if (!out || cap < size) return fail(MSC_ERR_INVALID_ARG, "out holds %llu bytes, the record needs %llu",
+                                        (unsigned long long)cap, (unsigned long long)size);
+    uint8_t head[32] = {'M', 'S', 'C', 'E', 2, 0, 0, 0};
+    put_u64(head + 8, e->n_vertices);
+    put_u64(head + 16, nl);
+    memcpy(out, head, 32);
+    uint8_t *ip = out + 32, *vp = out + 32 + 4 * nl;
+    for (uint64_t k = 0; k < nl; k++) {
+        const uint64_t v = e->lossless_idx[k];
+        if (v >= e->n_vertices || (k && v <= e->lossless_idx[k - 1]))
+            return fail(MSC_ERR_INVALID_ARG, "lossless_idx must be increasing vertex ids");
+        for (int b = 0; b < 4; b++) ip[4 * k + b] = (uint8_t)(v >> (8 * b));
+    }
+    memcpy(vp, e->lossless_val, 4 * nl);
+    return MSC_OK;
+}
+
+msc_status msc_unpack_edits_kv(const uint8_t *buf, uint64_t size, msc_edits *out)
+{
+    g_last_error.clear();
+    if (!buf || !out) return fail(MSC_ERR_INVALID_ARG, "buf and out must be non-NULL");
+    memset(out, 0, sizeof *out);
+    if (size < 32 || memcmp(buf, "MSCE", 4) != 0 || buf[4] != 2) return fail(MSC_ERR_INVALID_ARG, "not a key-value edit record");
+    const uint64_t n = get_u64(buf + 8), nl = get_u64(buf + 16);
+    if (n == 0 || n >= (1ull << 31) || nl > n || msc_kv_bytes(nl) != size)
+        return fail(MSC_ERR_INVALID_ARG, "key-value record of %llu bytes does not match its header", (unsigned long long)size);
+    out->q_map = (uint8_t *)host_take(n);
+    out->lossless_idx = (uint64_t *)host_take(nl ? nl * 8 : 8);
+    out->lossless_val = (float *)host_take(nl ? nl * 4 : 4);
+    if (!out->q_map || !out->lossless_idx || !out->lossless_val) {
+        msc_free_edits(out);
+        return fail(MSC_ERR_OOM, "host allocation of edits failed");
+    }
+    memset(out->q_map, 0, n);
+    const uint8_t *ip = buf + 32;
+    for (uint64_t k = 0; k < nl; k++) {
+        uint64_t v = 0;
+        for (int b = 0; b < 4; b++) v |= (uint64_t)ip[4 * k + b] << (8 * b);
+        if (v >= n || (k && v <= out->lossless_idx[k - 1])) {
+            msc_free_edits(out);
+            return fail(MSC_ERR_INVALID_ARG, "key-value record holds an out-of-order or out-of-range vertex");
+        }
+        out->lossless_idx[k] = v;
+        out->q_map[v] = MSC_QMAP_LOSSLESS;
+    }
+    memcpy(out->lossless_val, buf + 32 + 4 * nl, 4 * nl);
+    out->n_vertices = n;
+    out->n_lossless = nl;
     return MSC_OK;
 }
 

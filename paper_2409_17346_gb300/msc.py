@@ -15,7 +15,7 @@ from . import build as _build
 MSC_OK = 0
 STATUS_NAMES = {0: "MSC_OK", 1: "MSC_ERR_INVALID_ARG", 2: "MSC_ERR_OOM", 3: "MSC_ERR_CUDA",
                 4: "MSC_ERR_NOT_CONVERGED", 5: "MSC_ERR_DEVICE_TIMEOUT", 6: "MSC_ERR_STALLED",
-                7: "MSC_ERR_NO_DEVICE", 8: "MSC_ERR_CANCELLED"}
+                7: "MSC_ERR_NO_DEVICE", 8: "MSC_ERR_CANCELLED", 9: "MSC_ERR_UNAVAILABLE"}
 QMAP_LOSSLESS = 0xFF
 
 
@@ -29,7 +29,7 @@ class Options(ctypes.Structure):
     _fields_ = [("tier", ctypes.c_int), ("q_max", ctypes.c_int), ("max_iters", ctypes.c_int),
                 ("exact_fallback", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
                 ("tile_z", ctypes.c_int), ("stream", ctypes.c_void_p), ("record_trace", ctypes.c_int),
-                ("profile", ctypes.c_int), ("small_round", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("small_round", ctypes.c_int), ("edit_mode", ctypes.c_int)]
 
 
 KERNEL_CLASSES = ("dense", "cpass", "edit", "refresh", "rebuild", "sep_init", "sep_update", "sep_targets", "other",
@@ -141,11 +141,22 @@ def load():
     lib.msc_inject_alloc_failures.argtypes = [u64, u64]
     lib.msc_inject_alloc_failures.restype = u64
     lib.msc_server_cancel.argtypes = [vp, u64]
+    lib.msc_tile_report.argtypes = [i, i, i, vp, vp, vp, i, ctypes.POINTER(i)]
+    lib.msc_kv_bytes.argtypes = [u64]
+    lib.msc_kv_bytes.restype = u64
+    lib.msc_pack_edits_kv.argtypes = [ctypes.POINTER(Edits), vp, u64, ctypes.POINTER(u64)]
+    lib.msc_unpack_edits_kv.argtypes = [vp, u64, ctypes.POINTER(Edits)]
+    lib.msc_coded_bound.argtypes = [u64]
+    lib.msc_coded_bound.restype = u64
+    lib.msc_code_record.argtypes = [vp, u64, i, vp, u64, ctypes.POINTER(u64)]
+    lib.msc_decoded_size.argtypes = [vp, u64, ctypes.POINTER(u64)]
+    lib.msc_decode_record.argtypes = [vp, u64, vp, u64, ctypes.POINTER(u64)]
     for name in ("msc_prepare_original", "msc_fix", "msc_apply_edits", "msc_verify", "msc_fix_batch",
                  "msc_gradient_pairs", "msc_critical_cells", "msc_critical_cells_static", "msc_get_stats",
                  "msc_reset_stats", "msc_server_create", "msc_server_submit", "msc_server_wait", "msc_pack_edits",
                  "msc_unpack_edits", "msc_pool_used_bytes", "msc_release_cached_memory", "msc_selftest_barrier",
-                 "msc_server_cancel"):
+                 "msc_server_cancel", "msc_pack_edits_kv", "msc_unpack_edits_kv", "msc_code_record",
+                 "msc_decoded_size", "msc_decode_record", "msc_tile_report"):
         getattr(lib, name).restype = i
     _lib = lib
     return lib
@@ -177,8 +188,11 @@ def _ptr(a):
     raise TypeError("expected a numpy array or a torch tensor")
 
 
+EDITS_QUANTIZED, EDITS_FLOAT = 0, 1
+
+
 def options(tier=4, q_max=6, max_iters=100000, exact_fallback=1, stream=None, record_trace=False,
-            tile=(0, 0, 0), profile=False, small_round=0):
+            tile=(0, 0, 0), profile=False, small_round=0, edit_mode=EDITS_QUANTIZED):
     o = Options()
     load().msc_default_options(ctypes.byref(o))
     o.tier, o.q_max, o.max_iters, o.exact_fallback = tier, q_max, max_iters, exact_fallback
@@ -187,6 +201,7 @@ def options(tier=4, q_max=6, max_iters=100000, exact_fallback=1, stream=None, re
     o.record_trace = int(bool(record_trace))
     o.profile = profile_mask(profile)
     o.small_round = small_round
+    o.edit_mode = int(edit_mode)
     return o
 
 
@@ -341,6 +356,7 @@ def _edits_struct(edits):
     e = Edits()
     e.n_vertices = qm.size
     e.n_lossless = li.size
+    e.n_quant = int(np.count_nonzero((qm != 0) & (qm != QMAP_LOSSLESS)))
     e.q_map = qm.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
     e.lossless_idx = li.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
     e.lossless_val = lv.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
@@ -374,6 +390,52 @@ def unpack_edits(buf, shape):
     finally:
         lib.msc_free_edits(ctypes.byref(e))
     return out, q.value
+
+
+def pack_edits_kv(edits):
+    """Floating edits (edit_mode 1) as a key-value record (numpy uint8 array)."""
+    lib = load()
+    e, _keep = _edits_struct(edits)
+    n = ctypes.c_uint64(0)
+    _check(lib.msc_pack_edits_kv(ctypes.byref(e), None, 0, ctypes.byref(n)))
+    out = np.zeros(n.value, np.uint8)
+    _check(lib.msc_pack_edits_kv(ctypes.byref(e), out.ctypes.data_as(ctypes.c_void_p), n.value, ctypes.byref(n)))
+    return out
+
+
+def unpack_edits_kv(buf, shape):
+    """Edit record (dict as Handle.fix returns) from a key-value record."""
+    lib = load()
+    b = np.ascontiguousarray(buf, np.uint8)
+    e = Edits()
+    _check(lib.msc_unpack_edits_kv(b.ctypes.data_as(ctypes.c_void_p), b.size, ctypes.byref(e)))
+    return _edits_to_py(e, shape, _EditsOwner(e))
+
+
+def code_record(rec, level=3):
+    """Lossless coding of a record (zstd frame, Sec. 4.7 / 5.5): numpy uint8 array."""
+    lib = load()
+    r = np.ascontiguousarray(rec, np.uint8)
+    cap = int(lib.msc_coded_bound(r.size))
+    if cap == 0:
+        _check(lib.msc_code_record(None, 0, level, None, 0, ctypes.byref(ctypes.c_uint64(0))))
+    out = np.zeros(cap, np.uint8)
+    n = ctypes.c_uint64(0)
+    _check(lib.msc_code_record(r.ctypes.data_as(ctypes.c_void_p), r.size, int(level),
+                               out.ctypes.data_as(ctypes.c_void_p), cap, ctypes.byref(n)))
+    return out[: n.value].copy()
+
+
+def decode_record(coded):
+    """Inverse of code_record."""
+    lib = load()
+    c = np.ascontiguousarray(coded, np.uint8)
+    n = ctypes.c_uint64(0)
+    _check(lib.msc_decoded_size(c.ctypes.data_as(ctypes.c_void_p), c.size, ctypes.byref(n)))
+    out = np.zeros(max(n.value, 1), np.uint8)
+    _check(lib.msc_decode_record(c.ctypes.data_as(ctypes.c_void_p), c.size, out.ctypes.data_as(ctypes.c_void_p),
+                                 out.size, ctypes.byref(n)))
+    return out[: n.value]
 
 
 def fix_batch(handles, f_hats, xis, g_outs=None, **kw):
@@ -526,6 +588,23 @@ def critical_cells_static(field_ptr, shape, rows_ptr, dims_ptr, cap, stream=None
     n = ctypes.c_uint64(0)
     _check(load().msc_critical_cells_static(field_ptr, nx, ny, nz, rows_ptr, dims_ptr, cap, ctypes.byref(n), stream))
     return n.value
+
+
+def tile_report(shape):
+    """The tile autotuner's record for a 3D grid on the current device: dict with the
+    instantiated shapes, their times on the tuning pass (ms) and the shape kept (None if the
+    grid was not tuned yet)."""
+    lib = load()
+    nx, ny, nz = dims_of(shape)
+    n = ctypes.c_int(0)
+    _check(lib.msc_tile_report(nx, ny, nz, None, None, None, 0, ctypes.byref(n)))
+    chosen = np.zeros(3, np.int32)
+    shapes = np.zeros((n.value, 3), np.int32)
+    ms = np.zeros(n.value, np.float32)
+    _check(lib.msc_tile_report(nx, ny, nz, chosen.ctypes.data_as(ctypes.c_void_p), shapes.ctypes.data_as(ctypes.c_void_p),
+                               ms.ctypes.data_as(ctypes.c_void_p), n.value, ctypes.byref(n)))
+    return {"shapes": [tuple(int(v) for v in r) for r in shapes], "ms": [float(v) for v in ms],
+            "chosen": tuple(int(v) for v in chosen) if chosen[0] else None}
 
 
 def device_bytes(shape):

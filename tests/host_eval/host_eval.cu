@@ -255,10 +255,11 @@ extern "C" int host_spass(const float *f, const float *g1, const float *g2, cons
                   : spass_of<2>(f, g1, g2, state, G, exact_fallback, T_out, X_out, ncase);
 }
 
-// Eq. 2 as the edit kernel applies it: out_g[v * (q_max + 2) + k] and out_state[...] after
-// k = 0 (the re-clamped base) .. q_max + 1 edits of vertex v
-extern "C" int host_edit_sequence(const float *f, const float *fhat, uint32_t n, float xi, int q_max, float *out_g,
-                                  uint8_t *out_state)
+// Eq. 2 as the edit kernel applies it: out_g[v * K + k] and out_state[...] after k = 0 (the
+// re-clamped base) .. K - 1 edits of vertex v, K = q_max + 2 (quantised) or 0xEF + 2
+// (floating edits, edit_mode 1: no cap on the steps but the state byte's)
+extern "C" int host_edit_sequence(const float *f, const float *fhat, uint32_t n, float xi, int q_max, int edit_mode,
+                                  float *out_g, uint8_t *out_state)
 {
     using namespace msc;
     std::vector<float> g(n);
@@ -270,14 +271,15 @@ extern "C" int host_edit_sequence(const float *f, const float *fhat, uint32_t n,
     c.state = st.data();
     c.xi = xi;
     c.qmax = q_max;
+    c.qcap = edit_mode ? 0xEF : q_max;
     c.step = xi / (float)(1 << q_max);
-    const int K = q_max + 2;
+    const int K = c.qcap + 2;
     for (uint32_t v = 0; v < n; v++) {
         g[v] = clamp_base(f[v], fhat[v], xi);
         out_g[(size_t)v * K] = g[v];
         out_state[(size_t)v * K] = 0;
         for (int k = 1; k < K; k++) {
-            if (st[v] <= q_max) edit_apply(c, 1, 0, v);   // a quantised-step item (not a restore)
+            if (st[v] <= c.qcap) edit_apply(c, 1, 0, v);   // a quantised-step item (not a restore)
             out_g[(size_t)v * K + k] = g[v];
             out_state[(size_t)v * K + k] = st[v];
         }

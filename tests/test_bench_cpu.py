@@ -21,7 +21,7 @@ def test_reference_arm_json_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "GB/s"
     assert d["value"] > 0 and d["higher_is_better"] is True
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == os.cpu_count()
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
 
 
@@ -36,3 +36,19 @@ def test_class_bytes_defined_for_bandwidth_classes():
     r = bench.class_bytes("rounds", tot, n, 1, 3)
     assert r == 1000 * n / 8192.0 + 16.0 * 300 + 22.0 * 100 + 36.0 * 200
     assert set(bench.CLASS_KERNELS) >= {"dense", "cpass", "edit", "refresh", "rebuild", "sep_seed", "rounds"}
+
+
+def test_configs_cover_the_workloads():
+    """Every configuration names its generator, bound and tier; --size shrinks 3D sides and
+    2D grids alike."""
+    import argparse
+    assert set(bench.CONFIGS) == {1, 2, 3, 4}
+    for k, c in bench.CONFIGS.items():
+        a = argparse.Namespace(config=k, size=None, rel=None, tier=None)
+        cfg = bench.config_of(a)
+        assert cfg["tier"] in (3, 4) and cfg["rel"] in (1e-3, 1e-4)
+        d = bench.workload_desc(cfg, (64, 64) if k < 3 else (8, 8, 8))
+        assert "%g" not in d and "%d" not in d and "xi=" in d
+    a = argparse.Namespace(config=2, size=100, rel=None, tier=None)
+    assert bench.config_of(a)["size"] == (100, 200)
+    assert bench.CONFIGS[3]["batch"] == 8

@@ -73,3 +73,24 @@ def test_pack_rejects_inconsistent_edits(lib):
     junk[0] = ord("X")
     with pytest.raises(lib.MscError, match="header"):
         lib.unpack_edits(junk, f.shape)
+
+
+def test_coded_records_rebuild_the_fix(lib):
+    """Both stored forms of a fix go through the lossless coder and back: the quantised
+    record (packed, then coded) and the floating-edit key-value record (coded); each rebuilds
+    g bit-exactly through msc_apply_edits."""
+    if lib.load().msc_coded_bound(16) == 0:
+        pytest.skip("no zstd library on this machine")
+    f, fh, xi, _ = synth.config_case("kolmogorov3d", size=24, rel=1e-3)
+    g, ed = lib.Handle(f).fix(fh, xi, tier=4)
+    packed = lib.pack_edits(ed, 6)
+    coded = lib.code_record(packed, 3)
+    back, q_max = lib.unpack_edits(lib.decode_record(coded), f.shape)
+    assert q_max == 6
+    assert np.array_equal(lib.apply_edits(fh, xi, 6, back).view(np.uint32), g.view(np.uint32))
+    gf, edf = lib.Handle(f).fix(fh, xi, tier=4, edit_mode=1)
+    kv = lib.pack_edits_kv(edf)
+    backf = lib.unpack_edits_kv(lib.decode_record(lib.code_record(kv, 3)), f.shape)
+    assert np.array_equal(lib.apply_edits(fh, xi, 6, backf).view(np.uint32), gf.view(np.uint32))
+    ref = oracle.fix(f, fh, xi, tier=4, edit_mode=1)
+    assert np.array_equal(gf.view(np.uint32), ref["g"].view(np.uint32))

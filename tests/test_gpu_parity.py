@@ -73,17 +73,17 @@ FIX_CASES = [
 ]
 
 
-def _check_fix(lib, f, fh, xi, tier, q_max=6, exact_fallback=1, small_round=0):
-    ref = oracle.fix(f, fh, xi, tier=tier, q_max=q_max, exact_fallback=exact_fallback)
+def _check_fix(lib, f, fh, xi, tier, q_max=6, exact_fallback=1, small_round=0, edit_mode=0):
+    ref = oracle.fix(f, fh, xi, tier=tier, q_max=q_max, exact_fallback=exact_fallback, edit_mode=edit_mode)
     assert ref["status"] == 0
     h = lib.Handle(f)
     g, ed = h.fix(fh, xi, tier=tier, q_max=q_max, exact_fallback=exact_fallback, record_trace=True,
-                  small_round=small_round)
+                  small_round=small_round, edit_mode=edit_mode)
     assert np.array_equal(g.view(np.uint32), ref["g"].view(np.uint32))
     assert (ed["n_iters_c"], ed["n_iters_s"]) == (ref["n_c"], ref["n_s"])
     assert ed["n_fallback_iters"] == ref["n_exact_iters"]
     assert np.array_equal(ed["trace"], ref["trace"][:, :5])
-    qm, li, lv = oracle.edits_from_state(f, fh, xi, ref["state"], ref["g"])
+    qm, li, lv = oracle.edits_from_state(f, fh, xi, ref["state"], ref["g"], edit_mode=edit_mode)
     assert np.array_equal(ed["q_map"].reshape(-1), qm)
     assert np.array_equal(ed["lossless_idx"].astype(np.int64), li)
     assert np.array_equal(ed["lossless_val"].view(np.uint32), lv.view(np.uint32))
@@ -150,6 +150,52 @@ def test_fix_loop_matches_oracle_large(lib, idx):
     if big_rounds:
         assert int((tr[:, 1] + tr[:, 2] >= 8192).sum()) >= 3
     assert ed["n_iters_c"] > 100
+
+
+@pytest.mark.parametrize("idx", [0, 3, 5, 7])
+@pytest.mark.parametrize("q_max", [2, 6])
+def test_floating_edit_mode_matches_oracle(lib, idx, q_max):
+    """Floating edits (no cap on the step count; every edit stored as an exact value): the
+    same bit-exact agreement with the oracle, round by round."""
+    name, kw = FIX_CASES[idx]
+    f, fh, xi, _ = synth.config_case(name, **kw)
+    g, ed = _check_fix(lib, f, fh, xi, 4, q_max=q_max, edit_mode=1)
+    assert ed["n_quant"] == 0 and set(np.unique(ed["q_map"])) <= {0, 0xFF}
+    g2 = lib.apply_edits(fh, xi, q_max, ed)
+    assert np.array_equal(g2.view(np.uint32), g.view(np.uint32))
+
+
+def test_floating_edit_mode_rejects_q_max_7(lib):
+    f, fh, xi, _ = synth.config_case("gauss2d", seed=4, size=(20, 20), rel=1e-2)
+    with pytest.raises(lib.MscError) as e:
+        lib.Handle(f).fix(fh, xi, q_max=7, edit_mode=1)
+    assert e.value.status == 1
+
+
+def test_every_tile_shape_matches_oracle(lib):
+    """The dense 3D gradient gives the oracle's result with every instantiated tile shape (the
+    grid spans several tiles, slabs and a ragged edge in each direction), and the autotuner
+    keeps one of them."""
+    f, fh, xi, _ = synth.config_case("kolmogorov3d", seed=12, size=37, rel=3e-3)
+    f = np.ascontiguousarray(f[:, :29, :])
+    fh = np.ascontiguousarray(fh[:, :29, :])
+    ref = oracle.fix(f, fh, xi, tier=4)
+    pairs = oracle.gradient_pairs(f)
+    shapes = lib.tile_report(f.shape)["shapes"]
+    assert len(shapes) >= 4
+    for tile in shapes:
+        h = lib.Handle(f, opts=lib.options(tile=tile))
+        g, ed = h.fix(fh, xi, tier=4, tile=tile)
+        h.close()
+        assert np.array_equal(g.view(np.uint32), ref["g"].view(np.uint32)), tile
+        assert (ed["n_iters_c"], ed["n_iters_s"]) == (ref["n_c"], ref["n_s"]), tile
+    g, _ = lib.Handle(f).fix(fh, xi, tier=4)
+    rep = lib.tile_report(f.shape)
+    assert rep["chosen"] in shapes and all(m > 0 for m in rep["ms"])
+    assert np.array_equal(g.view(np.uint32), ref["g"].view(np.uint32))
+    assert np.array_equal(lib.gradient_pairs(f), pairs)
+    with pytest.raises(lib.MscError):
+        lib.Handle(f, opts=lib.options(tile=(32, 5, 16)))
 
 
 @pytest.mark.parametrize("q_max", [1, 3, 7])

@@ -50,7 +50,7 @@ def lib():
     h.host_codes.argtypes = [vp, i, i, i, vp]
     h.host_dirty.argtypes = [vp, vp, vp, i, i, i, vp]
     h.host_spass.argtypes = [vp, vp, vp, vp, i, i, i, i, vp, vp, ctypes.POINTER(ctypes.c_uint64)]
-    h.host_edit_sequence.argtypes = [vp, vp, ctypes.c_uint32, ctypes.c_float, i, vp, vp]
+    h.host_edit_sequence.argtypes = [vp, vp, ctypes.c_uint32, ctypes.c_float, i, i, vp, vp]
     h.host_spass_t3.argtypes = [vp, vp, vp, i, i, i, i, vp, vp]
     return h
 
@@ -177,11 +177,12 @@ def test_device_separatrix_state_matches_oracle_spass(lib, idx):
         assert (nc.value > 0) == (len(cases) > 0)
 
 
-@pytest.mark.parametrize("q_max", [1, 3, 6, 7])
-def test_device_edit_arithmetic_matches_oracle(lib, q_max):
-    """Every edit a vertex can take, from the re-clamped base through q_max quantised steps to
-    the floor, on values of three magnitudes, signed zeros, subnormals, bases 2 xi away (so the
-    clamp matters) and bases equal to f."""
+@pytest.mark.parametrize("q_max,edit_mode", [(1, 0), (3, 0), (6, 0), (7, 0), (2, 1), (6, 1)])
+def test_device_edit_arithmetic_matches_oracle(lib, q_max, edit_mode):
+    """Every edit a vertex can take, from the re-clamped base through q_max quantised steps
+    (every step down to f - xi for floating edits) to the floor, on values of three
+    magnitudes, signed zeros, subnormals, bases 2 xi away (so the clamp matters) and bases
+    equal to f."""
     rng = np.random.default_rng(100 + q_max)
     for xi in (1e-4, 1e-2, 0.5):
         n = 3000
@@ -190,18 +191,23 @@ def test_device_edit_arithmetic_matches_oracle(lib, q_max):
         xi = float(np.float32(xi))
         fh = (f + rng.uniform(-2 * xi, 2 * xi, n)).astype(np.float32)
         fh[60:80] = f[60:80]
-        K = q_max + 2
+        # floating edits: no cap but the state byte's 0xEF steps, reached only where a step is
+        # below half the float spacing of f and rounds back up to f - xi
+        cap = 0xEF if edit_mode else q_max
+        K = cap + 2
         g = np.zeros(n * K, np.float32)
         st = np.zeros(n * K, np.uint8)
-        lib.host_edit_sequence(f.ctypes.data, fh.ctypes.data, n, xi, q_max, g.ctypes.data, st.ctypes.data)
+        lib.host_edit_sequence(f.ctypes.data, fh.ctypes.data, n, xi, q_max, edit_mode, g.ctypes.data, st.ctypes.data)
         g, st = g.reshape(n, K), st.reshape(n, K)
-        lb, ub, fc, qv = oracle.edit_values(f, fh, xi, q_max)
+        lb, ub, fc, qv = oracle.edit_values(f, fh, xi, q_max, n_steps=K)
         assert np.array_equal(g[:, 0].view(np.uint32), fc.view(np.uint32))
         was_floor = np.zeros(n, bool)
         for k in range(1, K):
             quant, floor = st[:, k] == k, st[:, k] == 0xF0
             assert np.all(quant | floor)
-            if k <= q_max:
+            if edit_mode:
+                assert k < K - 1 or np.all(floor)              # past the cap every vertex is at its floor
+            if k <= cap:
                 assert np.array_equal(g[quant, k].view(np.uint32), qv[quant, k].view(np.uint32))
                 assert np.all(qv[quant, k] >= lb[quant])
                 first = floor & ~was_floor

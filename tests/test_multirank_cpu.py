@@ -21,9 +21,12 @@ def _rank_main(rank, world, port, q):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
+    import argparse
     import bench
     t = bench.max_over_ranks(10.0 * (rank + 1), dist, "cpu")
-    f, fh, xi = bench.workload(8, 1e-3, rank)
+    cfg = bench.config_of(argparse.Namespace(config=4, size=8, rel=1e-3, tier=None))
+    f, fh, xi = bench.workload(cfg, rank)
+    assert cfg["seed"] + rank == bench.replica_seed(rank)
     q.put((rank, t, bench.replica_seed(rank), float(f.sum()), xi))
     dist.barrier()
     dist.destroy_process_group()

@@ -1119,3 +1119,39 @@ def test_results_do_not_depend_on_threads(name, kw):
     assert np.array_equal(one["state"], many["state"])
     assert np.array_equal(one["trace"], many["trace"])
     assert vone == vmany
+
+
+# --------------------------------------------------------------------------------------
+# floating edits (Sec. 4.7: every edit stored as a float, so no cap on the step count)
+# --------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name,kw,tier", [("gauss2d", dict(seed=3, size=(40, 52), rel=1e-2), 3),
+                                          ("kolmogorov3d", dict(size=12, rel=1e-2), 4)])
+def test_floating_edits_loop(name, kw, tier):
+    """The floating-edit loop converges with |f - g| <= xi and the MSC of f; every vertex that
+    did not reach its floor holds exactly the value after its count of steps (Eq. 2 without
+    the q_max cap), some counts exceed q_max, and the stored (index, value) pairs rebuild g."""
+    f, fh, xi, _ = synth.config_case(name, **kw)
+    q_max = 2
+    r = oracle.fix(f, fh, xi, tier=tier, q_max=q_max, edit_mode=1)
+    assert r["status"] == 0
+    g, st = r["g"], r["state"].reshape(-1)
+    assert _exact_bound_ok(f, g, xi)
+    v = oracle.verify(f, g)
+    keys = [k for k in oracle.REPORT_KEYS if k.startswith(("fp", "fn", "term"))]
+    if tier == 4:
+        keys = list(oracle.REPORT_KEYS)
+    assert all(v[k] == 0 for k in keys), v
+    lb, ub, fc, qv = oracle.edit_values(f, fh, xi, q_max, n_steps=0xEF + 1)
+    quant = st <= 0xEF
+    assert np.array_equal(g.reshape(-1)[quant].view(np.uint32),
+                          qv[np.nonzero(quant)[0], st[quant]].view(np.uint32))
+    assert np.any(quant & (st > q_max))
+    q_map, idx, val = oracle.edits_from_state(f, fh, xi, r["state"], g, edit_mode=1)
+    assert set(np.unique(q_map)) <= {0, 0xFF}
+    assert np.array_equal(idx, np.nonzero((st > 0) | (fc.view(np.uint32) != fh.reshape(-1).view(np.uint32)))[0])
+    g2 = oracle.apply_edits(fh, xi, q_max, q_map, idx, val)
+    assert np.array_equal(g2.view(np.uint32), g.view(np.uint32))
+    # the same loop with quantised edits snaps vertices to the floor after q_max steps
+    rq = oracle.fix(f, fh, xi, tier=tier, q_max=q_max)
+    assert rq["status"] == 0 and np.all((rq["state"] <= q_max) | (rq["state"] >= 0xF0))
