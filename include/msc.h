@@ -79,6 +79,10 @@ typedef struct {
                             cap on their number (a vertex snaps to the floor only when the next
                             step would pass f - xi), and every edited vertex stored losslessly
                             as an (index, value) pair; q_max must then be 1..6 */
+    int cluster_round;   /* of the rounds that run in the persistent round kernel, those that
+                            follow a round which edited fewer than this many vertices run in one
+                            thread-block cluster (hardware barriers between their phases):
+                            0 (default) = 1024; 1 = never.  Results do not depend on it. */
 } msc_options;
 
 #define MSC_EDITS_QUANTIZED 0
@@ -119,6 +123,9 @@ typedef struct {
     double round_phase_ms[4];    /* persistent round kernel, device clock of its first block:
                                     C-pass, decision and edits, order changes, refresh and
                                     rebuild (each up to the end of its grid barrier) */
+    uint64_t cluster_launches;   /* launches of the round kernel's cluster form (counted also
+                                    in launches[MSC_K_ROUNDS]) and the rounds they ran */
+    uint64_t cluster_rounds;
 } msc_stats;
 
 /* one edit round: kind 0 = C-pass (false critical cells), 1 = S-pass (separatrices);
@@ -174,7 +181,8 @@ const char *msc_status_string(msc_status s);
 const char *msc_last_error(void);
 
 /* Fill *opt with defaults: tier 4, q_max 6, max_iters 100000, exact_fallback 1,
- * tiles 0, stream NULL, record_trace 0, profile 0, small_round 0, edit_mode quantized. */
+ * tiles 0, stream NULL, record_trace 0, profile 0, small_round 0, edit_mode quantized,
+ * cluster_round 0. */
 void msc_default_options(msc_options *opt);
 
 /* Sec. 4.2 (discrete gradient of f), Sec. 3.1 (critical cells, gradient paths): compute

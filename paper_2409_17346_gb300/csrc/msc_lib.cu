@@ -684,6 +684,7 @@ __global__ void k_init_g(const float *f, const float *fh, float *g, uint8_t *sta
 }
 
 constexpr unsigned long long SMALL_ROUND = 8192;   // edited vertices below which rounds run small grids
+constexpr unsigned long long CLUSTER_ROUND = 1024; // and below which they run in one thread-block cluster
 
 // a round kernel of a captured round graph does nothing once the phase is over (halt) or
 // the rounds have become small (leave)
@@ -1026,9 +1027,28 @@ __device__ bool grid_sync(GridBarrier *gb, LoopState *ls, unsigned long long tim
     return ok != 0;
 }
 
-template <int D>
+// Barrier between the phases of a round.  Full-grid form (cooperative launch): the bounded
+// grid barrier above.  Cluster form (the whole grid is one thread-block cluster): the
+// hardware cluster barrier with release/acquire at cluster scope, then a fence so that the
+// data other blocks wrote is read fresh, as after the grid barrier.  It waits for every
+// thread of every block of the cluster; every block reaches it the same number of times,
+// because each return below is taken by all threads alike (after a barrier, from the same
+// counters).
+template <bool CL> __device__ __forceinline__ bool round_sync(GridBarrier *gb, LoopState *ls)
+{
+    if constexpr (CL) {
+        asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+        __threadfence();
+        return true;
+    } else {
+        return grid_sync(gb, ls);
+    }
+}
+
+template <int D, bool CL>
 __global__ void __launch_bounds__(TPB, 2) k_rounds(Ctx c, GridBarrier *gb, Counters *cnt2, uint32_t *blk2, unsigned max_rounds,
-                                                unsigned long long leave_items)
+                                                unsigned long long leave_items, unsigned long long leave_below,
+                                                unsigned long long blk_limit)
 {
     __shared__ union {
         uint16_t q[TPB / 32][32 * 32];   // P1: compacted anchors of a block, per warp
@@ -1067,7 +1087,7 @@ __global__ void __launch_bounds__(TPB, 2) k_rounds(Ctx c, GridBarrier *gb, Count
                             [&](uint32_t b) { nl[atomicAdd(nn, 1ull)] = b; });
         }
         tally_end(tally, cc);
-        if (!grid_sync(gb, ls)) return;
+        if (!round_sync<CL>(gb, ls)) return;
         phase_end(0);
         // P2: the decision, taken alike by every thread from the finished counters (block 0
         // records it), then the edits
@@ -1089,7 +1109,7 @@ __global__ void __launch_bounds__(TPB, 2) k_rounds(Ctx c, GridBarrier *gb, Count
             }
             st_flush(se, c.Elist, &K->nE);
         }
-        if (!grid_sync(gb, ls)) return;
+        if (!round_sync<CL>(gb, ls)) return;
         phase_end(1);
         // P3: edited vertices whose order changed mark their windows dirty
         st_init(u.sd);
@@ -1104,7 +1124,7 @@ __global__ void __launch_bounds__(TPB, 2) k_rounds(Ctx c, GridBarrier *gb, Count
             }
             st_flush(u.sd, c.Dlist, &K->nD);
         }
-        if (!grid_sync(gb, ls)) return;
+        if (!round_sync<CL>(gb, ls)) return;
         phase_end(2);
         // P4: new codes and mismatch bits of the dirty anchors; clear the round's sets
         const unsigned long long nD = K->nD, nT = K->nT;
@@ -1131,9 +1151,14 @@ __global__ void __launch_bounds__(TPB, 2) k_rounds(Ctx c, GridBarrier *gb, Count
             atomicAdd(&ls->refresh_items, nD);
             ls->nbl[cur] = 0;                    // list cur was read in P1; it is the next "next"
         }
-        if (!grid_sync(gb, ls)) return;
+        if (!round_sync<CL>(gb, ls)) return;
         phase_end(3);
-        if (items >= leave_items) return;        // a large round: the next rounds run full grids
+        // a large round: the next rounds run full grids; a tiny one in the full-grid form: the
+        // next rounds run in one cluster.  The cluster form also leaves, and the full-grid form
+        // keeps the rounds, while the next round's C-pass lists more blocks than the cluster has
+        // warps to share them (the list is final after the barrier above, the same for all).
+        const bool few_blocks = ls->nbl[nxt] <= blk_limit;
+        if (items >= leave_items || (CL && !few_blocks) || (items < leave_below && few_blocks)) return;
     }
 }
 
@@ -1953,6 +1978,7 @@ void fill_defaults(msc_options *o)
     o->profile = 0;
     o->small_round = 0;
     o->edit_mode = MSC_EDITS_QUANTIZED;
+    o->cluster_round = 0;
 }
 
 msc_status check_options(const msc_options *o)
@@ -1961,6 +1987,7 @@ msc_status check_options(const msc_options *o)
     if (o->q_max < 1 || o->q_max > 7) return fail(MSC_ERR_INVALID_ARG, "q_max must be 1..7 (got %d)", o->q_max);
     if (o->max_iters < 0) return fail(MSC_ERR_INVALID_ARG, "max_iters must be >= 0");
     if (o->small_round < 0) return fail(MSC_ERR_INVALID_ARG, "small_round must be >= 0");
+    if (o->cluster_round < 0) return fail(MSC_ERR_INVALID_ARG, "cluster_round must be >= 0");
     if (o->edit_mode != MSC_EDITS_QUANTIZED && o->edit_mode != MSC_EDITS_FLOAT)
         return fail(MSC_ERR_INVALID_ARG, "edit_mode must be 0 (quantized) or 1 (float)");
     if (o->edit_mode == MSC_EDITS_FLOAT && o->q_max > 6)
@@ -1988,6 +2015,7 @@ struct msc_handle {
     DevBuf<uint32_t> Tbits, Xbits, Dbits, Tlist, Xlist, Dlist, Elist, Mbits, Cbits, Csum, Cblk, Cblk2;
     DevBuf<GridBarrier> bar;
     int rounds_grid = 0;   // blocks of the persistent round kernel (0: one per SM)
+    uint64_t cluster_launches = 0, cluster_rounds = 0;   // the round kernel's cluster form
     int tile_req = -1;     // tile shape of the dense 3D gradient the current call asks for (-1: tuned)
     int tile_used = -1;    // the shape its last dense pass ran with
     DevBuf<uint32_t> vis_v, vis_top, vis_tri, ovf0, ovf1;
@@ -2484,6 +2512,42 @@ void account_graph(msc_handle *h, RoundGraph &rg, unsigned active, bool halted)
     cudaGetLastError();
 }
 
+// blocks of the cluster form of the round kernel on the current device: 16 where a cluster
+// of that size can be resident (a size beyond the portable 8), else 8, else 0 (no cluster form)
+template <int D> int round_cluster_size()
+{
+    static std::mutex mu;
+    static std::map<int, int> by_dev;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return 0; }
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = by_dev.find(dev);
+    if (it != by_dev.end()) return it->second;
+    int best = 0;
+    if (cudaFuncSetAttribute(k_rounds<D, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+        cudaGetLastError();
+    for (int cs : {16, 8}) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)cs);
+        cfg.blockDim = dim3(TPB);
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, k_rounds<D, true>, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            n = 0;
+        }
+        if (n >= 1) { best = cs; break; }
+    }
+    by_dev[dev] = best;
+    return best;
+}
+
 template <int D>
 msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t s, FixResult &R)
 {
@@ -2501,7 +2565,7 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
     int rgrid = h->rounds_grid > 0 ? h->rounds_grid : sm_count();
     {
         int occ = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)k_rounds<D>, TPB, 0) != cudaSuccess) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)k_rounds<D, false>, TPB, 0) != cudaSuccess) {
             cudaGetLastError();
             occ = 0;
         }
@@ -2510,6 +2574,9 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
     const bool persistent = coop_supported() && rgrid > 0;
     L.rounds_kernel = persistent ? 1 : 0;
     const unsigned long long small_thr = o.small_round > 0 ? (unsigned long long)o.small_round : SMALL_ROUND;
+    // the rounds after one that edited fewer than clus_thr vertices run in one cluster
+    const unsigned long long clus_thr = o.cluster_round > 0 ? (unsigned long long)o.cluster_round : CLUSTER_ROUND;
+    const int csize = persistent && o.cluster_round != 1 ? round_cluster_size<D>() : 0;
     L.small_round = small_thr;
     CK(cudaMemcpyAsync(h->ls.p, &L, sizeof L, cudaMemcpyHostToDevice, s));
     KL(h, MSC_K_OTHER, s, k_init_g<<<grid_occ((const void *)k_init_g, h->G.n), TPB, 0, s>>>(h->f.p, h->fhat.p, h->g.p, h->state.p, h->G.n, xi));
@@ -2544,10 +2611,30 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
             uint32_t *blk2 = h->Cblk2.p;
             GridBarrier *gb = h->bar.p;
             unsigned max_rounds = 1u << 30;
-            unsigned long long leave = small_thr;
-            void *args[] = {(void *)&c, (void *)&gb, (void *)&cnt2, (void *)&blk2, (void *)&max_rounds, (void *)&leave};
+            // the cluster form's C-pass: up to two listed blocks per warp
+            unsigned long long blk_limit = 2ull * (unsigned long long)csize * (TPB / 32);
+            const bool tiny = csize > 0 && L.last_items < clus_thr && L.nblk <= blk_limit;
+            unsigned long long leave = tiny ? clus_thr : small_thr, below = !tiny && csize > 0 ? clus_thr : 0;
             cudaError_t le = cudaSuccess;
-            KL(h, MSC_K_ROUNDS, s, le = cudaLaunchCooperativeKernel((const void *)k_rounds<D>, dim3(rgrid), dim3(TPB), args, 0, s));
+            if (tiny) {
+                cudaLaunchConfig_t cfg = {};
+                cudaLaunchAttribute attr[1];
+                attr[0].id = cudaLaunchAttributeClusterDimension;
+                attr[0].val.clusterDim.x = (unsigned)csize;
+                attr[0].val.clusterDim.y = 1;
+                attr[0].val.clusterDim.z = 1;
+                cfg.gridDim = dim3((unsigned)csize);
+                cfg.blockDim = dim3(TPB);
+                cfg.stream = s;
+                cfg.attrs = attr;
+                cfg.numAttrs = 1;
+                KL(h, MSC_K_ROUNDS, s, le = cudaLaunchKernelEx(&cfg, k_rounds<D, true>, c, gb, cnt2, blk2, max_rounds, leave, below,
+                                                                blk_limit));
+            } else {
+                void *args[] = {(void *)&c, (void *)&gb, (void *)&cnt2, (void *)&blk2, (void *)&max_rounds, (void *)&leave,
+                                (void *)&below, (void *)&blk_limit};
+                KL(h, MSC_K_ROUNDS, s, le = cudaLaunchCooperativeKernel((const void *)k_rounds<D, false>, dim3(rgrid), dim3(TPB), args, 0, s));
+            }
             if (le != cudaSuccess) return fail(MSC_ERR_CUDA, "persistent round kernel launch failed: %s", cudaGetErrorString(le));
             KL(h, MSC_K_OTHER, s, k_rounds_leave<<<1, 1, 0, s>>>(ls));
             KL(h, MSC_K_REBUILD, s, k_list_blocks<<<grid_occ((const void *)k_list_blocks, h->G.n / 1024 + 1), TPB, 0, s>>>(c));
@@ -2557,6 +2644,10 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
             CK(cudaStreamSynchronize(s));
             prev_iters = L.iters;
             h->items[MSC_K_ROUNDS] += L.iters - L0.iters;
+            if (tiny) {
+                h->cluster_launches++;
+                h->cluster_rounds += L.iters - L0.iters;
+            }
             for (int q = 0; q < 4; q++) h->round_phase_ns[q] += L.phase_ns[q] - L0.phase_ns[q];
             fix_work[0] += L.edit_items - L0.edit_items;
             fix_work[1] += L.refresh_items - L0.refresh_items;
@@ -3530,6 +3621,8 @@ msc_status msc_get_stats(msc_handle *h, msc_stats *out)
     }
     for (int i = 0; i < 3; i++) out->round_work[i] = h->round_work[i];
     for (int i = 0; i < 4; i++) out->round_phase_ms[i] = h->round_phase_ns[i] * 1e-6;
+    out->cluster_launches = h->cluster_launches;
+    out->cluster_rounds = h->cluster_rounds;
     return MSC_OK;
 }
 
@@ -3539,6 +3632,7 @@ msc_status msc_reset_stats(msc_handle *h)
     for (int i = 0; i < 12; i++) { h->launches[i] = 0; h->ms[i] = 0.0; h->timed[i] = 0; h->items[i] = 0; }
     for (int i = 0; i < 3; i++) h->round_work[i] = 0;
     for (int i = 0; i < 4; i++) h->round_phase_ns[i] = 0;
+    h->cluster_launches = h->cluster_rounds = 0;
     return MSC_OK;
 }
 

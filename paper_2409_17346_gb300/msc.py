@@ -29,7 +29,8 @@ class Options(ctypes.Structure):
     _fields_ = [("tier", ctypes.c_int), ("q_max", ctypes.c_int), ("max_iters", ctypes.c_int),
                 ("exact_fallback", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
                 ("tile_z", ctypes.c_int), ("stream", ctypes.c_void_p), ("record_trace", ctypes.c_int),
-                ("profile", ctypes.c_int), ("small_round", ctypes.c_int), ("edit_mode", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("small_round", ctypes.c_int), ("edit_mode", ctypes.c_int),
+                ("cluster_round", ctypes.c_int)]
 
 
 KERNEL_CLASSES = ("dense", "cpass", "edit", "refresh", "rebuild", "sep_init", "sep_update", "sep_targets", "other",
@@ -54,7 +55,8 @@ def profile_mask(profile):
 class Stats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_uint64 * 12), ("ms", ctypes.c_double * 12),
                 ("timed_launches", ctypes.c_uint64 * 12), ("items", ctypes.c_uint64 * 12),
-                ("round_work", ctypes.c_uint64 * 3), ("round_phase_ms", ctypes.c_double * 4)]
+                ("round_work", ctypes.c_uint64 * 3), ("round_phase_ms", ctypes.c_double * 4),
+                ("cluster_launches", ctypes.c_uint64), ("cluster_rounds", ctypes.c_uint64)]
 
 
 class IterRecord(ctypes.Structure):
@@ -192,7 +194,7 @@ EDITS_QUANTIZED, EDITS_FLOAT = 0, 1
 
 
 def options(tier=4, q_max=6, max_iters=100000, exact_fallback=1, stream=None, record_trace=False,
-            tile=(0, 0, 0), profile=False, small_round=0, edit_mode=EDITS_QUANTIZED):
+            tile=(0, 0, 0), profile=False, small_round=0, edit_mode=EDITS_QUANTIZED, cluster_round=0):
     o = Options()
     load().msc_default_options(ctypes.byref(o))
     o.tier, o.q_max, o.max_iters, o.exact_fallback = tier, q_max, max_iters, exact_fallback
@@ -202,6 +204,7 @@ def options(tier=4, q_max=6, max_iters=100000, exact_fallback=1, stream=None, re
     o.profile = profile_mask(profile)
     o.small_round = small_round
     o.edit_mode = int(edit_mode)
+    o.cluster_round = int(cluster_round)
     return o
 
 
@@ -311,6 +314,8 @@ class Handle:
                                      cpass=int(st.round_work[2]))
         out["rounds"]["phase_ms"] = dict(zip(("cpass", "edit", "mark", "refresh"),
                                              (float(v) for v in st.round_phase_ms)))
+        out["rounds"]["cluster_launches"] = int(st.cluster_launches)
+        out["rounds"]["cluster_rounds"] = int(st.cluster_rounds)
         return out
 
     def reset_stats(self):

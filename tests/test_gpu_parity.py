@@ -112,6 +112,38 @@ def test_fix_loop_rounds_as_graph_nodes(lib, idx, tier):
     _check_fix(lib, f, fh, xi, tier, small_round=1)
 
 
+@pytest.mark.parametrize("idx", [1, 3, 5, 7])
+def test_fix_loop_without_cluster_rounds(lib, idx):
+    """With the cluster form off, every small round runs in the full-grid persistent kernel:
+    the same result, round by round."""
+    name, kw = FIX_CASES[idx]
+    f, fh, xi, _ = synth.config_case(name, **kw)
+    ref = oracle.fix(f, fh, xi, tier=4)
+    h = lib.Handle(f)
+    g, ed = h.fix(fh, xi, tier=4, record_trace=True, cluster_round=1)
+    st = h.stats()
+    h.close()
+    assert st["rounds"]["cluster_launches"] == 0
+    assert np.array_equal(g.view(np.uint32), ref["g"].view(np.uint32))
+    assert np.array_equal(ed["trace"], ref["trace"][:, :5])
+
+
+def test_tiny_rounds_run_in_one_cluster(lib):
+    """By default the rounds that follow one editing fewer than 1024 vertices run in the
+    cluster form of the round kernel; a large case moves between the graph rounds, the
+    full-grid kernel and the cluster form, and still equals the oracle round by round."""
+    name, kw, tier, _ = LARGE_CASES[0]
+    f, fh, xi, _ = synth.config_case(name, **kw)
+    ref = oracle.fix(f, fh, xi, tier=tier)
+    h = lib.Handle(f)
+    g, ed = h.fix(fh, xi, tier=tier, record_trace=True)
+    st = h.stats()
+    h.close()
+    assert st["rounds"]["cluster_launches"] > 0 and st["rounds"]["cluster_rounds"] > ed["n_iters_c"] // 2
+    assert np.array_equal(g.view(np.uint32), ref["g"].view(np.uint32))
+    assert np.array_equal(ed["trace"], ref["trace"][:, :5])
+
+
 def test_small_rounds_run_in_the_round_kernel(lib):
     """With the default threshold the rounds after the first run in the persistent round
     kernel (this case edits fewer than 8192 vertices per round)."""
