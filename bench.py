@@ -298,7 +298,10 @@ def serving_leg(msc, n_req=128, slots=8):
            "sizes": "2D 256^2/1024^2/2048^2, 3D 64^3/128^3/256^3", "tier": 4,
            "latency": "job end - submission at its arrival time, s"}
     gs = {}
-    for mode, k in (("plain", 1), ("batched", slots)):
+    # the Poisson replay (latency under the arrival rate), then every request at once
+    # (throughput with the queue always full), each with one slot and with `slots` slots
+    for mode, k, paced in (("plain", 1, True), ("batched", slots, True), ("plain_saturated", 1, False),
+                           ("batched_saturated", slots, False)):
         with msc.Server(max_jobs=k, tier=4) as srv:
             w = srv.submit(*fields[0][:2], fields[0][2])       # warm-up job
             srv.wait(w)
@@ -306,7 +309,7 @@ def serving_leg(msc, n_req=128, slots=8):
             tickets = []
             for r, (f, fh, xi) in zip(reqs, fields):
                 d = t0 + r["t"] - time.perf_counter()
-                if d > 0:
+                if paced and d > 0:
                     time.sleep(d)
                 tickets.append(srv.submit(f, fh, xi))
             res = [srv.wait(t) for t in tickets]
@@ -315,8 +318,10 @@ def serving_leg(msc, n_req=128, slots=8):
         gs[mode] = [g for g, _, _ in res]
         out[mode] = {"slots": k, "p50_s": pct(lat, 50), "p99_s": pct(lat, 99), "mean_s": sum(lat) / len(lat),
                      "makespan_s": span, "GB/s": total_bytes / span / 1e9}
+    out["saturated"] = "every request submitted at t = 0"
     out["mix_identical"] = all(np.array_equal(a.view(np.uint32), b.view(np.uint32))
-                               for a, b in zip(gs["plain"], gs["batched"]))
+                               for m in ("batched", "plain_saturated", "batched_saturated")
+                               for a, b in zip(gs["plain"], gs[m]))
     return out
 
 

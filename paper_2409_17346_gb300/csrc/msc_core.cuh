@@ -1381,14 +1381,11 @@ template <int D> MSC_HD inline void node_targets(const Ctx &c, uint32_t p)
 // ------------------------------------------------------------------------------------
 // kind 0: descending seeds (both vertices of every critical edge); kind 1: ascending seeds
 // (top cofacets of every critical (D-1)-cell); kind 2: 2-saddle triangles (3D)
-template <int D, class Emit> MSC_HD inline void seeds_anchor(const uint64_t *code, const Grid &G, uint32_t p, int kind,
-                                                             Emit &&emit)
+template <int D, class Emit> MSC_HD inline void seeds_of_code(uint64_t cf, const Grid &G, uint32_t p, int x, int y, int z,
+                                                              int kind, Emit &&emit)
 {
     using Tb = Tab<D>;
-    int x, y, z;
-    coords(G, p, x, y, z);
     const unsigned cin = corner_mask<D>(G, x, y, z);
-    const uint64_t cf = ld(code + p);
     if (kind == 0 || (D == 2 && kind == 1)) {
         static_for<Tb::NE>([&](auto ec) {
             constexpr int e = decltype(ec)::value;
@@ -1425,6 +1422,15 @@ template <int D, class Emit> MSC_HD inline void seeds_anchor(const uint64_t *cod
             });
         });
     }
+}
+
+// the separatrix seeds of f that anchor p owns, by kind (see seeds_of_code)
+template <int D, class Emit> MSC_HD inline void seeds_anchor(const uint64_t *code, const Grid &G, uint32_t p, int kind,
+                                                             Emit &&emit)
+{
+    int x, y, z;
+    coords(G, p, x, y, z);
+    seeds_of_code<D>(ld(code + p), G, p, x, y, z, kind, emit);
 }
 
 // ------------------------------------------------------------------------------------

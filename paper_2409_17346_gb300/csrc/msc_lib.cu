@@ -424,12 +424,13 @@ __global__ void __launch_bounds__(TPB, 3) k_eval_dense(const float *v, Grid G, u
 template <int TY, int ZS, int MINB>
 __global__ void __launch_bounds__(32 * TY, MINB) k_eval_tile(const float *v, Grid G, uint64_t *out, const uint64_t *ref,
                                                             uint32_t *mbits, uint32_t *cbits, uint32_t *csum, int tier,
-                                                            uint64_t *low)
+                                                            uint64_t *low, unsigned long long *seeds)
 {
     using namespace dense;
     using T3 = Tab<3>;
     using TL = Tile<TY, ZS>;
     constexpr int TX = TL::TX, NT = TL::NT;
+    unsigned long long nseed[3] = {0, 0, 0};
     constexpr int VX = TL::VX, VY = TL::VY, PX = TL::PX, PY = TL::PY, EX = TL::EX, EY = TL::EY, RX = TL::RX,
                   RY = TL::RY;
     __shared__ Smem<TL> S;
@@ -611,6 +612,9 @@ __global__ void __launch_bounds__(32 * TY, MINB) k_eval_tile(const float *v, Gri
                     });
                 }
                 out[p] = code;
+                if (seeds)   // the separatrix seeds this anchor owns, counted from its code
+                    for (int k = 0; k < 3; k++)
+                        seeds_of_code<3>(code, G, (uint32_t)p, x, y, zk, k, [&](uint32_t) { nseed[k]++; });
                 if (low) {
                     // lowest vertex slot of every triangle (bits 2t) and tetrahedron (bits 24 + 2k)
                     uint64_t lw = 0;
@@ -670,6 +674,14 @@ __global__ void __launch_bounds__(32 * TY, MINB) k_eval_tile(const float *v, Gri
             }
         }
         __syncthreads();
+    }
+    if (seeds) {
+        // one atomic per warp and kind (every thread of the block reaches this point)
+        for (int k = 0; k < 3; k++) {
+            unsigned long long v = nseed[k];
+            for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if ((threadIdx.x & 31) == 0 && v) atomicAdd(seeds + k, v);
+        }
     }
 }
 
@@ -2016,6 +2028,8 @@ struct msc_handle {
     DevBuf<GridBarrier> bar;
     int rounds_grid = 0;   // blocks of the persistent round kernel (0: one per SM)
     uint64_t cluster_launches = 0, cluster_rounds = 0;   // the round kernel's cluster form
+    DevBuf<unsigned long long> seed_count;   // seeds counted by prepare's dense pass over f
+    bool seeds_counted = false;
     int tile_req = -1;     // tile shape of the dense 3D gradient the current call asks for (-1: tuned)
     int tile_used = -1;    // the shape its last dense pass ran with
     DevBuf<uint32_t> vis_v, vis_top, vis_tri, ovf0, ovf1;
@@ -2196,7 +2210,7 @@ Ctx make_ctx(msc_handle *h, int tier, int qmax, int exact_fallback, float xi, in
 // shape on a device times every shape once on its input (all shapes write the same codes) and
 // keeps the fastest for that (device, nx, ny, nz); msc_options.tile_* picks one instead.
 using TileFn = void (*)(const float *, Grid, uint64_t *, const uint64_t *, uint32_t *, uint32_t *, uint32_t *, int,
-                        uint64_t *);
+                        uint64_t *, unsigned long long *);
 struct TileShape {
     int ty, zs, nt;
     TileFn fn;
@@ -2232,11 +2246,11 @@ msc_status tile_request(const msc_options &o, int *req)
 }
 
 void launch_tile(int i, const float *v, Grid G, uint64_t *out, cudaStream_t s, const uint64_t *ref, uint32_t *mbits,
-                 uint32_t *cbits, uint32_t *csum, int tier, uint64_t *low)
+                 uint32_t *cbits, uint32_t *csum, int tier, uint64_t *low, unsigned long long *seeds = nullptr)
 {
     const TileShape &t = TILE_SHAPES[i];
     const dim3 grid((G.nx + 31) / 32, (G.ny + t.ty - 1) / t.ty, (G.nz + t.zs - 1) / t.zs);
-    t.fn<<<grid, t.nt, 0, s>>>(v, G, out, ref, mbits, cbits, csum, tier, low);
+    t.fn<<<grid, t.nt, 0, s>>>(v, G, out, ref, mbits, cbits, csum, tier, low, seeds);
 }
 
 // the dense gradient of a 3D grid with the requested tile shape, or the tuned one (tuning it
@@ -2284,7 +2298,14 @@ msc_status eval_tile(msc_handle *h, const float *v, Grid G, uint64_t *out, cudaS
         }
     }
     if (h) h->tile_used = shape;
-    KL(h, MSC_K_DENSE, s, launch_tile(shape, v, G, out, s, ref, mbits, cbits, csum, tier, low));
+    // the pass over f in prepare also counts the separatrix seeds (build_seeds then needs
+    // only its fill pass); a tuning pass does not, as it runs every shape
+    unsigned long long *seeds = h && low && h->seed_count.p ? h->seed_count.p : nullptr;
+    if (seeds) {
+        CK(cudaMemsetAsync(seeds, 0, 3 * sizeof(unsigned long long), s));
+        h->seeds_counted = true;
+    }
+    KL(h, MSC_K_DENSE, s, launch_tile(shape, v, G, out, s, ref, mbits, cbits, csum, tier, low, seeds));
     CK(cudaGetLastError());
     return MSC_OK;
 }
@@ -2320,10 +2341,14 @@ template <int D> msc_status build_seeds(msc_handle *h, cudaStream_t s)
     uint32_t *ns[3] = {&h->n_desc, &h->n_asc, &h->n_ss};
     unsigned long long n[3] = {0, 0, 0};
     SeedOut so{{nullptr, nullptr, nullptr}};
-    CK(cudaMemsetAsync(cnt.p, 0, sizeof n, s));
-    KL(h, MSC_K_OTHER, s, k_seeds<D><<<grid_occ((const void *)k_seeds<D>, h->G.n), TPB, 0, s>>>(h->code_f.p, h->G, so, cnt.p));
-    CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(n, cnt.p, sizeof n, cudaMemcpyDeviceToHost, s));
+    if (h->seeds_counted) {
+        CK(cudaMemcpyAsync(n, h->seed_count.p, sizeof n, cudaMemcpyDeviceToHost, s));
+    } else {
+        CK(cudaMemsetAsync(cnt.p, 0, sizeof n, s));
+        KL(h, MSC_K_OTHER, s, k_seeds<D><<<grid_occ((const void *)k_seeds<D>, h->G.n), TPB, 0, s>>>(h->code_f.p, h->G, so, cnt.p));
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(n, cnt.p, sizeof n, cudaMemcpyDeviceToHost, s));
+    }
     CK(cudaStreamSynchronize(s));
     for (int k = 0; k < 3; k++) {
         CK(bufs[k]->alloc(n[k]));
@@ -3146,6 +3171,7 @@ msc_status msc_prepare_original(const float *f, int nx, int ny, int nz, const ms
         CK(h->nM.alloc(8));
         h->prof_mask = (unsigned)o.profile & MSC_PROFILE_ALL;
         CKS(upload_field(h, f, h->G.n, h->f.p, h->nM.p, s, "f"));
+        if (h->D == 3) CK(h->seed_count.alloc(3));
         CKS(eval_dense_any(h, h->D, h->f.p, h->G, h->code_f.p, s, h->D == 3 ? h->low_f.p : nullptr));
         h->items[MSC_K_DENSE] += h->G.n;
         CKS(h->D == 3 ? build_seeds<3>(h, s) : build_seeds<2>(h, s));
