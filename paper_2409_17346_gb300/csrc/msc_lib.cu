@@ -1235,9 +1235,10 @@ template <int D> __global__ void __launch_bounds__(TPB) k_node_init(Ctx c)
     GRID_STRIDE(p, c.G.n) node_bits<D>(c, (uint32_t)p, true);
 }
 
-template <int D> __global__ void k_node_seed(Ctx c, int kind, const uint32_t *seeds, uint32_t n)
+template <int D> __global__ void __launch_bounds__(TPB, 4) k_node_seed(Ctx c, int kind, const uint32_t *seeds, uint32_t n)
 {
-    path_seed_walks<D, 4>(c, kind, seeds, n, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+    path_seed_walks<D, 4>(c, kind, seeds, n, (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5,
+                          (gridDim.x * (unsigned long long)blockDim.x) >> 5);
 }
 
 // the first build's saddle-saddle propagation (3D): per-warp stacks in shared memory

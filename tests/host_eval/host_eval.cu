@@ -223,7 +223,7 @@ static int spass_of(const float *f, const float *g1, const float *g2, const uint
     // first build on g1
     for (uint32_t p = 0; p < n; p++) node_bits<D>(c, p, true);
     for (int kind = 0; kind < 2; kind++)
-        path_seed_walks<D, 4>(c, kind, seeds[kind].data(), (uint32_t)seeds[kind].size(), 0, 1);
+        path_seed_walks<D, 4>(c, kind, seeds[kind].data(), (uint32_t)seeds[kind].size(), 0, 1);   // one warp of one lane
     if (D == 3)
         for (uint32_t u : seeds[2]) {
             const int32_t o = node_or(c.ns_tri, u, NS_SEED);
