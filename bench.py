@@ -128,8 +128,9 @@ CLASS_KERNELS = {
 
 # what limits each class, from the ncu captures of its kernels (issue, stalls, DRAM throughput)
 CLASS_LIMITER = {
-    "sep_seed": "memory latency: dependent chains of node atomics and successor loads (path walks issue at "
-                "15-18%, DRAM well below peak); the saddle-saddle walk is issue-bound",
+    "sep_seed": "memory latency: dependent chains of node atomics and successor loads; the path walks run "
+                "converged (23 of 32 lanes per instruction, issue 50%), the saddle-saddle walk takes ~3/4 "
+                "of the class",
     "rounds": "latency: four grid barriers and short dependent phases per round",
     "dense": "instruction issue (78-82% SM throughput, ~3% of DRAM peak)",
     "cpass": "memory latency of the case lookups",
@@ -138,9 +139,9 @@ CLASS_LIMITER = {
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of a class's kernels per work
 # item, from one ncu capture of the same workload at 256^3 (the capture's launches over the
 # items they processed); a launch's traffic is that figure times the launch's items.  The
-# figure is from a capture of k_node_seed and k_node_seed_ss as they stand (3 launches,
-# 131,205,873 node steps).
-TRAFFIC_PER_ITEM = {"sep_seed": (279940608 + 22409728 + 2425982976 + 441205760 + 2871237120 + 1542544128) / 131205873.0}
+# figure is from a capture of k_node_seed (converged warp walks) and k_node_seed_ss as they
+# stand (3 launches, 131,205,873 node steps).
+TRAFFIC_PER_ITEM = {"sep_seed": (239320064 + 23293952 + 823610368 + 208239360 + 2817286400 + 1521402624) / 131205873.0}
 
 
 def class_bytes(cls, tot, n, steps, ndim):
@@ -216,6 +217,7 @@ CONFIGS = {
 
 def config_of(args):
     c = dict(CONFIGS[args.config])
+    c["named_size"] = c["size"]        # the size the description names
     if args.rel is not None:
         c["rel"] = args.rel
     if args.size is not None:
@@ -227,7 +229,8 @@ def config_of(args):
 
 def workload_desc(cfg, shape):
     d = cfg["desc"] % (cfg["rel"], cfg["tier"])
-    if tuple(shape) != (tuple(cfg["size"]) if isinstance(cfg["size"], tuple) else (cfg["size"],) * 3):
+    named = cfg.get("named_size", cfg["size"])
+    if tuple(shape) != (tuple(named) if isinstance(named, tuple) else (named,) * 3):
         d += " (run at %s)" % "x".join(str(x) for x in tuple(shape)[::-1])
     return d
 

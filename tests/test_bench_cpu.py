@@ -51,4 +51,10 @@ def test_configs_cover_the_workloads():
         assert "%g" not in d and "%d" not in d and "xi=" in d
     a = argparse.Namespace(config=2, size=100, rel=None, tier=None)
     assert bench.config_of(a)["size"] == (100, 200)
+    # a run at another size says so: the description keeps the named size and adds the run's
+    a = argparse.Namespace(config=4, size=256, rel=None, tier=None)
+    d = bench.workload_desc(bench.config_of(a), (256, 256, 256))
+    assert "512x512x512" in d and d.endswith("(run at 256x256x256)")
+    assert "run at" not in bench.workload_desc(bench.config_of(argparse.Namespace(
+        config=4, size=None, rel=None, tier=None)), (512, 512, 512))
     assert bench.CONFIGS[3]["batch"] == 8
