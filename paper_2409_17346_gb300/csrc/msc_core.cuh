@@ -33,6 +33,67 @@ template <> MSC_HD inline const Tab<3> &rt_tab<3>()
 #endif
 }
 
+// The tables of the 3D walks, one word per cell type, so that a lookup with a type that
+// differs from lane to lane is one load rather than one per field:
+//  nb[n]: neighbour offset n of a vertex, bits 0-1, 2-3, 4-5: x, y, z plus one;
+//  asc[t][j]: ascending step of a tet of type t whose lowest corner is slot j (asc_off,
+//    asc_type), bits 0-1, 2-3, 4-5: x, y, z offsets plus one, bits 8-10: the next tet's type;
+//  tri[t], byte j (j < 3): facet edge j of a triangle of type t, bits 0-2 its anchor offset
+//    (x, y, z, each 0 or 1), bits 3-5 its edge type; bits 24-29: tri_opp[t][0..2], 2 bits each;
+//  ecof[e], byte i (i < 6): cofacet triangle i of an edge of type e, bits 0-2 minus its anchor
+//    offset (each offset is 0 or -1), bits 4-7 its triangle type.
+struct TriPack {
+    uint32_t nb[14];
+    uint32_t asc[6][4];
+    uint32_t tri[12];
+    uint64_t ecof[7];
+};
+constexpr TriPack make_tri_pack()
+{
+    constexpr Tab<3> T = make_tab<3>();
+    TriPack k{};
+    for (int n = 0; n < 14; n++)
+        k.nb[n] = (uint32_t)(T.nb[n][0] + 1) | (uint32_t)(T.nb[n][1] + 1) << 2 | (uint32_t)(T.nb[n][2] + 1) << 4;
+    for (int t = 0; t < 6; t++)
+        for (int j = 0; j < 4; j++)
+            k.asc[t][j] = (uint32_t)(T.asc_off[t][j][0] + 1) | (uint32_t)(T.asc_off[t][j][1] + 1) << 2 |
+                          (uint32_t)(T.asc_off[t][j][2] + 1) << 4 | (uint32_t)T.asc_type[t][j] << 8;
+    for (int t = 0; t < 12; t++) {
+        uint32_t w = 0;
+        for (int j = 0; j < 3; j++) {
+            const uint32_t b = (uint32_t)T.tfac_anc[t][j][0] | (uint32_t)T.tfac_anc[t][j][1] << 1 |
+                               (uint32_t)T.tfac_anc[t][j][2] << 2 | (uint32_t)T.tfac_type[t][j] << 3;
+            w |= b << (8 * j);
+            w |= (uint32_t)T.tri_opp[t][j] << (24 + 2 * j);
+        }
+        k.tri[t] = w;
+    }
+    for (int e = 0; e < 7; e++) {
+        uint64_t w = 0;
+        for (int i = 0; i < T.necof[e]; i++) {
+            const uint64_t b = (uint64_t)-T.ecof_anc[e][i][0] | (uint64_t)-T.ecof_anc[e][i][1] << 1 |
+                               (uint64_t)-T.ecof_anc[e][i][2] << 2 | (uint64_t)T.ecof_type[e][i] << 4;
+            w |= b << (8 * i);
+        }
+        k.ecof[e] = w;
+    }
+    return k;
+}
+#ifdef __CUDACC__
+static __device__ const TriPack kTriPack = make_tri_pack();
+#endif
+#ifdef MSC_HOST_EMULATION
+static const TriPack hTriPack = make_tri_pack();
+#endif
+MSC_HD inline const TriPack &rt_tri_pack()
+{
+#if defined(__CUDA_ARCH__) || !defined(MSC_HOST_EMULATION)
+    return kTriPack;
+#else
+    return hTriPack;
+#endif
+}
+
 constexpr uint8_t ST_FLOOR = 0xF0;   // g == lb, stored losslessly (Eq. 2 "otherwise")
 constexpr uint8_t ST_EXACT = 0xF1;   // g == f, stored losslessly (stuck-case restore)
 
@@ -963,6 +1024,13 @@ template <int D> MSC_HD inline bool desc_succ(const Ctx &c, uint32_t u, uint32_t
     const Tab<D> &T = rt_tab<D>();
     const int ff = vfield<D>(ld(c.code_f + u));
     if (ff == 15) return false;
+    if constexpr (D == 3) {
+        // the lower neighbour a vertex is paired with is in the domain: no bounds to check
+        const uint32_t b = ld(rt_tri_pack().nb + ff);
+        w = u + (b & 3u) + ((b >> 2) & 3u) * (uint32_t)c.G.nx + ((b >> 4) & 3u) * (uint32_t)c.G.nx * (uint32_t)c.G.ny -
+            (1u + (uint32_t)c.G.nx + (uint32_t)c.G.nx * (uint32_t)c.G.ny);
+        return true;
+    }
     int x, y, z;
     coords(c.G, u, x, y, z);
     w = vid(c.G, x + T.nb[ff][0], y + T.nb[ff][1], z + T.nb[ff][2]);
@@ -974,16 +1042,16 @@ template <int D> MSC_HD inline bool asc_succ(const Ctx &c, uint32_t beta, uint32
 {
     if constexpr (D == 3) {
         // the tetrahedron's lowest vertex from the prepared slots: no vertex values to load
-        const Tab<3> &T = rt_tab<3>();
         const uint32_t a = beta / 6;
         const int t = (int)(beta % 6);
         const uint64_t cf = ld(c.code_f + a), lw = ld(c.low_f + a);
         if (kfield<3>(cf, t) == 0) return false;                 // a maximum
         const int jl = (int)((lw >> (24 + 2 * t)) & 3u);
+        const uint32_t b = ld(&rt_tri_pack().asc[t][jl]);
         int x, y, z;
         coords(c.G, a, x, y, z);
-        x += T.asc_off[t][jl][0]; y += T.asc_off[t][jl][1]; z += T.asc_off[t][jl][2];
-        const int t2 = T.asc_type[t][jl];
+        x += (int)(b & 3u) - 1; y += (int)((b >> 2) & 3u) - 1; z += (int)((b >> 4) & 3u) - 1;
+        const int t2 = (int)((b >> 8) & 7u);
         if (!top_exists<3>(c.G, x, y, z, t2)) return false;      // the path leaves the domain
         nb = vid(c.G, x, y, z) * 6 + (uint32_t)t2;
         return true;
@@ -1026,32 +1094,35 @@ template <int D> MSC_HD inline void path_change(const Ctx &c, int kind, uint32_t
 
 // children of a reached triangle node: its facet edges other than the one it is paired with
 // in f; an edge paired up in f leads to its partner triangle, an edge paired down is a dead
-// end, a critical edge (1-saddle) ends the walk
-MSC_HD inline int tri_children(const Ctx &c, uint32_t tri, uint32_t *out, bool *dead)
+// end, a critical edge (1-saddle) ends the walk.  One slot per facet edge j, so that every
+// index is a constant and the slots stay in registers: kind[j] 0 (no child: the pair edge or
+// a critical edge), 1 (a dead end: ch[j] is the edge id) or 2 (ch[j] is the partner triangle).
+constexpr int TC_NONE = 0, TC_DEAD = 1, TC_LIVE = 2;
+MSC_HD inline void tri_children(const Ctx &c, uint32_t tri, uint32_t (&ch)[3], int (&kind)[3])
 {
-    const Tab<3> &T = rt_tab<3>();
-    const int tt = (int)(tri % 12);
-    int x, y, z;
-    coords(c.G, tri / 12, x, y, z);
+    const TriPack &K = rt_tri_pack();
+    const uint32_t a = tri / 12, tt = tri % 12;
+    const uint32_t sy = (uint32_t)c.G.nx, sz = (uint32_t)c.G.nx * (uint32_t)c.G.ny;
+    const uint32_t P = ld(K.tri + tt);
     int entry = -1;
-    const uint64_t cf = ld(c.code_f + tri / 12), lw = ld(c.low_f + tri / 12);
-    if (tfield<3>(cf, tt) == 1) entry = T.tri_opp[tt][(lw >> (2 * tt)) & 3u];   // paired with the highest edge
-    int n = 0;
+    const uint64_t cf = ld(c.code_f + a), lw = ld(c.low_f + a);
+    if (tfield<3>(cf, (int)tt) == 1) entry = (int)(P >> (24 + 2 * ((lw >> (2 * tt)) & 3u))) & 3;   // paired with the highest edge
+#pragma unroll
     for (int j = 0; j < 3; j++) {
+        kind[j] = TC_NONE;
+        ch[j] = 0;
         if (j == entry) continue;
-        const int ex = x + T.tfac_anc[tt][j][0], ey = y + T.tfac_anc[tt][j][1], ez = z + T.tfac_anc[tt][j][2];
-        const int et = T.tfac_type[tt][j];
-        const uint32_t ea = vid(c.G, ex, ey, ez);
+        // a facet or cofacet of a cell in the domain is in the domain: offsets need no bounds
+        const uint32_t b = P >> (8 * j);
+        const uint32_t ea = a + (b & 1u) + ((b >> 1) & 1u) * sy + ((b >> 2) & 1u) * sz;
+        const int et = (int)((b >> 3) & 7u);
         const int ef = efield<3>(ld(c.code_f + ea), et);
         if (ef == 0) continue;
-        if (ef == 1) { out[n] = ea * 7 + (uint32_t)et; dead[n] = true; n++; continue; }
-        const int i = ef - 2;
-        out[n] = vid(c.G, ex + T.ecof_anc[et][i][0], ey + T.ecof_anc[et][i][1], ez + T.ecof_anc[et][i][2]) * 12 +
-                 (uint32_t)T.ecof_type[et][i];
-        dead[n] = false;
-        n++;
+        if (ef == 1) { ch[j] = ea * 7 + (uint32_t)et; kind[j] = TC_DEAD; continue; }
+        const uint32_t q = (uint32_t)(ld(K.ecof + et) >> (8 * (ef - 2)));
+        ch[j] = (ea - (q & 1u) - ((q >> 1) & 1u) * sy - ((q >> 2) & 1u) * sz) * 12 + ((q >> 4) & 15u);
+        kind[j] = TC_LIVE;
     }
-    return n;
 }
 
 MSC_HD inline void ss_spill(const Ctx &c, uint32_t tri, int delta)
@@ -1072,10 +1143,11 @@ MSC_HD inline void tri_propagate(const Ctx &c, uint32_t tri0, int dv0, bool appl
     if (apply_first) { st[sp] = tri0; sd[sp] = delta0; sp++; }
     auto expand = [&](uint32_t t, int dv) {
         uint32_t ch[3];
-        bool dead[3];
-        const int k = tri_children(c, t, ch, dead);
-        for (int i = 0; i < k; i++) {
-            if (dead[i]) { node_add(c.ns_dead, ch[i], dv); continue; }
+        int kind[3];
+        tri_children(c, t, ch, kind);
+        for (int i = 0; i < 3; i++) {
+            if (kind[i] == TC_DEAD) { node_add(c.ns_dead, ch[i], dv); continue; }
+            if (kind[i] == TC_NONE) continue;
             if (sp < SS_STACK) { st[sp] = ch[i]; sd[sp] = dv; sp++; }
             else ss_spill(c, ch[i], dv);
         }
@@ -1235,7 +1307,13 @@ MSC_HD inline void path_seed_walks(const Ctx &c, int kind, const uint32_t *seeds
                 if (kind == 0) {
                     const int ff = vfield<D>(cf[k]);
                     if (ff != 15) {
-                        w = (uint32_t)((int64_t)node[k] + T.nb[ff][0] + sy * T.nb[ff][1] + sz * T.nb[ff][2]);
+                        if constexpr (D == 3) {
+                            const uint32_t b = ld(rt_tri_pack().nb + ff);
+                            w = (uint32_t)((int64_t)node[k] + ((int)(b & 3u) - 1) + sy * ((int)((b >> 2) & 3u) - 1) +
+                                           sz * ((int)((b >> 4) & 3u) - 1));
+                        } else {
+                            w = (uint32_t)((int64_t)node[k] + T.nb[ff][0] + sy * T.nb[ff][1] + sz * T.nb[ff][2]);
+                        }
                         cont = true;
                     }
                 } else if (D == 3) {
@@ -1243,10 +1321,11 @@ MSC_HD inline void path_seed_walks(const Ctx &c, int kind, const uint32_t *seeds
                     const int t = (int)(node[k] % NTOP);
                     if (kfield<D>(cf[k], t) != 0) {
                         const int jl = (int)((lw[k] >> (24 + 2 * t)) & 3u);
+                        const uint32_t b = ld(&rt_tri_pack().asc[t][jl]);
                         int x, y, z;
                         coords(c.G, a, x, y, z);
-                        x += T.asc_off[t][jl][0]; y += T.asc_off[t][jl][1]; z += T.asc_off[t][jl][2];
-                        const int t2 = T.asc_type[t][jl];
+                        x += (int)(b & 3u) - 1; y += (int)((b >> 2) & 3u) - 1; z += (int)((b >> 4) & 3u) - 1;
+                        const int t2 = (int)((b >> 8) & 7u);
                         if (top_exists<D>(c.G, x, y, z, t2)) {
                             w = vid(c.G, x, y, z) * NTOP + (uint32_t)t2;
                             cont = true;
@@ -1280,14 +1359,13 @@ __device__ inline void tri_seed_walks(const Ctx &c, const uint32_t *seeds, uint3
     // push the live children of a triangle whose passing state changed by dv (lane-local
     // inputs; all lanes call it)
     auto push_children = [&](bool go, uint32_t t, int dv) {
-        uint32_t ch[3];
-        bool dead[3];
-        int k = 0;
-        if (go) k = tri_children(c, t, ch, dead);
+        uint32_t ch[3] = {0, 0, 0};
+        int kind[3] = {TC_NONE, TC_NONE, TC_NONE};
+        if (go) tri_children(c, t, ch, kind);
 #pragma unroll
         for (int r = 0; r < 3; r++) {
-            const bool live = r < k && !dead[r];
-            if (r < k && dead[r]) node_add(c.ns_dead, ch[r], dv);
+            const bool live = kind[r] == TC_LIVE;
+            if (kind[r] == TC_DEAD) node_add(c.ns_dead, ch[r], dv);
             const unsigned m = __ballot_sync(0xffffffffu, live);
             const int cnt = __popc(m);
             if (!cnt) continue;

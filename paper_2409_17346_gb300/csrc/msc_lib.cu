@@ -1241,8 +1241,12 @@ template <int D> __global__ void __launch_bounds__(TPB, 4) k_node_seed(Ctx c, in
                           (gridDim.x * (unsigned long long)blockDim.x) >> 5);
 }
 
-// the first build's saddle-saddle propagation (3D): per-warp stacks in shared memory
+// the first build's saddle-saddle propagation (3D): per-warp stacks in shared memory.  It
+// runs at most SS_BLOCKS_PER_SM blocks per SM: more warps walking at once contend for L1 and
+// L2 and finish later (kolmogorov3d 512^3: 8 blocks per SM 22 ms, 6: 19.5 ms, 4: 19.6 ms,
+// 3: 23 ms).
 constexpr int SS_WARP_STACK = 384;
+constexpr int SS_BLOCKS_PER_SM = 6;
 __global__ void k_node_seed_ss(Ctx c, const uint32_t *seeds, uint32_t n)
 {
     __shared__ uint32_t stk[TPB / 32][SS_WARP_STACK];
@@ -2412,7 +2416,10 @@ template <int D> msc_status s_pass_state(msc_handle *h, Ctx &c, bool &built, uns
         KL(h, MSC_K_SEP_INIT, s, k_node_init<D><<<grid_occ((const void *)k_node_init<D>, h->G.n), TPB, 0, s>>>(c));
         if (h->n_desc) KL(h, MSC_K_SEP_SEED, s, k_node_seed<D><<<grid_occ((const void *)k_node_seed<D>, h->n_desc), TPB, 0, s>>>(c, 0, h->seeds_desc.p, h->n_desc));
         if (h->n_asc) KL(h, MSC_K_SEP_SEED, s, k_node_seed<D><<<grid_occ((const void *)k_node_seed<D>, h->n_asc), TPB, 0, s>>>(c, 1, h->seeds_asc.p, h->n_asc));
-        if (D == 3 && h->n_ss) KL(h, MSC_K_SEP_SEED, s, k_node_seed_ss<<<grid_occ((const void *)k_node_seed_ss, 32ull * h->n_ss), TPB, 0, s>>>(c, h->seeds_ss.p, h->n_ss));
+        if (D == 3 && h->n_ss) {
+            const int ssg = std::min(grid_occ((const void *)k_node_seed_ss, 32ull * h->n_ss), SS_BLOCKS_PER_SM * sm_count());
+            KL(h, MSC_K_SEP_SEED, s, k_node_seed_ss<<<ssg, TPB, 0, s>>>(c, h->seeds_ss.p, h->n_ss));
+        }
         CK(cudaGetLastError());
         h->items[MSC_K_SEP_INIT] += h->G.n;
         built = true;
