@@ -236,6 +236,22 @@ __device__ __forceinline__ void count_add(unsigned long long *p, unsigned long l
 inline void count_add(unsigned long long *p, unsigned long long v) { *p += v; }
 #endif
 
+// a case into a shared (cases, live cases) tally: one pair of atomics per group of converged
+// threads (the lanes of a warp would otherwise queue on the same two words)
+#ifdef __CUDA_ARCH__
+__device__ __forceinline__ void tally_add(unsigned long long *t, bool live)
+{
+    const unsigned mask = __activemask();
+    const unsigned nl = (unsigned)__popc(__ballot_sync(mask, live));
+    if ((threadIdx.x & 31) == (unsigned)(__ffs(mask) - 1)) {
+        atomicAdd(t, (unsigned long long)__popc(mask));
+        if (nl) atomicAdd(t + 1, (unsigned long long)nl);
+    }
+}
+#else
+inline void tally_add(unsigned long long *t, bool live) { t[0] += 1; t[1] += live ? 1 : 0; }
+#endif
+
 // slot in a list whose length lives in *n: one atomic per group of converged threads
 #ifdef __CUDA_ARCH__
 __device__ __forceinline__ unsigned long long list_slot(unsigned long long *n)
@@ -400,8 +416,7 @@ template <int D> MSC_HD inline void add_case(const Ctx &c, uint32_t t, const Ver
     const uint8_t st = c.state[t];
     const bool live = st != ST_FLOOR && st != ST_EXACT;
     if (c.tally) {
-        a_add(c.tally, 1ull);
-        if (live) a_add(c.tally + 1, 1ull);
+        tally_add(c.tally, live);
     } else {
         count_add(&c.cnt->ncase, 1ull);
         if (live) count_add(&c.cnt->nlive, 1ull);

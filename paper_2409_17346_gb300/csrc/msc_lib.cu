@@ -159,9 +159,17 @@ template <int CAP> __device__ __forceinline__ void st_init(Stage<CAP> &s)
     __syncthreads();
 }
 
+// One shared atomic per group of converged lanes that push to the same stage (grouped by the
+// stage's address), not one per item: with every thread of a block pushing, the per-item
+// atomics on one counter queue up.
 template <int CAP> __device__ __forceinline__ void st_push(Stage<CAP> &s, uint32_t v, uint32_t *gl, unsigned long long *gn)
 {
-    const unsigned k = atomicAdd(&s.n, 1u);
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned grp = __match_any_sync(__activemask(), (unsigned long long)(uintptr_t)&s);
+    const int leader = __ffs(grp) - 1;
+    unsigned base = 0;
+    if ((int)lane == leader) base = atomicAdd(&s.n, (unsigned)__popc(grp));
+    const unsigned k = __shfl_sync(grp, base, leader) + (unsigned)__popc(grp & ((1u << lane) - 1u));
     if (k < CAP) s.buf[k] = v;
     else gl[atomicAdd(gn, 1ull)] = v;
 }
@@ -278,7 +286,7 @@ struct NoKeep {
 // other lanes wait.  Empty blocks have their summary bit cleared; non-empty blocks are handed
 // to keep.  Needs blockDim.x == TPB.
 constexpr int CASES_PER_ANCHOR = 26;
-template <int D, class K = NoKeep>
+template <int D, bool GROUP, class K = NoKeep>
 __device__ __forceinline__ void cpass_listed(const Ctx &c, uint16_t (*q)[32 * 32], uint16_t (*cq)[32 * CASES_PER_ANCHOR],
                                              const uint32_t *blk, unsigned long long nblk, unsigned long long *count,
                                              K &&keep = K{}, unsigned long long *next = nullptr)
@@ -287,7 +295,9 @@ __device__ __forceinline__ void cpass_listed(const Ctx &c, uint16_t (*q)[32 * 32
     uint16_t *mq = q[wib];   // anchors as offsets in their 1024-anchor block
     uint16_t *cw = cq[wib];
     const unsigned long long nw = (c.G.n + 31ull) / 32;
-    const unsigned long long warp = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+    // warps numbered across the blocks first (warp w of block b is b + w * blocks), so that a
+    // few listed blocks spread over the SMs
+    const unsigned long long warp = (unsigned long long)wib * gridDim.x + blockIdx.x;
     const unsigned long long nwarps = (gridDim.x * (unsigned long long)blockDim.x) >> 5;
     // with next: warps take blocks from a shared counter as they finish (blocks hold very
     // different numbers of cases); otherwise a fixed grid-stride share
@@ -326,30 +336,41 @@ __device__ __forceinline__ void cpass_listed(const Ctx &c, uint16_t (*q)[32 * 32
         __syncwarp();
         const uint32_t base = b * 1024u;
         for (unsigned k0 = 0; k0 < total; k0 += 32) {
-            uint32_t m = 0;
+            uint32_t m0 = 0;
             if (k0 + lane < total) {
                 const uint32_t p = base + mq[k0 + lane];
-                m = case_mask<D>(c, p, __ldg(c.code_f + p), c.code_g[p]);
+                m0 = case_mask<D>(c, p, __ldg(c.code_f + p), c.code_g[p]);
             }
-            const unsigned nc = __popc(m);
-            unsigned cpre = nc;
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned y = __shfl_up_sync(0xffffffffu, cpre, o);
-                if (lane >= (unsigned)o) cpre += y;
+            // GROUP: the cases of these anchors one cell dimension at a time, so that the lanes
+            // of a pass take the same branch of case_apply (mixed, a warp of a large C-pass ran
+            // 9 of 32 lanes); a round of a few cases does better with one pass
+            using Tb = Tab<D>;
+            constexpr uint32_t GRP[4] = {1u, ((1u << Tb::NE) - 1u) << 1, ((1u << Tb::NT) - 1u) << (1 + Tb::NE),
+                                         ((1u << Tb::NK) - 1u) << (1 + Tb::NE + Tb::NT)};
+#pragma unroll
+            for (int gi = 0; gi < (GROUP ? 4 : 1); gi++) {
+                uint32_t m = GROUP ? m0 & GRP[gi] : m0;
+                if (!__any_sync(0xffffffffu, m != 0)) continue;
+                const unsigned nc = __popc(m);
+                unsigned cpre = nc;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned y = __shfl_up_sync(0xffffffffu, cpre, o);
+                    if (lane >= (unsigned)o) cpre += y;
+                }
+                const unsigned ctot = __shfl_sync(0xffffffffu, cpre, 31);
+                unsigned ca = cpre - nc;
+                while (m) {
+                    const int k = __ffs(m) - 1;
+                    m &= m - 1;
+                    cw[ca++] = (uint16_t)((lane << 5) | (unsigned)k);
+                }
+                __syncwarp();
+                for (unsigned j = lane; j < ctot; j += 32) {
+                    const unsigned e = cw[j];
+                    case_apply<D>(c, base + mq[k0 + (e >> 5)], (int)(e & 31u));
+                }
+                __syncwarp();
             }
-            const unsigned ctot = __shfl_sync(0xffffffffu, cpre, 31);
-            unsigned ca = cpre - nc;
-            while (m) {
-                const int k = __ffs(m) - 1;
-                m &= m - 1;
-                cw[ca++] = (uint16_t)((lane << 5) | (unsigned)k);
-            }
-            __syncwarp();
-            for (unsigned j = lane; j < ctot; j += 32) {
-                const unsigned e = cw[j];
-                case_apply<D>(c, base + mq[k0 + (e >> 5)], (int)(e & 31u));
-            }
-            __syncwarp();
         }
     }
 }
@@ -686,11 +707,14 @@ __global__ void __launch_bounds__(32 * TY, MINB) k_eval_tile(const float *v, Gri
 }
 
 // g = f_hat re-clamped into [f - xi, f + xi] (bounds rounded inward), every vertex unedited
-__global__ void k_init_g(const float *f, const float *fh, float *g, uint8_t *state, uint32_t n, float xi)
+// g's starting values; gprev starts equal to g (between rounds gprev[v] == g[v] for every v)
+__global__ void k_init_g(const float *f, const float *fh, float *g, float *gprev, uint8_t *state, uint32_t n, float xi)
 {
     GRID_STRIDE(i, n)
     {
-        g[i] = clamp_base(f[i], fh[i], xi);
+        const float v = clamp_base(f[i], fh[i], xi);
+        g[i] = v;
+        gprev[i] = v;
         state[i] = 0;
     }
 }
@@ -729,7 +753,7 @@ __device__ __forceinline__ void tally_end(BlockTally &t, const Ctx &c)
     }
 }
 
-template <int D> __global__ void __launch_bounds__(TPB) k_ctargets(Ctx c)
+template <int D> __global__ void __launch_bounds__(TPB, 4) k_ctargets(Ctx c)
 {
     if (round_off(c.ls)) return;
     __shared__ unsigned long long wt[TPB / 32][2];   // per-warp case tallies
@@ -740,7 +764,7 @@ template <int D> __global__ void __launch_bounds__(TPB) k_ctargets(Ctx c)
     __syncwarp();
     Ctx cc = c;
     cc.tally = wt[wib];
-    cpass_listed<D>(cc, q, cq, c.Cblk, c.ls->nblk, &c.ls->cpass_items, NoKeep{}, &c.cnt->wnext);
+    cpass_listed<D, true>(cc, q, cq, c.Cblk, c.ls->nblk, &c.ls->cpass_items, NoKeep{}, &c.cnt->wnext);
     __syncwarp();
     if (lane == 0) {
         if (wt[wib][0]) atomicAdd(&c.cnt->ncase, wt[wib][0]);
@@ -857,35 +881,151 @@ template <int D> __global__ void k_edit(Ctx c)
     ws_flush(se[wib], c.Elist, &c.cnt->nE);
 }
 
+// The window of an anchor by rows: for each (y, z) offset of the window, the run of x offsets
+// [lo, hi] it holds (the window is [-1,1]^D u [0,2]^D, so every row is one run).  The anchors
+// whose window holds a vertex v are v - o: per row, a run of at most four consecutive anchors,
+// marked in their bitset with one or two word atomics instead of one atomic per anchor.
+template <int D> struct WinRows {
+    int n;
+    int oy[16], oz[16], lo[16], hi[16];
+};
+template <int D> constexpr WinRows<D> make_win_rows()
+{
+    constexpr Tab<D> T = make_tab<D>();
+    WinRows<D> r{};
+    for (int j = 0; j < T.nwin; j++) {
+        const int ox = T.win[j][0], oy = T.win[j][1], oz = T.win[j][2];
+        int k = 0;
+        while (k < r.n && !(r.oy[k] == oy && r.oz[k] == oz)) k++;
+        if (k == r.n) { r.oy[k] = oy; r.oz[k] = oz; r.lo[k] = ox; r.hi[k] = ox; r.n++; }
+        else { r.lo[k] = ox < r.lo[k] ? ox : r.lo[k]; r.hi[k] = ox > r.hi[k] ? ox : r.hi[k]; }
+    }
+    return r;
+}
+template <int D> constexpr bool win_rows_are_runs()
+{
+    constexpr Tab<D> T = make_tab<D>();
+    constexpr WinRows<D> r = make_win_rows<D>();
+    int cells = 0;
+    for (int k = 0; k < r.n; k++) cells += r.hi[k] - r.lo[k] + 1;
+    return cells == T.nwin && r.n <= 16;
+}
+static_assert(win_rows_are_runs<2>() && win_rows_are_runs<3>(), "window rows must be runs of x offsets");
+static __device__ const WinRows<2> kWinRows2 = make_win_rows<2>();
+static __device__ const WinRows<3> kWinRows3 = make_win_rows<3>();
+template <int D> __device__ __forceinline__ const WinRows<D> &win_rows();
+template <> __device__ __forceinline__ const WinRows<2> &win_rows<2>() { return kWinRows2; }
+template <> __device__ __forceinline__ const WinRows<3> &win_rows<3>() { return kWinRows3; }
+
+// what one lane of a warp handles of a changed vertex, held in registers for a whole kernel:
+// ring offsets lane and lane + 32 (the vertices whose order against it a rule compares) and
+// window row `lane`
+struct LaneGeom {
+    int rg[2][3];
+    bool ron[2];
+    int oy, oz, lo, hi;
+    bool row;
+};
+template <int D> __device__ __forceinline__ LaneGeom lane_geom(unsigned lane)
+{
+    const Tab<D> &T = rt_tab<D>();
+    const WinRows<D> &R = win_rows<D>();
+    LaneGeom g;
+#pragma unroll
+    for (int r = 0; r < 2; r++) {
+        const int j = (int)lane + 32 * r;
+        g.ron[r] = j < T.nring;
+        for (int k = 0; k < 3; k++) g.rg[r][k] = g.ron[r] ? T.ring[j][k] : 0;
+    }
+    g.row = (int)lane < R.n;
+    g.oy = g.row ? R.oy[lane] : 0;
+    g.oz = g.row ? R.oz[lane] : 0;
+    g.lo = g.row ? R.lo[lane] : 0;
+    g.hi = g.row ? R.hi[lane] : 0;
+    return g;
+}
+
+// order_changed (lanes as parts) with the ring offsets in registers.  A neighbour's value
+// before the round is gprev's: between rounds gprev equals g everywhere, and a round saves
+// the pre-round value of each vertex it edits there.
+template <int D> __device__ __forceinline__ bool ring_changed(const Ctx &c, uint32_t v, int x, int y, int z, const LaneGeom &g)
+{
+    const float ov = c.gprev[v], nv = c.g[v];
+    bool flip = false;
+#pragma unroll
+    for (int r = 0; r < 2; r++) {
+        if (!g.ron[r]) continue;
+        const int ux = x + g.rg[r][0], uy = y + g.rg[r][1], uz = z + g.rg[r][2];
+        if (!inside(c.G, ux, uy, uz)) continue;
+        const uint32_t u = vid(c.G, ux, uy, uz);
+        const float nu = c.g[u], ou = c.gprev[u];
+        flip |= sos_lt(ov, v, ou, u) != sos_lt(nv, v, nu, u);
+    }
+    return flip;
+}
+
+// marks the window row (oy, oz, x offsets lo..hi) of the changed vertex (x, y, z) dirty;
+// returns the first anchor of the row in p0 and bit i set when anchor p0 + i became dirty
+__device__ __forceinline__ unsigned mark_run(const Ctx &c, int oy, int oz, int lo, int hi, int x, int y, int z, uint32_t &p0)
+{
+    p0 = 0;
+    const int py = y - oy, pz = z - oz;
+    if (py < 0 || pz < 0 || py >= c.G.ny || pz >= c.G.nz) return 0;
+    const int a = max(x - hi, 0), b = min(x - lo, c.G.nx - 1);
+    if (a > b) return 0;
+    p0 = vid(c.G, a, py, pz);
+    const unsigned k = (unsigned)(b - a + 1), s = p0 & 31u;
+    const unsigned long long want = ((1ull << k) - 1ull) << s;
+    uint32_t *w = c.Dbits + (p0 >> 5);
+    unsigned long long got = 0;
+    const uint32_t m0 = (uint32_t)want, m1 = (uint32_t)(want >> 32);
+    if (m0) got |= (unsigned long long)(m0 & ~atomicOr(w, m0));
+    if (m1) got |= (unsigned long long)(m1 & ~atomicOr(w + 1, m1)) << 32;
+    return (unsigned)(got >> s);
+}
+
+// this lane's window row (LaneGeom)
+__device__ __forceinline__ unsigned mark_row(const Ctx &c, const LaneGeom &g, int x, int y, int z, uint32_t &p0)
+{
+    p0 = 0;
+    return g.row ? mark_run(c, g.oy, g.oz, g.lo, g.hi, x, y, z, p0) : 0u;
+}
+
+
 // one warp per changed vertex: when its order against some vertex within two edges
 // changed, the lanes share the dirty-anchor marks of its window; otherwise no code can
-// change and nothing is marked
+// change and nothing is marked.  (One thread per vertex loads less in the largest rounds,
+// but runs the ~60 ring checks of a vertex one after another in the middle-sized ones, and
+// lists the dirty anchors in an order that costs the refresh more than it saves.)
 template <int D> __global__ void k_mark(Ctx c)
 {
     if (round_off(c.ls)) return;
     __shared__ WarpStage<512> sd[TPB / 32];
-    __shared__ int ring[64][3];
-    for (int j = threadIdx.x; j < 64 * 3; j += blockDim.x) ring[j / 3][j % 3] = rt_tab<D>().ring[j / 3][j % 3];
+    __shared__ LaneGeom lgs[32];
+    __shared__ int win[64][3];
+    const Tab<D> &T = rt_tab<D>();
     const unsigned lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    if (threadIdx.x < 32) lgs[lane] = lane_geom<D>(lane);
+    for (int j = threadIdx.x; j < 64 * 3; j += blockDim.x) win[j / 3][j % 3] = j / 3 < T.nwin ? T.win[j / 3][j % 3] : 0;
     if (lane == 0) sd[wib].n = 0;
     __syncthreads();
-    const Tab<D> &T = rt_tab<D>();
+    const int nwin = T.nwin;
     const unsigned long long items = c.cnt->nE;
     const unsigned long long warp = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
     const unsigned long long nwarps = (gridDim.x * (unsigned long long)blockDim.x) >> 5;
     for (unsigned long long i = warp; i < items; i += nwarps) {
         const uint32_t v = c.Elist[i];
-        const bool flip = order_changed<D>(c, v, (int)lane, 32, ring);
-        if (!__any_sync(0xffffffffu, flip)) continue;
         int x, y, z;
         coords(c.G, v, x, y, z);
+        const bool flip = ring_changed<D>(c, v, x, y, z, lgs[lane]);
+        if (!__any_sync(0xffffffffu, flip)) continue;
 #pragma unroll
         for (int r = 0; r < 2; r++) {            // the window has at most 64 anchors
             const int j = (int)lane + 32 * r;
             bool has = false;
             uint32_t p = 0;
-            if (j < T.nwin) {
-                const int px = x - T.win[j][0], py = y - T.win[j][1], pz = z - T.win[j][2];
+            if (j < nwin) {
+                const int px = x - win[j][0], py = y - win[j][1], pz = z - win[j][2];
                 if (inside(c.G, px, py, pz)) {
                     p = vid(c.G, px, py, pz);
                     has = !test_and_set(c.Dbits, p);
@@ -945,18 +1085,30 @@ template <int D> __global__ void k_rebuild(Ctx c)
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ls->refresh_items, d);
 }
 
-// end of a round's edits: clear the round's sets through their lists, and list the blocks
-// of the critical-difference bitset that the next C-pass visits
+// end of a round's edits: clear the round's sets through their lists (and bring gprev back
+// to g at the round's items: between rounds gprev equals g everywhere, so the order-change
+// test reads a neighbour's pre-round value from gprev without asking whether it moved), and
+// list the blocks of the critical-difference bitset that the next C-pass visits
+__device__ __forceinline__ void clear_item(const Ctx &c, unsigned long long i, unsigned long long nT, unsigned long long nX)
+{
+    if (i < nT) {
+        const uint32_t v = c.Tlist[i];
+        c.Tbits[v >> 5] = 0;
+        c.gprev[v] = c.g[v];
+    } else if (i < nT + nX) {
+        const uint32_t v = c.Xlist[i - nT];
+        c.Xbits[v >> 5] = 0;
+        c.gprev[v] = c.g[v];
+    } else {
+        c.Dbits[c.Dlist[i - nT - nX] >> 5] = 0;
+    }
+}
+
 __global__ void k_clear(Ctx c)
 {
     if (round_off(c.ls)) return;
     const unsigned long long nT = c.cnt->nT, nX = c.cnt->nX, nD = c.cnt->nD;
-    GRID_STRIDE(i, nT + nX + nD)
-    {
-        if (i < nT) c.Tbits[c.Tlist[i] >> 5] = 0;
-        else if (i < nT + nX) c.Xbits[c.Xlist[i - nT] >> 5] = 0;
-        else c.Dbits[c.Dlist[i - nT - nX] >> 5] = 0;
-    }
+    GRID_STRIDE(i, nT + nX + nD) clear_item(c, i, nT, nX);
     list_blocks(c.Csum, csum_words(c.G.n), c.Cblk, &c.ls->nblk);
 }
 
@@ -1069,13 +1221,16 @@ __global__ void __launch_bounds__(TPB, 2) k_rounds(Ctx c, GridBarrier *gb, Count
     __shared__ uint16_t cq[TPB / 32][32 * CASES_PER_ANCHOR];   // P1: compacted false cases
     __shared__ Stage<TPB> se;            // P2: changed vertices; P4: separatrix dirty anchors
     __shared__ BlockTally tally;
-    __shared__ int ring[64][3];
-    for (int j = threadIdx.x; j < 64 * 3; j += blockDim.x) ring[j / 3][j % 3] = rt_tab<D>().ring[j / 3][j % 3];
+    const unsigned lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    __shared__ LaneGeom lgs[32];         // the same for every warp: kept in shared memory, where
+    if (threadIdx.x < 32) lgs[lane] = lane_geom<D>(lane);   // registers are scarce here
+    __syncthreads();
+    const LaneGeom &lg = lgs[lane];
     LoopState *ls = c.ls;
     uint32_t *const lists[2] = {c.Cblk, blk2};
-    const unsigned lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     const unsigned long long nthreads = (unsigned long long)gridDim.x * blockDim.x;
     const unsigned long long gtid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    const unsigned long long sgtid = (unsigned long long)threadIdx.x * gridDim.x + blockIdx.x;   // spread order
     unsigned long long tph = gtid == 0 ? global_ns() : 0;
     auto phase_end = [&](int ph) {   // block 0, thread 0: time since the last barrier
         if (gtid != 0) return;
@@ -1095,7 +1250,7 @@ __global__ void __launch_bounds__(TPB, 2) k_rounds(Ctx c, GridBarrier *gb, Count
         {
             uint32_t *nl = lists[nxt];
             unsigned long long *nn = &ls->nbl[nxt];
-            cpass_listed<D>(cc, u.q, cq, lists[cur], ls->nbl[cur], &ls->cpass_items,
+            cpass_listed<D, false>(cc, u.q, cq, lists[cur], ls->nbl[cur], &ls->cpass_items,
                             [&](uint32_t b) { nl[atomicAdd(nn, 1ull)] = b; });
         }
         tally_end(tally, cc);
@@ -1108,10 +1263,11 @@ __global__ void __launch_bounds__(TPB, 2) k_rounds(Ctx c, GridBarrier *gb, Count
         const unsigned long long nX = K->nX, items = nX + K->nT;
         if (gtid == 0) round_record(cc, K, 0, stop, status);
         if (stop) return;
+        // items are dealt round-robin over the blocks (i = k0 + thread * blocks + block), so that
+        // a round with fewer items than a block has threads still spreads them over every SM
         st_init(se);
-        BLOCK_ROUNDS(b, items)
-        {
-            const unsigned long long i = b + threadIdx.x;
+        for (unsigned long long k0 = 0; k0 < items; k0 += nthreads) {
+            const unsigned long long i = k0 + sgtid;
             if (i < items) {
                 uint32_t v;
                 if (edit_prepare(cc, (uint32_t)i, (uint32_t)nX, v)) {
@@ -1126,13 +1282,19 @@ __global__ void __launch_bounds__(TPB, 2) k_rounds(Ctx c, GridBarrier *gb, Count
         // P3: edited vertices whose order changed mark their windows dirty
         st_init(u.sd);
         const unsigned long long nE = K->nE;
-        for (unsigned long long b = (unsigned long long)blockIdx.x * wpb; b < nE; b += (unsigned long long)gridDim.x * wpb) {
-            const unsigned long long i = b + wib;
+        for (unsigned long long k0 = 0; k0 < nE; k0 += (unsigned long long)gridDim.x * wpb) {
+            const unsigned long long i = k0 + (unsigned long long)wib * gridDim.x + blockIdx.x;
             if (i < nE) {
                 const uint32_t v = c.Elist[i];
-                const bool flip = order_changed<D>(cc, v, (int)lane, 32, ring);
-                if (__any_sync(0xffffffffu, flip))
-                    mark_dirty<D>(cc, v, (int)lane, 32, [&](uint32_t p) { st_push(u.sd, p, c.Dlist, &K->nD); });
+                int x, y, z;
+                coords(c.G, v, x, y, z);
+                const bool flip = ring_changed<D>(cc, v, x, y, z, lg);
+                if (__any_sync(0xffffffffu, flip)) {
+                    uint32_t p0;
+                    const unsigned nm = mark_row(cc, lg, x, y, z, p0);
+                    for (int r = 0; r < 4; r++)
+                        if ((nm >> r) & 1u) st_push(u.sd, p0 + (uint32_t)r, c.Dlist, &K->nD);
+                }
             }
             st_flush(u.sd, c.Dlist, &K->nD);
         }
@@ -1142,9 +1304,8 @@ __global__ void __launch_bounds__(TPB, 2) k_rounds(Ctx c, GridBarrier *gb, Count
         const unsigned long long nD = K->nD, nT = K->nT;
         const int track = ls->track_dirty;
         st_init(se);
-        BLOCK_ROUNDS(b, nD)
-        {
-            const unsigned long long i = b + threadIdx.x;
+        for (unsigned long long k0 = 0; k0 < nD; k0 += nthreads) {
+            const unsigned long long i = k0 + sgtid;
             if (i < nD) {
                 const uint32_t p = c.Dlist[i];
                 const uint64_t cg = anchor_code<D, false>(c.g, c.G, p);
@@ -1154,11 +1315,7 @@ __global__ void __launch_bounds__(TPB, 2) k_rounds(Ctx c, GridBarrier *gb, Count
             }
             st_flush(se, c.sDlist, &ls->nSD);
         }
-        for (unsigned long long i = gtid; i < nT + nX + nD; i += nthreads) {
-            if (i < nT) c.Tbits[c.Tlist[i] >> 5] = 0;
-            else if (i < nT + nX) c.Xbits[c.Xlist[i - nT] >> 5] = 0;
-            else c.Dbits[c.Dlist[i - nT - nX] >> 5] = 0;
-        }
+        for (unsigned long long i = sgtid; i < nT + nX + nD; i += nthreads) clear_item(c, i, nT, nX);
         if (gtid == 0) {
             atomicAdd(&ls->refresh_items, nD);
             ls->nbl[cur] = 0;                    // list cur was read in P1; it is the next "next"
@@ -2612,7 +2769,7 @@ msc_status fix_loop(msc_handle *h, float xi, const msc_options &o, cudaStream_t 
     const int csize = persistent && o.cluster_round != 1 ? round_cluster_size<D>() : 0;
     L.small_round = small_thr;
     CK(cudaMemcpyAsync(h->ls.p, &L, sizeof L, cudaMemcpyHostToDevice, s));
-    KL(h, MSC_K_OTHER, s, k_init_g<<<grid_occ((const void *)k_init_g, h->G.n), TPB, 0, s>>>(h->f.p, h->fhat.p, h->g.p, h->state.p, h->G.n, xi));
+    KL(h, MSC_K_OTHER, s, k_init_g<<<grid_occ((const void *)k_init_g, h->G.n), TPB, 0, s>>>(h->f.p, h->fhat.p, h->g.p, h->gprev.p, h->state.p, h->G.n, xi));
     CK(cudaGetLastError());
     // sets left over by an earlier call that stopped with an error
     CK(cudaMemsetAsync(h->Tbits.p, 0, h->Tbits.n * 4, s));
