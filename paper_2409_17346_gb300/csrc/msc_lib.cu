@@ -159,17 +159,9 @@ template <int CAP> __device__ __forceinline__ void st_init(Stage<CAP> &s)
     __syncthreads();
 }
 
-// One shared atomic per group of converged lanes that push to the same stage (grouped by the
-// stage's address), not one per item: with every thread of a block pushing, the per-item
-// atomics on one counter queue up.
 template <int CAP> __device__ __forceinline__ void st_push(Stage<CAP> &s, uint32_t v, uint32_t *gl, unsigned long long *gn)
 {
-    const unsigned lane = threadIdx.x & 31;
-    const unsigned grp = __match_any_sync(__activemask(), (unsigned long long)(uintptr_t)&s);
-    const int leader = __ffs(grp) - 1;
-    unsigned base = 0;
-    if ((int)lane == leader) base = atomicAdd(&s.n, (unsigned)__popc(grp));
-    const unsigned k = __shfl_sync(grp, base, leader) + (unsigned)__popc(grp & ((1u << lane) - 1u));
+    const unsigned k = atomicAdd(&s.n, 1u);
     if (k < CAP) s.buf[k] = v;
     else gl[atomicAdd(gn, 1ull)] = v;
 }
@@ -1444,6 +1436,7 @@ __global__ void k_sd_clear(Ctx c, unsigned long long *nSD)
 // triangles (3D).  With out == nullptr only count[kind] is accumulated.
 struct SeedOut {
     uint32_t *out[3];
+    unsigned long long cap[3];   // entries each list holds; a seed past the end is not written
 };
 
 template <int D>
@@ -1468,24 +1461,49 @@ __global__ void k_seeds(const uint64_t *code, Grid G, SeedOut so, unsigned long 
         }
         return;
     }
-    // seeds are rare: the stages are flushed only once one is half full (and at the end);
-    // a push that finds its stage full goes to the list directly
-    constexpr int SCAP = 2048;
-    __shared__ Stage<SCAP> st[3];
-    for (int k = 0; k < NK; k++) st_init(st[k]);
+    // Every thread counts its anchor's seeds by kind; a block scan gives each thread its
+    // offsets and one atomic per block and kind reserves the block's range; then the thread
+    // derives its seeds again from the code and writes them there.  (Seeds are not rare: ~3
+    // per anchor in a noisy field, and one shared atomic per seed queued up.)
+    __shared__ unsigned wsum[NK][TPB / 32];
+    __shared__ unsigned long long base[NK];
+    const unsigned lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     BLOCK_ROUNDS(b, G.n)
     {
         const unsigned long long p = b + threadIdx.x;
-        if (p < G.n)
-            for (int k = 0; k < NK; k++)
-                seeds_anchor<D>(code, G, (uint32_t)p, k, [&](uint32_t v) { st_push(st[k], v, so.out[k], count + k); });
+        unsigned cnt[NK], off[NK];
+        for (int k = 0; k < NK; k++) {
+            cnt[k] = 0;
+            if (p < G.n) seeds_anchor<D>(code, G, (uint32_t)p, k, [&](uint32_t) { cnt[k]++; });
+            unsigned incl = cnt[k];
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= (unsigned)o) incl += y;
+            }
+            off[k] = incl - cnt[k];
+            if (lane == 31) wsum[k][wib] = incl;
+        }
         __syncthreads();
-        bool half = false;
-        for (int k = 0; k < NK; k++) half = half || st[k].n > SCAP / 2;
-        if (half)
-            for (int k = 0; k < NK; k++) st_flush(st[k], so.out[k], count + k);
+        if (threadIdx.x < NK) {
+            unsigned long long t = 0;
+            for (int w = 0; w < TPB / 32; w++) {
+                const unsigned x = wsum[threadIdx.x][w];
+                wsum[threadIdx.x][w] = (unsigned)t;       // exclusive prefix of the warps
+                t += x;
+            }
+            base[threadIdx.x] = t ? atomicAdd(count + threadIdx.x, t) : 0;
+        }
+        __syncthreads();
+        if (p < G.n)
+            for (int k = 0; k < NK; k++) {
+                unsigned long long at = base[k] + wsum[k][wib] + off[k];
+                seeds_anchor<D>(code, G, (uint32_t)p, k, [&](uint32_t v) {
+                    if (at < so.cap[k]) so.out[k][at] = v;
+                    at++;
+                });
+            }
+        __syncthreads();
     }
-    for (int k = 0; k < NK; k++) st_flush(st[k], so.out[k], count + k);
 }
 
 template <int D>
@@ -2502,7 +2520,7 @@ template <int D> msc_status build_seeds(msc_handle *h, cudaStream_t s)
     DevBuf<uint32_t> *bufs[3] = {&h->seeds_desc, &h->seeds_asc, &h->seeds_ss};
     uint32_t *ns[3] = {&h->n_desc, &h->n_asc, &h->n_ss};
     unsigned long long n[3] = {0, 0, 0};
-    SeedOut so{{nullptr, nullptr, nullptr}};
+    SeedOut so{{nullptr, nullptr, nullptr}, {0, 0, 0}};
     if (h->seeds_counted) {
         CK(cudaMemcpyAsync(n, h->seed_count.p, sizeof n, cudaMemcpyDeviceToHost, s));
     } else {
@@ -2515,12 +2533,17 @@ template <int D> msc_status build_seeds(msc_handle *h, cudaStream_t s)
     for (int k = 0; k < 3; k++) {
         CK(bufs[k]->alloc(n[k]));
         so.out[k] = bufs[k]->p;
+        so.cap[k] = n[k];
         *ns[k] = (uint32_t)n[k];
     }
     CK(cudaMemsetAsync(cnt.p, 0, sizeof n, s));
     KL(h, MSC_K_OTHER, s, k_seeds<D><<<grid_occ((const void *)k_seeds<D>, h->G.n), TPB, 0, s>>>(h->code_f.p, h->G, so, cnt.p));
     CK(cudaGetLastError());
+    unsigned long long m[3];
+    CK(cudaMemcpyAsync(m, cnt.p, sizeof m, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    for (int k = 0; k < 3; k++)
+        if (m[k] != n[k]) return fail(MSC_ERR_CUDA, "separatrix seed lists: %llu seeds listed, %llu counted", m[k], n[k]);
     cnt.release();
     return MSC_OK;
 }
