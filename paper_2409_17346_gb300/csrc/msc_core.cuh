@@ -850,6 +850,8 @@ template <int D> MSC_HD inline void asc_walk(const Ctx &c, uint32_t beta)
 // 2-saddle through edges paired upward in f; pairs missing from g's gradient are the
 // troublemakers; a local stack spills to a global queue when full
 constexpr int SS_STACK = 24;
+constexpr unsigned long long TRI_LOCAL_STEPS = 512;   // per-thread saddle-saddle steps before the rest is spilled
+                                                     // (512^3 update: 64 steps 18.9 ms, 512 17.1, no limit 17.3)
 
 MSC_HD inline void ss_push_global(const Ctx &c, uint32_t tri, uint32_t entry)
 {
@@ -1169,6 +1171,14 @@ MSC_HD inline void tri_propagate(const Ctx &c, uint32_t tri0, int dv0, bool appl
     };
     if (!apply_first) expand(tri0, dv0);
     while (sp > 0) {
+#ifdef __CUDA_ARCH__
+        // a long propagation goes on in the spill kernel, whose warps walk it converged: one
+        // thread walking a large subtree alone would hold the whole launch
+        if (n >= TRI_LOCAL_STEPS) {
+            for (int q = 0; q < sp; q++) ss_spill(c, st[q], sd[q]);
+            break;
+        }
+#endif
         sp--;
         const uint32_t t = st[sp];
         const int d = sd[sp];
@@ -1363,7 +1373,10 @@ MSC_HD inline void path_seed_walks(const Ctx &c, int kind, const uint32_t *seeds
 // lanes stay converged, where a depth-first walk per lane leaves most of them idle.  A full
 // stack spills to the global queue that k_tri_spill drains.  Every change is an atomic on a
 // node word, so the order of the items does not change the final state.  Must be called by
-// whole warps; seeds are taken 32 at a time by each warp of the grid.
+// whole warps; seeds are taken 32 at a time by each warp of the grid.  ITEMS: the list holds
+// n (triangle, delta) pairs to apply (the spill queue) instead of seeds; they go onto the
+// stack as they are.
+template <bool ITEMS = false>
 __device__ inline void tri_seed_walks(const Ctx &c, const uint32_t *seeds, uint32_t n, uint32_t *stk, int8_t *sdl, int cap)
 {
     const unsigned lane = threadIdx.x & 31;
@@ -1398,6 +1411,20 @@ __device__ inline void tri_seed_walks(const Ctx &c, const uint32_t *seeds, uint3
             // new seeds, one per lane: a 2-saddle triangle becomes a seed
             const unsigned long long i = next + lane;
             next += nwarps * 32;
+            if constexpr (ITEMS) {
+                const bool has = i < n;
+                const uint32_t t = has ? seeds[2 * i] : 0u;
+                const int d = has ? (int)seeds[2 * i + 1] : 0;
+                const unsigned m = __ballot_sync(0xffffffffu, has);
+                const int pos = sp + __popc(m & ((1u << lane) - 1u));
+                if (has) {
+                    if (pos < cap) { stk[pos] = t; sdl[pos] = (int8_t)d; }
+                    else ss_spill(c, t, d);
+                }
+                sp = min(sp + __popc(m), cap);
+                __syncwarp();
+                continue;
+            }
             bool go = false;
             int dv = 0;
             uint32_t u = 0;
@@ -1433,19 +1460,39 @@ __device__ inline void tri_seed_walks(const Ctx &c, const uint32_t *seeds, uint3
     count_add(&c.cnt->steps[2], steps);
 }
 
-// troublemakers among the pairs anchored at p (p has a code mismatch)
-// A pair's node carries the mismatch bit exactly when the pair's code field differs between
-// f and g (node_bits keeps it so for every anchor whose code changed), so only the node words
-// of differing pairs are read.
-template <int D> MSC_HD inline void node_targets(const Ctx &c, uint32_t p)
+// Troublemakers (Sec. 4.4) at a mismatched anchor p, one pair field at a time.  Field i:
+// 0 the vertex's pair, 1 + ft the pair of facet ft (tri in 3D, edge in 2D) with its top
+// cofacet, 1 + NFAC + et (3D) the pair of edge et with its triangle (or a dead end).
+// node_target_mask: bit i set iff field i is paired in f and differs in g (only those
+// nodes carry the mismatch bit, so only they are read).
+template <int D> MSC_HD inline uint32_t node_target_mask(uint64_t cf, uint64_t cg)
 {
     const Tab<D> &T = rt_tab<D>();
-    const uint64_t cf = ld(c.code_f + p), cg = c.code_g[p];
-    if (cf == cg) return;
+    if (cf == cg) return 0;
+    uint32_t m = 0;
+    const int vf = vfield<D>(cf);
+    if (vf != 15 && vfield<D>(cg) != vf) m |= 1u;
+    const int nfac = D == 3 ? T.NT : T.NE;
+    for (int ft = 0; ft < nfac; ft++) {
+        const int ff = facet_field<D>(cf, ft);
+        if (ff >= 2 && facet_field<D>(cg, ft) != ff) m |= 1u << (1 + ft);
+    }
+    if constexpr (D == 3)
+        for (int et = 0; et < T.NE; et++) {
+            const int ef = efield<D>(cf, et);
+            if (ef != 0 && efield<D>(cg, et) != ef) m |= 1u << (1 + nfac + et);
+        }
+    return m;
+}
+
+template <int D> MSC_HD inline void node_target_item(const Ctx &c, uint32_t p, uint64_t cf, int i)
+{
+    const Tab<D> &T = rt_tab<D>();
+    constexpr int NFAC = D == 3 ? Tab<D>::NT : Tab<D>::NE;
     int x, y, z;
     coords(c.G, p, x, y, z);
-    const int vf = vfield<D>(cf);
-    if (vf != 15 && vfield<D>(cg) != vf) {
+    if (i == 0) {
+        const int vf = vfield<D>(cf);
         const int32_t b = node_load(c.ns_v, p);
         if ((b & NS_MIS) && path_reached(b)) {
             Verts V;
@@ -1454,43 +1501,50 @@ template <int D> MSC_HD inline void node_targets(const Ctx &c, uint32_t p)
             vpush(V, c.G, x + T.nb[vf][0], y + T.nb[vf][1], z + T.nb[vf][2]);
             add_case<D>(c, V.id[1], V);
         }
+        return;
     }
-    const int nfac = D == 3 ? T.NT : T.NE;
-    for (int ft = 0; ft < nfac; ft++) {
+    if (i <= NFAC) {
+        const int ft = i - 1;
         const int ff = facet_field<D>(cf, ft);
-        if (ff < 2 || facet_field<D>(cg, ft) == ff) continue;
-        const int i = ff - 2;
-        const int *an = D == 3 ? T.tcof_anc[ft][i] : T.ecof_anc[ft][i];
-        const int bt = D == 3 ? T.tcof_type[ft][i] : T.ecof_type[ft][i];
+        const int k = ff - 2;
+        const int *an = D == 3 ? T.tcof_anc[ft][k] : T.ecof_anc[ft][k];
+        const int bt = D == 3 ? T.tcof_type[ft][k] : T.ecof_type[ft][k];
         const int bx = x + an[0], by = y + an[1], bz = z + an[2];
         const int32_t b = node_load(c.ns_top, vid(c.G, bx, by, bz) * T.NTOP + (uint32_t)bt);
         if ((b & NS_MIS) && path_reached(b)) {
             Verts V = top_verts<D>(c.G, bx, by, bz, bt);
             add_case<D>(c, V.id[lowest_of(V, c.f)], V);
         }
+        return;
     }
     if constexpr (D == 3) {
-        for (int et = 0; et < T.NE; et++) {
-            const int ef = efield<D>(cf, et);
-            if (ef == 0 || efield<D>(cg, et) == ef) continue;
-            if (ef == 1) {
-                const int32_t b = node_load(c.ns_dead, p * 7 + (uint32_t)et);
-                if ((b & NS_MIS) && node_count(b) > 0) {
-                    Verts V = cell_verts<3>(c.G, x, y, z, 1, et);
-                    add_case<3>(c, V.id[lowest_of(V, c.f)], V);
-                }
-                continue;
+        const int et = i - 1 - NFAC;
+        const int ef = efield<D>(cf, et);
+        if (ef == 1) {
+            const int32_t b = node_load(c.ns_dead, p * 7 + (uint32_t)et);
+            if ((b & NS_MIS) && node_count(b) > 0) {
+                Verts V = cell_verts<3>(c.G, x, y, z, 1, et);
+                add_case<3>(c, V.id[lowest_of(V, c.f)], V);
             }
-            const int i = ef - 2;
-            const int tx = x + T.ecof_anc[et][i][0], ty = y + T.ecof_anc[et][i][1], tz = z + T.ecof_anc[et][i][2];
-            const int t2 = T.ecof_type[et][i];
-            const int32_t b = node_load(c.ns_tri, vid(c.G, tx, ty, tz) * 12 + (uint32_t)t2);
-            if ((b & NS_MIS) && node_count(b) > 0 && !(b & NS_SEED)) {
-                Verts V = cell_verts<3>(c.G, tx, ty, tz, 2, t2);
-                add_case<3>(c, vid(c.G, x + T.ecof_v[et][i][0], y + T.ecof_v[et][i][1], z + T.ecof_v[et][i][2]), V);
-            }
+            return;
+        }
+        const int k = ef - 2;
+        const int tx = x + T.ecof_anc[et][k][0], ty = y + T.ecof_anc[et][k][1], tz = z + T.ecof_anc[et][k][2];
+        const int t2 = T.ecof_type[et][k];
+        const int32_t b = node_load(c.ns_tri, vid(c.G, tx, ty, tz) * 12 + (uint32_t)t2);
+        if ((b & NS_MIS) && node_count(b) > 0 && !(b & NS_SEED)) {
+            Verts V = cell_verts<3>(c.G, tx, ty, tz, 2, t2);
+            add_case<3>(c, vid(c.G, x + T.ecof_v[et][k][0], y + T.ecof_v[et][k][1], z + T.ecof_v[et][k][2]), V);
         }
     }
+}
+
+// all troublemakers at anchor p
+template <int D> MSC_HD inline void node_targets(const Ctx &c, uint32_t p)
+{
+    const uint64_t cf = ld(c.code_f + p), cg = c.code_g[p];
+    for (int i = 0; i < 32; i++)
+        if ((node_target_mask<D>(cf, cg) >> i) & 1u) node_target_item<D>(c, p, cf, i);
 }
 
 // ------------------------------------------------------------------------------------

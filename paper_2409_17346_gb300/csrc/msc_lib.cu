@@ -1410,17 +1410,88 @@ template <int D> __global__ void k_node_update(Ctx c, const unsigned long long *
     GRID_STRIDE(i, n) node_bits<D>(c, c.sDlist[i], false);
 }
 
+// (triangle, delta) items of the spill queue: the converged per-warp stack walk of the first
+// build, fed with items instead of seeds
 __global__ void k_tri_spill(Ctx c, const uint32_t *items, uint32_t n)
 {
-    GRID_STRIDE(i, n) tri_propagate(c, items[2 * i], 0, true, (int)items[2 * i + 1]);
+    __shared__ uint32_t stk[TPB / 32][SS_WARP_STACK];
+    __shared__ int8_t sdl[TPB / 32][SS_WARP_STACK];
+    const unsigned wib = threadIdx.x >> 5;
+    tri_seed_walks<true>(c, items, n, stk[wib], sdl[wib], SS_WARP_STACK);
 }
 
+// Troublemakers at the mismatched anchors.  A warp compacts the set bits of 32 words of the
+// mismatch bitset, then takes its anchors 32 at a time and their differing pair fields one
+// kind at a time (vertex, facet, edge), so that the lanes of a pass run the same branch of
+// node_target_item (per anchor, a warp ran ~5 of 32 lanes).
 template <int D> __global__ void k_node_targets(Ctx c)
 {
     __shared__ BlockTally tally;
+    __shared__ uint32_t aq[TPB / 32][32 * 32];
+    __shared__ uint16_t fq[TPB / 32][32 * 16];   // one kind's fields of 32 anchors (at most 12 each)
     Ctx cc = c;
     tally_begin(tally, cc);
-    for_each_set(c.Mbits, c.G.n, [&](uint32_t p) { node_targets<D>(cc, p); });
+    constexpr int NFAC = D == 3 ? Tab<D>::NT : Tab<D>::NE;
+    static_assert(NFAC <= 16 && Tab<D>::NE <= 16, "field queue too small");
+    constexpr uint32_t GRP[3] = {1u, ((1u << NFAC) - 1u) << 1, D == 3 ? ((1u << Tab<D>::NE) - 1u) << (1 + NFAC) : 0u};
+    const unsigned lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint32_t *mq = aq[wib];
+    uint16_t *cw = fq[wib];
+    const unsigned long long nw = (c.G.n + 31ull) / 32;
+    const unsigned long long warp = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long nwarps = (gridDim.x * (unsigned long long)blockDim.x) >> 5;
+    for (unsigned long long w0 = warp * 32; w0 < nw; w0 += nwarps * 32) {
+        uint32_t mine = w0 + lane < nw ? c.Mbits[w0 + lane] : 0u;
+        const unsigned cnt = __popc(mine);
+        unsigned pre = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, pre, o);
+            if (lane >= (unsigned)o) pre += y;
+        }
+        const unsigned total = __shfl_sync(0xffffffffu, pre, 31);
+        if (total == 0) continue;
+        unsigned at = pre - cnt;
+        const uint32_t base = (uint32_t)((w0 + lane) * 32);
+        while (mine) {
+            const int k = __ffs(mine) - 1;
+            mine &= mine - 1;
+            mq[at++] = base + (uint32_t)k;
+        }
+        __syncwarp();
+        for (unsigned k0 = 0; k0 < total; k0 += 32) {
+            uint32_t m0 = 0;
+            if (k0 + lane < total) {
+                const uint32_t p = mq[k0 + lane];
+                m0 = node_target_mask<D>(__ldg(c.code_f + p), c.code_g[p]);
+            }
+#pragma unroll
+            for (int gi = 0; gi < 3; gi++) {
+                uint32_t m = m0 & GRP[gi];
+                if (!__any_sync(0xffffffffu, m != 0)) continue;
+                const unsigned nc = __popc(m);
+                unsigned cpre = nc;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned y = __shfl_up_sync(0xffffffffu, cpre, o);
+                    if (lane >= (unsigned)o) cpre += y;
+                }
+                const unsigned ctot = __shfl_sync(0xffffffffu, cpre, 31);
+                unsigned ca = cpre - nc;
+                while (m) {
+                    const int k = __ffs(m) - 1;
+                    m &= m - 1;
+                    cw[ca++] = (uint16_t)((lane << 5) | (unsigned)k);
+                }
+                __syncwarp();
+                for (unsigned j = lane; j < ctot; j += 32) {
+                    const unsigned e = cw[j];
+                    const uint32_t p = mq[k0 + (e >> 5)];
+                    node_target_item<D>(cc, p, __ldg(c.code_f + p), (int)(e & 31u));
+                }
+                __syncwarp();
+            }
+        }
+        __syncwarp();
+    }
     tally_end(tally, c);
 }
 
@@ -2619,7 +2690,8 @@ template <int D> msc_status s_pass_state(msc_handle *h, Ctx &c, bool &built, uns
             const unsigned long long zero = 0;
             CK(cudaMemcpyAsync(&h->cnt.p->novf, &zero, sizeof zero, cudaMemcpyHostToDevice, s));
             c.ovf_out = out;
-            KL(h, spill_cls, s, k_tri_spill<<<grid_occ((const void *)k_tri_spill, hc.novf), TPB, 0, s>>>(c, in, (uint32_t)hc.novf));
+            const int tg = std::min(grid_occ((const void *)k_tri_spill, hc.novf), SS_BLOCKS_PER_SM * sm_count());
+            KL(h, spill_cls, s, k_tri_spill<<<tg, TPB, 0, s>>>(c, in, (uint32_t)hc.novf));
             CK(cudaGetLastError());
             std::swap(in, out);
         }
