@@ -139,9 +139,9 @@ CLASS_LIMITER = {
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of a class's kernels per work
 # item, from one ncu capture of the same workload at 256^3 (the capture's launches over the
 # items they processed); a launch's traffic is that figure times the launch's items.  The
-# figure is from a capture of k_node_seed (converged warp walks) and k_node_seed_ss as they
-# stand (3 launches, 131,205,873 node steps).
-TRAFFIC_PER_ITEM = {"sep_seed": (239320064 + 23293952 + 823610368 + 208239360 + 2817286400 + 1521402624) / 131205873.0}
+# figure is from captures of k_node_seed (converged warp walks) and k_node_seed_ss (children in
+# registers, 6 blocks per SM) as they stand (3 launches, 131,205,873 node steps).
+TRAFFIC_PER_ITEM = {"sep_seed": (239320064 + 23293952 + 823610368 + 208239360 + 2937810000 + 1391782000) / 131205873.0}
 
 
 def class_bytes(cls, tot, n, steps, ndim):
