@@ -357,6 +357,16 @@ msc_status msc_release_cached_memory(void);
  * injection off.  Process-wide; returns the number of failures injected so far. */
 uint64_t msc_inject_alloc_failures(uint64_t after, uint64_t count);
 
+/* Walk limits for tests (not part of the method).  The saddle-saddle propagation of the
+ * separatrix state (Sec. 4.4) keeps its pending triangles on a stack per warp in shared
+ * memory (384 entries) and, in the incremental update, lets one thread walk up to 512 steps
+ * before it hands the rest of its stack to a spill queue that a converged kernel drains.
+ * warp_stack (1..384) and local_steps (>= 1) lower these limits for the next fixes so that
+ * small fields take the spill paths; 0 for either restores its default.  Results do not
+ * depend on the limits (every change is an atomic on a node word).  Process-wide; returns
+ * MSC_ERR_INVALID_ARG for a warp_stack above 384. */
+msc_status msc_set_walk_limits(uint32_t warp_stack, uint32_t local_steps);
+
 /* Self-test of the bounded waits (not part of the method).  The persistent round kernel
  * separates its phases with a grid barrier whose wait gives up after 2 s of device time,
  * records MSC_ERR_DEVICE_TIMEOUT and ends the kernel, so that a block that never arrives

@@ -177,6 +177,8 @@ struct Ctx {
     uint32_t *vis_v, *vis_top, *vis_tri;
     uint32_t *ovf_in, *ovf_out;      // saddle-saddle spill queues: (triangle id, entry edge) pairs
     uint32_t ovf_cap;
+    uint32_t ss_stack_cap;           // entries of a warp's saddle-saddle stack in use (<= its size)
+    uint32_t tri_local_steps;        // steps one thread walks before it spills the rest
     Counters *cnt;
     // persistent separatrix state (tier 4): one byte per node, see "separatrix state" below
     uint32_t *ns_v, *ns_top, *ns_tri, *ns_dead;   // separatrix node words, two per uint32
@@ -850,8 +852,8 @@ template <int D> MSC_HD inline void asc_walk(const Ctx &c, uint32_t beta)
 // 2-saddle through edges paired upward in f; pairs missing from g's gradient are the
 // troublemakers; a local stack spills to a global queue when full
 constexpr int SS_STACK = 24;
-constexpr unsigned long long TRI_LOCAL_STEPS = 512;   // per-thread saddle-saddle steps before the rest is spilled
-                                                     // (512^3 update: 64 steps 18.9 ms, 512 17.1, no limit 17.3)
+constexpr unsigned TRI_LOCAL_STEPS = 512;   // per-thread saddle-saddle steps before the rest is spilled
+                                           // (512^3 update: 64 steps 18.9 ms, 512 17.1, no limit 17.3)
 
 MSC_HD inline void ss_push_global(const Ctx &c, uint32_t tri, uint32_t entry)
 {
@@ -1174,7 +1176,7 @@ MSC_HD inline void tri_propagate(const Ctx &c, uint32_t tri0, int dv0, bool appl
 #ifdef __CUDA_ARCH__
         // a long propagation goes on in the spill kernel, whose warps walk it converged: one
         // thread walking a large subtree alone would hold the whole launch
-        if (n >= TRI_LOCAL_STEPS) {
+        if (n >= c.tri_local_steps) {
             for (int q = 0; q < sp; q++) ss_spill(c, st[q], sd[q]);
             break;
         }

@@ -1055,24 +1055,20 @@ template <int D> __device__ __forceinline__ bool rebuild_anchor(const Ctx &c, ui
     return !(atomicOr(c.Csum + (p >> 15), sb) & sb);
 }
 
-// mismatch bitsets after a round: only re-evaluated (dirty) anchors can change membership
+// mismatch bitsets after a round: only re-evaluated (dirty) anchors can change membership.
+// A refreshed anchor also joins the separatrix dirty set (a bit, set without waiting for
+// the old value; the S-pass lists the set bits once, k_sd_list).
 template <int D> __global__ void k_rebuild(Ctx c)
 {
     if (round_off(c.ls)) return;
-    __shared__ Stage<TPB> ss;
-    st_init(ss);
     LoopState *ls = c.ls;
     const unsigned long long d = c.cnt->nD;
     const int track = ls->track_dirty;
-    BLOCK_ROUNDS(b, d)
+    GRID_STRIDE(i, d)
     {
-        const unsigned long long i = b + threadIdx.x;
-        if (i < d) {
-            const uint32_t p = c.Dlist[i];
-            if (track && !test_and_set(c.sDbits, p)) st_push(ss, p, c.sDlist, &ls->nSD);
-            rebuild_anchor<D>(c, p, c.code_g[p]);
-        }
-        st_flush(ss, c.sDlist, &ls->nSD);
+        const uint32_t p = c.Dlist[i];
+        if (track) atomicOr(c.sDbits + (p >> 5), 1u << (p & 31));
+        rebuild_anchor<D>(c, p, c.code_g[p]);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ls->refresh_items, d);
 }
@@ -1295,17 +1291,12 @@ __global__ void __launch_bounds__(TPB, 2) k_rounds(Ctx c, GridBarrier *gb, Count
         // P4: new codes and mismatch bits of the dirty anchors; clear the round's sets
         const unsigned long long nD = K->nD, nT = K->nT;
         const int track = ls->track_dirty;
-        st_init(se);
-        for (unsigned long long k0 = 0; k0 < nD; k0 += nthreads) {
-            const unsigned long long i = k0 + sgtid;
-            if (i < nD) {
-                const uint32_t p = c.Dlist[i];
-                const uint64_t cg = anchor_code<D, false>(c.g, c.G, p);
-                c.code_g[p] = cg;
-                if (track && !test_and_set(c.sDbits, p)) st_push(se, p, c.sDlist, &ls->nSD);
-                if (rebuild_anchor<D>(cc, p, cg)) lists[nxt][atomicAdd(&ls->nbl[nxt], 1ull)] = p >> 10;
-            }
-            st_flush(se, c.sDlist, &ls->nSD);
+        for (unsigned long long i = sgtid; i < nD; i += nthreads) {
+            const uint32_t p = c.Dlist[i];
+            const uint64_t cg = anchor_code<D, false>(c.g, c.G, p);
+            c.code_g[p] = cg;
+            if (track) atomicOr(c.sDbits + (p >> 5), 1u << (p & 31));
+            if (rebuild_anchor<D>(cc, p, cg)) lists[nxt][atomicAdd(&ls->nbl[nxt], 1ull)] = p >> 10;
         }
         for (unsigned long long i = sgtid; i < nT + nX + nD; i += nthreads) clear_item(c, i, nT, nX);
         if (gtid == 0) {
@@ -1384,9 +1375,11 @@ template <int D> __global__ void __launch_bounds__(TPB) k_node_init(Ctx c)
     GRID_STRIDE(p, c.G.n) node_bits<D>(c, (uint32_t)p, true);
 }
 
-template <int D> __global__ void __launch_bounds__(TPB, 4) k_node_seed(Ctx c, int kind, const uint32_t *seeds, uint32_t n)
+// two walk slots per lane at 6 blocks per SM (512^3 first build: 4 slots at 4 blocks 25.5 ms,
+// 2 at 6: 24.4 ms, 4 at 3: 27.0, 4 or 8 at 2: 31.0)
+template <int D> __global__ void __launch_bounds__(TPB, 6) k_node_seed(Ctx c, int kind, const uint32_t *seeds, uint32_t n)
 {
-    path_seed_walks<D, 4>(c, kind, seeds, n, (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5,
+    path_seed_walks<D, 2>(c, kind, seeds, n, (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5,
                           (gridDim.x * (unsigned long long)blockDim.x) >> 5);
 }
 
@@ -1401,7 +1394,7 @@ __global__ void k_node_seed_ss(Ctx c, const uint32_t *seeds, uint32_t n)
     __shared__ uint32_t stk[TPB / 32][SS_WARP_STACK];
     __shared__ int8_t sdl[TPB / 32][SS_WARP_STACK];
     const unsigned wib = threadIdx.x >> 5;
-    tri_seed_walks(c, seeds, n, stk[wib], sdl[wib], SS_WARP_STACK);
+    tri_seed_walks(c, seeds, n, stk[wib], sdl[wib], (int)c.ss_stack_cap);
 }
 
 template <int D> __global__ void k_node_update(Ctx c, const unsigned long long *nSD)
@@ -1417,7 +1410,7 @@ __global__ void k_tri_spill(Ctx c, const uint32_t *items, uint32_t n)
     __shared__ uint32_t stk[TPB / 32][SS_WARP_STACK];
     __shared__ int8_t sdl[TPB / 32][SS_WARP_STACK];
     const unsigned wib = threadIdx.x >> 5;
-    tri_seed_walks<true>(c, items, n, stk[wib], sdl[wib], SS_WARP_STACK);
+    tri_seed_walks<true>(c, items, n, stk[wib], sdl[wib], (int)c.ss_stack_cap);
 }
 
 // Troublemakers at the mismatched anchors.  A warp compacts the set bits of 32 words of the
@@ -1493,6 +1486,12 @@ template <int D> __global__ void k_node_targets(Ctx c)
         __syncwarp();
     }
     tally_end(tally, c);
+}
+
+// the separatrix dirty set as a list (its bits are set by the refreshes since the last S-pass)
+__global__ void k_sd_list(Ctx c, unsigned long long *nSD)
+{
+    for_each_set(c.sDbits, c.G.n, [&](uint32_t p) { c.sDlist[list_slot(nSD)] = p; });
 }
 
 __global__ void k_sd_clear(Ctx c, unsigned long long *nSD)
@@ -2014,27 +2013,6 @@ MemKind mem_kind(const void *p)
     return MemKind::PageableHost;
 }
 
-// Whether the current device reads pageable host memory through the host's page tables (a
-// Grace host over NVLink-C2C): there a copy from pageable memory runs at the link's rate
-// (~190 GB/s measured on GB300), above what host threads copying through pinned staging
-// buffers reach (~14 GB/s per thread), so host-to-device copies go direct.
-bool pageable_direct()
-{
-    static std::mutex mu;
-    static std::vector<std::pair<int, bool>> known;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return false; }
-    std::lock_guard<std::mutex> lk(mu);
-    for (auto &k : known) if (k.first == dev) return k.second;
-    int a = 0;
-    if (cudaDeviceGetAttribute(&a, cudaDevAttrPageableMemoryAccessUsesHostPageTables, dev) != cudaSuccess) {
-        cudaGetLastError();
-        a = 0;
-    }
-    known.emplace_back(dev, a == 1);
-    return a == 1;
-}
-
 constexpr size_t STAGE_CHUNK = 32u << 20;   // bytes per staging chunk
 constexpr int STAGE_BUFS = 3;               // chunks in flight
 
@@ -2068,8 +2046,10 @@ cudaError_t copy_to_device(void *dst, const void *src, size_t n, cudaStream_t s)
 {
     const MemKind k = mem_kind(src);
     if (k == MemKind::Device) return cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToDevice, s);
-    if (k == MemKind::PinnedHost || n <= STAGE_CHUNK || pageable_direct())
-        return cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, s);
+    // (no direct path from pageable memory, even where the device reads host page tables: its
+    // rate depends on how the host backs the pages, 190 GB/s on a fresh process, e2e at 512^3
+    // 1.3 GB/s direct against 2.4 GB/s staged after other work had run on the host)
+    if (k == MemKind::PinnedHost || n <= STAGE_CHUNK) return cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, s);
     Staging st;
     cudaError_t e = st.init(STAGE_CHUNK);
     if (e != cudaSuccess) return e;
@@ -2091,8 +2071,8 @@ cudaError_t copy_from_device(void *dst, const void *src, size_t n, cudaStream_t 
 {
     const MemKind k = mem_kind(dst);
     if (k == MemKind::Device) return cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToDevice, s);
-    // (no direct path here: a destination the host has not touched yet, such as a fresh
-    // result buffer, makes the device fault its pages in one by one: 27 GB/s measured)
+    // (no direct path here either: the device's first writes to a host buffer run slowly while
+    // it maps the pages, 27 GB/s for a fresh 512 MB array)
     if (k == MemKind::PinnedHost || n <= STAGE_CHUNK) return cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, s);
     Staging st;
     cudaError_t e = st.init(STAGE_CHUNK);
@@ -2146,6 +2126,14 @@ cudaMemPool_t lib_pool()
     g_pools.emplace_back(dev, pool);
     return pool;
 }
+
+// (triangle, delta) pairs a saddle-saddle spill queue holds: one per vertex, at least 1 M (a
+// small field whose walks spill often, for instance under lowered walk limits, still fits)
+uint64_t ovf_pairs(uint64_t n) { return std::max<uint64_t>(n + 1, 1ull << 20); }
+
+// walk limits (msc_set_walk_limits): the saddle-saddle stack entries a warp uses, the steps
+// a thread walks before spilling
+std::atomic<uint32_t> g_walk_stack{(uint32_t)SS_WARP_STACK}, g_walk_steps{TRI_LOCAL_STEPS};
 
 // allocation-failure injection (msc_inject_alloc_failures): the count of allocations still
 // allowed before failures start, and the failures left to inject
@@ -2414,8 +2402,8 @@ msc_status alloc_fix_state(msc_handle *h)
     CK(h->vis_top.alloc(words(n * ntop)));
     if (h->D == 3) {
         CK(h->vis_tri.alloc(words(n * 12)));
-        CK(h->ovf0.alloc(2 * n + 2));
-        CK(h->ovf1.alloc(2 * n + 2));
+        CK(h->ovf0.alloc(2 * ovf_pairs(n)));
+        CK(h->ovf1.alloc(2 * ovf_pairs(n)));
     }
     CK(h->ns_v.alloc(node_words(n + 4)));
     CK(h->ns_top.alloc(node_words(n * ntop + 4)));
@@ -2462,7 +2450,9 @@ Ctx make_ctx(msc_handle *h, int tier, int qmax, int exact_fallback, float xi, in
     c.Elist = h->Elist.p;
     c.gprev = h->gprev.p;
     c.vis_v = h->vis_v.p; c.vis_top = h->vis_top.p; c.vis_tri = h->vis_tri.p;
-    c.ovf_cap = (uint32_t)h->G.n + 1;
+    c.ovf_cap = (uint32_t)ovf_pairs(h->G.n);
+    c.ss_stack_cap = g_walk_stack.load();
+    c.tri_local_steps = g_walk_steps.load();
     c.cnt = h->cnt.p;
     c.ns_v = h->ns_v.p; c.ns_top = h->ns_top.p; c.ns_tri = h->ns_tri.p; c.ns_dead = h->ns_dead.p;
     c.sDbits = h->sDbits.p; c.sDlist = h->sDlist.p;
@@ -2700,6 +2690,8 @@ template <int D> msc_status s_pass_state(msc_handle *h, Ctx &c, bool &built, uns
         built = true;
         k_set_track<<<1, 1, 0, s>>>(h->ls.p, 1);
     } else {
+        CK(cudaMemsetAsync(nSD, 0, sizeof(unsigned long long), s));
+        KL(h, MSC_K_SEP_UPDATE, s, k_sd_list<<<grid_occ((const void *)k_sd_list, h->G.n / 1024 + 1), TPB, 0, s>>>(c, nSD));
         KL(h, MSC_K_SEP_UPDATE, s, k_node_update<D><<<grid_occ((const void *)k_node_update<D>, h->G.n / 16 + 1), TPB, 0, s>>>(c, nSD));
         CK(cudaGetLastError());
     }
@@ -3420,7 +3412,7 @@ uint64_t msc_device_bytes(int nx, int ny, int nz)
     const uint64_t ntop = d3 ? 6 : 2;
     uint64_t b = 12 * n + n + 16 * n;             // f, f_hat, g; state; code_f, code_g
     b += 4 * (n / 8 + 4) + 8 * 4 * n;             // four bitsets; eight index lists
-    b += n / 8 + ntop * n / 8 + (d3 ? 12 * n / 8 + 16 * n : 0);   // walk visited sets, spill queues
+    b += n / 8 + ntop * n / 8 + (d3 ? 12 * n / 8 + 16 * ovf_pairs(n) : 0);   // walk visited sets, spill queues
     b += 2 * n * (1 + ntop + (d3 ? 19 : 0));      // separatrix node words (16 bits each)
     b += (d3 ? 6 : 3) * 4 * n;                    // separatrix seeds (upper estimate)
     b += 8 * n;                                   // pre-round values and list of edited vertices
@@ -3894,6 +3886,16 @@ msc_status msc_release_cached_memory(void)
     host_trim();
     cudaMemPool_t pool = lib_pool();
     if (pool) CK(cudaMemPoolTrimTo(pool, 0));
+    return MSC_OK;
+}
+
+msc_status msc_set_walk_limits(uint32_t warp_stack, uint32_t local_steps)
+{
+    g_last_error.clear();
+    if (warp_stack > (uint32_t)SS_WARP_STACK)
+        return fail(MSC_ERR_INVALID_ARG, "warp_stack must be at most %d", SS_WARP_STACK);
+    g_walk_stack.store(warp_stack ? warp_stack : (uint32_t)SS_WARP_STACK);
+    g_walk_steps.store(local_steps ? local_steps : TRI_LOCAL_STEPS);
     return MSC_OK;
 }
 

@@ -140,6 +140,8 @@ def load():
     lib.msc_selftest_barrier.argtypes = [i, vp]
     lib.msc_release_cached_memory.argtypes = []
     lib.msc_pool_used_bytes.argtypes = [ctypes.POINTER(u64)]
+    lib.msc_set_walk_limits.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
+    lib.msc_set_walk_limits.restype = ctypes.c_int
     lib.msc_inject_alloc_failures.argtypes = [u64, u64]
     lib.msc_inject_alloc_failures.restype = u64
     lib.msc_server_cancel.argtypes = [vp, u64]
@@ -630,6 +632,13 @@ def inject_alloc_failures(after, count):
     """Test hook: after `after` more device allocations succeed, the next `count` fail as if
     the device were out of memory (count 0 turns it off).  Returns failures injected so far."""
     return int(load().msc_inject_alloc_failures(int(after), int(count)))
+
+
+def set_walk_limits(warp_stack=0, local_steps=0):
+    """Test hook: lower the saddle-saddle walk's per-warp stack (1..384 entries) and the steps
+    one thread walks before it spills, so that small fields take the spill paths (0 restores
+    a default).  Results do not depend on them."""
+    _check(load().msc_set_walk_limits(int(warp_stack), int(local_steps)))
 
 
 def pool_used_bytes():

@@ -184,6 +184,38 @@ def test_fix_loop_matches_oracle_large(lib, idx):
     assert ed["n_iters_c"] > 100
 
 
+@pytest.mark.parametrize("limits", [(2, 2), (8, 4), (32, 16)])
+@pytest.mark.parametrize("idx", [5, 7])
+def test_saddle_walk_spill_paths_match_oracle(lib, idx, limits):
+    """Tier 4 in 3D with the saddle-saddle walk's per-warp stack and per-thread step limit
+    lowered, so that the first build and the updates spill most of their pending triangles
+    to the queue that the converged spill kernel drains: the same result, round by round."""
+    name, kw = FIX_CASES[idx]
+    f, fh, xi, _ = synth.config_case(name, **kw)
+    lib.set_walk_limits(*limits)
+    try:
+        _check_fix(lib, f, fh, xi, 4)
+        _check_fix(lib, f, fh, xi, 4, small_round=1)
+    finally:
+        lib.set_walk_limits(0, 0)
+
+
+def test_saddle_walk_spill_paths_large(lib):
+    """The same on a 48^3 field with a 16-entry stack and 8-step walks."""
+    f, fh, xi, _ = synth.config_case("kolmogorov3d", size=48, rel=1e-3)
+    lib.set_walk_limits(16, 8)
+    try:
+        _check_fix(lib, f, fh, xi, 4)
+    finally:
+        lib.set_walk_limits(0, 0)
+
+
+def test_walk_limits_reject_a_stack_above_its_size(lib):
+    with pytest.raises(lib.MscError):
+        lib.set_walk_limits(385, 0)
+    lib.set_walk_limits(0, 0)
+
+
 @pytest.mark.parametrize("idx", [0, 3, 5, 7])
 @pytest.mark.parametrize("q_max", [2, 6])
 def test_floating_edit_mode_matches_oracle(lib, idx, q_max):
