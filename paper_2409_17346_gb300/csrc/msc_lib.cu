@@ -2691,7 +2691,7 @@ template <int D> msc_status s_pass_state(msc_handle *h, Ctx &c, bool &built, uns
         k_set_track<<<1, 1, 0, s>>>(h->ls.p, 1);
     } else {
         CK(cudaMemsetAsync(nSD, 0, sizeof(unsigned long long), s));
-        KL(h, MSC_K_SEP_UPDATE, s, k_sd_list<<<grid_occ((const void *)k_sd_list, h->G.n / 1024 + 1), TPB, 0, s>>>(c, nSD));
+        KL(h, MSC_K_SEP_UPDATE, s, k_sd_list<<<grid_occ((const void *)k_sd_list, ((unsigned long long)h->G.n + 31) / 32), TPB, 0, s>>>(c, nSD));
         KL(h, MSC_K_SEP_UPDATE, s, k_node_update<D><<<grid_occ((const void *)k_node_update<D>, h->G.n / 16 + 1), TPB, 0, s>>>(c, nSD));
         CK(cudaGetLastError());
     }
