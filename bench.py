@@ -138,10 +138,14 @@ CLASS_LIMITER = {
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of a class's kernels per work
 # item, from one ncu capture of the same workload at 256^3 (the capture's launches over the
-# items they processed); a launch's traffic is that figure times the launch's items.  The
-# figure is from captures of k_node_seed (converged warp walks) and k_node_seed_ss (children in
-# registers, 6 blocks per SM) as they stand (3 launches, 131,205,873 node steps).
-TRAFFIC_PER_ITEM = {"sep_seed": (239320064 + 23293952 + 823610368 + 208239360 + 2937810000 + 1391782000) / 131205873.0}
+# items they processed); a launch's traffic is that figure times the launch's items.
+#   sep_seed: k_node_seed (two converged walk slots per lane) and k_node_seed_ss as they stand,
+#     3 launches, 131,205,873 node steps;
+#   rounds: every k_rounds launch of two fixes, 138 launches, 1,732 rounds.
+TRAFFIC_PER_ITEM = {
+    "sep_seed": (261218816 + 23131392 + 1053371904 + 266854656 + 2967052800 + 1397244416) / 131205873.0,
+    "rounds": 182722048 / 1732.0,
+}
 
 
 def class_bytes(cls, tot, n, steps, ndim):
@@ -589,7 +593,7 @@ def main():
                     avg_launch_ms=avg_ms, launches_per_step=tot["launches"] / args.steps)
         if dom in TRAFFIC_PER_ITEM:
             roof["traffic"] = TRAFFIC_PER_ITEM[dom] * tot["items"] / tot["launches"]
-            roof["traffic_source"] = "ncu dram bytes per item at 256^3, scaled by items per launch"
+            roof["traffic_source"] = "ncu dram bytes per item (node step or round) at 256^3, scaled by the launch's items"
     # the whole loop against the same peak: every class's algorithmic bytes in the breakdown
     # step over the step's time (the worklist form counts its own bytes, not a dense pass's)
     loop_bytes = 0.0
