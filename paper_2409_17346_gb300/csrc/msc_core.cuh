@@ -193,6 +193,10 @@ struct Ctx {
     unsigned long long *tally;       // when set: per-block (cases, live cases) in shared memory
     int mark_only;                   // add_case only sets the target's T bit (no return value
                                      // awaited); k_tlist lists the T bits afterwards
+    float *fuse_g;                   // when set (persistent round kernel): the C-pass thread that
+                                     // lists a new target edits it at once, writing fuse_g (the
+                                     // live g) while the round's cases read g (here the pre-round
+                                     // copy); the state follows in the mark phase
     // verification of saddle-saddle connectors: triangles from which the walk found a
     // troublemaker (bitset over triangle ids, plus a list of them, ss_cap entries)
     uint32_t *ss_bad, *ss_list;
@@ -412,6 +416,8 @@ template <bool NC = true> MSC_HD inline int lowest_of(const Verts &V, const floa
 
 // a false case: vertex t is lowered this round; a stuck case restores the closed 1-rings of
 // the case cell's vertices to f (exact fallback)
+MSC_HD inline void fuse_target(const Ctx &c, uint32_t t);
+
 template <int D> MSC_HD inline void add_case(const Ctx &c, uint32_t t, const Verts &cell)
 {
     const Tab<D> &T = rt_tab<D>();
@@ -432,6 +438,7 @@ template <int D> MSC_HD inline void add_case(const Ctx &c, uint32_t t, const Ver
     } else if (!test_and_set(c.Tbits, t)) {
         c.Tlist[list_slot(&c.cnt->nT)] = t;
         count_add(&c.cnt->sumT, (unsigned long long)t);
+        if (c.fuse_g) fuse_target(c, t);
     }
     if (live || !c.exact_fallback) return;
     for (int i = 0; i < cell.n; i++) {
@@ -642,6 +649,42 @@ MSC_HD inline bool order_changed(const Ctx &c, uint32_t v, int part, int nparts,
 // Eq. 2 applied to a changing item: one step of xi / 2^q_max while q < q_max (q < qcap in
 // floating-edit mode) and the value stays >= f - xi, otherwise the floor f - xi; a restore
 // sets g = f exactly
+// Eq. 2's step of target v from state st: the new value, and the new state in nst
+MSC_HD inline float edit_value(const Ctx &c, uint32_t v, uint8_t st, uint8_t &nst)
+{
+    const float fv = ld(c.f + v);
+    const float lb = sub_ru(fv, c.xi);
+    if (st < c.qcap) {
+        const float fc = clamp_base(fv, ld(c.fhat + v), c.xi);
+        const float cand = sub_rn(fc, mul_rn((float)(st + 1), c.step));
+        if (cand >= lb) { nst = (uint8_t)(st + 1); return cand; }
+    }
+    nst = ST_FLOOR;
+    return lb;
+}
+
+// the edit of a new target by the C-pass thread that listed it (fuse_g set): the new value
+// into fuse_g and the vertex onto the list of changed vertices; its state is left for the
+// mark phase (state_after), so that every case of the round reads the pre-round state.  A
+// target that a restore of the round also owns is restored after the C-pass, which wins.
+MSC_HD inline void fuse_target(const Ctx &c, uint32_t t)
+{
+    const uint8_t st = c.state[t];
+    if (st > c.qcap) return;            // at the floor or restored: nothing to change
+    uint8_t nst;
+    c.fuse_g[t] = edit_value(c, t, st, nst);
+    c.Elist[list_slot(&c.cnt->nE)] = t;
+}
+
+// the state of a target that fuse_target edited in this round (not one a restore owns)
+MSC_HD inline void state_after(const Ctx &c, uint32_t v)
+{
+    if ((c.Xbits[v >> 5] >> (v & 31)) & 1u) return;
+    uint8_t nst;
+    edit_value(c, v, c.state[v], nst);
+    c.state[v] = nst;
+}
+
 MSC_HD inline void edit_apply(const Ctx &c, uint32_t i, uint32_t nX, uint32_t v)
 {
     if (i < nX) {
@@ -649,16 +692,9 @@ MSC_HD inline void edit_apply(const Ctx &c, uint32_t i, uint32_t nX, uint32_t v)
         c.state[v] = ST_EXACT;
         return;
     }
-    const uint8_t st = c.state[v];
-    const float fv = ld(c.f + v);
-    const float lb = sub_ru(fv, c.xi);
-    if (st < c.qcap) {
-        const float fc = clamp_base(fv, ld(c.fhat + v), c.xi);
-        const float cand = sub_rn(fc, mul_rn((float)(st + 1), c.step));
-        if (cand >= lb) { c.g[v] = cand; c.state[v] = (uint8_t)(st + 1); return; }
-    }
-    c.g[v] = lb;
-    c.state[v] = ST_FLOOR;
+    uint8_t nst;
+    c.g[v] = edit_value(c, v, c.state[v], nst);
+    c.state[v] = nst;
 }
 
 // one bit per cell the anchor owns: set if the cell is critical (tier 1: extrema only)

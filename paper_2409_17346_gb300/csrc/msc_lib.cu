@@ -1207,7 +1207,6 @@ __global__ void __launch_bounds__(TPB, 2) k_rounds(Ctx c, GridBarrier *gb, Count
         Stage<ROUND_STAGE> sd;           // P3: dirty anchors
     } u;
     __shared__ uint16_t cq[TPB / 32][32 * CASES_PER_ANCHOR];   // P1: compacted false cases
-    __shared__ Stage<TPB> se;            // P2: changed vertices; P4: separatrix dirty anchors
     __shared__ BlockTally tally;
     const unsigned lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     __shared__ LaneGeom lgs[32];         // the same for every warp: kept in shared memory, where
@@ -1236,36 +1235,40 @@ __global__ void __launch_bounds__(TPB, 2) k_rounds(Ctx c, GridBarrier *gb, Count
         if (gtid == 0) memset(cnt2 + nxt, 0, sizeof(Counters));
         tally_begin(tally, cc);
         {
+            // The C-pass reads the pre-round values (gprev equals g between rounds) and edits
+            // each target it lists at once into g (fuse_target), unless this round would be
+            // past max_iters.  No separate edit phase: a round that stops edits nothing (no
+            // case, or every target stuck at the floor or restored), and the rare restores of
+            // the exact fallback are applied after the barrier, overriding a target's step.
+            Ctx cp = cc;
+            cp.g = c.gprev;
+            cp.fuse_g = iters < ls->max_iters ? c.g : nullptr;
             uint32_t *nl = lists[nxt];
             unsigned long long *nn = &ls->nbl[nxt];
-            cpass_listed<D, false>(cc, u.q, cq, lists[cur], ls->nbl[cur], &ls->cpass_items,
-                            [&](uint32_t b) { nl[atomicAdd(nn, 1ull)] = b; });
+            cpass_listed<D, false>(cp, u.q, cq, lists[cur], ls->nbl[cur], &ls->cpass_items,
+                                   [&](uint32_t b) { nl[atomicAdd(nn, 1ull)] = b; });
         }
         tally_end(tally, cc);
         if (!round_sync<CL>(gb, ls)) return;
         phase_end(0);
         // P2: the decision, taken alike by every thread from the finished counters (block 0
-        // records it), then the edits
+        // records it); then the restores, if any (dealt round-robin over the blocks)
         int status;
         const bool stop = round_stop(ls, K, iters, status);
         const unsigned long long nX = K->nX, items = nX + K->nT;
         if (gtid == 0) round_record(cc, K, 0, stop, status);
         if (stop) return;
-        // items are dealt round-robin over the blocks (i = k0 + thread * blocks + block), so that
-        // a round with fewer items than a block has threads still spreads them over every SM
-        st_init(se);
-        for (unsigned long long k0 = 0; k0 < items; k0 += nthreads) {
-            const unsigned long long i = k0 + sgtid;
-            if (i < items) {
-                uint32_t v;
-                if (edit_prepare(cc, (uint32_t)i, (uint32_t)nX, v)) {
-                    edit_apply(cc, (uint32_t)i, (uint32_t)nX, v);
-                    st_push(se, v, c.Elist, &K->nE);
+        if (nX) {
+            for (unsigned long long i = sgtid; i < nX; i += nthreads) {
+                const uint32_t v = c.Xlist[i];
+                if (c.state[v] != ST_EXACT) {
+                    c.g[v] = ld(c.f + v);
+                    c.state[v] = ST_EXACT;
+                    c.Elist[list_slot(&K->nE)] = v;
                 }
             }
-            st_flush(se, c.Elist, &K->nE);
+            if (!round_sync<CL>(gb, ls)) return;
         }
-        if (!round_sync<CL>(gb, ls)) return;
         phase_end(1);
         // P3: edited vertices whose order changed mark their windows dirty
         st_init(u.sd);
@@ -1274,6 +1277,7 @@ __global__ void __launch_bounds__(TPB, 2) k_rounds(Ctx c, GridBarrier *gb, Count
             const unsigned long long i = k0 + (unsigned long long)wib * gridDim.x + blockIdx.x;
             if (i < nE) {
                 const uint32_t v = c.Elist[i];
+                if (lane == 0) state_after(cc, v);   // the state of a target edited in P1
                 int x, y, z;
                 coords(c.G, v, x, y, z);
                 const bool flip = ring_changed<D>(cc, v, x, y, z, lg);
