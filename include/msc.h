@@ -309,7 +309,8 @@ msc_status msc_critical_cells(const float *field, int nx, int ny, int nz,
  *    with MSC_ERR_INVALID_ARG.  No device memory is allocated or freed by this call.
  *  - Every call looks up the device address of that array (cudaGetSymbolAddress) on the
  *    current device, queues its kernels on stream, then waits for that stream before it
- *    returns, on success and on every error path alike.
+ *    returns, on success and on every error path alike (so no call can be captured into a
+ *    CUDA graph).
  *  - All calls share the one array (its counters are cleared at the start of each call):
  *    calls whose device work overlaps (other threads or streams) race and give wrong
  *    results.  stream: a cudaStream_t (NULL = the legacy default stream).
