@@ -591,7 +591,9 @@ def main():
         ach = per_launch / (avg_ms / 1e3) / 1e9
         roof.update(achieved=ach, frac=ach / peak, algorithmic_bytes_per_launch=per_launch,
                     avg_launch_ms=avg_ms, launches_per_step=tot["launches"] / args.steps)
-        if dom in TRAFFIC_PER_ITEM:
+        # the per-item figures were captured on the 3D kolmogorov workload: other workloads
+        # (2D, a different field) report no traffic
+        if dom in TRAFFIC_PER_ITEM and cfg["name"] == WORKLOAD:
             roof["traffic"] = TRAFFIC_PER_ITEM[dom] * tot["items"] / tot["launches"]
             roof["traffic_source"] = "ncu dram bytes per item (node step or round) at 256^3, scaled by the launch's items"
     # the whole loop against the same peak: every class's algorithmic bytes in the breakdown
