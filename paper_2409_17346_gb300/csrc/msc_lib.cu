@@ -873,77 +873,71 @@ template <int D> __global__ void k_edit(Ctx c)
     ws_flush(se[wib], c.Elist, &c.cnt->nE);
 }
 
-// The window of an anchor by rows: for each (y, z) offset of the window, the run of x offsets
-// [lo, hi] it holds (the window is [-1,1]^D u [0,2]^D, so every row is one run).  The anchors
-// whose window holds a vertex v are v - o: per row, a run of at most four consecutive anchors,
-// marked in their bitset with one or two word atomics instead of one atomic per anchor.
-template <int D> struct WinRows {
-    int n;
-    int oy[16], oz[16], lo[16], hi[16];
+// For a ring offset r (a vertex u = v + r whose order against the edited vertex v may flip):
+// bit i set iff the anchor p = v - win[i] (whose window holds v) also holds u in its window.
+// An anchor's code compares only vertices of its window, so a flip of (v, u) can change only
+// those anchors, and the anchors to refresh are the union over the flipped pairs.
+template <int D> struct RingWin {
+    uint64_t m[64];
 };
-template <int D> constexpr WinRows<D> make_win_rows()
+template <int D> constexpr RingWin<D> make_ring_win()
 {
     constexpr Tab<D> T = make_tab<D>();
-    WinRows<D> r{};
-    for (int j = 0; j < T.nwin; j++) {
-        const int ox = T.win[j][0], oy = T.win[j][1], oz = T.win[j][2];
-        int k = 0;
-        while (k < r.n && !(r.oy[k] == oy && r.oz[k] == oz)) k++;
-        if (k == r.n) { r.oy[k] = oy; r.oz[k] = oz; r.lo[k] = ox; r.hi[k] = ox; r.n++; }
-        else { r.lo[k] = ox < r.lo[k] ? ox : r.lo[k]; r.hi[k] = ox > r.hi[k] ? ox : r.hi[k]; }
-    }
-    return r;
+    RingWin<D> rw{};
+    for (int j = 0; j < T.nring; j++)
+        for (int i = 0; i < T.nwin; i++) {
+            const int o[3] = {T.win[i][0] + T.ring[j][0], T.win[i][1] + T.ring[j][1], T.win[i][2] + T.ring[j][2]};
+            bool in = false;
+            for (int k = 0; k < T.nwin; k++)
+                if (T.win[k][0] == o[0] && T.win[k][1] == o[1] && T.win[k][2] == o[2]) in = true;
+            if (in) rw.m[j] |= 1ull << i;
+        }
+    return rw;
 }
-template <int D> constexpr bool win_rows_are_runs()
-{
-    constexpr Tab<D> T = make_tab<D>();
-    constexpr WinRows<D> r = make_win_rows<D>();
-    int cells = 0;
-    for (int k = 0; k < r.n; k++) cells += r.hi[k] - r.lo[k] + 1;
-    return cells == T.nwin && r.n <= 16;
-}
-static_assert(win_rows_are_runs<2>() && win_rows_are_runs<3>(), "window rows must be runs of x offsets");
-static __device__ const WinRows<2> kWinRows2 = make_win_rows<2>();
-static __device__ const WinRows<3> kWinRows3 = make_win_rows<3>();
-template <int D> __device__ __forceinline__ const WinRows<D> &win_rows();
-template <> __device__ __forceinline__ const WinRows<2> &win_rows<2>() { return kWinRows2; }
-template <> __device__ __forceinline__ const WinRows<3> &win_rows<3>() { return kWinRows3; }
+static_assert(Tab<3>::WS <= 64 && make_tab<3>().nwin <= 64 && make_tab<3>().nring <= 64, "masks hold 64 positions");
+static __device__ const RingWin<2> kRingWin2 = make_ring_win<2>();
+static __device__ const RingWin<3> kRingWin3 = make_ring_win<3>();
+template <int D> __device__ __forceinline__ const RingWin<D> &ring_win();
+template <> __device__ __forceinline__ const RingWin<2> &ring_win<2>() { return kRingWin2; }
+template <> __device__ __forceinline__ const RingWin<3> &ring_win<3>() { return kRingWin3; }
 
 // what one lane of a warp handles of a changed vertex, held in registers for a whole kernel:
 // ring offsets lane and lane + 32 (the vertices whose order against it a rule compares) and
 // window row `lane`
 struct LaneGeom {
-    int rg[2][3];
+    int rg[2][3];        // ring offsets lane and lane + 32
     bool ron[2];
-    int oy, oz, lo, hi;
-    bool row;
+    uint64_t rwin[2];    // their window masks (RingWin)
+    int wg[2][3];        // window offsets lane and lane + 32
+    bool won[2];
 };
 template <int D> __device__ __forceinline__ LaneGeom lane_geom(unsigned lane)
 {
     const Tab<D> &T = rt_tab<D>();
-    const WinRows<D> &R = win_rows<D>();
+    const RingWin<D> &RW = ring_win<D>();
     LaneGeom g;
 #pragma unroll
     for (int r = 0; r < 2; r++) {
         const int j = (int)lane + 32 * r;
         g.ron[r] = j < T.nring;
         for (int k = 0; k < 3; k++) g.rg[r][k] = g.ron[r] ? T.ring[j][k] : 0;
+        g.rwin[r] = g.ron[r] ? RW.m[j] : 0ull;
+        g.won[r] = j < T.nwin;
+        for (int k = 0; k < 3; k++) g.wg[r][k] = g.won[r] ? T.win[j][k] : 0;
     }
-    g.row = (int)lane < R.n;
-    g.oy = g.row ? R.oy[lane] : 0;
-    g.oz = g.row ? R.oz[lane] : 0;
-    g.lo = g.row ? R.lo[lane] : 0;
-    g.hi = g.row ? R.hi[lane] : 0;
     return g;
 }
 
-// order_changed (lanes as parts) with the ring offsets in registers.  A neighbour's value
-// before the round is gprev's: between rounds gprev equals g everywhere, and a round saves
-// the pre-round value of each vertex it edits there.
-template <int D> __device__ __forceinline__ bool ring_changed(const Ctx &c, uint32_t v, int x, int y, int z, const LaneGeom &g)
+// The order-change test of an edited vertex v (lanes as parts, ring offsets from LaneGeom):
+// the window positions of v whose anchors a flipped pair (v, u) can change, OR-ed over the
+// warp (every lane gets the same mask).  A neighbour's value before the round is gprev's:
+// between rounds gprev equals g everywhere, and a round saves the pre-round value of each
+// vertex it edits there.
+template <int D>
+__device__ __forceinline__ uint64_t ring_window_mask(const Ctx &c, uint32_t v, int x, int y, int z, const LaneGeom &g)
 {
     const float ov = c.gprev[v], nv = c.g[v];
-    bool flip = false;
+    uint64_t m = 0;
 #pragma unroll
     for (int r = 0; r < 2; r++) {
         if (!g.ron[r]) continue;
@@ -951,42 +945,28 @@ template <int D> __device__ __forceinline__ bool ring_changed(const Ctx &c, uint
         if (!inside(c.G, ux, uy, uz)) continue;
         const uint32_t u = vid(c.G, ux, uy, uz);
         const float nu = c.g[u], ou = c.gprev[u];
-        flip |= sos_lt(ov, v, ou, u) != sos_lt(nv, v, nu, u);
+        if (sos_lt(ov, v, ou, u) != sos_lt(nv, v, nu, u)) m |= g.rwin[r];
     }
-    return flip;
+    const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)m), hi = __reduce_or_sync(0xffffffffu, (unsigned)(m >> 32));
+    return ((uint64_t)hi << 32) | lo;
 }
 
-// marks the window row (oy, oz, x offsets lo..hi) of the changed vertex (x, y, z) dirty;
-// returns the first anchor of the row in p0 and bit i set when anchor p0 + i became dirty
-__device__ __forceinline__ unsigned mark_run(const Ctx &c, int oy, int oz, int lo, int hi, int x, int y, int z, uint32_t &p0)
+// the anchor at window position lane + 32 r of v, if the mask holds it and it is inside the
+// domain; false otherwise
+__device__ __forceinline__ bool window_anchor(const Ctx &c, const LaneGeom &g, uint64_t mask, int r, int x, int y, int z,
+                                              uint32_t &p)
 {
-    p0 = 0;
-    const int py = y - oy, pz = z - oz;
-    if (py < 0 || pz < 0 || py >= c.G.ny || pz >= c.G.nz) return 0;
-    const int a = max(x - hi, 0), b = min(x - lo, c.G.nx - 1);
-    if (a > b) return 0;
-    p0 = vid(c.G, a, py, pz);
-    const unsigned k = (unsigned)(b - a + 1), s = p0 & 31u;
-    const unsigned long long want = ((1ull << k) - 1ull) << s;
-    uint32_t *w = c.Dbits + (p0 >> 5);
-    unsigned long long got = 0;
-    const uint32_t m0 = (uint32_t)want, m1 = (uint32_t)(want >> 32);
-    if (m0) got |= (unsigned long long)(m0 & ~atomicOr(w, m0));
-    if (m1) got |= (unsigned long long)(m1 & ~atomicOr(w + 1, m1)) << 32;
-    return (unsigned)(got >> s);
+    const int j = (int)(threadIdx.x & 31) + 32 * r;
+    if (!g.won[r] || !((mask >> j) & 1ull)) return false;
+    const int px = x - g.wg[r][0], py = y - g.wg[r][1], pz = z - g.wg[r][2];
+    if (!inside(c.G, px, py, pz)) return false;
+    p = vid(c.G, px, py, pz);
+    return true;
 }
 
-// this lane's window row (LaneGeom)
-__device__ __forceinline__ unsigned mark_row(const Ctx &c, const LaneGeom &g, int x, int y, int z, uint32_t &p0)
-{
-    p0 = 0;
-    return g.row ? mark_run(c, g.oy, g.oz, g.lo, g.hi, x, y, z, p0) : 0u;
-}
-
-
-// one warp per changed vertex: when its order against some vertex within two edges
-// changed, the lanes share the dirty-anchor marks of its window; otherwise no code can
-// change and nothing is marked.  (One thread per vertex loads less in the largest rounds,
+// one warp per changed vertex: the lanes test its order against the vertices within two
+// edges and mark dirty the anchors of its window that hold both ends of a flipped pair;
+// without a flip no code can change and nothing is marked.  (One thread per vertex loads less in the largest rounds,
 // but runs the ~60 ring checks of a vertex one after another in the middle-sized ones, and
 // lists the dirty anchors in an order that costs the refresh more than it saves.)
 template <int D> __global__ void k_mark(Ctx c)
@@ -994,14 +974,10 @@ template <int D> __global__ void k_mark(Ctx c)
     if (round_off(c.ls)) return;
     __shared__ WarpStage<512> sd[TPB / 32];
     __shared__ LaneGeom lgs[32];
-    __shared__ int win[64][3];
-    const Tab<D> &T = rt_tab<D>();
     const unsigned lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     if (threadIdx.x < 32) lgs[lane] = lane_geom<D>(lane);
-    for (int j = threadIdx.x; j < 64 * 3; j += blockDim.x) win[j / 3][j % 3] = j / 3 < T.nwin ? T.win[j / 3][j % 3] : 0;
     if (lane == 0) sd[wib].n = 0;
     __syncthreads();
-    const int nwin = T.nwin;
     const unsigned long long items = c.cnt->nE;
     const unsigned long long warp = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
     const unsigned long long nwarps = (gridDim.x * (unsigned long long)blockDim.x) >> 5;
@@ -1009,20 +985,12 @@ template <int D> __global__ void k_mark(Ctx c)
         const uint32_t v = c.Elist[i];
         int x, y, z;
         coords(c.G, v, x, y, z);
-        const bool flip = ring_changed<D>(c, v, x, y, z, lgs[lane]);
-        if (!__any_sync(0xffffffffu, flip)) continue;
+        const uint64_t mask = ring_window_mask<D>(c, v, x, y, z, lgs[lane]);
+        if (!mask) continue;                     // the same in every lane
 #pragma unroll
         for (int r = 0; r < 2; r++) {            // the window has at most 64 anchors
-            const int j = (int)lane + 32 * r;
-            bool has = false;
             uint32_t p = 0;
-            if (j < nwin) {
-                const int px = x - win[j][0], py = y - win[j][1], pz = z - win[j][2];
-                if (inside(c.G, px, py, pz)) {
-                    p = vid(c.G, px, py, pz);
-                    has = !test_and_set(c.Dbits, p);
-                }
-            }
+            const bool has = window_anchor(c, lgs[lane], mask, r, x, y, z, p) && !test_and_set(c.Dbits, p);
             ws_push(sd[wib], has, p, c.Dlist, &c.cnt->nD);
         }
     }
@@ -1280,13 +1248,14 @@ __global__ void __launch_bounds__(TPB, 2) k_rounds(Ctx c, GridBarrier *gb, Count
                 if (lane == 0) state_after(cc, v);   // the state of a target edited in P1
                 int x, y, z;
                 coords(c.G, v, x, y, z);
-                const bool flip = ring_changed<D>(cc, v, x, y, z, lg);
-                if (__any_sync(0xffffffffu, flip)) {
-                    uint32_t p0;
-                    const unsigned nm = mark_row(cc, lg, x, y, z, p0);
-                    for (int r = 0; r < 4; r++)
-                        if ((nm >> r) & 1u) st_push(u.sd, p0 + (uint32_t)r, c.Dlist, &K->nD);
-                }
+                const uint64_t mask = ring_window_mask<D>(cc, v, x, y, z, lg);
+                if (mask)
+#pragma unroll
+                    for (int r = 0; r < 2; r++) {
+                        uint32_t p;
+                        if (window_anchor(cc, lg, mask, r, x, y, z, p) && !test_and_set(c.Dbits, p))
+                            st_push(u.sd, p, c.Dlist, &K->nD);
+                    }
             }
             st_flush(u.sd, c.Dlist, &K->nD);
         }
