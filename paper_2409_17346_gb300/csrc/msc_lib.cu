@@ -3305,7 +3305,7 @@ template <int D>
 msc_status critical_static(const float *field, Grid G, int64_t *rows, int32_t *dims, uint64_t cap, uint64_t *n_out,
                            cudaStream_t s)
 {
-    unsigned long long *scr;
+    unsigned long long *scr = nullptr;
     CKS(static_scratch(&scr));
     // waits for the stream on every return path, so that no kernel of this call is still
     // writing the scratch or the caller's rows when it returns
