@@ -94,6 +94,54 @@ MSC_HD inline const TriPack &rt_tri_pack()
 #endif
 }
 
+// For a ring offset r (a vertex u = v + r whose order against an edited vertex v may flip):
+// bit i set iff the anchor p = v - win[i] (whose window holds v) also holds u in its window.
+// An anchor's code compares only vertices of its window, so a flip of (v, u) can change only
+// those anchors, and the anchors to refresh are the union over the flipped pairs.
+template <int D> struct RingWin {
+    uint64_t m[64];
+};
+template <int D> constexpr RingWin<D> make_ring_win()
+{
+    constexpr Tab<D> T = make_tab<D>();
+    RingWin<D> rw{};
+    for (int j = 0; j < T.nring; j++)
+        for (int i = 0; i < T.nwin; i++) {
+            const int o[3] = {T.win[i][0] + T.ring[j][0], T.win[i][1] + T.ring[j][1], T.win[i][2] + T.ring[j][2]};
+            bool in = false;
+            for (int k = 0; k < T.nwin; k++)
+                if (T.win[k][0] == o[0] && T.win[k][1] == o[1] && T.win[k][2] == o[2]) in = true;
+            if (in) rw.m[j] |= 1ull << i;
+        }
+    return rw;
+}
+static_assert(make_tab<3>().nwin <= 64 && make_tab<3>().nring <= 64, "masks hold 64 positions");
+#ifdef __CUDACC__
+static __device__ const RingWin<2> kRingWin2 = make_ring_win<2>();
+static __device__ const RingWin<3> kRingWin3 = make_ring_win<3>();
+#endif
+#ifdef MSC_HOST_EMULATION
+static const RingWin<2> hRingWin2 = make_ring_win<2>();
+static const RingWin<3> hRingWin3 = make_ring_win<3>();
+#endif
+template <int D> MSC_HD inline const RingWin<D> &rt_ring_win();
+template <> MSC_HD inline const RingWin<2> &rt_ring_win<2>()
+{
+#if defined(__CUDA_ARCH__) || !defined(MSC_HOST_EMULATION)
+    return kRingWin2;
+#else
+    return hRingWin2;
+#endif
+}
+template <> MSC_HD inline const RingWin<3> &rt_ring_win<3>()
+{
+#if defined(__CUDA_ARCH__) || !defined(MSC_HOST_EMULATION)
+    return kRingWin3;
+#else
+    return hRingWin3;
+#endif
+}
+
 constexpr uint8_t ST_FLOOR = 0xF0;   // g == lb, stored losslessly (Eq. 2 "otherwise")
 constexpr uint8_t ST_EXACT = 0xF1;   // g == f, stored losslessly (stuck-case restore)
 

@@ -873,34 +873,6 @@ template <int D> __global__ void k_edit(Ctx c)
     ws_flush(se[wib], c.Elist, &c.cnt->nE);
 }
 
-// For a ring offset r (a vertex u = v + r whose order against the edited vertex v may flip):
-// bit i set iff the anchor p = v - win[i] (whose window holds v) also holds u in its window.
-// An anchor's code compares only vertices of its window, so a flip of (v, u) can change only
-// those anchors, and the anchors to refresh are the union over the flipped pairs.
-template <int D> struct RingWin {
-    uint64_t m[64];
-};
-template <int D> constexpr RingWin<D> make_ring_win()
-{
-    constexpr Tab<D> T = make_tab<D>();
-    RingWin<D> rw{};
-    for (int j = 0; j < T.nring; j++)
-        for (int i = 0; i < T.nwin; i++) {
-            const int o[3] = {T.win[i][0] + T.ring[j][0], T.win[i][1] + T.ring[j][1], T.win[i][2] + T.ring[j][2]};
-            bool in = false;
-            for (int k = 0; k < T.nwin; k++)
-                if (T.win[k][0] == o[0] && T.win[k][1] == o[1] && T.win[k][2] == o[2]) in = true;
-            if (in) rw.m[j] |= 1ull << i;
-        }
-    return rw;
-}
-static_assert(Tab<3>::WS <= 64 && make_tab<3>().nwin <= 64 && make_tab<3>().nring <= 64, "masks hold 64 positions");
-static __device__ const RingWin<2> kRingWin2 = make_ring_win<2>();
-static __device__ const RingWin<3> kRingWin3 = make_ring_win<3>();
-template <int D> __device__ __forceinline__ const RingWin<D> &ring_win();
-template <> __device__ __forceinline__ const RingWin<2> &ring_win<2>() { return kRingWin2; }
-template <> __device__ __forceinline__ const RingWin<3> &ring_win<3>() { return kRingWin3; }
-
 // what one lane of a warp handles of a changed vertex, held in registers for a whole kernel:
 // ring offsets lane and lane + 32 (the vertices whose order against it a rule compares) and
 // window row `lane`
@@ -914,7 +886,7 @@ struct LaneGeom {
 template <int D> __device__ __forceinline__ LaneGeom lane_geom(unsigned lane)
 {
     const Tab<D> &T = rt_tab<D>();
-    const RingWin<D> &RW = ring_win<D>();
+    const RingWin<D> &RW = rt_ring_win<D>();
     LaneGeom g;
 #pragma unroll
     for (int r = 0; r < 2; r++) {

@@ -121,8 +121,11 @@ extern "C" int host_codes(const float *field, int nx, int ny, int nz, uint64_t *
 // moved[v] != 0 went from g_old[v] to g_new[v] in the round (gprev = g_old there); the
 // anchors in the window of each moved vertex whose order against a vertex within two
 // edges changed (order_changed) are flagged in dirty_out
+// pairwise = 1: as the CUDA path marks them, only the anchors whose windows hold both ends of
+// a pair whose order flipped (the window masks of msc::rt_ring_win, OR-ed over the flipped pairs)
 template <int D>
-static void dirty_of(const float *g_old, const float *g_new, const uint8_t *moved, const msc::Grid &G, uint8_t *dirty_out)
+static void dirty_of(const float *g_old, const float *g_new, const uint8_t *moved, const msc::Grid &G, int pairwise,
+                     uint8_t *dirty_out)
 {
     using namespace msc;
     const Tab<D> &T = rt_tab<D>();
@@ -137,11 +140,27 @@ static void dirty_of(const float *g_old, const float *g_new, const uint8_t *move
     c.gprev = gprev.data();
     c.Tbits = Tbits.data();
     c.Xbits = Xbits.data();
+    const RingWin<D> &RW = rt_ring_win<D>();
     for (uint32_t v = 0; v < n; v++) {
         if (!moved[v] || !order_changed<D>(c, v, 0, 1, T.ring)) continue;
         int x, y, z;
         coords(G, v, x, y, z);
+        uint64_t mask = ~0ull;
+        if (pairwise) {
+            // each ring vertex u on its own: a flip of (v, u) adds the anchors that hold both
+            mask = 0;
+            const float ov = gprev[v], nv = g[v];
+            for (int j = 0; j < T.nring; j++) {
+                const int ux = x + T.ring[j][0], uy = y + T.ring[j][1], uz = z + T.ring[j][2];
+                if (!inside(G, ux, uy, uz)) continue;
+                const uint32_t u = vid(G, ux, uy, uz);
+                const bool mu = (Tbits[u >> 5] >> (u & 31)) & 1u;
+                const float nu = g[u], ou = mu ? gprev[u] : nu;
+                if (sos_lt(ov, v, ou, u) != sos_lt(nv, v, nu, u)) mask |= RW.m[j];
+            }
+        }
         for (int j = 0; j < T.nwin; j++) {
+            if (!((mask >> j) & 1ull)) continue;
             const int px = x - T.win[j][0], py = y - T.win[j][1], pz = z - T.win[j][2];
             if (inside(G, px, py, pz)) dirty_out[vid(G, px, py, pz)] = 1;
         }
@@ -149,11 +168,11 @@ static void dirty_of(const float *g_old, const float *g_new, const uint8_t *move
 }
 
 extern "C" int host_dirty(const float *g_old, const float *g_new, const uint8_t *moved, int nx, int ny, int nz,
-                          uint8_t *dirty_out)
+                          int pairwise, uint8_t *dirty_out)
 {
     const msc::Grid G = msc::make_grid(nx, ny, nz);
-    if (nz > 1) dirty_of<3>(g_old, g_new, moved, G, dirty_out);
-    else dirty_of<2>(g_old, g_new, moved, G, dirty_out);
+    if (nz > 1) dirty_of<3>(g_old, g_new, moved, G, pairwise, dirty_out);
+    else dirty_of<2>(g_old, g_new, moved, G, pairwise, dirty_out);
     return 0;
 }
 

@@ -48,7 +48,7 @@ def lib():
     h.host_cpass.argtypes = [vp, vp, vp, i, i, i, i, i, vp, vp, ctypes.POINTER(ctypes.c_uint64),
                              ctypes.POINTER(ctypes.c_uint64)]
     h.host_codes.argtypes = [vp, i, i, i, vp]
-    h.host_dirty.argtypes = [vp, vp, vp, i, i, i, vp]
+    h.host_dirty.argtypes = [vp, vp, vp, i, i, i, i, vp]
     h.host_spass.argtypes = [vp, vp, vp, vp, i, i, i, i, vp, vp, ctypes.POINTER(ctypes.c_uint64)]
     h.host_edit_sequence.argtypes = [vp, vp, ctypes.c_uint32, ctypes.c_float, i, i, vp, vp]
     h.host_spass_t3.argtypes = [vp, vp, vp, i, i, i, i, vp, vp]
@@ -122,10 +122,13 @@ def test_device_cpass_matches_oracle_targets(lib, shape, tier, fallback):
 def test_order_change_filter_never_misses_a_changed_code(lib):
     """Random rounds: a fifth of the vertices lowered, by small or large amounts, so that
     moved vertices are often compared with other moved ones (each at its pre-round value).
-    Every anchor whose code changed must be in the refresh set; the set must also leave many
-    anchors out, or the filter would be doing nothing."""
+    Every anchor whose code changed must be in the refresh set, both for the whole window of a
+    vertex with any flipped pair and for the CUDA path's finer set (only the anchors whose
+    windows hold both ends of a flipped pair); the sets must also leave many anchors out, the
+    finer one more, or the filters would be doing nothing."""
     rng = np.random.default_rng(3)
     skipped = []
+    skipped_pairwise = []
     for trial in range(200):
         shape = (tuple(int(s) for s in rng.integers(4, 9, 2)) if trial % 2 else tuple(int(s) for s in rng.integers(3, 7, 3)))
         a = rng.standard_normal(shape).astype(np.float32)
@@ -137,10 +140,16 @@ def test_order_change_filter_never_misses_a_changed_code(lib):
         lib.host_codes(a.ctypes.data, *_dims(shape), c0.ctypes.data)
         lib.host_codes(b.ctypes.data, *_dims(shape), c1.ctypes.data)
         dirty = np.zeros(a.size, np.uint8)
-        lib.host_dirty(a.ctypes.data, b.ctypes.data, moved.ctypes.data, *_dims(shape), dirty.ctypes.data)
+        lib.host_dirty(a.ctypes.data, b.ctypes.data, moved.ctypes.data, *_dims(shape), 0, dirty.ctypes.data)
         assert not np.any((c0 != c1) & (dirty == 0)), trial
         skipped.append(1.0 - dirty.mean())
+        pdirty = np.zeros(a.size, np.uint8)
+        lib.host_dirty(a.ctypes.data, b.ctypes.data, moved.ctypes.data, *_dims(shape), 1, pdirty.ctypes.data)
+        assert not np.any((c0 != c1) & (pdirty == 0)), trial
+        assert not np.any((pdirty == 1) & (dirty == 0)), trial      # a subset of the whole windows
+        skipped_pairwise.append(1.0 - pdirty.mean())
     assert np.mean(skipped) > 0.1
+    assert np.mean(skipped_pairwise) > np.mean(skipped)
 
 
 SPASS_CASES = [("gauss2d", dict(seed=9, size=(23, 41), rel=1e-2)), ("multiscale2d", dict(size=(40, 56), rel=1e-2)),
