@@ -121,8 +121,9 @@ typedef struct {
                                     refreshed (and rebuilt) anchors, anchors with differing
                                     critical cells visited by the C-pass */
     double round_phase_ms[4];    /* persistent round kernel, device clock of its first block:
-                                    C-pass, decision and edits, order changes, refresh and
-                                    rebuild (each up to the end of its grid barrier) */
+                                    C-pass with the targets' edits, decision and restores, order
+                                    changes, refresh and rebuild (each up to the end of its
+                                    barrier) */
     uint64_t cluster_launches;   /* launches of the round kernel's cluster form (counted also
                                     in launches[MSC_K_ROUNDS]) and the rounds they ran */
     uint64_t cluster_rounds;
