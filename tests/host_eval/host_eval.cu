@@ -109,6 +109,91 @@ extern "C" int host_cpass(const float *f, const float *g, const uint8_t *state, 
     return 0;
 }
 
+// One C-round from (g, state) on the host, in either of the CUDA path's forms; g and state
+// are updated in place, and the numbers of targets and restores are returned.
+//  fused = 0 (round graphs): the C-pass lists the targets and restores, then every item is
+//    edited (edit_prepare / edit_apply);
+//  fused = 1 (persistent round kernel): the C-pass reads the pre-round values from gprev and
+//    edits each target when it lists it (fuse_target, value only); then the restores; then
+//    the new state of every edited target (state_after).
+template <int D>
+static void round_of(const float *f, const float *fhat, float *g, uint8_t *state, const msc::Grid &G, int tier,
+                     int exact_fallback, float xi, int q_max, int fused, uint64_t *nT, uint64_t *nX)
+{
+    using namespace msc;
+    const uint32_t n = G.n;
+    std::vector<uint64_t> cf(n), cg(n);
+    for (uint32_t p = 0; p < n; p++) {
+        cf[p] = anchor_code<D>(f, G, p);
+        cg[p] = anchor_code<D>(g, G, p);
+    }
+    std::vector<uint32_t> Tbits((n + 31) / 32), Xbits((n + 31) / 32), Tlist(n), Xlist(n), Elist(2 * (size_t)n);
+    std::vector<float> gprev(g, g + n);
+    Counters cnt{};
+    Ctx c{};
+    c.G = G;
+    c.tier = tier;
+    c.exact_fallback = exact_fallback;
+    c.f = f;
+    c.fhat = fhat;
+    c.g = g;
+    c.gprev = gprev.data();
+    c.state = state;
+    c.xi = xi;
+    c.qmax = q_max;
+    c.qcap = q_max;
+    c.step = xi / (float)(1 << q_max);
+    c.code_f = cf.data();
+    c.code_g = cg.data();
+    c.Tbits = Tbits.data();
+    c.Xbits = Xbits.data();
+    c.Tlist = Tlist.data();
+    c.Xlist = Xlist.data();
+    c.Elist = Elist.data();
+    c.cnt = &cnt;
+    Ctx cp = c;
+    if (fused) {
+        cp.g = gprev.data();        // the cases read the pre-round values
+        cp.fuse_g = g;              // targets are edited into g as they are listed
+    }
+    for (uint32_t p = 0; p < n; p++) {
+        uint32_t m = case_mask<D>(cp, p, cf[p], cg[p]);
+        while (m) {
+            const int i = __builtin_ctz(m);
+            m &= m - 1;
+            case_apply<D>(cp, p, i);
+        }
+    }
+    const uint32_t t = (uint32_t)cnt.nT, x = (uint32_t)cnt.nX;
+    if (!fused) {
+        for (uint32_t i = 0; i < x + t; i++) {
+            uint32_t v;
+            if (edit_prepare(c, i, x, v)) edit_apply(c, i, x, v);
+        }
+    } else {
+        for (uint32_t i = 0; i < x; i++) {
+            const uint32_t v = Xlist[i];
+            if (state[v] != ST_EXACT) {
+                g[v] = f[v];
+                state[v] = ST_EXACT;
+                Elist[cnt.nE++] = v;
+            }
+        }
+        for (uint64_t i = 0; i < cnt.nE; i++) state_after(c, Elist[i]);
+    }
+    *nT = t;
+    *nX = x;
+}
+
+extern "C" int host_round(const float *f, const float *fhat, float *g, uint8_t *state, int nx, int ny, int nz, int tier,
+                          int exact_fallback, float xi, int q_max, int fused, uint64_t *nT, uint64_t *nX)
+{
+    const msc::Grid G = msc::make_grid(nx, ny, nz);
+    if (nz > 1) round_of<3>(f, fhat, g, state, G, tier, exact_fallback, xi, q_max, fused, nT, nX);
+    else round_of<2>(f, fhat, g, state, G, tier, exact_fallback, xi, q_max, fused, nT, nX);
+    return 0;
+}
+
 // every anchor's packed gradient code
 extern "C" int host_codes(const float *field, int nx, int ny, int nz, uint64_t *out)
 {

@@ -52,6 +52,8 @@ def lib():
     h.host_spass.argtypes = [vp, vp, vp, vp, i, i, i, i, vp, vp, ctypes.POINTER(ctypes.c_uint64)]
     h.host_edit_sequence.argtypes = [vp, vp, ctypes.c_uint32, ctypes.c_float, i, i, vp, vp]
     h.host_spass_t3.argtypes = [vp, vp, vp, i, i, i, i, vp, vp]
+    h.host_round.argtypes = [vp, vp, vp, vp, i, i, i, i, i, ctypes.c_float, i, i, ctypes.POINTER(ctypes.c_uint64),
+                             ctypes.POINTER(ctypes.c_uint64)]
     return h
 
 
@@ -241,3 +243,48 @@ def test_device_tier3_walks_match_oracle_spass(lib, idx):
         To[np.unique(cases[:, 0])] = 1
     assert np.array_equal(T, To)
     assert np.array_equal(X, (markX != 0).astype(np.uint8))
+
+
+ROUND_CASES = [("gauss2d", dict(seed=9, size=(23, 41), rel=1e-2)), ("multiscale2d", dict(size=(40, 56), rel=1e-2)),
+               ("grf3d", dict(size=9, rel=1e-2)), ("kolmogorov3d", dict(size=10, rel=3e-3))]
+
+
+@pytest.mark.parametrize("idx", range(len(ROUND_CASES)))
+@pytest.mark.parametrize("fallback", [0, 1])
+def test_fused_round_edits_equal_the_two_phase_round(lib, idx, fallback):
+    """The persistent round kernel edits each target in its C-pass (reading the pre-round
+    values from gprev, leaving the state for later), then applies the restores and the
+    targets' states; the round graphs list all items first and edit them after.  From the
+    same state, rounds of both forms give the same g (bit for bit), states, targets and
+    restores, round after round (q_max 2 reaches the floor and stuck cases early)."""
+    name, kw = ROUND_CASES[idx]
+    f, fh, xi, _ = synth.config_case(name, **kw)
+    f = np.ascontiguousarray(f, np.float32)
+    fh = np.ascontiguousarray(fh, np.float32)
+    q_max = 2
+    n = f.size
+    K = q_max + 2
+    g0 = np.zeros(n * K, np.float32)
+    s0 = np.zeros(n * K, np.uint8)
+    lib.host_edit_sequence(f.ctypes.data, fh.ctypes.data, n, xi, q_max, 0, g0.ctypes.data, s0.ctypes.data)
+    g = g0.reshape(n, K)[:, 0].copy()            # clamp(f_hat, [f - xi, f + xi])
+    st = np.zeros(n, np.uint8)
+    nt, nx = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    rounds = edited = 0
+    for r in range(40):
+        ga, sa = g.copy(), st.copy()
+        gb, sb = g.copy(), st.copy()
+        lib.host_round(f.ctypes.data, fh.ctypes.data, ga.ctypes.data, sa.ctypes.data, *_dims(f.shape), 4, fallback,
+                       xi, q_max, 0, ctypes.byref(nt), ctypes.byref(nx))
+        t0, x0 = nt.value, nx.value
+        lib.host_round(f.ctypes.data, fh.ctypes.data, gb.ctypes.data, sb.ctypes.data, *_dims(f.shape), 4, fallback,
+                       xi, q_max, 1, ctypes.byref(nt), ctypes.byref(nx))
+        assert (nt.value, nx.value) == (t0, x0), r
+        assert np.array_equal(ga.view(np.uint32), gb.view(np.uint32)), r
+        assert np.array_equal(sa, sb), r
+        if t0 + x0 == 0:
+            break
+        edited += int((ga != g).sum())
+        rounds += 1
+        g, st = ga, sa
+    assert rounds >= 3 and edited > 0
