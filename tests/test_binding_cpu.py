@@ -5,6 +5,7 @@ import ctypes
 import gc
 
 import numpy as np
+import pytest
 
 from paper_2409_17346_gb300 import msc
 
@@ -72,7 +73,6 @@ def test_record_views_keep_their_owner_until_the_last_view_goes():
 def test_walk_limits_hook_checks_its_arguments_on_the_host():
     """msc_set_walk_limits validates on the host and touches no device: a per-warp stack
     above its 384 entries is rejected with MSC_ERR_INVALID_ARG; 0 restores the defaults."""
-    from paper_2409_17346_gb300 import msc
     msc.set_walk_limits(8, 4)
     msc.set_walk_limits(0, 0)
     with pytest.raises(msc.MscError) as e:
