@@ -938,9 +938,10 @@ __device__ __forceinline__ bool window_anchor(const Ctx &c, const LaneGeom &g, u
 
 // one warp per changed vertex: the lanes test its order against the vertices within two
 // edges and mark dirty the anchors of its window that hold both ends of a flipped pair;
-// without a flip no code can change and nothing is marked.  (One thread per vertex loads less in the largest rounds,
-// but runs the ~60 ring checks of a vertex one after another in the middle-sized ones, and
-// lists the dirty anchors in an order that costs the refresh more than it saves.)
+// without a flip no code can change and nothing is marked.  (One thread per vertex loads
+// less in the largest rounds, but runs the ~60 ring checks of a vertex one after another in
+// the middle-sized ones, and lists the dirty anchors in an order that costs the refresh more
+// than it saves.)
 template <int D> __global__ void k_mark(Ctx c)
 {
     if (round_off(c.ls)) return;
